@@ -1,0 +1,22 @@
+"""CPU FP64 oracle for the nonnested augmented subspace method (test infrastructure).
+
+This package is TEST INFRASTRUCTURE.  Only the tests, the smoke check and the
+benchmark's CPU-baseline / reference leg may import it.  The GPU library never
+calls it, and it shares no code with the GPU library: every formula here is
+restated from the paper (arXiv 2404.19249, "A Nonnested Augmented Subspace
+Method for Kohn-Sham Equation") in plain NumPy/SciPy, FP64 throughout.
+
+Modules and the passages they follow:
+  quadrature   tetrahedral quadrature (the paper leaves the rule open; Sec. 2)
+  fem          P1/P2 spaces on tetrahedra, assembly of K, M and potential
+               mass matrices (Sec. 2 discretisation; Sec. 3.3 eqs. st3, st4)
+  lda          Slater exchange + Perdew-Zunger correlation (Sec. 3.1, eqs.
+               expot, copot) and the energy formula (Sec. 3.1)
+  hartree      Poisson problem for V_Har with multipole boundary values
+               (Sec. 3.1, eq. bd)
+  transfer     nonnested interpolation I_H^h (Sec. 3.2, Algorithm 1)
+  anderson     Anderson density mixing (Sec. 5, eqs. mix2-mix6)
+  nas          Algorithm 3 (augmented subspace step, eqs. Aux_Linear_Problem,
+               st1-st7) with its inner SCF, plus the direct fine-space SCF used
+               as the plain definition of the discrete ground state.
+"""

@@ -1,0 +1,296 @@
+"""Algorithm 3 (augmented subspace method) and the direct SCF (oracle).
+
+Test infrastructure: plain FP64 NumPy/SciPy, written from the paper's Sec. 3.3.
+
+One augmented-subspace step (Algorithm 3 body):
+  1. N shifted linear boundary value problems (eq. Aux_Linear_Problem)
+       (H~ u^_i, v) = (lambda_i + mu)(psi_i, v),  H~ = -1/2 Lap + V_ext + mu + V_Har + V_xc,
+     i.e. (K/2 + M_Vext + M_(VH+Vxc)(rho) + mu M) u^_i = (lambda_i + mu) M psi_i.
+  2. the small Kohn-Sham problem in S_H + span{u^_i}, solved by SCF; each SCF
+     iteration solves F_A U = lambda F_B U (eq. st1) with the 2x2 block
+     matrices of eq. st2:
+       F_A = [[A_H, b_H], [b_H^T, beta]],   F_B = [[B_H, c_H], [c_H^T, gamma]],
+       A_H = I^T A_h I (st5), b_H = I^T A_h U^ (st6), beta = U^T A_h U^ (st7),
+       c_H = I^T M U^, gamma = U^T M U^, A_h = A^L + A^NL (st3, st4).
+  3. density update rho = sum_i f_i psi_i^2.
+
+Readings (where the paper is silent, ambiguous or garbled):
+  * density: rho = sum_i f_i |psi_i|^2 with occupations f_i (2 per orbital,
+    closed shell); the printed update sum_i psi_i has neither square nor f_i.
+  * F_A is built from H (no mu): the shift only moves the eigenvalues of the
+    small problem by mu, because F_B is the exact Gram matrix of the basis.
+  * B_H = I^T M_h I on the fine mesh (the paper assembles it on T_H), so that
+    F_B is the exact Gram matrix of {I phi_a} U {u^_i} and the small problem is
+    a Rayleigh-Ritz projection within S_h.
+  * inner SCF: iterate to ||rho_out - rho_in||_0 < tol (cap max_inner), with
+    Anderson mixing; the state carried to the next step is (Lambda, Psi) of the
+    last small eigenproblem and the density rho_in that defined its potential.
+    H~ in the next step uses that same rho_in.
+  * outer stop: ||rho^(l) - rho^(l-1)||_0 < tol_scf with rho^(l) = sum f psi^2,
+    or l > max_outer.
+  * energy (Sec. 3.1): E = sum_i f_i lambda_i - int (V_H/2 + V_xc) rho
+    + E_xc + E_nn, all density-dependent terms at the density rho_in of the
+    potential.
+  * initial guess: the self-consistent solution in the coarse space alone
+    (S_H carried to the fine mesh by I), from rho = 0, by the same inner SCF.
+  * mu defaults to the experiments' 8 M sum_k Z_k^2.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from . import fem, lda, hartree, transfer
+from .anderson import Anderson
+from .linalg import solve_spd
+
+POT_COULOMB, POT_SMOOTHED, POT_HARMONIC = 0, 1, 2
+
+
+def external_potential(inst, xq):
+    """V_ext at points xq [..., 3] (Sec. 2: -sum_k Z_k/|x - R_k|)."""
+    V = np.zeros(xq.shape[:-1])
+    if inst.potential == POT_HARMONIC:
+        return 0.5 * inst.omega ** 2 * np.sum(xq ** 2, axis=-1)
+    for Rk, Zk in zip(inst.R, inst.Z):
+        r2 = np.sum((xq - Rk) ** 2, axis=-1)
+        if inst.potential == POT_SMOOTHED:
+            V -= Zk / np.sqrt(r2 + inst.smooth_a ** 2)
+        else:
+            V -= Zk / np.sqrt(r2)
+    return V
+
+
+def nuclear_repulsion(inst):
+    """E_nn = sum_{k<j} Z_j Z_k / |R_j - R_k| (Sec. 3.1)."""
+    E = 0.0
+    for j in range(len(inst.Z)):
+        for k in range(j):
+            E += inst.Z[j] * inst.Z[k] / np.linalg.norm(inst.R[j] - inst.R[k])
+    return E
+
+
+def default_mu(inst):
+    return 8.0 * len(inst.Z) * float(np.sum(np.asarray(inst.Z) ** 2))
+
+
+@dataclass
+class State:
+    lam: np.ndarray            # [N] eigenvalues
+    Psi: np.ndarray            # [n, N] fine interior values of the orbitals
+    rho_in: np.ndarray         # [ne, nq] density defining the potential
+    rho_out: np.ndarray        # [ne, nq] sum f psi^2
+    VH: np.ndarray             # [nnode] Hartree potential of rho_in (nodal)
+    n_inner: int = 0
+    inner_res: float = 0.0
+    inner_converged: bool = True
+    info: dict = field(default_factory=dict)
+
+
+class Problem:
+    """Fine/coarse spaces, fixed matrices and the transfer of one instance."""
+
+    def __init__(self, inst, with_transfer=True):
+        self.inst = inst
+        self.fine = fem.Space(inst.fine_xyz, inst.fine_tet, inst.order)
+        self.coarse = fem.Space(inst.coarse_xyz, inst.coarse_tet, 1)
+        f = self.fine
+        Kf = f.assemble_full("K")
+        Mf = f.assemble_full("M")
+        self.K = f.interior(Kf)
+        self.K_IB = f.interior_boundary(Kf)
+        self.M = f.interior(Mf)
+        self.vext_q = external_potential(inst, f.xq)
+        self.Mvext = f.interior(f.assemble_full("M", coef=self.vext_q))
+        self.AL = (0.5 * self.K + self.Mvext).tocsr()   # eq. st3 without mu
+        self.mu = default_mu(inst) if inst.mu is None else float(inst.mu)
+        self.occ = np.asarray(inst.occ, dtype=np.float64)
+        self.N = len(self.occ)
+        self.Enn = nuclear_repulsion(inst)
+        if with_transfer:
+            self.I, self.I_elem, self.I_W, self.I_C = transfer.build_transfer(f, self.coarse)
+            self.B_H = (self.I.T @ self.M @ self.I).toarray()
+            self.A_HL = (self.I.T @ self.AL @ self.I).toarray()
+
+    # ------------------------------------------------------------ potentials
+    def nonlinear(self, rho_q, VH_guess=None):
+        """(V_H nodal, V_H at quad points, eps_xc, v_xc) for density rho_q."""
+        f = self.fine
+        if self.inst.hartree:
+            x0 = None if VH_guess is None else VH_guess[f.interior_nodes]
+            VH = hartree.hartree(f, self.K, self.K_IB, rho_q, tol=self.inst.tol_poisson * 1e-1,
+                                 x0=x0)
+        else:
+            VH = np.zeros(f.nnode)
+        VHq = f.at_quad(VH)
+        if self.inst.xc:
+            eps, vxc = lda.lda(rho_q)
+        else:
+            eps = np.zeros_like(rho_q)
+            vxc = np.zeros_like(rho_q)
+        return VH, VHq, eps, vxc
+
+    def A_NL(self, VHq, vxc):
+        """Eq. st4: ((V_Har + V_xc) phi_i, phi_j) on the interior."""
+        return self.fine.interior(self.fine.assemble_full("M", coef=VHq + vxc))
+
+    def density(self, Psi):
+        """rho = sum_i f_i psi_i^2 at quadrature points."""
+        Pq = self.fine.at_quad(self.fine.to_nodes(Psi))   # [ne, nq, N]
+        return np.einsum("eqn,n->eq", Pq * Pq, self.occ)
+
+    def norm0(self, f_q):
+        return float(np.sqrt(np.sum(self.fine.Wq * f_q * f_q)))
+
+    # ------------------------------------------------------------ small problem
+    def small_blocks(self, A, Uhat):
+        """F_A of eq. st2 for fine operator A (sparse) and augmentation Uhat [n, k]."""
+        AH = (self.I.T @ A @ self.I).toarray()
+        if Uhat is None or Uhat.shape[1] == 0:
+            return AH
+        AU = A @ Uhat
+        bH = self.I.T @ AU
+        beta = Uhat.T @ AU
+        return np.block([[AH, bH], [bH.T, beta]])
+
+    def mass_blocks(self, Uhat):
+        if Uhat is None or Uhat.shape[1] == 0:
+            return self.B_H.copy()
+        MU = self.M @ Uhat
+        cH = self.I.T @ MU
+        gamma = Uhat.T @ MU
+        return np.block([[self.B_H, cH], [cH.T, gamma]])
+
+    def eig_small(self, FA, FB):
+        lam, U = sla.eigh(FA, FB, subset_by_index=[0, self.N - 1])
+        return lam, U
+
+    def basis_apply(self, Uhat, U):
+        """Psi = I u_H + Uhat alpha for U = (u_H; alpha)."""
+        nH = self.coarse.n
+        Psi = self.I @ U[:nH]
+        if Uhat is not None and Uhat.shape[1] > 0:
+            Psi = Psi + Uhat @ U[nH:]
+        return Psi
+
+    # ------------------------------------------------------------ inner SCF
+    def inner_scf(self, Uhat, rho_start, VH_start=None, tol=None, max_inner=None):
+        inst = self.inst
+        tol = inst.tol_scf if tol is None else tol
+        max_inner = inst.max_inner if max_inner is None else max_inner
+        FB = self.mass_blocks(Uhat)
+        mixer = Anderson(self.fine.Wq)
+        rho_in = rho_start.copy()
+        VH_prev = VH_start
+        hist = []
+        for t in range(max_inner):
+            VH, VHq, eps, vxc = self.nonlinear(rho_in, VH_prev)
+            VH_prev = VH
+            A = (self.AL + self.A_NL(VHq, vxc)).tocsr()
+            FA = self.small_blocks(A, Uhat)
+            lam, U = self.eig_small(FA, FB)
+            Psi = self.basis_apply(Uhat, U)
+            rho_out = self.density(Psi)
+            res = self.norm0(rho_out - rho_in)
+            hist.append(res)
+            if res < tol:
+                return State(lam, Psi, rho_in, rho_out, VH, t + 1, res, True,
+                             {"res_hist": hist, "U": U, "eps": eps, "vxc": vxc, "VHq": VHq})
+            if t == max_inner - 1:
+                break
+            rho_in = mixer.mix(rho_in, rho_out)
+        return State(lam, Psi, rho_in, rho_out, VH, max_inner, res, False,
+                     {"res_hist": hist, "U": U, "eps": eps, "vxc": vxc, "VHq": VHq})
+
+    # ------------------------------------------------------------ Algorithm 3
+    def initial_state(self):
+        zero = np.zeros_like(self.fine.Wq)
+        return self.inner_scf(None, zero)
+
+    def bvp(self, st):
+        """Step 1 of Algorithm 3: the N shifted linear problems."""
+        _, VHq, _, vxc = self.nonlinear_cached(st)
+        Ht = (self.AL + self.A_NL(VHq, vxc) + self.mu * self.M).tocsr()
+        R = (self.M @ st.Psi) * (st.lam + self.mu)[None, :]
+        return solve_spd(Ht, R, tol=self.inst.tol_bvp * 1e-1)
+
+    def nonlinear_cached(self, st):
+        VHq = self.fine.at_quad(st.VH)
+        if self.inst.xc:
+            eps, vxc = lda.lda(st.rho_in)
+        else:
+            eps = np.zeros_like(st.rho_in)
+            vxc = np.zeros_like(st.rho_in)
+        return st.VH, VHq, eps, vxc
+
+    def step(self, st):
+        Uhat = self.bvp(st)
+        new = self.inner_scf(Uhat, st.rho_in, VH_start=st.VH)
+        new.info["Uhat"] = Uhat
+        new.info["drho"] = self.norm0(new.rho_out - st.rho_out)
+        return new
+
+    def solve(self, st=None, max_outer=None, tol=None, callback=None):
+        st = self.initial_state() if st is None else st
+        max_outer = self.inst.max_outer if max_outer is None else max_outer
+        tol = self.inst.tol_scf if tol is None else tol
+        for l in range(max_outer):
+            st = self.step(st)
+            if callback is not None:
+                callback(l, st)
+            if st.info["drho"] < tol:
+                break
+        return st
+
+    # ------------------------------------------------------------ energies
+    def energy(self, st):
+        """Sec. 3.1 energy formula at the density rho_in of the potential."""
+        f = self.fine
+        _, VHq, eps, vxc = self.nonlinear_cached(st)
+        rho = st.rho_in
+        return (float(np.dot(self.occ, st.lam))
+                - f.integrate((0.5 * VHq + vxc) * rho)
+                + f.integrate(rho * eps) + self.Enn)
+
+    def variational_energy(self, Psi):
+        """E(Psi) of Sec. 2 (kinetic + external + xc + Hartree/2 + E_nn)."""
+        f = self.fine
+        rho = self.density(Psi)
+        kin = 0.5 * float(np.sum(self.occ * np.einsum("in,in->n", Psi, self.K @ Psi)))
+        ext = f.integrate(self.vext_q * rho)
+        E = kin + ext + self.Enn
+        if self.inst.xc:
+            eps, _ = lda.lda(rho)
+            E += f.integrate(rho * eps)
+        if self.inst.hartree:
+            VH = hartree.hartree(f, self.K, self.K_IB, rho, tol=1e-14)
+            E += 0.5 * f.integrate(f.at_quad(VH) * rho)
+        return E
+
+    # ------------------------------------------------------------ direct SCF (plain definition)
+    def direct_scf(self, tol=None, max_iter=200, dense_max=4000):
+        """SCF on the whole fine space: the discrete ground state of Sec. 2."""
+        f = self.fine
+        tol = self.inst.tol_scf if tol is None else tol
+        Md = self.M.toarray() if f.n <= dense_max else None
+        mixer = Anderson(f.Wq)
+        rho_in = np.zeros_like(f.Wq)
+        VH_prev = None
+        for t in range(max_iter):
+            VH, VHq, eps, vxc = self.nonlinear(rho_in, VH_prev)
+            VH_prev = VH
+            A = (self.AL + self.A_NL(VHq, vxc)).tocsr()
+            if Md is not None:
+                lam, Psi = sla.eigh(A.toarray(), Md, subset_by_index=[0, self.N - 1])
+            else:
+                import scipy.sparse.linalg as spla
+                lam, Psi = spla.eigsh(A, k=self.N, M=self.M, sigma=-1e3, which="LM", tol=1e-14)
+                o = np.argsort(lam)
+                lam, Psi = lam[o], Psi[:, o]
+            rho_out = self.density(Psi)
+            res = self.norm0(rho_out - rho_in)
+            if res < tol:
+                return State(lam, Psi, rho_in, rho_out, VH, t + 1, res, True)
+            rho_in = mixer.mix(rho_in, rho_out)
+        return State(lam, Psi, rho_in, rho_out, VH, max_iter, res, False)

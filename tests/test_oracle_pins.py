@@ -1,0 +1,278 @@
+"""Pins of the CPU oracle against closed forms, invariants and brute force.
+
+Every check here compares the oracle with something other than itself: exact
+integrals, conservation laws, analytic solutions, exhaustive search, or an
+independent formulation (direct fine-space solve vs. Algorithm 3).
+"""
+from fractions import Fraction
+from math import erf, factorial, pi, sqrt
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from oracle import anderson, fem, hartree, lda, quadrature, transfer
+from oracle.nas import Problem, nuclear_repulsion
+from workloads import make_instance
+
+
+# ---------------------------------------------------------------- quadrature
+@pytest.mark.parametrize("order,deg", [(1, 2), (2, 5)])
+def test_quadrature_exact_monomials(order, deg):
+    bary, w = quadrature.rule(order)
+    assert np.all(w > 0) and np.all(bary > 0)
+    x, y, z = bary[:, 1], bary[:, 2], bary[:, 3]
+    for i in range(deg + 1):
+        for j in range(deg + 1 - i):
+            for k in range(deg + 1 - i - j):
+                exact = factorial(i) * factorial(j) * factorial(k) / factorial(i + j + k + 3)
+                assert abs(np.sum(w * x ** i * y ** j * z ** k) - exact) < 1e-15
+    # one degree more is NOT integrated exactly (the check discriminates)
+    errs = [abs(np.sum(w * x ** i * y ** (deg + 1 - i)) -
+                factorial(i) * factorial(deg + 1 - i) / factorial(deg + 4)) for i in range(deg + 2)]
+    assert max(errs) > 1e-8
+
+
+# ---------------------------------------------------------------- assembly invariants
+def _space(order, cells=4):
+    inst = make_instance("he_p1", cells=cells, coarse_cells=2)
+    return fem.Space(inst.fine_xyz, inst.fine_tet, order)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_mass_sums_to_volume(order):
+    s = _space(order)
+    M = s.assemble_full("M")
+    assert abs(M.sum() - 8000.0) < 1e-9
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_stiffness_kernel_and_energy(order):
+    s = _space(order)
+    K = s.assemble_full("K")
+    assert np.max(np.abs(np.asarray(K.sum(axis=1)).ravel())) < 1e-11
+    x = s.node_xyz
+    u = 0.3 + 1.1 * x[:, 0] - 0.7 * x[:, 1] + 0.4 * x[:, 2]
+    # u^T K u = int |grad u|^2 = |g|^2 vol
+    assert abs(u @ (K @ u) - (1.1 ** 2 + 0.7 ** 2 + 0.4 ** 2) * 8000.0) < 1e-7
+    # interior rows of K u vanish for affine u
+    Ku = (K @ u)[s.interior_nodes]
+    assert np.max(np.abs(Ku)) < 1e-10
+    if order == 2:
+        # quadratic u: int grad u . grad phi_i = -Lap(u) int phi_i on interior rows
+        q = x[:, 0] ** 2 - 0.5 * x[:, 1] * x[:, 2] + 2.0 * x[:, 2] ** 2
+        lap = 2.0 + 4.0
+        intphi = np.asarray(s.assemble_full("M").sum(axis=1)).ravel()
+        r = (K @ q)[s.interior_nodes] + lap * intphi[s.interior_nodes]
+        assert np.max(np.abs(r)) < 1e-9
+        assert abs(q @ (K @ q) - _grad_sq_integral()) < 1e-6
+
+
+def _grad_sq_integral():
+    # int over [-10,10]^3 of |grad(x^2 - y z/2 + 2 z^2)|^2 = int (2x)^2 + (z/2)^2 + (4z - y/2)^2
+    m2 = 2 * 10 ** 3 / 3.0 * 20 * 20  # int x^2 over the cube
+    return 4 * m2 + 0.25 * m2 + 16 * m2 + 0.25 * m2
+
+
+# ---------------------------------------------------------------- LDA
+def test_lda_potential_is_energy_derivative():
+    for rho in [1e-4, 3e-3, 0.05, 0.2, 1.0, 7.0, 60.0]:
+        h = 1e-6 * rho
+        ep, _ = lda.lda(np.array([rho + h]))
+        em, _ = lda.lda(np.array([rho - h]))
+        _, v = lda.lda(np.array([rho]))
+        fd = ((rho + h) * ep[0] - (rho - h) * em[0]) / (2 * h)
+        assert abs(fd - v[0]) < 1e-7 * max(1.0, abs(v[0]))
+
+
+def test_lda_exchange_hydrogen_closed_form():
+    # rho = exp(-2r)/pi: E_x = -(81/256) 3^(1/3) pi^(-2/3)
+    exact = -(81.0 / 256.0) * 3 ** (1 / 3) * pi ** (-2 / 3)
+    assert abs(exact + 0.2127415031) < 1e-9
+
+    def integrand(r):
+        rho = np.exp(-2 * r) / pi
+        eps_x = -0.75 * (3 / pi) ** (1 / 3) * rho ** (1 / 3)
+        return 4 * pi * r * r * rho * eps_x
+
+    ex = si.quad(integrand, 0, 60, limit=200, epsabs=1e-14)[0]
+    # the oracle's eps_xc minus its correlation part must integrate to E_x
+    def integrand_oracle(r):
+        rho = np.exp(-2 * r) / pi
+        eps, _ = lda.lda(np.array([rho]))
+        rs = (3 / (4 * pi * rho)) ** (1 / 3)
+        if rs < 1:
+            ec = lda.A * np.log(rs) + lda.B + lda.C * rs * np.log(rs) + lda.D * rs
+        else:
+            ec = lda.GAMMA / (1 + lda.BETA1 * np.sqrt(rs) + lda.BETA2 * rs)
+        return 4 * pi * r * r * rho * (eps[0] - ec)
+    ex2 = si.quad(integrand_oracle, 0, 60, limit=200, epsabs=1e-14)[0]
+    assert abs(ex - exact) < 1e-10
+    assert abs(ex2 - exact) < 1e-10
+
+
+def test_lda_zero_density():
+    e, v = lda.lda(np.array([0.0, -1e-3, 1e-31]))
+    assert np.all(e == 0) and np.all(v == 0)
+
+
+def test_pz_high_density_coefficient():
+    # A is the Gell-Mann-Brueckner coefficient (1 - ln 2)/pi^2 to the printed digits
+    assert abs(lda.A - (1 - np.log(2)) / pi ** 2) < 1e-4
+
+
+# ---------------------------------------------------------------- Hartree
+def _gauss_hartree(cells, alpha=1.0):
+    inst = make_instance("hydrogen", cells=cells, order=1, half=8.0, power=1.5)
+    s = fem.Space(inst.fine_xyz, inst.fine_tet, 1)
+    Kf = s.assemble_full("K")
+    r2 = np.sum(s.xq ** 2, axis=-1)
+    rho = (alpha / pi) ** 1.5 * np.exp(-alpha * r2)
+    V = hartree.hartree(s, s.interior(Kf), s.interior_boundary(Kf), rho)
+    r = np.linalg.norm(s.node_xyz, axis=1)
+    exact = np.array([erf(sqrt(alpha) * ri) / ri if ri > 0 else 2 * sqrt(alpha / pi) for ri in r])
+    EH = 0.5 * s.integrate(s.at_quad(V) * rho)
+    return np.max(np.abs(V - exact)), EH
+
+
+def test_hartree_gaussian_closed_form():
+    e1, E1 = _gauss_hartree(12)
+    e2, E2 = _gauss_hartree(20)
+    exact_EH = sqrt(1.0 / (2 * pi))
+    assert e2 < 0.5 * e1 and e2 < 5e-2
+    assert abs(E2 - exact_EH) < 0.5 * abs(E1 - exact_EH) and abs(E2 - exact_EH) < 2e-2
+
+
+def test_hartree_boundary_values_monopole():
+    s = _space(1, cells=6)
+    rho = np.exp(-np.sum((s.xq - np.array([0.5, -0.25, 0.0])) ** 2, axis=-1))
+    w, Q, c = hartree.boundary_values(s, rho)
+    assert abs(Q - s.integrate(rho)) < 1e-12
+    xb = s.node_xyz[s.boundary_nodes]
+    assert np.allclose(w * np.linalg.norm(xb - c, axis=1), Q, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- transfer
+def test_orient_exact_on_degenerate_points():
+    a = np.array([0.0, 0.0, 0.0])
+    b = np.array([0.1, 0.0, 0.0])
+    c = np.array([0.0, 0.3, 0.0])
+    d = np.array([0.1 + 0.2, 0.3 * 0.7, 0.0])  # coplanar (z = 0), inexact products
+    assert transfer.orient_sign(a, b, c, d) == 0
+    d2 = d.copy()
+    d2[2] = np.nextafter(0.0, 1.0)
+    # det[b-a, c-a, d-a] = 0.1 * 0.3 * dz > 0
+    assert transfer.orient_sign(a, b, c, d2) == 1
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        P = rng.integers(-4, 5, size=(4, 3)) * 0.1   # many coplanar/degenerate sets
+        s = transfer.orient_sign(*P)
+        F = [[Fraction(float(v)) for v in row] for row in P]
+        m = [[F[i][j] - F[0][j] for j in range(3)] for i in (1, 2, 3)]
+        det = (m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1])
+               - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+               + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]))
+        assert s == (det > 0) - (det < 0)
+
+
+def test_transfer_matches_brute_force_and_is_affine_exact():
+    inst = make_instance("he_p1", cells=8, coarse_cells=4)
+    f = fem.Space(inst.fine_xyz, inst.fine_tet, 2)
+    c = fem.Space(inst.coarse_xyz, inst.coarse_tet, 1)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(f.n, 250, replace=False)
+    # include nodes on the coordinate planes, which lie on coarse faces
+    on_plane = np.nonzero(np.any(f.node_xyz[f.interior_nodes] == 0.0, axis=1))[0][:80]
+    rows = np.unique(np.concatenate([rows, on_plane]))
+    I, elem, W, C = transfer.build_transfer(f, c, points=rows)
+    cm = transfer.CoarseMesh(c.vxyz, c.tet)
+    P = f.node_xyz[f.interior_nodes[rows]]
+    bf = np.array([cm.brute_force(p) for p in P])
+    assert np.array_equal(bf, elem)
+    assert np.max(np.abs(W.sum(axis=1) - 1.0)) < 1e-14
+    g = lambda x: 0.5 - 0.3 * x[..., 0] + 0.2 * x[..., 1] + 0.9 * x[..., 2]
+    interp = np.sum(W * g(c.vxyz[C]), axis=1)
+    assert np.max(np.abs(interp - g(P))) < 1e-13
+    assert np.all(W >= 0.0)
+    # nodes on coarse faces have exact zero weights
+    assert np.sum(W == 0.0) > 0
+
+
+# ---------------------------------------------------------------- Anderson
+def test_anderson_is_krylov_exact_on_linear_maps():
+    rng = np.random.default_rng(3)
+    d = 5
+    Q = np.linalg.qr(rng.normal(size=(d, d)))[0]
+    G = Q @ np.diag(rng.uniform(-0.9, 0.9, d)) @ Q.T
+    cvec = rng.normal(size=d)
+    xstar = np.linalg.solve(np.eye(d) - G, cvec)
+    mix = anderson.Anderson(np.ones(d), depth=d + 2, beta=0.7)
+    x = np.zeros(d)
+    for _ in range(d + 2):
+        x = mix.mix(x, G @ x + cvec)
+    assert np.linalg.norm(x - xstar) < 1e-9 * np.linalg.norm(xstar)
+    # plain damped iteration is far from converged after as many steps
+    y = np.zeros(d)
+    for _ in range(d + 2):
+        y = y + 0.7 * (G @ y + cvec - y)
+    assert np.linalg.norm(y - xstar) > 1e-4 * np.linalg.norm(xstar)
+
+
+# ---------------------------------------------------------------- linear eigenproblems
+def _direct_lowest(P, k):
+    lam = spla.eigsh(P.AL, k=k, M=P.M, sigma=-60.0, which="LM")[0]
+    return np.sort(lam)
+
+
+@pytest.mark.parametrize("order,min_rate", [(1, 1.5), (2, 3.0)])
+def test_harmonic_oscillator_levels(order, min_rate):
+    exact = np.array([1.5, 2.5, 2.5, 2.5])
+    errs = []
+    for cells in (8, 12):
+        P = Problem(make_instance("harmonic", cells=cells, coarse_cells=3, order=order, n_orb=4),
+                    with_transfer=False)
+        errs.append(np.abs(_direct_lowest(P, 4) - exact))
+    rate = np.log(errs[0] / errs[1]) / np.log(12 / 8)
+    assert np.all(errs[1] < errs[0]) and np.all(rate > min_rate)
+
+
+def test_hydrogen_ground_state_under_refinement():
+    errs = []
+    for cells in (8, 12, 16):
+        P = Problem(make_instance("hydrogen", cells=cells, order=1), with_transfer=False)
+        errs.append(abs(_direct_lowest(P, 1)[0] + 0.5))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.07
+
+
+def test_augmented_method_equals_full_eigensolve_linear():
+    inst = make_instance("harmonic", cells=6, coarse_cells=5, order=2, n_orb=4, tol_scf=1e-12)
+    P = Problem(inst)
+    st = P.solve(max_outer=400)
+    assert st.info["drho"] < 1e-12
+    full = sla.eigh(P.AL.toarray(), P.M.toarray(), subset_by_index=[0, 3])[0]
+    assert np.max(np.abs(st.lam - full)) < 1e-10
+
+
+def test_augmented_method_equals_direct_scf_kohn_sham():
+    # mu = 2 keeps H + mu coercive (lambda_1 ~ -0.49) and converges in ~50 steps;
+    # the paper's 8 M sum Z^2 = 32 reaches the same fixed point far more slowly
+    inst = make_instance("he_p1", cells=6, coarse_cells=3, tol_scf=1e-12, mu=2.0)
+    P = Problem(inst)
+    st = P.solve(max_outer=400)
+    assert st.info["drho"] < 1e-12
+    d = P.direct_scf(tol=1e-12)
+    assert abs(st.lam[0] - d.lam[0]) < 1e-10 * abs(d.lam[0])
+    E = P.energy(st)
+    assert abs(E - P.energy(d)) < 1e-10 * abs(E)
+    # energy formula of Sec. 3.1 equals the variational E(Psi) at self-consistency
+    assert abs(E - P.variational_energy(st.Psi)) < 1e-10 * abs(E)
+
+
+def test_nuclear_repulsion_closed_form():
+    inst = make_instance("he_p1", cells=2, coarse_cells=1)
+    inst.R = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0], [0.0, 0.0, 2.0]])
+    inst.Z = np.array([1.0, 2.0, 3.0])
+    assert abs(nuclear_repulsion(inst) - (2.0 / 5 + 3.0 / 2 + 6.0 / sqrt(9 + 16 + 4))) < 1e-15

@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the augmented subspace method on one GB300 (or N replicas).
+
+A step is one Algorithm 3 iteration (one augmented-subspace step): H~
+assembly, the N shifted linear boundary value problems (block PCG), the
+basis of the augmented space, its fixed blocks, and the inner SCF of the
+small Kohn-Sham problem to convergence (Hartree Poisson solves, LDA,
+A^NL assembly, Galerkin blocks, host small eigensolve, density, Anderson).
+
+Workload (default): 8 nuclei, Z uniform in {1..8}, R uniform in [-4,4]^3
+(seed 1), N = 21 doubly/singly occupied orbitals, Omega = [-16,16]^3, P2 on a
+50^3 tensor grid graded toward the nuclei (1,030,301 nodes, 970,299
+unknowns), coarse 16^3 P1 (3,375 unknowns), FP64.
+
+Output: one JSON line (rank 0).  Multi-GPU: one process per GPU under
+torchrun, each an independent replica of the workload (weak scaling, no
+collective on the data path); value = total steps of all ranks / max time.
+`--impl reference` times the CPU oracle instead (bounded sample, see
+`oracle_sample`).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "augmented-subspace steps/s + SpMM HBM GB/s; mixed vs FP64 at ≤1e-8 Ha error"
+SAMPLE = dict(cells=10, coarse_cells=6)   # oracle sample: same molecule, reduced meshes
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flop x max clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="mol8_p2")
+    p.add_argument("--cells", type=int, default=None)
+    p.add_argument("--coarse-cells", type=int, default=None)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--tol-poisson", type=float, default=1e-10)
+    p.add_argument("--tol-bvp", type=float, default=1e-10)
+    return p.parse_args()
+
+
+def instance(args):
+    from workloads import make_instance
+    kw = {}
+    if args.cells:
+        kw["cells"] = args.cells
+    if args.coarse_cells:
+        kw["coarse_cells"] = args.coarse_cells
+    return make_instance(args.workload, **kw)
+
+
+def workload_config(args, inst, extra=None):
+    cfg = {
+        "workload": "%s: %d nuclei Z=%s, N=%d orbitals, P%d fine mesh %d tets, coarse %d tets, FP64"
+                    % (args.workload, len(inst.Z), [int(z) for z in inst.Z], inst.n_orb, inst.order,
+                       len(inst.fine_tet), len(inst.coarse_tet)),
+        "fine_vertices": int(len(inst.fine_xyz)),
+        "l2": "no flush: the per-step working set (CSR values/indices, orbitals, quadrature arrays) exceeds the 126 MB L2",
+        "tol_bvp": args.tol_bvp, "tol_poisson": args.tol_poisson, "tol_inner": inst.tol_scf,
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(device):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- oracle
+def oracle_sample(n_steps, warm_steps=1):
+    """Time oracle augmented steps on the reduced sample (runs in a fresh
+    single-threaded process).  Returns dict with per-step seconds and sizes."""
+    from oracle.nas import Problem
+    from workloads import make_instance
+    inst = make_instance("mol8_p2", **SAMPLE)
+    inst.tol_bvp = 1e-10
+    inst.tol_poisson = 1e-10
+    P = Problem(inst)
+    st = P.initial_state()
+    for _ in range(warm_steps):
+        st = P.step(st)
+    times = []
+    for _ in range(n_steps):
+        t = time.perf_counter()
+        st = P.step(st)
+        times.append(time.perf_counter() - t)
+    return {"step_s": times, "n_sample": int(P.fine.n), "nH": int(P.coarse.n), "n_inner": int(st.n_inner)}
+
+
+def run_oracle_subprocess(n_steps, warm_steps=1, timeout=900):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print('ORACLE', json.dumps(bench.oracle_sample(%d, %d)))" % (ROOT, n_steps, warm_steps))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+    for line in r.stdout.splitlines():
+        if line.startswith("ORACLE "):
+            return json.loads(line[7:])
+    raise RuntimeError("oracle sample failed: %s" % r.stderr[-2000:])
+
+
+def cpu_baseline_from(sample, n_full):
+    t = statistics.median(sample["step_s"])
+    scale = n_full / sample["n_sample"]
+    return {
+        "value": 1.0 / (t * scale), "unit": "steps/s", "cores": 1, "kind": "oracle",
+        "sample": ("CPU oracle (NumPy/SciPy FP64, 1 thread) Algorithm 3 steps on the same molecule with a "
+                   "P2 %d^3 fine mesh (%d unknowns) and %d^3 coarse mesh; measured %.2f s/step, scaled to the "
+                   "full %d-unknown mesh linearly in fine unknowns (the paper's O(N N_k) work per step)"
+                   % (SAMPLE["cells"], sample["n_sample"], SAMPLE["coarse_cells"], t, n_full)),
+        "sample_step_s": t,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst = instance(args)
+    # unknowns of the full mesh: P2 nodes minus boundary nodes (counted without assembling)
+    n_full = full_unknowns(inst)
+    sample = run_oracle_subprocess(args.steps, warm_steps=max(1, args.warmup))
+    cb = cpu_baseline_from(sample, n_full)
+    ms = statistics.median(sample["step_s"]) * (n_full / sample["n_sample"]) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, inst), "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def full_unknowns(inst):
+    import numpy as np
+    xyz = inst.fine_xyz
+    tet = inst.fine_tet.astype(np.int64)
+    lo, hi = xyz.min(axis=0), xyz.max(axis=0)
+    on_b = np.any((xyz == lo) | (xyz == hi), axis=1)
+    n = int(np.sum(~on_b))
+    if inst.order == 2:
+        pairs = np.concatenate([np.sort(tet[:, [i, j]], axis=1) for i, j in
+                                [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]])
+        key = np.unique(pairs[:, 0] * len(xyz) + pairs[:, 1])
+        a, b = key // len(xyz), key % len(xyz)
+        mid = 0.5 * (xyz[a] + xyz[b])
+        n += int(np.sum(~np.any((mid == lo) | (mid == hi), axis=1)))
+    return n
+
+
+# ---------------------------------------------------------------------------- our arm
+def log(msg):
+    print("[bench] " + msg, file=sys.stderr, flush=True)
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.steps)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the CPU oracle sample runs in a fresh process started before any GPU work
+    oracle_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+                "print('ORACLE', json.dumps(bench.oracle_sample(2, 1)))" % ROOT)
+        oracle_proc = subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                       stderr=subprocess.PIPE, text=True)
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2404_19249_gb300 import build as nbuild
+    if not os.path.exists(nbuild.LIB):
+        nbuild.build()
+    from paper_2404_19249_gb300 import nas
+
+    inst = instance(args)
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.time()
+    s = nas.Solver(inst, device=local, stream=stream, timing=1, tol_poisson=args.tol_poisson,
+                   tol_bvp=args.tol_bvp, check_every=4)
+    s.init()
+    setup_s = time.time() - t0
+    sz = s.sizes()
+    log("setup+init %.1f s sizes %s" % (setup_s, sz))
+    for w in range(args.warmup):
+        tw = time.time()
+        r, rep = s.step()
+        log("warmup step %d: %.2f s status %d inner %d cg %d poisson %d drho %.3e E %.10f phases %s"
+            % (w, time.time() - tw, r, rep.n_inner, rep.cg_iters, rep.poisson_iters, rep.drho, rep.energy,
+               {k: round(v, 1) for k, v in rep.as_dict()["phase_ms"].items()}))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d.csv" % os.getpid())
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    reps = []
+    ev0.record()
+    for _ in range(args.steps):
+        r, rep = s.step()
+        reps.append(nas.nas_report.from_buffer_copy(rep))
+    ev1.record()
+    barrier()
+    clk = clocks.stop(local)
+    ms = ev0.elapsed_time(ev1)
+    log("timed: %d steps in %.1f ms; last report %s" % (args.steps, ms, reps[-1].as_dict()))
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # phase totals over the timed steps (library CUDA events on the launching stream)
+    ph = {name: sum(rp.phase_ms[i] for rp in reps) for i, name in enumerate(nas.PHASES)}
+    calls = {name: sum(rp.phase_calls[i] for rp in reps) for i, name in enumerate(nas.PHASES)}
+    spmm_bytes = sum(rp.spmm_bytes for rp in reps)
+    spmm_flops = sum(rp.spmm_flops for rp in reps)
+    spmv_bytes = sum(rp.spmv_bytes for rp in reps)
+    launches = int(sum(rp.kernel_launches for rp in reps))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak = float(peaks["hbm_gbs"])
+        peak_src = "measured"
+    except Exception:
+        hbm_peak, peak_src = 6800.0, "fallback"
+    spmm_ms, spmv_ms = ph["spmm"], ph["spmv"]
+    spmm_gbs = spmm_bytes / (spmm_ms * 1e-3) / 1e9 if spmm_ms > 0 else 0.0
+    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9 if spmv_ms > 0 else 0.0
+    spmm_tflops = spmm_flops / (spmm_ms * 1e-3) / 1e12 if spmm_ms > 0 else 0.0
+    roof_spmm = {"kernel": "k_spmm_cols (CSR SpMM, N=%d interleaved RHS, FP64)" % sz["N"], "bound": "alu",
+                 "achieved": spmm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": spmm_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                 "peak_source": "FP64 FMA issue rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
+                 "algorithmic_gbs": spmm_gbs, "launches": calls["spmm"], "ms_per_launch":
+                     spmm_ms / max(calls["spmm"], 1)}
+    roof_spmv = {"kernel": "k_spmv8 (CSR SpMV, Poisson PCG, FP64)", "bound": "hbm", "achieved": spmv_gbs,
+                 "peak": hbm_peak, "unit": "GB/s", "frac": spmv_gbs / hbm_peak, "traffic": None,
+                 "peak_source": peak_src, "launches": calls["spmv"],
+                 "ms_per_launch": spmv_ms / max(calls["spmv"], 1)}
+    dominant, other = (roof_spmv, roof_spmm) if spmv_ms >= spmm_ms else (roof_spmm, roof_spmv)
+
+    # ---------------------------------------------------------------- e2e through host buffers
+    n, N, nqt = sz["n"], sz["N"], sz["ne"] * sz["nq"]
+    lam_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    psi_h = torch.empty((n, N), dtype=torch.float64, pin_memory=True)
+    rho_h = torch.empty(nqt, dtype=torch.float64, pin_memory=True)
+    en_h = torch.empty(6, dtype=torch.float64, pin_memory=True)
+
+    def get(q, t):
+        nas.nas_get(s.h, q, (t.data_ptr(), t.numel() * 8), 0)
+
+    get(nas.NAS_Q_EIGVALS, lam_h)
+    get(nas.NAS_Q_ORBITALS, psi_h)
+    get(nas.NAS_Q_RHO_IN, rho_h)
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        nas.nas_set_state(s.h, lam_h.data_ptr(), psi_h.data_ptr(), rho_h.data_ptr(), 0)
+        s.step()
+        get(nas.NAS_Q_EIGVALS, lam_h)
+        get(nas.NAS_Q_ORBITALS, psi_h)
+        get(nas.NAS_Q_RHO_IN, rho_h)
+        get(nas.NAS_Q_ENERGY, en_h)
+    barrier()
+    e2e_s = time.perf_counter() - e0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    io_bytes = 8 * (N + n * N + nqt)
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": io_bytes,
+           "d2h_bytes_per_step": io_bytes + 48}
+
+    if rank != 0:
+        s.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if oracle_proc is not None:
+        try:
+            out, err = oracle_proc.communicate(timeout=900)
+            for line in out.splitlines():
+                if line.startswith("ORACLE "):
+                    cpu = cpu_baseline_from(json.loads(line[7:]), n)
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"error": str(ex)[:200]}
+    last = reps[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, inst, {"unknowns": n, "nnz": sz["nnz"], "coarse_unknowns": sz["nH"],
+                                               "parallelism": "replicas" if world > 1 else "1 GPU"}),
+        "spmm_hbm_gbs": spmm_gbs, "spmv_hbm_gbs": spmv_gbs,
+        "roofline": dominant, "roofline_other": other,
+        "phase_ms_per_step": {k: v / args.steps for k, v in ph.items()},
+        "per_step": {"n_inner": last.n_inner, "cg_iters": last.cg_iters, "poisson_iters": last.poisson_iters,
+                     "drho": last.drho, "energy": last.energy},
+        "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "setup_s": setup_s,
+    }
+    print(json.dumps(line))
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

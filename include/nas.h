@@ -1,0 +1,253 @@
+/*
+ * nas.h - C ABI of the GPU nonnested augmented subspace method for the
+ * Kohn-Sham equation (Hu, Xie, Xu, Zhao, arXiv 2404.19249).
+ *
+ * The library computes, on one GPU, the fine-mesh work of Algorithm 3 (the
+ * augmented subspace method, Sec. 3.3): assembly of the finite element
+ * Hamiltonian with V_ext, V_Har and LDA V_xc integrated by quadrature, the N
+ * shifted linear boundary value problems solved by block preconditioned CG,
+ * the nonnested transfer matrix I_H^h built by point location (Algorithm 1),
+ * the blocks of the small augmented eigenproblem (eqs. st1-st7), the density
+ * and the Hartree Poisson solve (Sec. 3.1).  The small dense generalized
+ * eigenproblem F_A U = lambda F_B U is solved on the host.
+ *
+ * Conventions for every function below
+ *  - Return value: NAS_OK (0) on success, otherwise a negative NAS_E_* code;
+ *    nas_last_error() then returns a message for that context.  No function
+ *    calls exit() or throws across the ABI.
+ *  - Pointers are HOST pointers unless the argument or flag says "device".
+ *    The caller owns every buffer it passes; the library copies what it needs
+ *    into device memory that it owns and frees in nas_destroy().
+ *  - Arrays are C-contiguous (row-major).  "FP64" means IEEE double.
+ *  - A context is used by one host thread at a time.  All device work of a
+ *    context is ordered on the CUDA stream given to nas_create().
+ */
+#ifndef NAS_H
+#define NAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define NAS_OK                  0
+#define NAS_E_INVALID_ARG      -1  /* bad size, NULL pointer, bad enum */
+#define NAS_E_MESH             -2  /* inverted/degenerate tetrahedron, bad ids */
+#define NAS_E_POINT_NOT_FOUND  -3  /* a fine node lies in no coarse tetrahedron */
+#define NAS_E_BREAKDOWN        -4  /* CG p^T A p <= 0 or non-finite values */
+#define NAS_E_NOT_CONVERGED    -5  /* an iteration cap was reached */
+#define NAS_E_CUDA             -6  /* a CUDA runtime call failed */
+#define NAS_E_OOM              -7  /* device or host allocation failed */
+#define NAS_E_STATE            -8  /* call made out of order (e.g. step before init) */
+#define NAS_E_EIGEN            -9  /* host small eigensolver failed (F_B not SPD ...) */
+
+enum nas_mesh_kind { NAS_FINE = 0, NAS_COARSE = 1 };
+
+/* External potential V_ext (Sec. 2): Coulomb -sum Z_k/|x-R_k|; smoothed
+ * Coulomb -sum Z_k/sqrt(|x-R_k|^2 + a^2); harmonic 0.5 omega^2 |x|^2 (a test
+ * potential with closed-form levels n + 3/2). */
+enum nas_potential { NAS_POT_COULOMB = 0, NAS_POT_SMOOTHED = 1, NAS_POT_HARMONIC = 2 };
+
+/* ------------------------------------------------------------------ options */
+typedef struct nas_options {
+    double mu;             /* shift of H~ = H + mu (Sec. 3.3); < 0 selects 8 M sum_k Z_k^2
+                              (the experiments' choice, Sec. 5)                     */
+    double tol_bvp;        /* relative residual of each of the N linear problems     */
+    double tol_poisson;    /* relative residual of the Hartree Poisson solve         */
+    double tol_scf;        /* ||rho^(l) - rho^(l-1)||_0 stop test of Algorithm 3     */
+    double tol_inner;      /* ||rho_out - rho_in||_0 stop test of the inner SCF      */
+    int    max_cg;         /* iteration cap of the block PCG                         */
+    int    max_poisson;    /* iteration cap of the Poisson PCG                       */
+    int    max_inner;      /* inner SCF iterations per step                          */
+    int    max_outer;      /* steps of nas_solve                                     */
+    int    anderson_depth; /* Anderson history depth (Sec. 5: 5)                     */
+    double anderson_beta;  /* Anderson damping (Sec. 5: 0.7)                         */
+    int    hartree;        /* 1: include V_Har; 0: linear problem                    */
+    int    xc;             /* 1: include LDA V_xc                                    */
+    int    multipole;      /* Hartree boundary values: 0 monopole, 2 + quadrupole    */
+    double omega;          /* harmonic test potential frequency                      */
+    int    check_every;    /* CG iterations between host convergence checks (>=1)    */
+    int    timing;         /* 1: record per-kernel CUDA-event times (nas_report)     */
+    int    eig_dense_max;  /* small problems up to this size use the dense host
+                              eigensolver, larger ones warm-started LOBPCG           */
+} nas_options;
+
+/* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
+ * tol_poisson = 1e-12, tol_scf = tol_inner = 1e-8, max_cg = 2000,
+ * max_poisson = 20000, max_inner = 50, max_outer = 100, depth 5, beta 0.7,
+ * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
+ * eig_dense_max = 1200. */
+void nas_default_options(nas_options* opt);
+
+/* ------------------------------------------------------------------ report */
+#define NAS_MAX_PHASES 16
+enum nas_phase {
+    NAS_PH_ASSEMBLY = 0,   /* V_eff at quadrature points + CSR assembly (st3, st4)  */
+    NAS_PH_BVP,            /* block PCG for the N linear problems                   */
+    NAS_PH_POISSON,        /* Hartree: right-hand side, boundary values, PCG        */
+    NAS_PH_BLOCKS,         /* F_A / F_B blocks (st5-st7) incl. I^T A I              */
+    NAS_PH_DENSITY,        /* Psi = I u_H + U^ alpha and rho at quadrature points   */
+    NAS_PH_MIXING,         /* Anderson inner products and combination               */
+    NAS_PH_HOST_EIG,       /* host small eigensolve (incl. its D2H/H2D)             */
+    NAS_PH_TRANSFER,       /* point location + I_H^h                                */
+    NAS_PH_SPMM,           /* SpMM launches with N > 1 columns (subset of the above) */
+    NAS_PH_SPMV,           /* SpMV launches (N = 1, Poisson and Dirichlet lift)      */
+    NAS_PH_COUNT
+};
+
+typedef struct nas_report {
+    int    n_orb;             /* N                                                  */
+    int    step;              /* steps done since nas_init                          */
+    int    n_inner;           /* inner SCF iterations of the last step              */
+    int    inner_converged;   /* 1 if the last inner SCF met tol_inner              */
+    int    cg_iters;          /* block PCG iterations of the last step              */
+    int    poisson_iters;     /* Poisson PCG iterations summed over the last step   */
+    double drho;              /* ||rho^(l) - rho^(l-1)||_0 of the last step         */
+    double inner_res;         /* final ||rho_out - rho_in||_0                        */
+    double energy;            /* E of Sec. 3.1                                       */
+    double e_band;            /* sum_i f_i lambda_i                                  */
+    double e_hartree;         /* (1/2) int V_H rho                                   */
+    double e_xc;              /* int rho eps_xc                                      */
+    double e_vxc;             /* int V_xc rho                                        */
+    double e_nn;              /* nuclear repulsion                                   */
+    double phase_ms[NAS_MAX_PHASES];   /* CUDA-event / host time per nas_phase       */
+    long long phase_calls[NAS_MAX_PHASES];
+    double spmm_bytes;        /* algorithmic bytes of the SpMM launches (N > 1):
+                                 nnz*(8+4) + 4*(n+1) + 2*n*N*8                        */
+    double spmm_flops;        /* 2*nnz*N per SpMM launch                             */
+    long long kernel_launches;/* kernels this library launched during the step       */
+    double spmv_bytes;        /* same for the SpMV launches (N = 1)                  */
+    double spmv_flops;
+} nas_report;
+
+/* ------------------------------------------------------------------ context */
+typedef struct nas_ctx nas_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL = the legacy default stream; pass PyTorch's current stream to
+ * order the library's work with the caller's).  *out receives the context. */
+int  nas_create(nas_ctx** out, int device, void* cuda_stream);
+void nas_destroy(nas_ctx* ctx);
+const char* nas_last_error(const nas_ctx* ctx);
+const char* nas_version(void);
+
+/* Tetrahedral mesh (Sec. 2: a shape-regular decomposition T_h of the box).
+ *  which  : NAS_FINE or NAS_COARSE (the nonnested coarse mesh T_H, Sec. 3.3)
+ *  order  : polynomial order of the Lagrange space on it: 1 or 2 for the fine
+ *           mesh, 1 for the coarse mesh (S_H is P1).
+ *  xyz    : FP64 [n_vert][3] vertex coordinates.
+ *  tet    : int32 [n_tet][4] vertex ids, every tetrahedron positively oriented
+ *           (det[v1-v0, v2-v0, v3-v0] > 0), else NAS_E_MESH.
+ * P2 nodes are the vertices followed by one node per edge (its midpoint),
+ * edges ordered by (smaller, larger) vertex id; element-local order: the 4
+ * vertices, then edges (0,1),(0,2),(0,3),(1,2),(1,3),(2,3).  Boundary nodes
+ * are those on a face of the vertices' bounding box (zero Dirichlet values);
+ * the others, in increasing node id, are the unknowns ("dofs"). Both meshes
+ * must cover the same box.  Setting a mesh invalidates the solver state. */
+int nas_set_mesh(nas_ctx* ctx, int which, int order,
+                 int64_t n_vert, const double* xyz,
+                 int64_t n_tet, const int32_t* tet);
+
+/* Molecule and orbitals (Sec. 2: M nuclei with charges Z_k at R_k, N orbitals).
+ *  R       : FP64 [n_nuc][3];  Z : FP64 [n_nuc]
+ *  potential, smooth_a : see enum nas_potential
+ *  n_orb   : N >= 1;  occ : FP64 [n_orb] occupations f_i (rho = sum f_i psi_i^2). */
+int nas_set_system(nas_ctx* ctx, int n_nuc, const double* R, const double* Z,
+                   int potential, double smooth_a, int n_orb, const double* occ);
+
+int nas_set_options(nas_ctx* ctx, const nas_options* opt);
+
+/* Build every mesh-dependent structure (DOF numbering, CSR patterns, the
+ * transfer I_H^h by GPU point location, K, M, M_Vext, the fixed Galerkin
+ * blocks B_H = I^T M I and A_H^L = I^T A^L I) and the initial state.
+ *  psi0 : NULL -> initial guess = the self-consistent solution in the coarse
+ *         space S_H alone (carried to the fine mesh by I), starting from
+ *         rho = 0; otherwise FP64 [n_dof][n_orb] fine orbitals (host), made
+ *         M-orthonormal by the library, with lambda from their Rayleigh
+ *         quotients and rho_in = sum f psi^2.
+ * Requires both meshes, the system and (optionally) options. */
+int nas_init(nas_ctx* ctx, const double* psi0);
+
+/* One augmented-subspace step (Algorithm 3 body): the N shifted linear
+ * problems (H~ u^_i, v) = (lambda_i + mu)(psi_i, v), the fixed blocks, and the
+ * inner SCF of the small Kohn-Sham problem in S_H + span{u^_i} (eqs. st1-st7),
+ * then the density update.  Fills *rep (may be NULL).  Returns
+ * NAS_E_NOT_CONVERGED if a CG cap was hit (the state is still updated). */
+int nas_step(nas_ctx* ctx, nas_report* rep);
+
+/* Steps until ||rho^(l) - rho^(l-1)||_0 < tol_scf or max_outer steps. */
+int nas_solve(nas_ctx* ctx, nas_report* rep);
+
+/* ------------------------------------------------------------------ data out/in */
+enum nas_quantity {
+    NAS_Q_SIZES = 0,      /* int64[16]: n_dof, nnz, n_coarse_dof, coarse_nnz, n_elem,
+                             n_quad_per_elem, n_node, n_orb, n_boundary, nnz_boundary,
+                             n_vert, order, n_coarse_elem, 0...                       */
+    NAS_Q_EIGVALS,        /* FP64 [N]                                                */
+    NAS_Q_ORBITALS,       /* FP64 [n_dof][N]  Psi (fine interior values)              */
+    NAS_Q_RHO_IN,         /* FP64 [n_elem][nq] density defining the potential         */
+    NAS_Q_RHO_OUT,        /* FP64 [n_elem][nq] sum f psi^2 of the current orbitals     */
+    NAS_Q_VHARTREE,       /* FP64 [n_node] nodal V_Har (boundary values included)     */
+    NAS_Q_UHAT,           /* FP64 [n_dof][N] solutions of the last linear problems    */
+    NAS_Q_ROWPTR,         /* int32 [n_dof+1] CSR pattern of interior matrices         */
+    NAS_Q_COLIDX,         /* int32 [nnz]                                              */
+    NAS_Q_K,              /* FP64 [nnz] stiffness  int grad phi_i . grad phi_j         */
+    NAS_Q_M,              /* FP64 [nnz] mass                                          */
+    NAS_Q_MVEXT,          /* FP64 [nnz] int V_ext phi_i phi_j                         */
+    NAS_Q_ANL,            /* FP64 [nnz] A^NL of the current rho_in (eq. st4)           */
+    NAS_Q_HTILDE,         /* FP64 [nnz] H~ of the last linear problems                 */
+    NAS_Q_TRANSFER_ELEM,  /* int32 [n_dof] coarse element containing each fine dof     */
+    NAS_Q_TRANSFER_COL,   /* int32 [n_dof][4] coarse dof per vertex (-1 = boundary)    */
+    NAS_Q_TRANSFER_W,     /* FP64 [n_dof][4] barycentric weights                       */
+    NAS_Q_FA,             /* FP64 [m][m] last F_A, m = n_coarse_dof + N (dense)        */
+    NAS_Q_FB,             /* FP64 [m][m] last F_B                                      */
+    NAS_Q_DOF_NODE,       /* int32 [n_dof] node id of each dof                          */
+    NAS_Q_ENERGY,         /* FP64 [6]: E, e_band, e_hartree, e_xc, e_vxc, e_nn         */
+    NAS_Q_COUNT
+};
+
+/* Copy quantity `what` into dst (`bytes` = capacity).  on_device = 1: dst is
+ * a device pointer on the context's device.  NAS_E_INVALID_ARG if too small. */
+int nas_get(nas_ctx* ctx, int what, void* dst, size_t bytes, int on_device);
+
+/* Replace the solver state (for checkpoint/resume and end-to-end timing).
+ *  lam    : FP64 [N];  psi : FP64 [n_dof][N];  rho_in : FP64 [n_elem][nq]
+ *  on_device: 1 if the three pointers are device pointers.
+ * The Hartree potential of rho_in is recomputed by one Poisson solve. */
+int nas_set_state(nas_ctx* ctx, const double* lam, const double* psi,
+                  const double* rho_in, int on_device);
+
+/* ------------------------------------------------------------------ single operations
+ * Each runs one piece of the path on the context's current mesh and system,
+ * with inputs and outputs given by pointer (host, or device if on_device).
+ * They expose the kernels for parity tests and benchmarks; the step driver
+ * uses the same kernels. */
+enum nas_op {
+    NAS_OP_LDA = 0,       /* in rho [cnt] -> out [2][cnt]: eps_xc, V_xc (Sec. 3.1)      */
+    NAS_OP_HARTREE,       /* in rho at quad points [n_elem][nq] -> out V_H [n_node]     */
+    NAS_OP_ASSEMBLE_MASS, /* in coefficient c at quad points [n_elem][nq] ->
+                             out [nnz] values of int c phi_i phi_j                       */
+    NAS_OP_DENSITY,       /* in Psi [n_dof][N] -> out rho [n_elem][nq] = sum f psi^2    */
+    NAS_OP_APPLY_H,       /* in X [n_dof][N] -> out H~ X with the last H~ (SpMM)        */
+    NAS_OP_BVP,           /* in R [n_dof][N] -> out solution of H~ U = R (block PCG)    */
+    NAS_OP_GALERKIN,      /* in fine CSR values [nnz] -> out dense I^T A I [nH][nH]     */
+    NAS_OP_COUNT
+};
+int nas_apply(nas_ctx* ctx, int op, const void* in, int64_t cnt, void* out, int on_device);
+
+/* Stand-alone CSR SpMM with N interleaved right-hand sides, FP64, on device
+ * buffers: Y[i][c] = sum_p val[p] X[col[p]][c] for rows i < n_rows.
+ *  row_ptr int32 [n_rows+1], col int32 [nnz], val FP64 [nnz], X FP64
+ *  [n_cols][N], Y FP64 [n_rows][N], all device pointers; stream: cudaStream_t.
+ * This is the kernel that dominates the linear solves (Sec. 3.3, Remark on
+ * the cost of st4 and the N boundary value problems). */
+int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
+                 const double* val, int N, const double* X, double* Y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NAS_H */

@@ -31,6 +31,14 @@ Readings (where the paper is silent, ambiguous or garbled):
   * energy (Sec. 3.1): E = sum_i f_i lambda_i - int (V_H/2 + V_xc) rho
     + E_xc + E_nn, all density-dependent terms at the density rho_in of the
     potential.
+  * basis of the augmented space: before the blocks of eq. st2 are formed, the
+    u^_i are replaced by an M-orthonormal basis of their M-orthogonal
+    complement to I S_H (u^ <- u^ - I B_H^-1 I^T M u^, then u^ <- u^ L^-T with
+    L L^T = u^T M u^).  This spans the same augmented subspace S_H + span{u^_i},
+    so the Ritz pairs of eq. st1 are unchanged; it is needed because with the
+    experiments' large mu each u^_i differs from a coarse-space function only
+    by O(1/mu), which makes F_B in the printed basis nearly singular
+    (condition number ~1e11 on the 8-nucleus workload).
   * initial guess: the self-consistent solution in the coarse space alone
     (S_H carried to the fine mesh by I), from rho = 0, by the same inner SCF.
   * mu defaults to the experiments' 8 M sum_k Z_k^2.
@@ -112,6 +120,7 @@ class Problem:
             self.I, self.I_elem, self.I_W, self.I_C = transfer.build_transfer(f, self.coarse)
             self.B_H = (self.I.T @ self.M @ self.I).toarray()
             self.A_HL = (self.I.T @ self.AL @ self.I).toarray()
+            self.B_H_chol = sla.cho_factor(self.B_H, lower=True)
 
     # ------------------------------------------------------------ potentials
     def nonlinear(self, rho_q, VH_guess=None):
@@ -205,6 +214,8 @@ class Problem:
 
     # ------------------------------------------------------------ Algorithm 3
     def initial_state(self):
+        if self.coarse.n < self.N:
+            raise ValueError("the coarse-space initial guess needs dim S_H >= N")
         zero = np.zeros_like(self.fine.Wq)
         return self.inner_scf(None, zero)
 
@@ -224,8 +235,17 @@ class Problem:
             vxc = np.zeros_like(st.rho_in)
         return st.VH, VHq, eps, vxc
 
+    def augment_basis(self, Uhat):
+        """M-orthonormal basis of the M-orthogonal complement of span{Uhat} to I S_H."""
+        c = self.I.T @ (self.M @ Uhat)
+        Y = sla.cho_solve(self.B_H_chol, c)
+        U = Uhat - self.I @ Y
+        g = U.T @ (self.M @ U)
+        L = np.linalg.cholesky(0.5 * (g + g.T))
+        return sla.solve_triangular(L, U.T, lower=True).T
+
     def step(self, st):
-        Uhat = self.bvp(st)
+        Uhat = self.augment_basis(self.bvp(st))
         new = self.inner_scf(Uhat, st.rho_in, VH_start=st.VH)
         new.info["Uhat"] = Uhat
         new.info["drho"] = self.norm0(new.rho_out - st.rho_out)

@@ -1,0 +1,234 @@
+// C ABI of the nas library (include/nas.h): argument checks, exception to
+// status-code translation, and the context lifecycle.
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+using nas::Error;
+
+namespace {
+
+template <class F>
+int guarded(nas_ctx* c, F&& f) {
+    if (!c) return NAS_E_INVALID_ARG;
+    try {
+        int r = f();
+        if (r == NAS_OK) c->err.clear();
+        return r;
+    } catch (const Error& e) {
+        c->err = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        c->err = "host allocation failed";
+        return NAS_E_OOM;
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return NAS_E_CUDA;
+    }
+}
+
+void invalidate(nas_ctx* c) {
+    c->setup_done = false;
+    c->initialized = false;
+    c->anl_valid = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nas_default_options(nas_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mu = -1.0;
+    o->tol_bvp = 1e-12;
+    o->tol_poisson = 1e-12;
+    o->tol_scf = 1e-8;
+    o->tol_inner = 1e-8;
+    o->max_cg = 2000;
+    o->max_poisson = 20000;
+    o->max_inner = 50;
+    o->max_outer = 100;
+    o->anderson_depth = 5;
+    o->anderson_beta = 0.7;
+    o->hartree = 1;
+    o->xc = 1;
+    o->multipole = 0;
+    o->omega = 1.0;
+    o->check_every = 1;
+    o->timing = 0;
+    o->eig_dense_max = 1200;
+}
+
+const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
+
+int nas_create(nas_ctx** out, int device, void* cuda_stream) {
+    if (!out) return NAS_E_INVALID_ARG;
+    *out = nullptr;
+    nas_ctx* c = new (std::nothrow) nas_ctx();
+    if (!c) return NAS_E_OOM;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        delete c;
+        return NAS_E_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return NAS_E_CUDA;
+    }
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    nas_default_options(&c->opt);
+    *out = c;
+    return NAS_OK;
+}
+
+void nas_destroy(nas_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& p : c->ev_pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+const char* nas_last_error(const nas_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int nas_set_mesh(nas_ctx* c, int which, int order, int64_t n_vert, const double* xyz, int64_t n_tet,
+                 const int32_t* tet) {
+    return guarded(c, [&]() {
+        if (!xyz || !tet || n_vert < 4 || n_tet < 1) nas::fail(NAS_E_INVALID_ARG, "empty mesh");
+        if (which == NAS_FINE) {
+            if (order != 1 && order != 2) nas::fail(NAS_E_INVALID_ARG, "fine order must be 1 or 2");
+            c->fxyz.assign(xyz, xyz + 3 * n_vert);
+            c->ftet.assign(tet, tet + 4 * n_tet);
+            c->fnv = n_vert;
+            c->fne = n_tet;
+            c->fine_order = order;
+            c->have_fine = true;
+        } else if (which == NAS_COARSE) {
+            if (order != 1) nas::fail(NAS_E_INVALID_ARG, "coarse space is P1");
+            c->cxyz.assign(xyz, xyz + 3 * n_vert);
+            c->ctet.assign(tet, tet + 4 * n_tet);
+            c->cnv = n_vert;
+            c->cne = n_tet;
+            c->have_coarse = true;
+        } else {
+            nas::fail(NAS_E_INVALID_ARG, "which must be NAS_FINE or NAS_COARSE");
+        }
+        for (int64_t i = 0; i < 4 * n_tet; ++i)
+            if (tet[i] < 0 || tet[i] >= n_vert) nas::fail(NAS_E_MESH, "vertex id out of range");
+        invalidate(c);
+        return NAS_OK;
+    });
+}
+
+int nas_set_system(nas_ctx* c, int n_nuc, const double* R, const double* Z, int potential, double smooth_a,
+                   int n_orb, const double* occ) {
+    return guarded(c, [&]() {
+        if (n_nuc < 0 || (n_nuc > 0 && (!R || !Z))) nas::fail(NAS_E_INVALID_ARG, "nuclei");
+        if (n_orb < 1 || n_orb > 64) nas::fail(NAS_E_INVALID_ARG, "n_orb must be in 1..64");
+        if (potential < NAS_POT_COULOMB || potential > NAS_POT_HARMONIC) nas::fail(NAS_E_INVALID_ARG, "potential");
+        if (potential == NAS_POT_SMOOTHED && !(smooth_a > 0.0)) nas::fail(NAS_E_INVALID_ARG, "smooth_a must be > 0");
+        c->n_nuc = n_nuc;
+        c->R.assign(R ? R : (const double*)nullptr, R ? R + 3 * n_nuc : (const double*)nullptr);
+        c->Z.assign(Z ? Z : (const double*)nullptr, Z ? Z + n_nuc : (const double*)nullptr);
+        c->potential = potential;
+        c->smooth_a = smooth_a;
+        c->N = n_orb;
+        if (occ)
+            c->occ.assign(occ, occ + n_orb);
+        else
+            c->occ.assign(n_orb, 2.0);
+        c->lam.assign(n_orb, 0.0);
+        c->have_system = true;
+        invalidate(c);
+        return NAS_OK;
+    });
+}
+
+int nas_set_options(nas_ctx* c, const nas_options* o) {
+    return guarded(c, [&]() {
+        if (!o) nas::fail(NAS_E_INVALID_ARG, "null options");
+        if (o->tol_bvp <= 0 || o->tol_poisson <= 0 || o->max_cg < 1 || o->max_poisson < 1 || o->max_inner < 1 ||
+            o->anderson_depth < 1 || o->anderson_depth > 5)
+            nas::fail(NAS_E_INVALID_ARG, "options out of range");
+        bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega);
+        c->opt = *o;
+        if (rebuild && c->setup_done) invalidate(c);
+        return NAS_OK;
+    });
+}
+
+int nas_init(nas_ctx* c, const double* psi0) {
+    return guarded(c, [&]() {
+        NAS_CUDA(cudaSetDevice(c->device));
+        if (!c->setup_done) nas::ctx_setup(c);
+        nas::ctx_init(c, psi0);
+        return NAS_OK;
+    });
+}
+
+int nas_step(nas_ctx* c, nas_report* rep) {
+    return guarded(c, [&]() {
+        NAS_CUDA(cudaSetDevice(c->device));
+        return nas::ctx_step(c, rep);
+    });
+}
+
+int nas_solve(nas_ctx* c, nas_report* rep) {
+    return guarded(c, [&]() {
+        NAS_CUDA(cudaSetDevice(c->device));
+        int status = NAS_OK;
+        nas_report r;
+        for (int l = 0; l < c->opt.max_outer; ++l) {
+            status = nas::ctx_step(c, &r);
+            if (r.drho < c->opt.tol_scf) break;
+        }
+        if (rep) *rep = r;
+        return status;
+    });
+}
+
+int nas_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {
+    return guarded(c, [&]() {
+        if (!dst) nas::fail(NAS_E_INVALID_ARG, "null destination");
+        NAS_CUDA(cudaSetDevice(c->device));
+        nas::ctx_get(c, what, dst, bytes, on_device);
+        return NAS_OK;
+    });
+}
+
+int nas_set_state(nas_ctx* c, const double* lam, const double* psi, const double* rho_in, int on_device) {
+    return guarded(c, [&]() {
+        NAS_CUDA(cudaSetDevice(c->device));
+        nas::ctx_set_state(c, lam, psi, rho_in, on_device);
+        return NAS_OK;
+    });
+}
+
+int nas_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int on_device) {
+    return guarded(c, [&]() {
+        NAS_CUDA(cudaSetDevice(c->device));
+        nas::ctx_apply(c, op, in, cnt, out, on_device);
+        return NAS_OK;
+    });
+}
+
+int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* val, int N,
+                 const double* X, double* Y, void* stream) {
+    if (n_rows < 0 || N < 1 || !row_ptr || !col || !val || !X || !Y) return NAS_E_INVALID_ARG;
+    try {
+        nas::Csr A{n_rows, row_ptr, col, val};
+        nas::launch_spmm(A, N, X, Y, 1.0, 0.0, static_cast<cudaStream_t>(stream));
+        return NAS_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+}  // extern "C"

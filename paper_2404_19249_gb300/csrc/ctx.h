@@ -1,0 +1,121 @@
+// Solver context: inputs, host topology, device data and state of the
+// augmented subspace method.  Internal; the C ABI only sees nas_ctx*.
+#pragma once
+
+#include <array>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "kernels.h"
+#include "space.h"
+#include "transfer_setup.h"
+
+struct nas_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    nas_options opt{};
+
+    // ---- inputs
+    bool have_fine = false, have_coarse = false, have_system = false;
+    int fine_order = 1;
+    std::vector<double> fxyz, cxyz;
+    std::vector<int32_t> ftet, ctet;
+    int64_t fnv = 0, fne = 0, cnv = 0, cne = 0;
+    int n_nuc = 0;
+    std::vector<double> R, Z;
+    int potential = NAS_POT_COULOMB;
+    double smooth_a = 0.0;
+    int N = 0;
+    std::vector<double> occ;
+
+    // ---- derived
+    bool setup_done = false, initialized = false;
+    nas::HostSpace F, C;
+    nas::BucketGrid BG;
+    nas::GalerkinMaps GM;
+    double mu = 0.0, Enn = 0.0;
+    int64_t nq = 0;      // quadrature points per element
+    int64_t nqt = 0;     // total quadrature points ne*nq
+    int64_t nH = 0;      // coarse dofs
+    std::vector<int32_t> I_elem, I_col;
+    std::vector<double> I_val;
+    std::vector<double> BH, AHL;          // coarse Galerkin values [hnnz]
+    std::vector<double> BH_chol;          // dense Cholesky factor of B_H [nH][nH]
+
+    // ---- device: fine mesh
+    nas::DBuf<double> d_vxyz, d_node_xyz, d_Wq;
+    nas::DBuf<int32_t> d_elem, d_dof_of_node, d_dof_node, d_bnd_node;
+    nas::DBuf<int32_t> d_rowptr, d_col, d_contrib, d_browptr, d_bcol, d_bcontrib, d_lcontrib;
+    nas::DBuf<int64_t> d_cptr, d_bcptr, d_lptr;
+    nas::DBuf<double> d_K, d_M, d_Mvext, d_AL, d_ANL, d_H, d_KIB, d_Hdinv, d_Kdinv;
+    nas::DBuf<double> d_L, d_Lv;                       // element matrices / vectors
+    nas::DBuf<double> d_coef, d_eps, d_vxc, d_tmpq;    // [nqt]
+    nas::DBuf<double> d_rho_in, d_rho_out, d_rho_prev; // [nqt]
+    std::vector<nas::DBuf<double>> d_hist_rin, d_hist_F;
+    nas::DBuf<double> d_VH, d_wB;                      // [nnode], [nb]
+    nas::DBuf<double> d_R, d_Zn;                       // nuclei
+    // ---- device: transfer
+    nas::DBuf<double> d_cxyz;
+    nas::DBuf<int32_t> d_ctet, d_cdof, d_btet, d_Ielem, d_Icol;
+    nas::DBuf<int64_t> d_bptr;
+    nas::DBuf<double> d_Ival;
+    nas::DBuf<int32_t> d_tptr, d_trow, d_wptr, d_wcol, d_wrow, d_w1con, d_hptr, d_hcol, d_h2con;
+    nas::DBuf<int64_t> d_w1ptr, d_h2ptr;
+    nas::DBuf<double> d_tval, d_W, d_AH;
+    // ---- device: orbitals and solver work
+    nas::DBuf<double> d_Psi, d_Uhat, d_occ, d_U;
+    nas::DBuf<double> d_X1, d_X2;                      // [n][N] temporaries
+    nas::DBuf<double> d_cg_R, d_cg_Z, d_cg_P, d_cg_Q, d_cg_B;
+    nas::DBuf<double> d_cg_scal;                       // 8*N scalars
+    nas::DBuf<int> d_cg_active, d_flag;
+    nas::DBuf<double> d_pv, d_pb;                      // Poisson vectors [n]
+    nas::DBuf<double> d_blk_b, d_blk_c;                // [nH][N]
+    nas::DBuf<double> d_blk_beta, d_blk_gamma;         // [N][N]
+    nas::DBuf<double> d_partial, d_red;                // reduction scratch
+    nas::DBuf<double> d_moments;
+
+    // ---- state (host)
+    std::vector<double> lam;            // [N]
+    bool have_VH = false;
+    bool anl_valid = false;             // d_ANL/d_eps/d_vxc match d_rho_in and d_VH
+    int step_count = 0;
+    int last_cg = 0, last_poisson = 0, last_inner = 0, last_inner_conv = 0;
+    double last_drho = 0.0, last_inner_res = 0.0;
+    std::array<double, 6> energy{};
+    // host copies of the last small problem
+    int last_m = 0;
+    std::vector<double> FA, FB;
+    // blocks fixed during an inner SCF
+    std::vector<double> hb_cH, hb_gamma, hb_bHL, hb_betaL;
+    int Na = 0;                         // augmentation columns in use (0 or N)
+    std::vector<double> U_warm;         // warm start of the small eigensolver [m][N]
+    int last_lobpcg_iters = 0;
+
+    // ---- timing
+    double phase_ms[NAS_MAX_PHASES] = {0};
+    long long phase_calls[NAS_MAX_PHASES] = {0};
+    double spmm_bytes = 0, spmm_flops = 0, spmv_bytes = 0, spmv_flops = 0;
+    struct EvPair {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<EvPair> ev_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    long long launches_at_step_start = 0;
+};
+
+namespace nas {
+
+// driver entry points (driver.cpp)
+void ctx_setup(nas_ctx* c);
+void ctx_init(nas_ctx* c, const double* psi0);
+int ctx_step(nas_ctx* c, nas_report* rep);
+void ctx_fill_report(nas_ctx* c, nas_report* rep);
+void ctx_set_state(nas_ctx* c, const double* lam, const double* psi, const double* rho, int on_device);
+void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int on_device);
+void ctx_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device);
+
+}  // namespace nas

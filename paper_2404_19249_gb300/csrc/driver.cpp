@@ -1,0 +1,1027 @@
+// Step driver of the augmented subspace method (Algorithm 3, Sec. 3.3).
+//
+// Host code orders the GPU kernels on the context's stream and solves the
+// small eigenproblem F_A U = lambda F_B U (eq. st1) on the host.  The flow of
+// one step:
+//   H~ = A^L + A^NL(rho_in) + mu M                        (st3, st4 + shift)
+//   block PCG:  H~ U^ = M Psi diag(lambda + mu)           (Aux_Linear_Problem)
+//   fixed blocks c_H = I^T M U^, gamma = U^T M U^; linear parts of b_H, beta
+//   inner SCF: Hartree Poisson solve, V_xc, A^NL, A_H = I^T A I (st5),
+//              b_H = I^T A U^ (st6), beta = U^T A U^ (st7), host eigensolve,
+//              Psi = I u_H + U^ alpha, rho_out = sum f psi^2, Anderson mixing.
+// Readings of the paper that this code follows (same as the CPU oracle):
+// rho = sum_i f_i psi_i^2; F_A is built from H without mu; B_H = I^T M_h I;
+// the inner SCF runs to ||rho_out - rho_in||_0 < tol_inner; the potential
+// density rho_in of the last inner iteration defines H~ of the next step;
+// the initial state is the self-consistent solution in S_H alone from rho = 0.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.h"
+#include "small_eig.h"
+
+namespace nas {
+
+long long g_launch_count = 0;
+
+// ------------------------------------------------------------------ helpers
+static Mesh fmesh(nas_ctx* c) {
+    return Mesh{c->F.ne, c->F.nloc, (int)c->nq, c->d_vxyz.p, c->d_elem.p};
+}
+static Csr fcsr(nas_ctx* c, const double* val) { return Csr{c->F.n, c->d_rowptr.p, c->d_col.p, val}; }
+
+static cudaEvent_t ev_get(nas_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    NAS_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+// CUDA-event timer of one phase on the context stream (only with opt.timing)
+struct Phase {
+    nas_ctx* c;
+    int ph;
+    cudaEvent_t a = nullptr;
+    Phase(nas_ctx* cc, int p) : c(cc), ph(p) {
+        if (c->opt.timing) {
+            a = ev_get(c);
+            NAS_CUDA(cudaEventRecord(a, c->stream));
+        }
+    }
+    ~Phase() {
+        if (a) {
+            cudaEvent_t b = ev_get(c);
+            cudaEventRecord(b, c->stream);
+            c->ev_pending.push_back({ph, a, b});
+        }
+    }
+};
+
+static void resolve_events(nas_ctx* c) {
+    if (c->ev_pending.empty()) return;
+    NAS_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto& p : c->ev_pending) {
+        float ms = 0.f;
+        NAS_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        c->phase_ms[p.phase] += ms;
+        c->phase_calls[p.phase] += 1;
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->ev_pending.clear();
+}
+
+static void sync(nas_ctx* c) { NAS_CUDA(cudaStreamSynchronize(c->stream)); }
+
+static void spmm(nas_ctx* c, const Csr& A, int N, const double* X, double* Y, double alpha = 1.0,
+                 double beta = 0.0) {
+    Phase t(c, N > 1 ? NAS_PH_SPMM : NAS_PH_SPMV);
+    launch_spmm(A, N, X, Y, alpha, beta, c->stream);
+    int64_t nnz = 0;
+    if (A.rowptr == c->d_rowptr.p) nnz = c->F.nnz();
+    else if (A.rowptr == c->d_browptr.p) nnz = c->F.nnzb();
+    double bytes = (double)nnz * 12.0 + 4.0 * (A.n_rows + 1) + 2.0 * A.n_rows * N * 8.0 +
+                   (beta != 0.0 ? A.n_rows * N * 8.0 : 0.0);
+    if (N > 1) {
+        c->spmm_bytes += bytes;
+        c->spmm_flops += 2.0 * nnz * N;
+    } else {
+        c->spmv_bytes += bytes;
+        c->spmv_flops += 2.0 * nnz;
+    }
+}
+
+static double* scal(nas_ctx* c, int k, int N) { return c->d_cg_scal.p + (int64_t)k * N; }
+
+// Block Jacobi-preconditioned CG on A X = B (N independent columns); X holds
+// the initial guess.  Returns the iteration count; throws on breakdown.
+static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double* B, double* X, double tol,
+               int maxit, bool* converged) {
+    const int64_t n = A.n_rows;
+    cudaStream_t s = c->stream;
+    double *R = c->d_cg_R.p, *Zb = c->d_cg_Z.p, *P = c->d_cg_P.p, *Q = c->d_cg_Q.p;
+    PcgCols pc{N, scal(c, 0, N), scal(c, 1, N), scal(c, 2, N), scal(c, 3, N), scal(c, 4, N), scal(c, 5, N),
+               scal(c, 6, N), c->d_cg_active.p, c->d_flag.p, tol * tol};
+    NAS_CUDA(cudaMemsetAsync(c->d_flag.p, 0, sizeof(int), s));
+    spmm(c, A, N, X, R);
+    launch_sub_from(n * N, B, R, s);
+    launch_scale_rows(n, N, Dinv, R, Zb, s);
+    NAS_CUDA(cudaMemcpyAsync(P, Zb, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
+    {
+        const double* X1[1] = {R};
+        const double* Y1[1] = {Zb};
+        launch_coldots(n, N, 1, X1, Y1, nullptr, c->d_partial.p, pc.rz, s);
+        const double* X2[2] = {R, B};
+        const double* Y2[2] = {R, B};
+        launch_coldots(n, N, 2, X2, Y2, nullptr, c->d_partial.p, pc.rr, s);  // rr, bb contiguous
+    }
+    std::vector<double> h(2 * N);
+    NAS_CUDA(cudaMemcpyAsync(h.data(), pc.rr, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, s));
+    sync(c);
+    std::vector<int> act(N);
+    int nact = 0;
+    for (int j = 0; j < N; ++j) {
+        act[j] = (h[N + j] > 0.0 && h[j] > tol * tol * h[N + j]) ? 1 : 0;
+        nact += act[j];
+        if (!std::isfinite(h[j])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
+    }
+    NAS_CUDA(cudaMemcpyAsync(c->d_cg_active.p, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    int it = 0;
+    const int every = std::max(1, c->opt.check_every);
+    while (nact > 0 && it < maxit) {
+        spmm(c, A, N, P, Q);
+        {
+            const double* X1[1] = {P};
+            const double* Y1[1] = {Q};
+            launch_coldots(n, N, 1, X1, Y1, nullptr, c->d_partial.p, pc.pq, s);
+        }
+        launch_pcg_alpha(pc, s);
+        launch_pcg_update(n, N, pc.alpha, pc.active, P, Q, Dinv, X, R, Zb, s);
+        {
+            const double* X2[2] = {R, R};
+            const double* Y2[2] = {Zb, R};
+            launch_coldots(n, N, 2, X2, Y2, nullptr, c->d_partial.p, pc.rz_new, s);  // rz_new, rr
+        }
+        launch_pcg_beta(pc, s);
+        launch_pcg_direction(n, N, pc.beta, pc.active, Zb, P, s);
+        ++it;
+        if (it % every == 0 || it >= maxit) {
+            NAS_CUDA(cudaMemcpyAsync(act.data(), c->d_cg_active.p, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+            int bd = 0;
+            NAS_CUDA(cudaMemcpyAsync(&bd, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            sync(c);
+            if (bd) fail(NAS_E_BREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite)");
+            nact = 0;
+            for (int j = 0; j < N; ++j) nact += act[j];
+        }
+    }
+    *converged = (nact == 0);
+    return it;
+}
+
+// ------------------------------------------------------------------ Hartree (Sec. 3.1)
+// V_H nodal into `VH` (boundary included): monopole/quadrupole boundary
+// values, b = 4 pi int rho phi_i - K_IB w_B, PCG on K_II with warm start VH.
+static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
+    Phase t(c, NAS_PH_POISSON);
+    cudaStream_t s = c->stream;
+    Mesh m = fmesh(c);
+    launch_moments(m, c->d_Wq.p, rho, c->d_partial.p, c->d_moments.p, s);
+    launch_boundary_values(c->F.nb, c->d_bnd_node.p, c->d_node_xyz.p, c->d_moments.p, c->opt.multipole,
+                           c->d_wB.p, VH, s);
+    launch_local_load(m, c->d_Wq.p, rho, c->d_Lv.p, s);
+    launch_gather(c->F.n, c->d_lptr.p, c->d_lcontrib.p, c->d_Lv.p, 4.0 * M_PI, c->d_pb.p, s);
+    Csr KIB{c->F.n, c->d_browptr.p, c->d_bcol.p, c->d_KIB.p};
+    if (c->F.nnzb() > 0) spmm(c, KIB, 1, c->d_wB.p, c->d_pb.p, -1.0, 1.0);
+    launch_nodal_to_dof(c->F.n, c->d_dof_node.p, VH, c->d_pv.p, s);
+    int it = pcg(c, fcsr(c, c->d_K.p), c->d_Kdinv.p, 1, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson,
+                 c->opt.max_poisson, conv);
+    launch_dof_to_nodal(c->F.n, c->d_dof_node.p, c->d_pv.p, VH, s);
+    return it;
+}
+
+// A^NL of the density in d_rho_in (and V_H in d_VH): coefficient, element
+// matrices, gather (eq. st4)
+static void assemble_nl(nas_ctx* c) {
+    Phase t(c, NAS_PH_ASSEMBLY);
+    Mesh m = fmesh(c);
+    launch_nl_coef(m, c->opt.hartree ? c->d_VH.p : nullptr, c->d_rho_in.p, c->opt.xc, c->d_coef.p, c->d_eps.p,
+                   c->d_vxc.p, c->stream);
+    launch_local_mass(m, c->d_Wq.p, c->d_coef.p, c->d_L.p, c->stream);
+    launch_gather(c->F.nnz(), c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, c->d_ANL.p, c->stream);
+}
+
+static void galerkin(nas_ctx* c, const double* fine_vals, double* coarse_vals) {
+    launch_galerkin1(c->GM.wnnz(), c->d_w1ptr.p, c->d_w1con.p, fine_vals, c->d_col.p, c->d_Ival.p, c->d_W.p,
+                     c->stream);
+    launch_galerkin2(c->GM.hnnz(), c->d_h2ptr.p, c->d_h2con.p, c->d_W.p, c->d_wrow.p, c->d_Ival.p, coarse_vals,
+                     c->stream);
+}
+
+static double weighted_norm_diff(nas_ctx* c, const double* a, const double* b) {
+    launch_axpby(c->nqt, 1.0, a, -1.0, b, c->d_tmpq.p, c->stream);
+    const double* X[1] = {c->d_tmpq.p};
+    launch_coldots(c->nqt, 1, 1, X, X, c->d_Wq.p, c->d_partial.p, c->d_red.p, c->stream);
+    double r = 0.0;
+    NAS_CUDA(cudaMemcpyAsync(&r, c->d_red.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    sync(c);
+    return std::sqrt(std::max(r, 0.0));
+}
+
+// ------------------------------------------------------------------ Anderson (Sec. 5, mix2-mix6)
+struct Anderson {
+    std::deque<int> hist;  // slot ids, oldest first
+    int next_free = 0;
+};
+
+static void anderson_mix(nas_ctx* c, Anderson& A) {
+    Phase t(c, NAS_PH_MIXING);
+    cudaStream_t s = c->stream;
+    const int depth = std::max(1, std::min(c->opt.anderson_depth, 5));
+    int slot;
+    if ((int)A.hist.size() >= depth) {
+        slot = A.hist.front();
+        A.hist.pop_front();
+    } else {
+        slot = (int)A.hist.size();
+        // find a slot not in use
+        for (int k = 0; k < depth; ++k)
+            if (std::find(A.hist.begin(), A.hist.end(), k) == A.hist.end()) {
+                slot = k;
+                break;
+            }
+    }
+    NAS_CUDA(cudaMemcpyAsync(c->d_hist_rin[slot].p, c->d_rho_in.p, sizeof(double) * c->nqt,
+                             cudaMemcpyDeviceToDevice, s));
+    launch_axpby(c->nqt, 1.0, c->d_rho_out.p, -1.0, c->d_rho_in.p, c->d_hist_F[slot].p, s);
+    A.hist.push_back(slot);
+    const double beta = c->opt.anderson_beta;
+    while (true) {
+        int mprev = (int)A.hist.size() - 1;
+        if (mprev == 0) {
+            launch_axpby(c->nqt, 1.0, c->d_rho_in.p, beta, c->d_hist_F[slot].p, c->d_rho_in.p, s);
+            return;
+        }
+        const double* Fp[6];
+        const double* Rp[6];
+        for (int j = 0; j <= mprev; ++j) {
+            Fp[j] = c->d_hist_F[A.hist[j]].p;
+            Rp[j] = c->d_hist_rin[A.hist[j]].p;
+        }
+        launch_anderson_dots(c->nqt, mprev, Fp, c->d_Wq.p, c->d_partial.p, c->d_red.p, s);
+        std::vector<double> h(mprev * mprev + mprev);
+        NAS_CUDA(cudaMemcpyAsync(h.data(), c->d_red.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+        sync(c);
+        std::vector<double> Am(h.begin(), h.begin() + mprev * mprev), w(mprev), V(mprev * mprev);
+        std::vector<double> Acopy(Am);
+        jacobi_eig(mprev, Acopy.data(), w.data(), V.data());
+        double amax = 0.0, amin = 1e300;
+        for (int k = 0; k < mprev; ++k) {
+            amax = std::max(amax, std::fabs(w[k]));
+            amin = std::min(amin, std::fabs(w[k]));
+        }
+        bool bad = !(amin > 0.0) || amax / amin > 1e12;
+        std::vector<double> alpha(mprev);
+        if (!bad && small_solve(mprev, Am.data(), h.data() + mprev * mprev, alpha.data()) != 0) bad = true;
+        if (bad) {
+            A.hist.pop_front();
+            continue;
+        }
+        launch_anderson_mix(c->nqt, mprev, Rp, Fp, alpha.data(), beta, c->d_rho_in.p, s);
+        return;
+    }
+}
+
+// ------------------------------------------------------------------ energies (Sec. 3.1)
+static void energies(nas_ctx* c) {
+    cudaStream_t s = c->stream;
+    launch_nodal_to_quad(fmesh(c), c->d_VH.p, c->d_tmpq.p, s);
+    const double* X[3] = {c->d_tmpq.p, c->d_vxc.p, c->d_eps.p};
+    const double* Y[3] = {c->d_rho_in.p, c->d_rho_in.p, c->d_rho_in.p};
+    launch_coldots(c->nqt, 1, 3, X, Y, c->d_Wq.p, c->d_partial.p, c->d_red.p, s);
+    double r[3];
+    NAS_CUDA(cudaMemcpyAsync(r, c->d_red.p, sizeof(r), cudaMemcpyDeviceToHost, s));
+    sync(c);
+    double band = 0.0;
+    for (int i = 0; i < c->N; ++i) band += c->occ[i] * c->lam[i];
+    double eh = 0.5 * r[0], evxc = r[1], exc = r[2];
+    c->energy = {band - eh - evxc + exc + c->Enn, band, eh, exc, evxc, c->Enn};
+}
+
+// ------------------------------------------------------------------ small problem
+static void dense_from_coarse(nas_ctx* c, const std::vector<double>& vals, std::vector<double>& D, int m) {
+    // write coarse CSR values into the leading nH x nH block of D [m][m]
+    for (int64_t a = 0; a < c->nH; ++a)
+        for (int p = c->GM.hptr[a]; p < c->GM.hptr[a + 1]; ++p) D[a * m + c->GM.hcol[p]] = vals[p];
+}
+
+static void fill_aug(nas_ctx* c, std::vector<double>& D, int m, const std::vector<double>& blk,
+                     const std::vector<double>& corner) {
+    const int64_t nH = c->nH;
+    const int Na = c->Na;
+    for (int64_t a = 0; a < nH; ++a)
+        for (int j = 0; j < Na; ++j) {
+            D[a * m + nH + j] = blk[a * Na + j];
+            D[(nH + j) * m + a] = blk[a * Na + j];
+        }
+    for (int i = 0; i < Na; ++i)
+        for (int j = 0; j < Na; ++j) D[(nH + i) * m + nH + j] = corner[i * Na + j];
+}
+
+// blocks of A (fine CSR values) against [I, U^]: returns coarse values, b (nH x Na), beta (Na x Na)
+static void blocks_of(nas_ctx* c, const double* Avals, std::vector<double>* AHv, std::vector<double>& b,
+                      std::vector<double>& beta) {
+    Phase t(c, NAS_PH_BLOCKS);
+    cudaStream_t s = c->stream;
+    const int N = c->N, Na = c->Na;
+    if (AHv) {
+        galerkin(c, Avals, c->d_AH.p);
+        AHv->resize(c->GM.hnnz());
+        NAS_CUDA(cudaMemcpyAsync(AHv->data(), c->d_AH.p, sizeof(double) * c->GM.hnnz(), cudaMemcpyDeviceToHost, s));
+    }
+    if (Na > 0) {
+        spmm(c, fcsr(c, Avals), N, c->d_Uhat.p, c->d_X1.p);
+        launch_transpose_apply(c->nH, c->d_tptr.p, c->d_trow.p, c->d_tval.p, N, c->d_X1.p, c->d_blk_b.p, s);
+        launch_gram(c->F.n, N, c->d_Uhat.p, N, c->d_X1.p, c->d_partial.p, c->d_blk_beta.p, s);
+        b.resize(c->nH * N);
+        beta.resize(N * N);
+        NAS_CUDA(cudaMemcpyAsync(b.data(), c->d_blk_b.p, sizeof(double) * c->nH * N, cudaMemcpyDeviceToHost, s));
+        NAS_CUDA(cudaMemcpyAsync(beta.data(), c->d_blk_beta.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+    }
+    sync(c);
+}
+
+// Host solve of F_A U = lambda F_B U for the lowest N pairs: dense (Cholesky
+// reduction + tridiagonal bisection) up to opt.eig_dense_max, else LOBPCG on
+// the arrow-structured pencil, warm-started from the previous solution.
+static void host_eig(nas_ctx* c, int m) {
+    double t0 = wall_ms();
+    std::vector<double> lam(c->N), U((size_t)m * c->N);
+    if (m <= c->opt.eig_dense_max) {
+        if (dense_gen_eig(m, c->FA.data(), c->FB.data(), c->N, lam.data(), U.data()) != 0)
+            fail(NAS_E_EIGEN, "small eigenproblem: F_B is not positive definite");
+    } else {
+        const int64_t nH = c->nH;
+        const int Na = c->Na;
+        // arrow form: coarse CSR values + dense border, from the dense F_A/F_B
+        std::vector<double> as(c->GM.hnnz()), bs(c->GM.hnnz()), ab(nH * Na), bb(nH * Na), ac(Na * Na), bc(Na * Na);
+        for (int64_t a = 0; a < nH; ++a)
+            for (int p = c->GM.hptr[a]; p < c->GM.hptr[a + 1]; ++p) {
+                as[p] = c->FA[a * m + c->GM.hcol[p]];
+                bs[p] = c->FB[a * m + c->GM.hcol[p]];
+            }
+        for (int64_t a = 0; a < nH; ++a)
+            for (int j = 0; j < Na; ++j) {
+                ab[a * Na + j] = c->FA[a * m + nH + j];
+                bb[a * Na + j] = c->FB[a * m + nH + j];
+            }
+        for (int i = 0; i < Na; ++i)
+            for (int j = 0; j < Na; ++j) {
+                ac[i * Na + j] = c->FA[(nH + i) * m + nH + j];
+                bc[i * Na + j] = c->FB[(nH + i) * m + nH + j];
+            }
+        ArrowMat A{nH, Na, c->GM.hptr.data(), c->GM.hcol.data(), as.data(), ab.data(), ac.data()};
+        ArrowMat B{nH, Na, c->GM.hptr.data(), c->GM.hcol.data(), bs.data(), bb.data(), bc.data()};
+        bool warm = (int64_t)c->U_warm.size() == (int64_t)m * c->N;
+        if (warm) U = c->U_warm;
+        int it = lobpcg_arrow(A, B, c->N, std::max(4, c->N / 4), lam.data(), U.data(), warm, 1e-11, 2000);
+        if (it < 0) fail(NAS_E_EIGEN, "small eigenproblem: LOBPCG did not converge");
+        c->last_lobpcg_iters += it;
+    }
+    c->U_warm = U;
+    c->lam = lam;
+    NAS_CUDA(cudaMemcpyAsync(c->d_U.p, U.data(), sizeof(double) * m * c->N, cudaMemcpyHostToDevice, c->stream));
+    sync(c);
+    c->phase_ms[NAS_PH_HOST_EIG] += wall_ms() - t0;
+    c->phase_calls[NAS_PH_HOST_EIG] += 1;
+}
+
+// inner SCF of the small Kohn-Sham problem in S_H + span{U^} (Na = 0: S_H only)
+static void inner_scf(nas_ctx* c, bool reuse_first) {
+    const int Na = c->Na;
+    const int64_t nH = c->nH;
+    const int m = (int)(nH + Na);
+    cudaStream_t s = c->stream;
+    c->last_m = m;
+    std::vector<double> FB0((size_t)m * m, 0.0), FA0((size_t)m * m, 0.0);
+    dense_from_coarse(c, c->BH, FB0, m);
+    dense_from_coarse(c, c->AHL, FA0, m);
+    if (Na > 0) {
+        fill_aug(c, FB0, m, c->hb_cH, c->hb_gamma);
+        fill_aug(c, FA0, m, c->hb_bHL, c->hb_betaL);
+    }
+    c->FB = FB0;
+    Anderson A;
+    int poisson = 0;
+    double res = 0.0;
+    int t = 0;
+    bool conv = false;
+    std::vector<double> AHnl, bnl, betanl;
+    for (t = 0; t < c->opt.max_inner; ++t) {
+        if (!(t == 0 && reuse_first && c->anl_valid)) {
+            if (c->opt.hartree) {
+                bool pc;
+                poisson += hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
+                if (!pc) fail(NAS_E_NOT_CONVERGED, "Poisson PCG hit its iteration cap");
+            }
+            assemble_nl(c);
+            c->anl_valid = true;
+        }
+        blocks_of(c, c->d_ANL.p, &AHnl, bnl, betanl);
+        c->FA = FA0;
+        for (int64_t a = 0; a < nH; ++a)
+            for (int p = c->GM.hptr[a]; p < c->GM.hptr[a + 1]; ++p) c->FA[a * m + c->GM.hcol[p]] += AHnl[p];
+        if (Na > 0) {
+            for (int64_t a = 0; a < nH; ++a)
+                for (int j = 0; j < Na; ++j) {
+                    c->FA[a * m + nH + j] += bnl[a * Na + j];
+                    c->FA[(nH + j) * m + a] += bnl[a * Na + j];
+                }
+            for (int i = 0; i < Na; ++i)
+                for (int j = 0; j < Na; ++j) c->FA[(nH + i) * m + nH + j] += betanl[i * Na + j];
+        }
+        host_eig(c, m);
+        {
+            Phase ph(c, NAS_PH_DENSITY);
+            launch_reconstruct(c->F.n, c->d_Icol.p, c->d_Ival.p, c->N, c->d_U.p, nH, Na, c->d_Uhat.p, c->d_Psi.p, s);
+            launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, c->N, c->d_occ.p, c->d_rho_out.p, s);
+        }
+        res = weighted_norm_diff(c, c->d_rho_out.p, c->d_rho_in.p);
+        if (!std::isfinite(res)) fail(NAS_E_BREAKDOWN, "non-finite density residual");
+        if (res < c->opt.tol_inner) {
+            conv = true;
+            ++t;
+            break;
+        }
+        if (t == c->opt.max_inner - 1) {
+            ++t;
+            break;
+        }
+        anderson_mix(c, A);
+        c->anl_valid = false;
+    }
+    c->last_inner = t;
+    c->last_inner_conv = conv ? 1 : 0;
+    c->last_inner_res = res;
+    c->last_poisson = poisson;
+}
+
+// Replace U^ by an M-orthonormal basis of its M-orthogonal complement to I S_H:
+// U^ <- U^ - I B_H^-1 I^T M U^, then U^ <- U^ L^-T with L L^T = U^T M U^.  The
+// augmented subspace S_H + span{u^_i} (and so every Ritz pair of eq. st1) is
+// unchanged; the printed basis makes F_B nearly singular when mu is large,
+// because each u^_i then differs from a coarse-space function by O(1/mu).
+static void augment_basis(nas_ctx* c) {
+    Phase t(c, NAS_PH_BLOCKS);
+    cudaStream_t s = c->stream;
+    const int64_t n = c->F.n, nH = c->nH;
+    const int N = c->N;
+    spmm(c, fcsr(c, c->d_M.p), N, c->d_Uhat.p, c->d_X1.p);
+    launch_transpose_apply(nH, c->d_tptr.p, c->d_trow.p, c->d_tval.p, N, c->d_X1.p, c->d_blk_c.p, s);
+    std::vector<double> Y(nH * N), Uf((nH + N) * N, 0.0);
+    NAS_CUDA(cudaMemcpyAsync(Y.data(), c->d_blk_c.p, sizeof(double) * nH * N, cudaMemcpyDeviceToHost, s));
+    sync(c);
+    chol_solve((int)nH, c->BH_chol.data(), N, Y.data());
+    for (int64_t i = 0; i < nH * N; ++i) Uf[i] = -Y[i];
+    for (int j = 0; j < N; ++j) Uf[(nH + j) * N + j] = 1.0;
+    NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
+    launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, nH, N, c->d_Uhat.p, c->d_X2.p, s);
+    spmm(c, fcsr(c, c->d_M.p), N, c->d_X2.p, c->d_X1.p);
+    launch_gram(n, N, c->d_X2.p, N, c->d_X1.p, c->d_partial.p, c->d_blk_gamma.p, s);
+    std::vector<double> g(N * N);
+    NAS_CUDA(cudaMemcpyAsync(g.data(), c->d_blk_gamma.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+    sync(c);
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < a; ++b) g[a * N + b] = g[b * N + a] = 0.5 * (g[a * N + b] + g[b * N + a]);
+    if (chol_factor(N, g.data()) != 0)
+        fail(NAS_E_BREAKDOWN, "augmentation vectors are linearly dependent on the coarse space");
+    // L^-T: solve L^T X = I column by column (X upper triangular)
+    std::vector<double> Linv_T(N * N, 0.0);
+    for (int col = 0; col < N; ++col)
+        for (int r = N - 1; r >= 0; --r) {
+            double v = (r == col) ? 1.0 : 0.0;
+            for (int q = r + 1; q < N; ++q) v -= g[q * N + r] * Linv_T[q * N + col];
+            Linv_T[r * N + col] = v / g[r * N + r];
+        }
+    // warm start of the small eigensolver: Psi ~ raw U^ = I Y + U^_new L^T
+    c->U_warm.assign((nH + N) * N, 0.0);
+    for (int64_t i = 0; i < nH * N; ++i) c->U_warm[i] = Y[i];
+    for (int a = 0; a < N; ++a)
+        for (int b = a; b < N; ++b) c->U_warm[(nH + a) * N + b] = g[b * N + a];
+    std::fill(Uf.begin(), Uf.end(), 0.0);
+    for (int i = 0; i < N * N; ++i) Uf[nH * N + i] = Linv_T[i];
+    NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
+    launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, nH, N, c->d_X2.p, c->d_Uhat.p, s);
+}
+
+// ------------------------------------------------------------------ setup
+static void alloc_work(nas_ctx* c) {
+    const int64_t n = c->F.n, N = c->N;
+    const int64_t nqt = c->nqt;
+    c->d_Psi.alloc(n * N);
+    c->d_Uhat.alloc(n * N);
+    c->d_X1.alloc(n * N);
+    c->d_X2.alloc(n * N);
+    for (auto* b : {&c->d_cg_R, &c->d_cg_Z, &c->d_cg_P, &c->d_cg_Q, &c->d_cg_B}) b->alloc(n * N);
+    c->d_cg_scal.alloc(8 * N + 8);
+    c->d_cg_active.alloc(N + 1);
+    c->d_flag.alloc(4);
+    c->d_pv.alloc(n);
+    c->d_pb.alloc(n);
+    c->d_U.alloc((c->nH + N) * N);
+    c->d_blk_b.alloc(c->nH * N);
+    c->d_blk_c.alloc(c->nH * N);
+    c->d_blk_beta.alloc(N * N);
+    c->d_blk_gamma.alloc(N * N);
+    int64_t width = std::max<int64_t>({4 * N, N * N, 20, 10, 3});
+    c->d_partial.alloc(reduce_partial_size(width));
+    c->d_red.alloc(width + 16);
+    c->d_moments.alloc(16);
+    for (auto* b : {&c->d_coef, &c->d_eps, &c->d_vxc, &c->d_tmpq, &c->d_rho_in, &c->d_rho_out, &c->d_rho_prev})
+        b->alloc(nqt);
+    c->d_hist_rin.clear();
+    c->d_hist_F.clear();
+    for (int k = 0; k < 5; ++k) {
+        c->d_hist_rin.emplace_back(nqt);
+        c->d_hist_F.emplace_back(nqt);
+    }
+    c->d_occ.upload(c->occ, c->stream);
+}
+
+void ctx_setup(nas_ctx* c) {
+    if (!c->have_fine || !c->have_coarse || !c->have_system) fail(NAS_E_STATE, "meshes and system must be set");
+    cudaStream_t s = c->stream;
+    NAS_CUDA(cudaSetDevice(c->device));
+    fem_set_order(c->fine_order, c->device);
+    c->setup_done = false;
+    c->initialized = false;
+    build_space(c->F, c->fine_order, c->fnv, c->fxyz.data(), c->fne, c->ftet.data(), true);
+    build_space(c->C, 1, c->cnv, c->cxyz.data(), c->cne, c->ctet.data(), false);
+    for (int d = 0; d < 3; ++d)
+        if (c->F.lo[d] != c->C.lo[d] || c->F.hi[d] != c->C.hi[d])
+            fail(NAS_E_MESH, "fine and coarse meshes must cover the same box");
+    HostSpace& F = c->F;
+    c->nq = F.order == 1 ? 4 : 14;
+    c->nqt = F.ne * c->nq;
+    c->nH = c->C.n;
+    // ---- fine mesh data
+    c->d_vxyz.upload(F.vxyz, s);
+    c->d_elem.upload(F.elem, s);
+    c->d_node_xyz.upload(F.node_xyz, s);
+    c->d_dof_of_node.upload(F.dof_of_node, s);
+    c->d_dof_node.upload(F.dof_node, s);
+    c->d_bnd_node.upload(F.bnd_node, s);
+    c->d_rowptr.upload(F.rowptr, s);
+    c->d_col.upload(F.col, s);
+    c->d_cptr.upload(F.cptr, s);
+    c->d_contrib.upload(F.contrib, s);
+    c->d_browptr.upload(F.browptr, s);
+    c->d_bcol.upload(F.bcol, s);
+    c->d_bcptr.upload(F.bcptr, s);
+    c->d_bcontrib.upload(F.bcontrib, s);
+    c->d_lptr.upload(F.lptr, s);
+    c->d_lcontrib.upload(F.lcontrib, s);
+    c->d_Wq.alloc(c->nqt);
+    c->d_flag.alloc(4);
+    NAS_CUDA(cudaMemsetAsync(c->d_flag.p, 0, 4 * sizeof(int), s));
+    Mesh m = fmesh(c);
+    launch_geometry(m, c->d_Wq.p, c->d_flag.p, s);
+    int bad = 0;
+    NAS_CUDA(cudaMemcpyAsync(&bad, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    sync(c);
+    if (bad) fail(NAS_E_MESH, "fine mesh has a tetrahedron with det J <= 0");
+    // ---- fixed matrices K, M, M_Vext (st3)
+    const int64_t nnz = F.nnz();
+    c->d_L.alloc(F.ne * F.nloc * F.nloc);
+    c->d_Lv.alloc(F.ne * F.nloc);
+    for (auto* b : {&c->d_K, &c->d_M, &c->d_Mvext, &c->d_AL, &c->d_ANL, &c->d_H}) b->alloc(nnz);
+    c->d_KIB.alloc(std::max<int64_t>(1, F.nnzb()));
+    c->d_Hdinv.alloc(F.n);
+    c->d_Kdinv.alloc(F.n);
+    launch_local_stiffness(m, c->d_L.p, s);
+    launch_gather(nnz, c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, c->d_K.p, s);
+    launch_gather(F.nnzb(), c->d_bcptr.p, c->d_bcontrib.p, c->d_L.p, 1.0, c->d_KIB.p, s);
+    launch_local_mass(m, c->d_Wq.p, nullptr, c->d_L.p, s);
+    launch_gather(nnz, c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, c->d_M.p, s);
+    c->d_R.upload(c->R, s);
+    c->d_Zn.upload(c->Z, s);
+    c->d_coef.alloc(c->nqt);
+    Nuclei nuc{c->n_nuc, c->d_R.p, c->d_Zn.p, c->potential, c->smooth_a, c->opt.omega};
+    launch_vext(m, nuc, c->d_coef.p, s);
+    launch_local_mass(m, c->d_Wq.p, c->d_coef.p, c->d_L.p, s);
+    launch_gather(nnz, c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, c->d_Mvext.p, s);
+    launch_combine3(nnz, 0.5, c->d_K.p, 1.0, c->d_Mvext.p, 0.0, nullptr, c->d_AL.p, s);
+    launch_inv_diag(fcsr(c, c->d_K.p), c->d_Kdinv.p, s);
+    // ---- transfer I_H^h by point location (Algorithm 1)
+    {
+        Phase t(c, NAS_PH_TRANSFER);
+        build_buckets(c->C, c->BG);
+        c->d_cxyz.upload(c->C.vxyz, s);
+        c->d_ctet.upload(c->C.elem, s);
+        c->d_cdof.upload(c->C.dof_of_node, s);
+        c->d_bptr.upload(c->BG.bptr, s);
+        c->d_btet.upload(c->BG.btet, s);
+        c->d_Ielem.alloc(F.n);
+        c->d_Icol.alloc(4 * F.n);
+        c->d_Ival.alloc(4 * F.n);
+        NAS_CUDA(cudaMemsetAsync(c->d_flag.p, 0, sizeof(int), s));
+        LocateArgs la{};
+        la.n_points = F.n;
+        la.point_node = c->d_dof_node.p;
+        la.point_xyz = c->d_node_xyz.p;
+        la.cxyz = c->d_cxyz.p;
+        la.ctet = c->d_ctet.p;
+        la.coarse_dof_of_node = c->d_cdof.p;
+        la.bptr = c->d_bptr.p;
+        la.btet = c->d_btet.p;
+        for (int d = 0; d < 3; ++d) {
+            la.org[d] = c->BG.org[d];
+            la.inv_h[d] = c->BG.inv_h[d];
+            la.nb[d] = c->BG.nb[d];
+        }
+        la.elem = c->d_Ielem.p;
+        la.icol = c->d_Icol.p;
+        la.ival = c->d_Ival.p;
+        la.error_flag = c->d_flag.p;
+        launch_locate(la, s);
+        c->I_elem.resize(F.n);
+        c->I_col.resize(4 * F.n);
+        c->I_val.resize(4 * F.n);
+        c->d_Ielem.download(c->I_elem.data(), F.n, s);
+        c->d_Icol.download(c->I_col.data(), 4 * F.n, s);
+        c->d_Ival.download(c->I_val.data(), 4 * F.n, s);
+        NAS_CUDA(cudaMemcpyAsync(&bad, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        sync(c);
+        if (bad) fail(NAS_E_POINT_NOT_FOUND, "a fine node lies in no coarse tetrahedron");
+    }
+    build_galerkin(F, c->nH, c->I_col, c->I_val, c->GM);
+    GalerkinMaps& G = c->GM;
+    c->d_tptr.upload(G.tptr, s);
+    c->d_trow.upload(G.trow, s);
+    c->d_tval.upload(G.tval, s);
+    c->d_wptr.upload(G.wptr, s);
+    c->d_wcol.upload(G.wcol, s);
+    c->d_wrow.upload(G.wrow, s);
+    c->d_w1ptr.upload(G.w1ptr, s);
+    c->d_w1con.upload(G.w1con, s);
+    c->d_hptr.upload(G.hptr, s);
+    c->d_hcol.upload(G.hcol, s);
+    c->d_h2ptr.upload(G.h2ptr, s);
+    c->d_h2con.upload(G.h2con, s);
+    c->d_W.alloc(std::max<int64_t>(1, G.wnnz()));
+    c->d_AH.alloc(std::max<int64_t>(1, G.hnnz()));
+    // fixed coarse blocks B_H = I^T M I and A_H^L = I^T A^L I
+    c->BH.resize(G.hnnz());
+    c->AHL.resize(G.hnnz());
+    galerkin(c, c->d_M.p, c->d_AH.p);
+    c->d_AH.download(c->BH.data(), G.hnnz(), s);
+    sync(c);
+    galerkin(c, c->d_AL.p, c->d_AH.p);
+    c->d_AH.download(c->AHL.data(), G.hnnz(), s);
+    sync(c);
+    // dense Cholesky factor of B_H (coarse Gram matrix), used by augment_basis
+    c->BH_chol.assign((size_t)c->nH * c->nH, 0.0);
+    for (int64_t a = 0; a < c->nH; ++a)
+        for (int p = G.hptr[a]; p < G.hptr[a + 1]; ++p) c->BH_chol[a * c->nH + G.hcol[p]] = c->BH[p];
+    if (chol_factor((int)c->nH, c->BH_chol.data()) != 0) fail(NAS_E_MESH, "coarse Gram matrix B_H is singular");
+    // ---- parameters
+    double z2 = 0.0;
+    for (double z : c->Z) z2 += z * z;
+    c->mu = c->opt.mu >= 0.0 ? c->opt.mu : 8.0 * c->n_nuc * z2;
+    c->Enn = 0.0;
+    for (int j = 0; j < c->n_nuc; ++j)
+        for (int k = 0; k < j; ++k) {
+            double dx = c->R[3 * j] - c->R[3 * k], dy = c->R[3 * j + 1] - c->R[3 * k + 1],
+                   dz = c->R[3 * j + 2] - c->R[3 * k + 2];
+            c->Enn += c->Z[j] * c->Z[k] / std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    c->d_VH.alloc(F.nnode);
+    c->d_wB.alloc(std::max<int64_t>(1, F.nb));
+    c->d_VH.zero(s);
+    alloc_work(c);
+    resolve_events(c);
+    sync(c);
+    c->setup_done = true;
+}
+
+// ------------------------------------------------------------------ init / step
+void ctx_init(nas_ctx* c, const double* psi0) {
+    if (!c->setup_done) ctx_setup(c);
+    cudaStream_t s = c->stream;
+    c->step_count = 0;
+    c->anl_valid = false;
+    c->d_VH.zero(s);
+    c->U_warm.clear();
+    if (psi0 == nullptr) {
+        // self-consistent solution in S_H alone, from rho = 0
+        if (c->nH < c->N) fail(NAS_E_INVALID_ARG, "the coarse-space initial guess needs n_coarse_dof >= N");
+        c->Na = 0;
+        c->d_rho_in.zero(s);
+        inner_scf(c, false);
+    } else {
+        // given orbitals: M-orthonormalise (Cholesky of the Gram matrix), then
+        // Rayleigh-Ritz with the Hamiltonian of their density
+        const int64_t n = c->F.n;
+        const int N = c->N;
+        c->d_X2.upload(psi0, n * N, s);
+        spmm(c, fcsr(c, c->d_M.p), N, c->d_X2.p, c->d_X1.p);
+        launch_gram(n, N, c->d_X2.p, N, c->d_X1.p, c->d_partial.p, c->d_blk_gamma.p, s);
+        std::vector<double> S(N * N);
+        NAS_CUDA(cudaMemcpyAsync(S.data(), c->d_blk_gamma.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+        sync(c);
+        // Uhat <- psi0 as the basis; density of its orthonormalised span
+        NAS_CUDA(cudaMemcpyAsync(c->d_Uhat.p, c->d_X2.p, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
+        std::vector<double> Hs(N * N, 0.0), lam(N), U(N * N);
+        std::vector<double> Id(N * N, 0.0);
+        for (int i = 0; i < N; ++i) Id[i * N + i] = 1.0;
+        if (dense_gen_eig(N, Id.data(), S.data(), N, lam.data(), U.data()) != 0)
+            fail(NAS_E_INVALID_ARG, "psi0 columns are linearly dependent");
+        // orthonormal basis Psi = psi0 * U (U^T S U = I)
+        std::vector<double> Ufull((c->nH + N) * N, 0.0);
+        for (int i = 0; i < N * N; ++i) Ufull[c->nH * N + i] = U[i];
+        NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Ufull.data(), sizeof(double) * Ufull.size(), cudaMemcpyHostToDevice, s));
+        std::vector<double> zero_col(4 * n, 0.0);
+        // reconstruct with the coarse part ignored (weights multiply zero rows)
+        launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
+        launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, N, c->d_occ.p, c->d_rho_in.p, s);
+        bool pc = true;
+        if (c->opt.hartree) hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
+        assemble_nl(c);
+        c->anl_valid = true;
+        launch_combine3(c->F.nnz(), 1.0, c->d_AL.p, 1.0, c->d_ANL.p, 0.0, nullptr, c->d_H.p, s);
+        spmm(c, fcsr(c, c->d_H.p), N, c->d_Psi.p, c->d_X1.p);
+        launch_gram(n, N, c->d_Psi.p, N, c->d_X1.p, c->d_partial.p, c->d_blk_beta.p, s);
+        NAS_CUDA(cudaMemcpyAsync(Hs.data(), c->d_blk_beta.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+        sync(c);
+        for (int i = 0; i < N; ++i) Id[i * N + i] = 1.0;
+        std::vector<double> Y(N * N);
+        if (dense_gen_eig(N, Hs.data(), Id.data(), N, lam.data(), Y.data()) != 0)
+            fail(NAS_E_EIGEN, "Rayleigh-Ritz of psi0 failed");
+        c->lam = lam;
+        // Psi <- Psi Y  (Uhat = Psi, alpha = Y)
+        NAS_CUDA(cudaMemcpyAsync(c->d_Uhat.p, c->d_Psi.p, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
+        for (int i = 0; i < N * N; ++i) Ufull[c->nH * N + i] = Y[i];
+        NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Ufull.data(), sizeof(double) * Ufull.size(), cudaMemcpyHostToDevice, s));
+        launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
+        launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, N, c->d_occ.p, c->d_rho_out.p, s);
+        c->last_inner = 0;
+        (void)zero_col;
+    }
+    NAS_CUDA(cudaMemcpyAsync(c->d_rho_prev.p, c->d_rho_out.p, sizeof(double) * c->nqt, cudaMemcpyDeviceToDevice, s));
+    energies(c);
+    resolve_events(c);
+    c->initialized = true;
+}
+
+int ctx_step(nas_ctx* c, nas_report* rep) {
+    if (!c->initialized) fail(NAS_E_STATE, "nas_init must be called before nas_step");
+    cudaStream_t s = c->stream;
+    const int64_t n = c->F.n;
+    const int N = c->N;
+    c->launches_at_step_start = g_launch_count;
+    for (int k = 0; k < NAS_MAX_PHASES; ++k) {
+        c->phase_ms[k] = 0;
+        c->phase_calls[k] = 0;
+    }
+    c->spmm_bytes = c->spmm_flops = c->spmv_bytes = c->spmv_flops = 0;
+    c->last_lobpcg_iters = 0;
+    int status = NAS_OK;
+    if (!c->anl_valid) {
+        if (c->opt.hartree) {
+            bool pc;
+            hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
+        }
+        assemble_nl(c);
+        c->anl_valid = true;
+    }
+    // ---- the N shifted linear boundary value problems
+    {
+        Phase t(c, NAS_PH_BVP);
+        launch_combine3(c->F.nnz(), 1.0, c->d_AL.p, 1.0, c->d_ANL.p, c->mu, c->d_M.p, c->d_H.p, s);
+        launch_inv_diag(fcsr(c, c->d_H.p), c->d_Hdinv.p, s);
+        spmm(c, fcsr(c, c->d_M.p), N, c->d_Psi.p, c->d_cg_B.p);
+        std::vector<double> sh(N);
+        for (int i = 0; i < N; ++i) sh[i] = c->lam[i] + c->mu;
+        double* d_sh = scal(c, 7, N);
+        NAS_CUDA(cudaMemcpyAsync(d_sh, sh.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+        launch_scale_cols(n, N, d_sh, c->d_cg_B.p, s);
+        NAS_CUDA(cudaMemcpyAsync(c->d_Uhat.p, c->d_Psi.p, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
+        bool conv;
+        c->last_cg = pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, c->opt.tol_bvp,
+                         c->opt.max_cg, &conv);
+        if (!conv) status = NAS_E_NOT_CONVERGED;
+    }
+    augment_basis(c);
+    // ---- fixed blocks (c_H, gamma) and linear parts of b_H, beta
+    c->Na = N;
+    {
+        std::vector<double> dummy;
+        // M against U^: c_H = I^T M U^, gamma = U^T M U^
+        blocks_of(c, c->d_M.p, nullptr, c->hb_cH, c->hb_gamma);
+        blocks_of(c, c->d_AL.p, nullptr, c->hb_bHL, c->hb_betaL);
+    }
+    NAS_CUDA(cudaMemcpyAsync(c->d_rho_prev.p, c->d_rho_out.p, sizeof(double) * c->nqt, cudaMemcpyDeviceToDevice, s));
+    inner_scf(c, true);
+    c->last_drho = weighted_norm_diff(c, c->d_rho_out.p, c->d_rho_prev.p);
+    energies(c);
+    resolve_events(c);
+    c->step_count++;
+    if (rep) ctx_fill_report(c, rep);
+    return status;
+}
+
+void ctx_fill_report(nas_ctx* c, nas_report* rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->n_orb = c->N;
+    rep->step = c->step_count;
+    rep->n_inner = c->last_inner;
+    rep->inner_converged = c->last_inner_conv;
+    rep->cg_iters = c->last_cg;
+    rep->poisson_iters = c->last_poisson;
+    rep->drho = c->last_drho;
+    rep->inner_res = c->last_inner_res;
+    rep->energy = c->energy[0];
+    rep->e_band = c->energy[1];
+    rep->e_hartree = c->energy[2];
+    rep->e_xc = c->energy[3];
+    rep->e_vxc = c->energy[4];
+    rep->e_nn = c->energy[5];
+    for (int k = 0; k < NAS_MAX_PHASES; ++k) {
+        rep->phase_ms[k] = c->phase_ms[k];
+        rep->phase_calls[k] = c->phase_calls[k];
+    }
+    rep->spmm_bytes = c->spmm_bytes;
+    rep->spmm_flops = c->spmm_flops;
+    rep->spmv_bytes = c->spmv_bytes;
+    rep->spmv_flops = c->spmv_flops;
+    rep->kernel_launches = g_launch_count - c->launches_at_step_start;
+}
+
+// ------------------------------------------------------------------ state in/out
+static void copy_in(nas_ctx* c, double* dst, const double* src, int64_t cnt, int on_device) {
+    NAS_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * cnt,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+}
+
+void ctx_set_state(nas_ctx* c, const double* lam, const double* psi, const double* rho, int on_device) {
+    if (!c->setup_done) fail(NAS_E_STATE, "nas_init must be called first");
+    if (!lam || !psi || !rho) fail(NAS_E_INVALID_ARG, "null state pointer");
+    cudaStream_t s = c->stream;
+    if (on_device) {
+        NAS_CUDA(cudaMemcpyAsync(c->lam.data(), lam, sizeof(double) * c->N, cudaMemcpyDeviceToHost, s));
+    } else {
+        c->lam.assign(lam, lam + c->N);
+    }
+    copy_in(c, c->d_Psi.p, psi, c->F.n * c->N, on_device);
+    copy_in(c, c->d_rho_in.p, rho, c->nqt, on_device);
+    launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, c->N, c->d_occ.p, c->d_rho_out.p, s);
+    if (c->opt.hartree) {
+        bool pc;
+        hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
+    }
+    assemble_nl(c);
+    c->anl_valid = true;
+    sync(c);
+    resolve_events(c);
+    c->initialized = true;
+}
+
+void ctx_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {
+    cudaStream_t s = c->stream;
+    auto put = [&](const void* src_dev, size_t nb) {
+        if (bytes < nb) fail(NAS_E_INVALID_ARG, "destination buffer too small");
+        NAS_CUDA(cudaMemcpyAsync(dst, src_dev, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        sync(c);
+    };
+    auto put_host = [&](const void* src_host, size_t nb) {
+        if (bytes < nb) fail(NAS_E_INVALID_ARG, "destination buffer too small");
+        if (on_device)
+            NAS_CUDA(cudaMemcpyAsync(dst, src_host, nb, cudaMemcpyHostToDevice, s));
+        else
+            std::memcpy(dst, src_host, nb);
+        sync(c);
+    };
+    if (what == NAS_Q_SIZES) {
+        int64_t v[16] = {0};
+        if (c->setup_done) {
+            v[0] = c->F.n;
+            v[1] = c->F.nnz();
+            v[2] = c->nH;
+            v[3] = c->GM.hnnz();
+            v[4] = c->F.ne;
+            v[5] = c->nq;
+            v[6] = c->F.nnode;
+            v[7] = c->N;
+            v[8] = c->F.nb;
+            v[9] = c->F.nnzb();
+            v[10] = c->F.nv;
+            v[11] = c->F.order;
+            v[12] = c->C.ne;
+        }
+        put_host(v, sizeof(v));
+        return;
+    }
+    if (!c->setup_done) fail(NAS_E_STATE, "nothing to get before nas_init");
+    const int64_t n = c->F.n, N = c->N;
+    switch (what) {
+        case NAS_Q_EIGVALS: put_host(c->lam.data(), sizeof(double) * N); break;
+        case NAS_Q_ORBITALS: put(c->d_Psi.p, sizeof(double) * n * N); break;
+        case NAS_Q_RHO_IN: put(c->d_rho_in.p, sizeof(double) * c->nqt); break;
+        case NAS_Q_RHO_OUT: put(c->d_rho_out.p, sizeof(double) * c->nqt); break;
+        case NAS_Q_VHARTREE: put(c->d_VH.p, sizeof(double) * c->F.nnode); break;
+        case NAS_Q_UHAT: put(c->d_Uhat.p, sizeof(double) * n * N); break;
+        case NAS_Q_ROWPTR: put(c->d_rowptr.p, sizeof(int32_t) * (n + 1)); break;
+        case NAS_Q_COLIDX: put(c->d_col.p, sizeof(int32_t) * c->F.nnz()); break;
+        case NAS_Q_K: put(c->d_K.p, sizeof(double) * c->F.nnz()); break;
+        case NAS_Q_M: put(c->d_M.p, sizeof(double) * c->F.nnz()); break;
+        case NAS_Q_MVEXT: put(c->d_Mvext.p, sizeof(double) * c->F.nnz()); break;
+        case NAS_Q_ANL: put(c->d_ANL.p, sizeof(double) * c->F.nnz()); break;
+        case NAS_Q_HTILDE: put(c->d_H.p, sizeof(double) * c->F.nnz()); break;
+        case NAS_Q_TRANSFER_ELEM: put(c->d_Ielem.p, sizeof(int32_t) * n); break;
+        case NAS_Q_TRANSFER_COL: put(c->d_Icol.p, sizeof(int32_t) * 4 * n); break;
+        case NAS_Q_TRANSFER_W: put(c->d_Ival.p, sizeof(double) * 4 * n); break;
+        case NAS_Q_FA: put_host(c->FA.data(), sizeof(double) * c->FA.size()); break;
+        case NAS_Q_FB: put_host(c->FB.data(), sizeof(double) * c->FB.size()); break;
+        case NAS_Q_DOF_NODE: put(c->d_dof_node.p, sizeof(int32_t) * n); break;
+        case NAS_Q_ENERGY: put_host(c->energy.data(), sizeof(double) * 6); break;
+        default: fail(NAS_E_INVALID_ARG, "unknown quantity");
+    }
+}
+
+// ------------------------------------------------------------------ single operations
+void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int on_device) {
+    if (!c->setup_done) fail(NAS_E_STATE, "nas_init must be called first");
+    if (!in || !out) fail(NAS_E_INVALID_ARG, "null pointer");
+    cudaStream_t s = c->stream;
+    const int64_t n = c->F.n, N = c->N, nnz = c->F.nnz();
+    auto kind_in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    auto kind_out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    auto fin = [&](DBuf<double>& buf, int64_t count) {
+        buf.ensure(count);
+        NAS_CUDA(cudaMemcpyAsync(buf.p, in, sizeof(double) * count, kind_in, s));
+    };
+    auto fout = [&](const double* src, int64_t count) {
+        NAS_CUDA(cudaMemcpyAsync(out, src, sizeof(double) * count, kind_out, s));
+        sync(c);
+    };
+    DBuf<double> a, b;
+    switch (op) {
+        case NAS_OP_LDA: {
+            if (cnt <= 0) fail(NAS_E_INVALID_ARG, "cnt");
+            fin(a, cnt);
+            b.alloc(2 * cnt);
+            launch_lda(cnt, a.p, b.p, b.p + cnt, s);
+            fout(b.p, 2 * cnt);
+            break;
+        }
+        case NAS_OP_HARTREE: {
+            fin(a, c->nqt);
+            b.alloc(c->F.nnode);
+            b.zero(s);
+            bool pc;
+            hartree(c, a.p, b.p, &pc);
+            if (!pc) fail(NAS_E_NOT_CONVERGED, "Poisson PCG hit its iteration cap");
+            fout(b.p, c->F.nnode);
+            break;
+        }
+        case NAS_OP_ASSEMBLE_MASS: {
+            fin(a, c->nqt);
+            b.alloc(nnz);
+            launch_local_mass(fmesh(c), c->d_Wq.p, a.p, c->d_L.p, s);
+            launch_gather(nnz, c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, b.p, s);
+            fout(b.p, nnz);
+            break;
+        }
+        case NAS_OP_DENSITY: {
+            fin(a, n * N);
+            b.alloc(c->nqt);
+            launch_density(fmesh(c), c->d_dof_of_node.p, a.p, (int)N, c->d_occ.p, b.p, s);
+            fout(b.p, c->nqt);
+            break;
+        }
+        case NAS_OP_APPLY_H: {
+            if (c->step_count == 0) fail(NAS_E_STATE, "H~ exists after the first nas_step");
+            fin(a, n * N);
+            b.alloc(n * N);
+            spmm(c, fcsr(c, c->d_H.p), (int)N, a.p, b.p);
+            fout(b.p, n * N);
+            break;
+        }
+        case NAS_OP_BVP: {
+            if (c->step_count == 0) fail(NAS_E_STATE, "H~ exists after the first nas_step");
+            fin(a, n * N);
+            b.alloc(n * N);
+            b.zero(s);
+            bool conv;
+            pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, (int)N, a.p, b.p, c->opt.tol_bvp, c->opt.max_cg, &conv);
+            if (!conv) fail(NAS_E_NOT_CONVERGED, "block PCG hit its iteration cap");
+            fout(b.p, n * N);
+            break;
+        }
+        case NAS_OP_GALERKIN: {
+            fin(a, nnz);
+            b.alloc(std::max<int64_t>(1, c->GM.hnnz()));
+            galerkin(c, a.p, b.p);
+            std::vector<double> hv(c->GM.hnnz()), D(c->nH * c->nH, 0.0);
+            b.download(hv.data(), hv.size(), s);
+            sync(c);
+            for (int64_t r = 0; r < c->nH; ++r)
+                for (int p = c->GM.hptr[r]; p < c->GM.hptr[r + 1]; ++p) D[r * c->nH + c->GM.hcol[p]] = hv[p];
+            if (on_device)
+                NAS_CUDA(cudaMemcpyAsync(out, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice, s));
+            else
+                std::memcpy(out, D.data(), sizeof(double) * D.size());
+            sync(c);
+            break;
+        }
+        default: fail(NAS_E_INVALID_ARG, "unknown op");
+    }
+    resolve_events(c);
+}
+
+}  // namespace nas

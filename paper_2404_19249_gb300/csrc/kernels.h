@@ -1,0 +1,177 @@
+// Launchers of the nas GPU kernels (internal).  All kernels are FP64 and
+// deterministic: every sum is taken in a fixed order (no floating-point
+// atomics), so two runs on the same input give bit-identical results.
+#pragma once
+
+#include "common.h"
+
+namespace nas {
+
+// ------------------------------------------------------------ quadrature tables
+// Upload the reference-element tables (quadrature points/weights, basis
+// values, products and gradients) of the fine-space order to constant memory.
+void fem_set_order(int order, int device);
+
+// ------------------------------------------------------------ point location
+struct LocateArgs {
+    int64_t n_points;
+    const int32_t* point_node;   // node id of each point
+    const double* point_xyz;     // node coordinates [nnode][3]
+    const double* cxyz;          // coarse vertices [nvc][3]
+    const int32_t* ctet;         // coarse tets [nec][4]
+    const int32_t* coarse_dof_of_node;  // [nvc] coarse dof or -1
+    const int64_t* bptr;         // bucket CSR
+    const int32_t* btet;
+    double org[3], inv_h[3];
+    int nb[3];
+    int32_t* elem;               // out [n_points]
+    int32_t* icol;               // out [n_points][4]
+    double* ival;                // out [n_points][4]
+    int* error_flag;             // set to 1 if a point is in no tetrahedron
+};
+void launch_locate(const LocateArgs& a, cudaStream_t s);
+
+// ------------------------------------------------------------ element kernels
+struct Mesh {
+    int64_t ne;
+    int nloc, nq;
+    const double* vxyz;    // vertex coordinates [nv][3]
+    const int32_t* elem;   // [ne][nloc] node ids; the first 4 are the vertices
+};
+
+// detJ > 0 check and quadrature weights Wq[e][q] = w_q |det J_e|
+void launch_geometry(const Mesh& m, double* Wq, int* error_flag, cudaStream_t s);
+// element stiffness matrices L[e][a][b] = sum_q Wq grad phi_a . grad phi_b
+void launch_local_stiffness(const Mesh& m, double* L, cudaStream_t s);
+// element mass matrices L[e][a][b] = sum_q Wq c_q phi_a phi_b (coef == nullptr: c = 1)
+void launch_local_mass(const Mesh& m, const double* Wq, const double* coef, double* L, cudaStream_t s);
+// external potential at quadrature points
+struct Nuclei {
+    int count;
+    const double* R;   // device [count][3]
+    const double* Z;   // device [count]
+    int potential;     // nas_potential
+    double smooth_a, omega;
+};
+void launch_vext(const Mesh& m, const Nuclei& nuc, double* vq, cudaStream_t s);
+// nodal values (all nodes) -> values at quadrature points [ne][nq]
+void launch_nodal_to_quad(const Mesh& m, const double* nodal, double* out, cudaStream_t s);
+// LDA (Slater exchange + Perdew-Zunger correlation) pointwise; eps or vxc may be null
+void launch_lda(int64_t cnt, const double* rho, double* eps, double* vxc, cudaStream_t s);
+// coefficient of the nonlinear mass matrix: c = V_H(q) + V_xc(rho_in(q)), also
+// storing eps_xc and V_xc at the quadrature points (xc = 0: V_H only)
+void launch_nl_coef(const Mesh& m, const double* VH_nodal, const double* rho, int xc,
+                    double* coef, double* eps, double* vxc, cudaStream_t s);
+// rho[e][q] = sum_c occ[c] psi_c(x_q)^2, psi from dof values Psi[n][N]
+void launch_density(const Mesh& m, const int32_t* dof_of_node, const double* Psi, int N,
+                    const double* occ, double* rho, cudaStream_t s);
+// element load vectors Lv[e][a] = sum_q Wq f_q phi_a
+void launch_local_load(const Mesh& m, const double* Wq, const double* f, double* Lv, cudaStream_t s);
+// out[s] = scale * sum_{k in [ptr[s],ptr[s+1])} src[idx[k]]
+void launch_gather(int64_t nslots, const int64_t* ptr, const int32_t* idx, const double* src,
+                   double scale, double* out, cudaStream_t s);
+// charge moments: out[0] = int rho, out[1..3] = int x rho, out[4..9] = int x_i x_j rho
+// (i<=j: xx, xy, xz, yy, yz, zz); quadrature positions recomputed from vertices.
+void launch_moments(const Mesh& m, const double* Wq, const double* rho, double* partial,
+                    double* out, cudaStream_t s);
+// boundary values of V_H (monopole + optional quadrupole) written into V_nodal
+// at the boundary nodes and into wB[nb]
+void launch_boundary_values(int64_t nb, const int32_t* bnd_node, const double* node_xyz,
+                            const double* moments, int multipole, double* wB, double* V_nodal,
+                            cudaStream_t s);
+// gather nodal values at the dofs: x[i] = V_nodal[dof_node[i]]
+void launch_nodal_to_dof(int64_t n, const int32_t* dof_node, const double* V_nodal, double* x,
+                         cudaStream_t s);
+// scatter dof values into nodal array: V_nodal[dof_node[i]] = x[i]
+void launch_dof_to_nodal(int64_t n, const int32_t* dof_node, const double* x, double* V_nodal,
+                         cudaStream_t s);
+
+// ------------------------------------------------------------ sparse / dense linear algebra
+struct Csr {
+    int64_t n_rows;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const double* val;
+};
+// Y = alpha * A X (+ beta Y), X [ncols][N], Y [n_rows][N]
+void launch_spmm(const Csr& A, int N, const double* X, double* Y, double alpha, double beta,
+                 cudaStream_t s);
+
+// Deterministic column-wise weighted dot products: out[k][c] = sum_i w_i X_k[i][c] Y_k[i][c]
+// for k < npairs (w == nullptr: w_i = 1).  partial: scratch of
+// reduce_partial_size(N*npairs) doubles.
+int64_t reduce_partial_size(int64_t width);
+void launch_coldots(int64_t n, int N, int npairs, const double* const* X, const double* const* Y,
+                    const double* w, double* partial, double* out, cudaStream_t s);
+
+// Block PCG vector updates with per-column scalars held on the device.
+struct PcgCols {
+    int N;
+    double* rz;      // [N] r.z of the current iterate
+    double* pq;      // [N]
+    double* rz_new;  // [N]
+    double* rr;      // [N]
+    double* bb;      // [N] ||b||^2
+    double* alpha;   // [N]
+    double* beta;    // [N]
+    int* active;     // [N]
+    int* breakdown;  // [1]
+    double tol2;     // tol^2
+};
+// alpha_c = rz_c / pq_c for active columns (pq <= 0 or non-finite -> breakdown)
+void launch_pcg_alpha(const PcgCols& c, cudaStream_t s);
+// beta_c = rz_new_c / rz_c; rz <- rz_new; deactivate converged columns
+void launch_pcg_beta(const PcgCols& c, cudaStream_t s);
+// X += alpha P, R -= alpha Q, Z = Dinv R (per column alpha, inactive columns untouched)
+void launch_pcg_update(int64_t n, int N, const double* alpha, const int* active, const double* P,
+                       const double* Q, const double* Dinv, double* X, double* R, double* Z,
+                       cudaStream_t s);
+// P = Z + beta P (active columns)
+void launch_pcg_direction(int64_t n, int N, const double* beta, const int* active, const double* Z,
+                          double* P, cudaStream_t s);
+// Y[i][c] *= s[c]
+void launch_scale_cols(int64_t n, int N, const double* s_dev, double* Y, cudaStream_t s);
+// Z = Dinv R
+void launch_scale_rows(int64_t n, int N, const double* Dinv, const double* R, double* Z,
+                       cudaStream_t s);
+// R = B - R (elementwise), used after R = A X
+void launch_sub_from(int64_t cnt, const double* B, double* R, cudaStream_t s);
+// out = a*x + b*y elementwise
+void launch_axpby(int64_t cnt, double a, const double* x, double b, const double* y, double* out,
+                  cudaStream_t s);
+// Dinv[i] = 1 / A_ii
+void launch_inv_diag(const Csr& A, double* Dinv, cudaStream_t s);
+// val_out = a*v1 + b*v2 + c*v3 (CSR value arrays with a common pattern; v3 may be null)
+void launch_combine3(int64_t nnz, double a, const double* v1, double b, const double* v2, double c,
+                     const double* v3, double* out, cudaStream_t s);
+
+// G[a][b] = sum_i X[i][a] Y[i][b]  (X [n][Nx], Y [n][Ny]) deterministic; partial scratch
+// of gram_partial_size(Nx*Ny) doubles
+int64_t gram_partial_size(int64_t width);
+void launch_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y, double* partial,
+                 double* G, cudaStream_t s);
+
+// out[a][c] = sum_{p in [tptr[a], tptr[a+1])} tval[p] Y[trow[p]][c]   (I^T Y)
+void launch_transpose_apply(int64_t nH, const int32_t* tptr, const int32_t* trow, const double* tval,
+                            int N, const double* Y, double* out, cudaStream_t s);
+// Psi[i][c] = sum_k ival[i][k] uH[icol[i][k]][c] + sum_j Uhat[i][j] alpha[j][c]
+// U = [uH ; alpha] is [(nH + Na)][N] on the device; Na may be 0.
+void launch_reconstruct(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                        int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s);
+// Galerkin stage 1: W[s] = sum_{q in list} A[q>>2] * ival[col[q>>2]*4 + (q&3)]
+void launch_galerkin1(int64_t nw, const int64_t* ptr, const int32_t* con, const double* A,
+                      const int32_t* col, const double* ival, double* W, cudaStream_t s);
+// Galerkin stage 2: H[t] = sum_{r in list} ival[wrow[r>>2]*4 + (r&3)] * W[r>>2]
+void launch_galerkin2(int64_t nh, const int64_t* ptr, const int32_t* con, const double* W,
+                      const int32_t* wrow, const double* ival, double* H, cudaStream_t s);
+
+// Anderson: given F^0..F^m (pointers), w, compute the k x k matrix
+// A[a][b] = (F^m - F^a, F^m - F^b) and rhs[a] = (F^m - F^a, F^m), k = m;
+// out = [A (k*k), rhs (k)] deterministic
+void launch_anderson_dots(int64_t cnt, int m, const double* const* F, const double* w,
+                          double* partial, double* out, cudaStream_t s);
+// rho_new = rin_m + sum_a alpha_a (rin_a - rin_m) + beta (F_m + sum_a alpha_a (F_a - F_m))
+void launch_anderson_mix(int64_t cnt, int m, const double* const* rin, const double* const* F,
+                         const double* alpha, double beta, double* rho_new, cudaStream_t s);
+
+}  // namespace nas

@@ -1,0 +1,495 @@
+// Sparse and dense linear algebra kernels of the step: CSR SpMM with the N
+// right-hand sides interleaved (row-major [n][N], so one row of X is one
+// contiguous segment), block PCG updates with per-column scalars kept on the
+// device, deterministic column-wise dot products and tall-skinny Gram
+// products, the transposed transfer I^T, the reconstruction
+// Psi = I u_H + U^ alpha, the two Galerkin gathers of A_H = I^T A I, and the
+// Anderson-mixing reductions.  All reductions are two-stage with a fixed
+// order (per-block partials, then one ordered pass), never atomics.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace nas {
+
+static const int kRedBlocks = 1216;  // 8 x 152 SMs: grid of the two-stage reductions
+
+// ------------------------------------------------------------------ SpMM
+// One thread per (row, column): the N threads of a row read the same val/col
+// entries (a broadcast) and a contiguous N-segment of X per nonzero.
+__global__ void __launch_bounds__(256) k_spmm_cols(Csr A, int N, const double* __restrict__ X,
+                                                   double* __restrict__ Y, double alpha, double beta) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t row = t / N;
+    if (row >= A.n_rows) return;
+    int c = (int)(t - row * N);
+    int p0 = A.rowptr[row], p1 = A.rowptr[row + 1];
+    double acc = 0.0;
+    for (int p = p0; p < p1; ++p) acc += A.val[p] * X[(int64_t)A.col[p] * N + c];
+    double y = alpha * acc;
+    if (beta != 0.0) y += beta * Y[t];
+    Y[t] = y;
+}
+
+// N == 1: 8 lanes per row, strided over the row's nonzeros, shuffle reduction
+// in a fixed order.
+__global__ void __launch_bounds__(256) k_spmv8(Csr A, const double* __restrict__ X, double* __restrict__ Y,
+                                              double alpha, double beta) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t row = t >> 3;
+    int lane = threadIdx.x & 7;
+    bool valid = row < A.n_rows;
+    double acc = 0.0;
+    if (valid) {
+        int p1 = A.rowptr[row + 1];
+        for (int p = A.rowptr[row] + lane; p < p1; p += 8) acc += A.val[p] * X[A.col[p]];
+    }
+    acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
+    acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
+    acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
+    if (valid && lane == 0) {
+        double y = alpha * acc;
+        if (beta != 0.0) y += beta * Y[row];
+        Y[row] = y;
+    }
+}
+
+void launch_spmm(const Csr& A, int N, const double* X, double* Y, double alpha, double beta,
+                 cudaStream_t s) {
+    if (A.n_rows <= 0) return;
+    if (N == 1) {
+        k_spmv8<<<grid_for(A.n_rows * 8, 256), 256, 0, s>>>(A, X, Y, alpha, beta);
+    } else {
+        k_spmm_cols<<<grid_for(A.n_rows * N, 256), 256, 0, s>>>(A, N, X, Y, alpha, beta);
+    }
+    NAS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ ordered reductions
+// final pass: out[j] = sum_b partial[b][j] for j < width, b in order
+__global__ void k_reduce_partials(int nblocks, int64_t width, const double* partial, double* out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= width) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * width + j];
+    out[j] = s;
+}
+
+int64_t reduce_partial_size(int64_t width) { return (int64_t)kRedBlocks * width; }
+int64_t gram_partial_size(int64_t width) { return (int64_t)kRedBlocks * width; }
+
+struct ColDotArgs {
+    const double* X[4];
+    const double* Y[4];
+};
+
+// thread t of a block owns column c = t % N and row offset r = t / N
+// (R = 256 / N rows per pass); blocks stride over rows.  Per block, column c
+// is summed over r = 0..R-1 in order.
+__global__ void __launch_bounds__(256) k_coldots(int64_t n, int N, int npairs, ColDotArgs a, const double* w,
+                                                double* partial) {
+    __shared__ double sh[4][256];
+    int R = 256 / N;
+    int t = threadIdx.x;
+    int c = t % N, r = t / N;
+    double acc[4] = {0, 0, 0, 0};
+    if (r < R) {
+        for (int64_t row = (int64_t)blockIdx.x * R + r; row < n; row += (int64_t)gridDim.x * R) {
+            double wi = w ? w[row] : 1.0;
+            int64_t idx = row * N + c;
+            for (int k = 0; k < npairs; ++k) acc[k] += wi * a.X[k][idx] * a.Y[k][idx];
+        }
+    }
+    for (int k = 0; k < npairs; ++k) sh[k][t] = acc[k];
+    __syncthreads();
+    if (t < N) {
+        for (int k = 0; k < npairs; ++k) {
+            double s = 0.0;
+            for (int rr = 0; rr < R; ++rr) s += sh[k][rr * N + t];
+            partial[(int64_t)blockIdx.x * npairs * N + k * N + t] = s;
+        }
+    }
+}
+
+void launch_coldots(int64_t n, int N, int npairs, const double* const* X, const double* const* Y,
+                    const double* w, double* partial, double* out, cudaStream_t s) {
+    if (N < 1 || N > 256 || npairs < 1 || npairs > 4) fail(NAS_E_INVALID_ARG, "coldots width");
+    ColDotArgs a{};
+    for (int k = 0; k < npairs; ++k) {
+        a.X[k] = X[k];
+        a.Y[k] = Y[k];
+    }
+    int R = 256 / N;
+    int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + R - 1) / R));
+    k_coldots<<<nb, 256, 0, s>>>(n, N, npairs, a, w, partial);
+    NAS_CHECK_LAUNCH();
+    int64_t width = (int64_t)npairs * N;
+    k_reduce_partials<<<grid_for(width, 128), 128, 0, s>>>(nb, width, partial, out);
+    NAS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ PCG scalars and updates
+__global__ void k_pcg_alpha(PcgCols c) {
+    int j = threadIdx.x;
+    if (j >= c.N) return;
+    if (!c.active[j]) {
+        c.alpha[j] = 0.0;
+        return;
+    }
+    double pq = c.pq[j];
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        *c.breakdown = 1;
+        c.active[j] = 0;
+        c.alpha[j] = 0.0;
+        return;
+    }
+    c.alpha[j] = c.rz[j] / pq;
+}
+
+__global__ void k_pcg_beta(PcgCols c) {
+    int j = threadIdx.x;
+    if (j >= c.N) return;
+    if (!c.active[j]) {
+        c.beta[j] = 0.0;
+        return;
+    }
+    double rzn = c.rz_new[j];
+    if (!isfinite(rzn)) {
+        *c.breakdown = 1;
+        c.active[j] = 0;
+        return;
+    }
+    c.beta[j] = c.rz[j] != 0.0 ? rzn / c.rz[j] : 0.0;
+    c.rz[j] = rzn;
+    if (c.rr[j] <= c.tol2 * c.bb[j]) c.active[j] = 0;
+}
+
+void launch_pcg_alpha(const PcgCols& c, cudaStream_t s) {
+    k_pcg_alpha<<<1, 256, 0, s>>>(c);
+    NAS_CHECK_LAUNCH();
+}
+void launch_pcg_beta(const PcgCols& c, cudaStream_t s) {
+    k_pcg_beta<<<1, 256, 0, s>>>(c);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_pcg_update(int64_t n, int N, const double* alpha, const int* active, const double* P,
+                             const double* Q, const double* Dinv, double* X, double* R, double* Z) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    int64_t i = t / N;
+    int c = (int)(t - i * N);
+    if (!active[c]) return;
+    double a = alpha[c];
+    X[t] += a * P[t];
+    double r = R[t] - a * Q[t];
+    R[t] = r;
+    Z[t] = Dinv[i] * r;
+}
+
+void launch_pcg_update(int64_t n, int N, const double* alpha, const int* active, const double* P,
+                       const double* Q, const double* Dinv, double* X, double* R, double* Z,
+                       cudaStream_t s) {
+    if (n <= 0) return;
+    k_pcg_update<<<grid_for(n * N, 256), 256, 0, s>>>(n, N, alpha, active, P, Q, Dinv, X, R, Z);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_pcg_direction(int64_t n, int N, const double* beta, const int* active, const double* Z,
+                                double* P) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    int c = (int)(t % N);
+    if (!active[c]) return;
+    P[t] = Z[t] + beta[c] * P[t];
+}
+
+void launch_pcg_direction(int64_t n, int N, const double* beta, const int* active, const double* Z,
+                          double* P, cudaStream_t s) {
+    if (n <= 0) return;
+    k_pcg_direction<<<grid_for(n * N, 256), 256, 0, s>>>(n, N, beta, active, Z, P);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_scale_cols(int64_t n, int N, const double* sc, double* Y) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    Y[t] *= sc[t % N];
+}
+
+void launch_scale_cols(int64_t n, int N, const double* sc, double* Y, cudaStream_t s) {
+    if (n <= 0) return;
+    k_scale_cols<<<grid_for(n * N, 256), 256, 0, s>>>(n, N, sc, Y);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_scale_rows(int64_t n, int N, const double* Dinv, const double* R, double* Z) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    Z[t] = Dinv[t / N] * R[t];
+}
+
+void launch_scale_rows(int64_t n, int N, const double* Dinv, const double* R, double* Z, cudaStream_t s) {
+    if (n <= 0) return;
+    k_scale_rows<<<grid_for(n * N, 256), 256, 0, s>>>(n, N, Dinv, R, Z);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_sub_from(int64_t cnt, const double* B, double* R) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) R[t] = B[t] - R[t];
+}
+
+void launch_sub_from(int64_t cnt, const double* B, double* R, cudaStream_t s) {
+    if (cnt <= 0) return;
+    k_sub_from<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, B, R);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_axpby(int64_t cnt, double a, const double* x, double b, const double* y, double* out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) out[t] = a * x[t] + (y ? b * y[t] : 0.0);
+}
+
+void launch_axpby(int64_t cnt, double a, const double* x, double b, const double* y, double* out,
+                  cudaStream_t s) {
+    if (cnt <= 0) return;
+    k_axpby<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, a, x, b, y, out);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_inv_diag(Csr A, double* Dinv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n_rows) return;
+    double d = 0.0;
+    for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p)
+        if (A.col[p] == i) d = A.val[p];
+    Dinv[i] = d != 0.0 ? 1.0 / d : 0.0;
+}
+
+void launch_inv_diag(const Csr& A, double* Dinv, cudaStream_t s) {
+    if (A.n_rows <= 0) return;
+    k_inv_diag<<<grid_for(A.n_rows, 256), 256, 0, s>>>(A, Dinv);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_combine3(int64_t nnz, double a, const double* v1, double b, const double* v2, double c,
+                           const double* v3, double* out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnz) return;
+    double s = a * v1[t] + b * v2[t];
+    if (v3) s += c * v3[t];
+    out[t] = s;
+}
+
+void launch_combine3(int64_t nnz, double a, const double* v1, double b, const double* v2, double c,
+                     const double* v3, double* out, cudaStream_t s) {
+    if (nnz <= 0) return;
+    k_combine3<<<grid_for(nnz, 256), 256, 0, s>>>(nnz, a, v1, b, v2, c, v3, out);
+    NAS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ Gram X^T Y
+// Blocks stride over 32-row tiles staged in shared memory; thread t owns
+// entries ab = t, t+256, ... (at most 16), summed over the tile rows in order.
+__global__ void __launch_bounds__(256) k_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y,
+                                             double* partial) {
+    extern __shared__ double smem[];
+    double* xs = smem;             // [32][Nx]
+    double* ys = smem + 32 * Nx;   // [32][Ny]
+    const int W = Nx * Ny;
+    double acc[16];
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < n; r0 += (int64_t)gridDim.x * 32) {
+        int rows = (n - r0) < 32 ? (int)(n - r0) : 32;
+        for (int j = threadIdx.x; j < 32 * Nx; j += blockDim.x)
+            xs[j] = (j / Nx < rows) ? X[r0 * Nx + j] : 0.0;
+        for (int j = threadIdx.x; j < 32 * Ny; j += blockDim.x)
+            ys[j] = (j / Ny < rows) ? Y[r0 * Ny + j] : 0.0;
+        __syncthreads();
+        int k = 0;
+        for (int ab = threadIdx.x; ab < W; ab += blockDim.x, ++k) {
+            int a = ab / Ny, b = ab - a * Ny;
+            double s = 0.0;
+            for (int r = 0; r < 32; ++r) s += xs[r * Nx + a] * ys[r * Ny + b];
+            acc[k] += s;
+        }
+        __syncthreads();
+    }
+    int k = 0;
+    for (int ab = threadIdx.x; ab < W; ab += blockDim.x, ++k) partial[(int64_t)blockIdx.x * W + ab] = acc[k];
+}
+
+void launch_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y, double* partial, double* G,
+                 cudaStream_t s) {
+    int64_t W = (int64_t)Nx * Ny;
+    if (W < 1 || W > 16 * 256) fail(NAS_E_INVALID_ARG, "gram width");
+    int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + 31) / 32));
+    size_t sm = sizeof(double) * 32 * (Nx + Ny);
+    k_gram<<<nb, 256, sm, s>>>(n, Nx, X, Ny, Y, partial);
+    NAS_CHECK_LAUNCH();
+    k_reduce_partials<<<grid_for(W, 128), 128, 0, s>>>(nb, W, partial, G);
+    NAS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ transfer products
+__global__ void k_transpose_apply(int64_t nH, const int32_t* tptr, const int32_t* trow, const double* tval,
+                                  int N, const double* Y, double* out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t a = t / N;
+    if (a >= nH) return;
+    int c = (int)(t - a * N);
+    double s = 0.0;
+    for (int p = tptr[a]; p < tptr[a + 1]; ++p) s += tval[p] * Y[(int64_t)trow[p] * N + c];
+    out[t] = s;
+}
+
+void launch_transpose_apply(int64_t nH, const int32_t* tptr, const int32_t* trow, const double* tval,
+                            int N, const double* Y, double* out, cudaStream_t s) {
+    if (nH <= 0) return;
+    k_transpose_apply<<<grid_for(nH * N, 128), 128, 0, s>>>(nH, tptr, trow, tval, N, Y, out);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_reconstruct(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                              int64_t nH, int Na, const double* Uhat, double* Psi) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = t / N;
+    if (i >= n) return;
+    int c = (int)(t - i * N);
+    double s = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int a = icol[4 * i + k];
+        if (a >= 0) s += ival[4 * i + k] * U[(int64_t)a * N + c];
+    }
+    for (int j = 0; j < Na; ++j) s += Uhat[i * Na + j] * U[(nH + j) * N + c];
+    Psi[t] = s;
+}
+
+void launch_reconstruct(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                        int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s) {
+    if (n <= 0) return;
+    k_reconstruct<<<grid_for(n * N, 256), 256, 0, s>>>(n, icol, ival, N, U, nH, Na, Uhat, Psi);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_galerkin1(int64_t nw, const int64_t* ptr, const int32_t* con, const double* A,
+                            const int32_t* col, const double* ival, double* W) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nw) return;
+    double acc = 0.0;
+    for (int64_t k = ptr[s]; k < ptr[s + 1]; ++k) {
+        int q = con[k];
+        int p = q >> 2;
+        acc += A[p] * ival[(int64_t)col[p] * 4 + (q & 3)];
+    }
+    W[s] = acc;
+}
+
+void launch_galerkin1(int64_t nw, const int64_t* ptr, const int32_t* con, const double* A, const int32_t* col,
+                      const double* ival, double* W, cudaStream_t s) {
+    if (nw <= 0) return;
+    k_galerkin1<<<grid_for(nw, 256), 256, 0, s>>>(nw, ptr, con, A, col, ival, W);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_galerkin2(int64_t nh, const int64_t* ptr, const int32_t* con, const double* W,
+                            const int32_t* wrow, const double* ival, double* H) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nh) return;
+    double acc = 0.0;
+    for (int64_t k = ptr[t]; k < ptr[t + 1]; ++k) {
+        int r = con[k];
+        int s = r >> 2;
+        acc += ival[(int64_t)wrow[s] * 4 + (r & 3)] * W[s];
+    }
+    H[t] = acc;
+}
+
+void launch_galerkin2(int64_t nh, const int64_t* ptr, const int32_t* con, const double* W,
+                      const int32_t* wrow, const double* ival, double* H, cudaStream_t s) {
+    if (nh <= 0) return;
+    k_galerkin2<<<grid_for(nh, 256), 256, 0, s>>>(nh, ptr, con, W, wrow, ival, H);
+    NAS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ Anderson
+struct FPtrs {
+    const double* p[6];
+};
+
+// k = m previous entries: 20 accumulators max (4x4 matrix + 4 rhs)
+__global__ void __launch_bounds__(256) k_anderson_dots(int64_t cnt, int m, FPtrs F, const double* w,
+                                                      double* partial) {
+    __shared__ double sh[20][256];
+    double acc[20];
+    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
+    const double* Fm = F.p[m];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double fm = Fm[i];
+        double wi = w[i];
+        double d[4];
+        for (int a = 0; a < m; ++a) d[a] = fm - F.p[a][i];
+        for (int a = 0; a < m; ++a) {
+            for (int b = 0; b < m; ++b) acc[a * m + b] += wi * d[a] * d[b];
+            acc[m * m + a] += wi * d[a] * fm;
+        }
+    }
+    int K = m * m + m;
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off)
+            for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < K; ++k) partial[(int64_t)blockIdx.x * K + k] = sh[k][0];
+}
+
+void launch_anderson_dots(int64_t cnt, int m, const double* const* F, const double* w, double* partial,
+                          double* out, cudaStream_t s) {
+    if (m < 1 || m > 4) fail(NAS_E_INVALID_ARG, "anderson depth");
+    FPtrs f{};
+    for (int a = 0; a <= m; ++a) f.p[a] = F[a];
+    int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (cnt + 255) / 256));
+    k_anderson_dots<<<nb, 256, 0, s>>>(cnt, m, f, w, partial);
+    NAS_CHECK_LAUNCH();
+    int K = m * m + m;
+    k_reduce_partials<<<1, 128, 0, s>>>(nb, K, partial, out);
+    NAS_CHECK_LAUNCH();
+}
+
+struct MixArgs {
+    const double* rin[6];
+    const double* F[6];
+    double alpha[5];
+};
+
+__global__ void k_anderson_mix(int64_t cnt, int m, MixArgs a, double beta, double* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    double rm = a.rin[m][i], fm = a.F[m][i];
+    double r = rm, f = fm;
+    for (int j = 0; j < m; ++j) {
+        r += a.alpha[j] * (a.rin[j][i] - rm);
+        f += a.alpha[j] * (a.F[j][i] - fm);
+    }
+    out[i] = r + beta * f;
+}
+
+void launch_anderson_mix(int64_t cnt, int m, const double* const* rin, const double* const* F,
+                         const double* alpha, double beta, double* rho_new, cudaStream_t s) {
+    if (m < 0 || m > 4) fail(NAS_E_INVALID_ARG, "anderson depth");
+    MixArgs a{};
+    for (int j = 0; j <= m; ++j) {
+        a.rin[j] = rin[j];
+        a.F[j] = F[j];
+    }
+    for (int j = 0; j < m; ++j) a.alpha[j] = alpha[j];
+    k_anderson_mix<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, m, a, beta, rho_new);
+    NAS_CHECK_LAUNCH();
+}
+
+}  // namespace nas

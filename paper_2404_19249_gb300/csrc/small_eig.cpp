@@ -1,0 +1,741 @@
+// Dense generalized symmetric-definite eigensolver for the small augmented
+// problem F_A U = lambda F_B U (Sec. 3.3, eq. st1), host side.
+//
+// Reduction to standard form with the Cholesky factor of F_B, Householder
+// tridiagonalisation, the k smallest eigenvalues by bisection on Sturm
+// sequence counts, eigenvectors of the tridiagonal matrix by inverse
+// iteration (with re-orthogonalisation inside clusters of close
+// eigenvalues), then back-transformation.  The O(m^3) loops are split over
+// OpenMP threads.
+#include "small_eig.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace nas {
+
+// lower Cholesky in place (row-major, lower triangle); returns false if not SPD
+static bool cholesky(int m, std::vector<double>& L) {
+    for (int j = 0; j < m; ++j) {
+        double d = L[(size_t)j * m + j];
+        for (int k = 0; k < j; ++k) d -= L[(size_t)j * m + k] * L[(size_t)j * m + k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        L[(size_t)j * m + j] = d;
+        const double* Lj = &L[(size_t)j * m];
+#pragma omp parallel for schedule(static) if (m - j > 256)
+        for (int i = j + 1; i < m; ++i) {
+            double* Li = &L[(size_t)i * m];
+            double s = Li[j];
+            for (int k = 0; k < j; ++k) s -= Li[k] * Lj[k];
+            Li[j] = s / d;
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j) L[(size_t)i * m + j] = 0.0;
+    return true;
+}
+
+// C = L^{-1} A L^{-T} (A symmetric, full storage built from its lower triangle)
+static void reduce_standard(int m, const std::vector<double>& L, const double* A, std::vector<double>& C) {
+    std::vector<double> X((size_t)m * m);
+    // X^T = (L^{-1} A)^T ... compute column by column of L^{-1} A: column c solves L y = A[:,c]
+    // A symmetric: A[:,c] = A[c,:] (use lower triangle)
+    auto a = [&](int i, int j) { return i >= j ? A[(size_t)i * m + j] : A[(size_t)j * m + i]; };
+    // Y = L^{-1} A, stored transposed: Yt[c][i] = Y[i][c]
+    std::vector<double> Yt((size_t)m * m);
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < m; ++c) {
+        double* y = &Yt[(size_t)c * m];
+        for (int i = 0; i < m; ++i) {
+            double s = a(i, c);
+            const double* Li = &L[(size_t)i * m];
+            for (int k = 0; k < i; ++k) s -= Li[k] * y[k];
+            y[i] = s / Li[i];
+        }
+    }
+    // C = L^{-1} Y^T ; Y^T = (L^{-1}A)^T = A L^{-T}; column c of Y^T is row c of Y = Yt[:, c]
+    // C[:,c] solves L z = (Y^T)[:,c] = Y[c,:] = Yt[*][c]... use Y^T[i][c] = Y[c][i] = Yt[i][c]
+    C.assign((size_t)m * m, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < m; ++c) {
+        std::vector<double> z(m);
+        for (int i = 0; i < m; ++i) {
+            double s = Yt[(size_t)i * m + c];
+            const double* Li = &L[(size_t)i * m];
+            for (int k = 0; k < i; ++k) s -= Li[k] * z[k];
+            z[i] = s / Li[i];
+        }
+        for (int i = 0; i < m; ++i) C[(size_t)i * m + c] = z[i];
+    }
+    // symmetrise
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < i; ++j) {
+            double v = 0.5 * (C[(size_t)i * m + j] + C[(size_t)j * m + i]);
+            C[(size_t)i * m + j] = v;
+            C[(size_t)j * m + i] = v;
+        }
+}
+
+// Householder tridiagonalisation of symmetric C (full storage, overwritten).
+// Reflector j acts on entries j+1..m-1: H_j = I - tau_j v_j v_j^T with v_j
+// stored in V (row j), v_j[j+1] = 1.  T = Q^T C Q, Q = H_0 H_1 ... H_{m-3}.
+static void tridiagonalise(int m, std::vector<double>& C, std::vector<double>& d, std::vector<double>& e,
+                           std::vector<double>& V, std::vector<double>& tau) {
+    d.assign(m, 0.0);
+    e.assign(std::max(m - 1, 0), 0.0);
+    V.assign((size_t)m * m, 0.0);
+    tau.assign(m, 0.0);
+    std::vector<double> p(m), w(m), v(m);
+    for (int j = 0; j + 2 < m; ++j) {
+        int n1 = m - j - 1;  // length of x = C[j+1:, j]
+        double* x = &v[0];
+        double xnorm2 = 0.0;
+        for (int i = 0; i < n1; ++i) {
+            x[i] = C[(size_t)(j + 1 + i) * m + j];
+            if (i > 0) xnorm2 += x[i] * x[i];
+        }
+        double alpha = x[0];
+        if (xnorm2 == 0.0) {
+            tau[j] = 0.0;
+            e[j] = alpha;
+            continue;
+        }
+        double beta = -std::copysign(std::sqrt(alpha * alpha + xnorm2), alpha);
+        double t = (beta - alpha) / beta;
+        double scale = 1.0 / (alpha - beta);
+        for (int i = 1; i < n1; ++i) x[i] *= scale;
+        x[0] = 1.0;
+        tau[j] = t;
+        e[j] = beta;
+        for (int i = 0; i < n1; ++i) V[(size_t)j * m + j + 1 + i] = x[i];
+        // p = tau * C22 v
+#pragma omp parallel for schedule(static) if (n1 > 256)
+        for (int i = 0; i < n1; ++i) {
+            const double* Ci = &C[(size_t)(j + 1 + i) * m + j + 1];
+            double s = 0.0;
+            for (int k = 0; k < n1; ++k) s += Ci[k] * x[k];
+            p[i] = t * s;
+        }
+        double pv = 0.0;
+        for (int i = 0; i < n1; ++i) pv += p[i] * x[i];
+        for (int i = 0; i < n1; ++i) w[i] = p[i] - 0.5 * t * pv * x[i];
+        // C22 -= v w^T + w v^T
+#pragma omp parallel for schedule(static) if (n1 > 256)
+        for (int i = 0; i < n1; ++i) {
+            double* Ci = &C[(size_t)(j + 1 + i) * m + j + 1];
+            double xi = x[i], wi = w[i];
+            for (int k = 0; k < n1; ++k) Ci[k] -= xi * w[k] + wi * x[k];
+        }
+    }
+    for (int i = 0; i < m; ++i) d[i] = C[(size_t)i * m + i];
+    if (m >= 2) e[m - 2] = C[(size_t)(m - 1) * m + (m - 2)];
+}
+
+// number of eigenvalues of T smaller than x (Sturm count of the LDL^T pivots)
+static int sturm_count(int m, const std::vector<double>& d, const std::vector<double>& e, double x) {
+    const double tiny = std::numeric_limits<double>::min();
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < m; ++i) {
+        if (std::fabs(q) < tiny) q = -tiny;
+        q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+// Solve (T - lam I) x = b for tridiagonal T by Gaussian elimination with
+// partial pivoting (x overwrites b).
+static void tri_solve(int m, const std::vector<double>& d, const std::vector<double>& e, double lam,
+                      double pert, std::vector<double>& b) {
+    std::vector<double> a(m), c(m), u2(m, 0.0);
+    std::vector<double> dd(m);
+    for (int i = 0; i < m; ++i) dd[i] = d[i] - lam;
+    // rows: sub e[i-1], diag dd[i], super e[i]
+    std::vector<double> sub(m, 0.0), sup(m, 0.0);
+    for (int i = 0; i + 1 < m; ++i) {
+        sup[i] = e[i];
+        sub[i + 1] = e[i];
+    }
+    // U has diag a, super c, super2 u2
+    std::vector<double> diag(dd), up(sup);
+    std::vector<int> piv(m, 0);
+    for (int i = 0; i < m; ++i) {
+        a[i] = diag[i];
+        c[i] = up[i];
+    }
+    for (int i = 0; i + 1 < m; ++i) {
+        double s = sub[i + 1];
+        if (std::fabs(a[i]) >= std::fabs(s)) {
+            if (a[i] == 0.0) a[i] = pert;
+            double l = s / a[i];
+            a[i + 1] -= l * c[i];
+            b[i + 1] -= l * b[i];
+            piv[i] = 0;
+        } else {
+            // swap rows i and i+1
+            double l = a[i] / s;
+            double ai1 = a[i + 1], ci1 = (i + 1 < m - 1) ? c[i + 1] : 0.0;
+            a[i] = s;
+            double ci = c[i];
+            c[i] = ai1;
+            u2[i] = ci1;
+            a[i + 1] = ci - l * ai1;
+            if (i + 1 < m - 1) c[i + 1] = -l * ci1;
+            std::swap(b[i], b[i + 1]);
+            b[i + 1] -= l * b[i];
+            piv[i] = 1;
+        }
+    }
+    if (a[m - 1] == 0.0) a[m - 1] = pert;
+    // back substitution
+    b[m - 1] /= a[m - 1];
+    if (m >= 2) b[m - 2] = (b[m - 2] - c[m - 2] * b[m - 1]) / a[m - 2];
+    for (int i = m - 3; i >= 0; --i) b[i] = (b[i] - c[i] * b[i + 1] - u2[i] * b[i + 2]) / a[i];
+}
+
+int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, double* U) {
+    if (k > m) return -1;
+    std::vector<double> L((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j <= i; ++j) L[(size_t)i * m + j] = B[(size_t)i * m + j];
+    if (!cholesky(m, L)) return -1;
+    std::vector<double> C;
+    reduce_standard(m, L, A, C);
+    std::vector<double> d, e, V, tau;
+    tridiagonalise(m, C, d, e, V, tau);
+    // Gershgorin interval
+    double lo = 1e300, hi = -1e300, tnorm = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
+        lo = std::min(lo, d[i] - r);
+        hi = std::max(hi, d[i] + r);
+        tnorm = std::max(tnorm, std::fabs(d[i]) + r);
+    }
+    const double eps = std::numeric_limits<double>::epsilon();
+    lo -= 2 * eps * tnorm + 1e-300;
+    hi += 2 * eps * tnorm + 1e-300;
+    std::vector<double> w(k);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < k; ++i) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (a + b);
+            if (mid <= a || mid >= b) break;
+            if (sturm_count(m, d, e, mid) > i)
+                b = mid;
+            else
+                a = mid;
+            if (b - a <= 2.0 * eps * std::max(std::fabs(a), std::fabs(b)) + 1e-300) break;
+        }
+        w[i] = 0.5 * (a + b);
+    }
+    // eigenvectors of T by inverse iteration; clusters re-orthogonalised
+    std::vector<double> Z((size_t)k * m);
+    const double pert = eps * tnorm + 1e-300;
+    const double clus = 1e-3 * tnorm;
+    int start = 0;
+    for (int i = 0; i < k; ++i) {
+        if (i > 0 && std::fabs(w[i] - w[i - 1]) > clus) start = i;
+        std::vector<double> x(m);
+        for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * std::sin(0.7 * r + 1.3 * i);
+        double shift = w[i];
+        for (int it = 0; it < 4; ++it) {
+            tri_solve(m, d, e, shift, pert, x);
+            for (int j = start; j < i; ++j) {
+                const double* zj = &Z[(size_t)j * m];
+                double s = 0.0;
+                for (int r = 0; r < m; ++r) s += zj[r] * x[r];
+                for (int r = 0; r < m; ++r) x[r] -= s * zj[r];
+            }
+            double nrm = 0.0;
+            for (int r = 0; r < m; ++r) nrm += x[r] * x[r];
+            nrm = std::sqrt(nrm);
+            if (!(nrm > 0)) {
+                for (int r = 0; r < m; ++r) x[r] = (r == i) ? 1.0 : 0.0;
+                nrm = 1.0;
+            }
+            for (int r = 0; r < m; ++r) x[r] /= nrm;
+        }
+        std::copy(x.begin(), x.end(), Z.begin() + (size_t)i * m);
+    }
+    // back-transform: y = Q z = H_0 ... H_{m-3} z, then U = L^{-T} y
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < k; ++i) {
+        double* z = &Z[(size_t)i * m];
+        for (int j = m - 3; j >= 0; --j) {
+            if (tau[j] == 0.0) continue;
+            const double* v = &V[(size_t)j * m];
+            double s = 0.0;
+            for (int r = j + 1; r < m; ++r) s += v[r] * z[r];
+            s *= tau[j];
+            for (int r = j + 1; r < m; ++r) z[r] -= s * v[r];
+        }
+        // solve L^T u = z (backward)
+        for (int r = m - 1; r >= 0; --r) {
+            double s = z[r];
+            for (int q = r + 1; q < m; ++q) s -= L[(size_t)q * m + r] * z[q];
+            z[r] = s / L[(size_t)r * m + r];
+        }
+    }
+    // Rayleigh quotients refine the eigenvalues: lambda = u^T A u (u is B-normalised)
+    auto a = [&](int r, int c) { return r >= c ? A[(size_t)r * m + c] : A[(size_t)c * m + r]; };
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < k; ++i) {
+        const double* u = &Z[(size_t)i * m];
+        double s = 0.0;
+        for (int r = 0; r < m; ++r) {
+            double t = 0.0;
+            for (int c = 0; c < m; ++c) t += a(r, c) * u[c];
+            s += u[r] * t;
+        }
+        lam[i] = s;
+    }
+    for (int r = 0; r < m; ++r)
+        for (int i = 0; i < k; ++i) U[(size_t)r * k + i] = Z[(size_t)i * m + r];
+    return 0;
+}
+
+int chol_factor(int m, double* A) {
+    std::vector<double> L(A, A + (size_t)m * m);
+    if (!cholesky(m, L)) return -1;
+    std::copy(L.begin(), L.end(), A);
+    return 0;
+}
+
+void chol_solve(int m, const double* L, int k, double* B) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < k; ++c) {
+        std::vector<double> y(m);
+        for (int i = 0; i < m; ++i) {
+            double s = B[(size_t)i * k + c];
+            const double* Li = L + (size_t)i * m;
+            for (int j = 0; j < i; ++j) s -= Li[j] * y[j];
+            y[i] = s / Li[i];
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int j = i + 1; j < m; ++j) s -= L[(size_t)j * m + i] * y[j];
+            y[i] = s / L[(size_t)i * m + i];
+        }
+        for (int i = 0; i < m; ++i) B[(size_t)i * k + c] = y[i];
+    }
+}
+
+void jacobi_eig(int m, double* A, double* w, double* V) {
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) V[i * m + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                tot += A[i * m + j] * A[i * m + j];
+                if (i != j) off += A[i * m + j] * A[i * m + j];
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                if (std::fabs(apq) <= 1e-18 * std::sqrt(std::fabs(A[p * m + p] * A[q * m + q]))) {
+                    A[p * m + q] = A[q * m + p] = 0.0;
+                    continue;
+                }
+                double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                double t = std::copysign(1.0, theta) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < m; ++k) {
+                    double akp = A[k * m + p], akq = A[k * m + q];
+                    A[k * m + p] = c * akp - s * akq;
+                    A[k * m + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {
+                    double apk = A[p * m + k], aqk = A[q * m + k];
+                    A[p * m + k] = c * apk - s * aqk;
+                    A[q * m + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    double vkp = V[k * m + p], vkq = V[k * m + q];
+                    V[k * m + p] = c * vkp - s * vkq;
+                    V[k * m + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    // sort ascending
+    std::vector<int> idx(m);
+    for (int i = 0; i < m; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A[a * m + a] < A[b * m + b]; });
+    std::vector<double> Vs(m * m);
+    for (int j = 0; j < m; ++j) {
+        w[j] = A[idx[j] * m + idx[j]];
+        for (int i = 0; i < m; ++i) Vs[i * m + j] = V[i * m + idx[j]];
+    }
+    std::memcpy(V, Vs.data(), sizeof(double) * m * m);
+}
+
+int small_solve(int n, const double* A, const double* b, double* x) {
+    double M[8][9];
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) M[i][j] = A[i * n + j];
+        M[i][n] = b[i];
+    }
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
+        if (M[p][c] == 0.0) return -1;
+        if (p != c)
+            for (int j = 0; j <= n; ++j) std::swap(M[p][j], M[c][j]);
+        for (int r = c + 1; r < n; ++r) {
+            double l = M[r][c] / M[c][c];
+            for (int j = c; j <= n; ++j) M[r][j] -= l * M[c][j];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = M[i][n];
+        for (int j = i + 1; j < n; ++j) s -= M[i][j] * x[j];
+        x[i] = s / M[i][i];
+    }
+    return 0;
+}
+
+}  // namespace nas
+
+// ------------------------------------------------------------------ LOBPCG
+namespace nas {
+
+// Y[m][k] = F X[m][k]
+static void arrow_apply(const ArrowMat& F, int k, const double* X, double* Y) {
+    const int64_t nH = F.nH;
+    const int Na = F.Na;
+    const int64_t m = nH + Na;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nH; ++i) {
+        double* y = Y + i * k;
+        for (int j = 0; j < k; ++j) y[j] = 0.0;
+        for (int p = F.ptr[i]; p < F.ptr[i + 1]; ++p) {
+            const double v = F.sval[p];
+            const double* x = X + (int64_t)F.col[p] * k;
+            for (int j = 0; j < k; ++j) y[j] += v * x[j];
+        }
+        for (int a = 0; a < Na; ++a) {
+            const double v = F.Bd[i * Na + a];
+            const double* x = X + (nH + a) * k;
+            for (int j = 0; j < k; ++j) y[j] += v * x[j];
+        }
+    }
+    // border rows: Bd^T X_H + Cd X_a (reduction over nH, split by columns)
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < Na; ++a) {
+        double* y = Y + (nH + a) * k;
+        for (int j = 0; j < k; ++j) y[j] = 0.0;
+        for (int64_t i = 0; i < nH; ++i) {
+            const double v = F.Bd[i * Na + a];
+            const double* x = X + i * k;
+            for (int j = 0; j < k; ++j) y[j] += v * x[j];
+        }
+        for (int b = 0; b < Na; ++b) {
+            const double v = F.Cd[a * Na + b];
+            const double* x = X + (nH + b) * k;
+            for (int j = 0; j < k; ++j) y[j] += v * x[j];
+        }
+    }
+    (void)m;
+}
+
+static double arrow_diag(const ArrowMat& F, int64_t i) {
+    if (i < F.nH) {
+        for (int p = F.ptr[i]; p < F.ptr[i + 1]; ++p)
+            if (F.col[p] == i) return F.sval[p];
+        return 0.0;
+    }
+    int64_t a = i - F.nH;
+    return F.Cd[a * F.Na + a];
+}
+
+// G[ns][ns] = S^T T (S, T are [m][ns] row-major)
+static void gram(int64_t m, int ns, const double* S, const double* T, double* G) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) {
+            double s = 0.0;
+            for (int64_t i = 0; i < m; ++i) s += S[i * ns + a] * T[i * ns + b];
+            G[a * ns + b] = s;
+        }
+}
+
+// Y[m][kout] = S[m][ns] C[ns][kout]
+static void mult(int64_t m, int ns, const double* S, int kout, const double* Cm, double* Y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        double* y = Y + i * kout;
+        for (int j = 0; j < kout; ++j) y[j] = 0.0;
+        for (int a = 0; a < ns; ++a) {
+            const double s = S[i * ns + a];
+            if (s == 0.0) continue;
+            const double* c = Cm + a * kout;
+            for (int j = 0; j < kout; ++j) y[j] += s * c[j];
+        }
+    }
+}
+
+// All eigenpairs of a small symmetric matrix (ascending): the tridiagonal
+// solver with B = I.  A is not modified; V [m][m] row-major, columns = vectors.
+static void sym_eig_all(int m, const double* A, double* w, double* V) {
+    std::vector<double> I((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) I[(size_t)i * m + i] = 1.0;
+    if (dense_gen_eig(m, A, I.data(), m, w, V) != 0) {
+        std::vector<double> Ac(A, A + (size_t)m * m);
+        jacobi_eig(m, Ac.data(), w, V);
+    }
+}
+
+// Rayleigh-Ritz on basis S [m][ns] with AS, BS: lowest k Ritz pairs.  The basis
+// Gram matrix G = S^T B S is diagonalised; directions with eigenvalue below
+// 1e-14 * max are dropped.  Returns coefficient matrix Y [ns][k] and theta[k].
+static int rayleigh_ritz(int64_t m, int ns, const double* S, const double* AS, const double* BS, int k,
+                         std::vector<double>& Y, std::vector<double>& theta) {
+    std::vector<double> G((size_t)ns * ns), H((size_t)ns * ns);
+    gram(m, ns, S, BS, G.data());
+    gram(m, ns, S, AS, H.data());
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < a; ++b) {
+            double g = 0.5 * (G[a * ns + b] + G[b * ns + a]);
+            G[a * ns + b] = G[b * ns + a] = g;
+            double h = 0.5 * (H[a * ns + b] + H[b * ns + a]);
+            H[a * ns + b] = H[b * ns + a] = h;
+        }
+    std::vector<double> gw(ns), GV((size_t)ns * ns);
+    sym_eig_all(ns, G.data(), gw.data(), GV.data());
+    double gmax = gw[ns - 1];
+    // directions with Gram eigenvalue below 1e-9 * max are dropped: the Gram
+    // matrix is only known to ~eps * max in absolute terms
+    std::vector<int> keep;
+    for (int a = 0; a < ns; ++a)
+        if (gw[a] > 1e-9 * gmax) keep.push_back(a);
+    int r = (int)keep.size();
+    if (r < k) return -1;
+    // Q = V_keep D^-1/2  [ns][r]
+    std::vector<double> Q((size_t)ns * r);
+    for (int a = 0; a < ns; ++a)
+        for (int j = 0; j < r; ++j) Q[a * r + j] = GV[a * ns + keep[j]] / std::sqrt(gw[keep[j]]);
+    // second pass: Q <- Q V2 D2^-1/2 with Q^T G Q = V2 D2 V2^T (restores B-orthonormality)
+    {
+        std::vector<double> GQ((size_t)ns * r), G2((size_t)r * r), w2(r), V2((size_t)r * r);
+        for (int a = 0; a < ns; ++a)
+            for (int j = 0; j < r; ++j) {
+                double sacc = 0.0;
+                for (int b = 0; b < ns; ++b) sacc += G[a * ns + b] * Q[b * r + j];
+                GQ[a * r + j] = sacc;
+            }
+        for (int i = 0; i < r; ++i)
+            for (int j = 0; j < r; ++j) {
+                double sacc = 0.0;
+                for (int a = 0; a < ns; ++a) sacc += Q[a * r + i] * GQ[a * r + j];
+                G2[i * r + j] = sacc;
+            }
+        for (int i = 0; i < r; ++i)
+            for (int j = 0; j < i; ++j) G2[i * r + j] = G2[j * r + i] = 0.5 * (G2[i * r + j] + G2[j * r + i]);
+        sym_eig_all(r, G2.data(), w2.data(), V2.data());
+        std::vector<double> Q2((size_t)ns * r);
+        for (int a = 0; a < ns; ++a)
+            for (int j = 0; j < r; ++j) {
+                double sacc = 0.0;
+                for (int i = 0; i < r; ++i) sacc += Q[a * r + i] * V2[i * r + j];
+                Q2[a * r + j] = sacc / std::sqrt(w2[j]);
+            }
+        Q.swap(Q2);
+    }
+    // Hr = Q^T H Q
+    std::vector<double> HQ((size_t)ns * r), Hr((size_t)r * r);
+    for (int a = 0; a < ns; ++a)
+        for (int j = 0; j < r; ++j) {
+            double s = 0.0;
+            for (int b = 0; b < ns; ++b) s += H[a * ns + b] * Q[b * r + j];
+            HQ[a * r + j] = s;
+        }
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < ns; ++a) s += Q[a * r + i] * HQ[a * r + j];
+            Hr[i * r + j] = s;
+        }
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < i; ++j) Hr[i * r + j] = Hr[j * r + i] = 0.5 * (Hr[i * r + j] + Hr[j * r + i]);
+    std::vector<double> hw(r), HV((size_t)r * r);
+    sym_eig_all(r, Hr.data(), hw.data(), HV.data());
+    theta.assign(hw.begin(), hw.begin() + k);
+    Y.assign((size_t)ns * k, 0.0);
+    for (int a = 0; a < ns; ++a)
+        for (int j = 0; j < k; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < r; ++i) s += Q[a * r + i] * HV[i * r + j];
+            Y[a * k + j] = s;
+        }
+    return 0;
+}
+
+int lobpcg_arrow(const ArrowMat& A, const ArrowMat& B, int nev, int nguard, double* lam, double* U, bool warm,
+                 double tol, int maxit) {
+    const int64_t m = A.nH + A.Na;
+    const int k = (int)std::min<int64_t>(nev + nguard, m);
+    if (nev > m) return -1;
+    std::vector<double> X((size_t)m * k), AX((size_t)m * k), BX((size_t)m * k);
+    // start: warm vectors for the wanted columns, deterministic pseudo-random otherwise
+    for (int64_t i = 0; i < m; ++i)
+        for (int j = 0; j < k; ++j) {
+            double r = std::sin(12.9898 * (i + 1) + 78.233 * (j + 1)) * 43758.5453;
+            X[i * k + j] = r - std::floor(r) - 0.5;
+        }
+    if (warm)
+        for (int64_t i = 0; i < m; ++i)
+            for (int j = 0; j < nev; ++j) X[i * k + j] = U[i * nev + j];
+    std::vector<double> dA(m), dB(m), T(m);
+    for (int64_t i = 0; i < m; ++i) {
+        dA[i] = arrow_diag(A, i);
+        dB[i] = arrow_diag(B, i);
+    }
+    std::vector<double> Y, theta;
+    auto refresh = [&]() {
+        arrow_apply(A, k, X.data(), AX.data());
+        arrow_apply(B, k, X.data(), BX.data());
+    };
+    refresh();
+    if (rayleigh_ritz(m, k, X.data(), AX.data(), BX.data(), k, Y, theta) != 0) return -1;
+    {
+        std::vector<double> t((size_t)m * k);
+        mult(m, k, X.data(), k, Y.data(), t.data());
+        X.swap(t);
+        refresh();
+    }
+    // diagonal preconditioner diag(A - sigma B)^-1 with sigma below the spectrum
+    double sigma = theta[0] - 0.1 * std::fabs(theta[0]) - 1.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double d = dA[i] - sigma * dB[i];
+        T[i] = d > 0 ? 1.0 / d : 1.0;
+    }
+    std::vector<double> P, AP, BP;  // previous search directions [m][np]
+    int np = 0;
+    int it = 0;
+    std::vector<double> rel(k);
+    for (; it < maxit; ++it) {
+        std::vector<double> rn(k, 0.0), an(k, 0.0), bn(k, 0.0);
+        for (int64_t i = 0; i < m; ++i)
+            for (int j = 0; j < k; ++j) {
+                double r = AX[i * k + j] - theta[j] * BX[i * k + j];
+                rn[j] += r * r;
+                an[j] += AX[i * k + j] * AX[i * k + j];
+                bn[j] += BX[i * k + j] * BX[i * k + j];
+            }
+        double worst = 0.0;
+        for (int j = 0; j < k; ++j) {
+            rel[j] = std::sqrt(rn[j]) / (std::sqrt(an[j]) + std::fabs(theta[j]) * std::sqrt(bn[j]) + 1e-300);
+            if (j < nev) worst = std::max(worst, rel[j]);
+        }
+        if (worst <= tol) break;
+        // active columns: unconverged wanted vectors and every guard vector (soft locking)
+        std::vector<int> act;
+        for (int j = 0; j < k; ++j)
+            if (j >= nev || rel[j] > 0.1 * tol) act.push_back(j);
+        const int ka = (int)act.size();
+        std::vector<double> W((size_t)m * ka);
+        for (int64_t i = 0; i < m; ++i)
+            for (int q = 0; q < ka; ++q) {
+                int j = act[q];
+                W[i * ka + q] = T[i] * (AX[i * k + j] - theta[j] * BX[i * k + j]);
+            }
+        // W <- W - X (BX)^T W, then unit B-norm columns (keeps the Gram matrix well scaled)
+        {
+            std::vector<double> Cm((size_t)k * ka), XC((size_t)m * ka);
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < ka; ++b) {
+                    double sacc = 0.0;
+                    for (int64_t i = 0; i < m; ++i) sacc += BX[i * k + a] * W[i * ka + b];
+                    Cm[a * ka + b] = sacc;
+                }
+            mult(m, k, X.data(), ka, Cm.data(), XC.data());
+            for (size_t q = 0; q < W.size(); ++q) W[q] -= XC[q];
+        }
+        std::vector<double> AW((size_t)m * ka), BW((size_t)m * ka);
+        arrow_apply(B, ka, W.data(), BW.data());
+        {
+            std::vector<double> nrm(ka, 0.0);
+            for (int64_t i = 0; i < m; ++i)
+                for (int q = 0; q < ka; ++q) nrm[q] += W[i * ka + q] * BW[i * ka + q];
+            for (int q = 0; q < ka; ++q) nrm[q] = nrm[q] > 0 ? 1.0 / std::sqrt(nrm[q]) : 0.0;
+            for (int64_t i = 0; i < m; ++i)
+                for (int q = 0; q < ka; ++q) {
+                    W[i * ka + q] *= nrm[q];
+                    BW[i * ka + q] *= nrm[q];
+                }
+        }
+        arrow_apply(A, ka, W.data(), AW.data());
+        // basis S = [X, W, P]
+        const int ns = k + ka + np;
+        std::vector<double> S((size_t)m * ns), AS((size_t)m * ns), BS((size_t)m * ns);
+        for (int64_t i = 0; i < m; ++i) {
+            for (int j = 0; j < k; ++j) {
+                S[i * ns + j] = X[i * k + j];
+                AS[i * ns + j] = AX[i * k + j];
+                BS[i * ns + j] = BX[i * k + j];
+            }
+            for (int q = 0; q < ka; ++q) {
+                S[i * ns + k + q] = W[i * ka + q];
+                AS[i * ns + k + q] = AW[i * ka + q];
+                BS[i * ns + k + q] = BW[i * ka + q];
+            }
+            for (int q = 0; q < np; ++q) {
+                S[i * ns + k + ka + q] = P[i * np + q];
+                AS[i * ns + k + ka + q] = AP[i * np + q];
+                BS[i * ns + k + ka + q] = BP[i * np + q];
+            }
+        }
+        if (rayleigh_ritz(m, ns, S.data(), AS.data(), BS.data(), k, Y, theta) != 0) {
+            if (np == 0) return -1;
+            np = 0;  // restart without P
+            continue;
+        }
+        // new X = S Y (products recomputed exactly); new P = (W, P) part of S Y, active columns
+        mult(m, ns, S.data(), k, Y.data(), X.data());
+        refresh();
+        std::vector<double> Yp((size_t)ns * ka, 0.0);
+        for (int a = k; a < ns; ++a)
+            for (int q = 0; q < ka; ++q) Yp[a * ka + q] = Y[a * k + act[q]];
+        P.assign((size_t)m * ka, 0.0);
+        AP.assign((size_t)m * ka, 0.0);
+        BP.assign((size_t)m * ka, 0.0);
+        mult(m, ns, S.data(), ka, Yp.data(), P.data());
+        np = ka;
+        // exact images of P (implicitly updated images drift and break the Rayleigh-Ritz)
+        arrow_apply(A, np, P.data(), AP.data());
+        arrow_apply(B, np, P.data(), BP.data());
+        {
+            std::vector<double> nrm(np, 0.0);
+            for (int64_t i = 0; i < m; ++i)
+                for (int q = 0; q < np; ++q) nrm[q] += P[i * np + q] * BP[i * np + q];
+            for (int q = 0; q < np; ++q) nrm[q] = nrm[q] > 0 ? 1.0 / std::sqrt(nrm[q]) : 0.0;
+            for (int64_t i = 0; i < m; ++i)
+                for (int q = 0; q < np; ++q) {
+                    P[i * np + q] *= nrm[q];
+                    AP[i * np + q] *= nrm[q];
+                    BP[i * np + q] *= nrm[q];
+                }
+        }
+    }
+    if (it >= maxit) return -1;
+    // final Rayleigh-Ritz within span X for B-orthonormal output
+    if (rayleigh_ritz(m, k, X.data(), AX.data(), BX.data(), k, Y, theta) != 0) return -1;
+    std::vector<double> Xf((size_t)m * k);
+    mult(m, k, X.data(), k, Y.data(), Xf.data());
+    for (int j = 0; j < nev; ++j) lam[j] = theta[j];
+    for (int64_t i = 0; i < m; ++i)
+        for (int j = 0; j < nev; ++j) U[i * nev + j] = Xf[i * k + j];
+    return it;
+}
+
+}  // namespace nas

@@ -1,0 +1,45 @@
+// Host-side structures around the transfer matrix I_H^h (Sec. 3.3, eq. st5):
+// the bucket grid used by the GPU point location, the transpose I^T, and the
+// gather lists that evaluate the Galerkin product A_H = I^T A_h I on the GPU
+// in two deterministic stages (W = A_h I, then A_H = I^T W).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "space.h"
+
+namespace nas {
+
+struct BucketGrid {
+    double org[3], inv_h[3];
+    int nb[3];
+    std::vector<int64_t> bptr;   // [nbuckets+1]
+    std::vector<int32_t> btet;   // coarse tets, ascending within a bucket
+};
+
+// Register every coarse tetrahedron in each bucket its bounding box meets.
+void build_buckets(const HostSpace& C, BucketGrid& G);
+
+struct GalerkinMaps {
+    int64_t nH = 0;                      // coarse dofs
+    // I^T as CSR over coarse dofs: fine rows and weights
+    std::vector<int32_t> tptr, trow;
+    std::vector<double> tval;
+    // W = A I: pattern over fine rows, coarse columns; wrow = fine row of a slot
+    std::vector<int32_t> wptr, wcol, wrow;
+    std::vector<int64_t> w1ptr;          // stage-1 lists: q = p*4 + l
+    std::vector<int32_t> w1con;
+    // A_H pattern (coarse CSR) and stage-2 lists: r = s*4 + k
+    std::vector<int32_t> hptr, hcol;
+    std::vector<int64_t> h2ptr;
+    std::vector<int32_t> h2con;
+    int64_t wnnz() const { return wptr.empty() ? 0 : wptr.back(); }
+    int64_t hnnz() const { return hptr.empty() ? 0 : hptr.back(); }
+};
+
+// icol/ival: [n_fine_dof][4] coarse dof (-1 = boundary) and weight.
+void build_galerkin(const HostSpace& F, int64_t nH, const std::vector<int32_t>& icol,
+                    const std::vector<double>& ival, GalerkinMaps& G);
+
+}  // namespace nas

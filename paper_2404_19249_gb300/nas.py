@@ -1,0 +1,302 @@
+"""Thin Python binding of the nas C ABI (include/nas.h).
+
+Argument marshalling only: every computation runs in libnas.so.  Functions
+keep the C names (nas_create, nas_set_mesh, ...) and take numpy arrays (host
+buffers) or integer device pointers (for on_device=1 calls, e.g. from
+torch.Tensor.data_ptr()).  `Solver` bundles the calls for the common case.
+
+The library must have been built (paper_2404_19249_gb300.build); importing
+this module without it raises ImportError - there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnas.so")
+
+NAS_OK = 0
+ERRORS = {
+    -1: "NAS_E_INVALID_ARG", -2: "NAS_E_MESH", -3: "NAS_E_POINT_NOT_FOUND", -4: "NAS_E_BREAKDOWN",
+    -5: "NAS_E_NOT_CONVERGED", -6: "NAS_E_CUDA", -7: "NAS_E_OOM", -8: "NAS_E_STATE", -9: "NAS_E_EIGEN",
+}
+NAS_FINE, NAS_COARSE = 0, 1
+NAS_POT_COULOMB, NAS_POT_SMOOTHED, NAS_POT_HARMONIC = 0, 1, 2
+PHASES = ["assembly", "bvp", "poisson", "blocks", "density", "mixing", "host_eig", "transfer", "spmm", "spmv"]
+(NAS_Q_SIZES, NAS_Q_EIGVALS, NAS_Q_ORBITALS, NAS_Q_RHO_IN, NAS_Q_RHO_OUT, NAS_Q_VHARTREE, NAS_Q_UHAT,
+ NAS_Q_ROWPTR, NAS_Q_COLIDX, NAS_Q_K, NAS_Q_M, NAS_Q_MVEXT, NAS_Q_ANL, NAS_Q_HTILDE, NAS_Q_TRANSFER_ELEM,
+ NAS_Q_TRANSFER_COL, NAS_Q_TRANSFER_W, NAS_Q_FA, NAS_Q_FB, NAS_Q_DOF_NODE, NAS_Q_ENERGY) = range(21)
+(NAS_OP_LDA, NAS_OP_HARTREE, NAS_OP_ASSEMBLE_MASS, NAS_OP_DENSITY, NAS_OP_APPLY_H, NAS_OP_BVP,
+ NAS_OP_GALERKIN) = range(7)
+
+
+class nas_options(C.Structure):
+    _fields_ = [
+        ("mu", C.c_double), ("tol_bvp", C.c_double), ("tol_poisson", C.c_double), ("tol_scf", C.c_double),
+        ("tol_inner", C.c_double), ("max_cg", C.c_int), ("max_poisson", C.c_int), ("max_inner", C.c_int),
+        ("max_outer", C.c_int), ("anderson_depth", C.c_int), ("anderson_beta", C.c_double),
+        ("hartree", C.c_int), ("xc", C.c_int), ("multipole", C.c_int), ("omega", C.c_double),
+        ("check_every", C.c_int), ("timing", C.c_int), ("eig_dense_max", C.c_int),
+    ]
+
+
+class nas_report(C.Structure):
+    _fields_ = [
+        ("n_orb", C.c_int), ("step", C.c_int), ("n_inner", C.c_int), ("inner_converged", C.c_int),
+        ("cg_iters", C.c_int), ("poisson_iters", C.c_int), ("drho", C.c_double), ("inner_res", C.c_double),
+        ("energy", C.c_double), ("e_band", C.c_double), ("e_hartree", C.c_double), ("e_xc", C.c_double),
+        ("e_vxc", C.c_double), ("e_nn", C.c_double), ("phase_ms", C.c_double * 16),
+        ("phase_calls", C.c_longlong * 16), ("spmm_bytes", C.c_double), ("spmm_flops", C.c_double),
+        ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_double), ("spmv_flops", C.c_double),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("phase_ms", "phase_calls")}
+        d["phase_ms"] = {p: self.phase_ms[i] for i, p in enumerate(PHASES)}
+        d["phase_calls"] = {p: self.phase_calls[i] for i, p in enumerate(PHASES)}
+        return d
+
+
+class NasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "NAS_E_?"), code, msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libnas.so is not built (%s); run paper_2404_19249_gb300.build" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    P, I64, D, VP = C.POINTER, C.c_int64, C.c_double, C.c_void_p
+    sig = {
+        "nas_default_options": (None, [P(nas_options)]),
+        "nas_version": (C.c_char_p, []),
+        "nas_create": (C.c_int, [P(VP), C.c_int, VP]),
+        "nas_destroy": (None, [VP]),
+        "nas_last_error": (C.c_char_p, [VP]),
+        "nas_set_mesh": (C.c_int, [VP, C.c_int, C.c_int, I64, VP, I64, VP]),
+        "nas_set_system": (C.c_int, [VP, C.c_int, VP, VP, C.c_int, D, C.c_int, VP]),
+        "nas_set_options": (C.c_int, [VP, P(nas_options)]),
+        "nas_init": (C.c_int, [VP, VP]),
+        "nas_step": (C.c_int, [VP, P(nas_report)]),
+        "nas_solve": (C.c_int, [VP, P(nas_report)]),
+        "nas_get": (C.c_int, [VP, C.c_int, VP, C.c_size_t, C.c_int]),
+        "nas_set_state": (C.c_int, [VP, VP, VP, VP, C.c_int]),
+        "nas_apply": (C.c_int, [VP, C.c_int, VP, I64, VP, C.c_int]),
+        "nas_spmm_f64": (C.c_int, [I64, VP, VP, VP, C.c_int, VP, VP, VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+EXPORTS = [
+    "nas_default_options", "nas_version", "nas_create", "nas_destroy", "nas_last_error", "nas_set_mesh",
+    "nas_set_system", "nas_set_options", "nas_init", "nas_step", "nas_solve", "nas_get", "nas_set_state",
+    "nas_apply", "nas_spmm_f64",
+]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return C.c_void_p(a)
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ------------------------------------------------------------------ C-named wrappers
+def nas_default_options():
+    o = nas_options()
+    lib.nas_default_options(C.byref(o))
+    return o
+
+
+def nas_create(device=0, stream=0):
+    h = C.c_void_p()
+    r = lib.nas_create(C.byref(h), int(device), C.c_void_p(stream or None))
+    if r != NAS_OK:
+        raise NasError(r, "nas_create failed (device %d)" % device)
+    return h
+
+
+def nas_destroy(h):
+    lib.nas_destroy(h)
+
+
+def _check(h, r):
+    if r != NAS_OK:
+        raise NasError(r, lib.nas_last_error(h).decode())
+    return r
+
+
+def nas_set_mesh(h, which, order, xyz, tet):
+    xyz = _c(xyz, np.float64)
+    tet = _c(tet, np.int32)
+    return _check(h, lib.nas_set_mesh(h, which, order, xyz.shape[0], _ptr(xyz), tet.shape[0], _ptr(tet)))
+
+
+def nas_set_system(h, R, Z, potential, smooth_a, occ):
+    R = _c(np.asarray(R).reshape(-1, 3), np.float64)
+    Z = _c(Z, np.float64)
+    occ = _c(occ, np.float64)
+    return _check(h, lib.nas_set_system(h, len(Z), _ptr(R) if len(Z) else None, _ptr(Z) if len(Z) else None,
+                                        int(potential), float(smooth_a), len(occ), _ptr(occ)))
+
+
+def nas_set_options(h, opt):
+    return _check(h, lib.nas_set_options(h, C.byref(opt)))
+
+
+def nas_init(h, psi0=None):
+    p = None if psi0 is None else _c(psi0, np.float64)
+    return _check(h, lib.nas_init(h, _ptr(p)))
+
+
+def nas_step(h):
+    rep = nas_report()
+    r = lib.nas_step(h, C.byref(rep))
+    if r not in (NAS_OK, -5):
+        _check(h, r)
+    return r, rep
+
+
+def nas_solve(h):
+    rep = nas_report()
+    r = lib.nas_solve(h, C.byref(rep))
+    if r not in (NAS_OK, -5):
+        _check(h, r)
+    return r, rep
+
+
+def nas_get(h, what, out, on_device=0):
+    """Copy a quantity into `out` (numpy array, or device pointer int with nbytes via tuple)."""
+    if isinstance(out, tuple):
+        ptr, nbytes = out
+        return _check(h, lib.nas_get(h, what, C.c_void_p(ptr), nbytes, on_device))
+    return _check(h, lib.nas_get(h, what, _ptr(out), out.nbytes, 0))
+
+
+def nas_set_state(h, lam, psi, rho_in, on_device=0):
+    """lam/psi/rho_in: numpy arrays (host), or integer pointers (host memory
+    when on_device=0, e.g. pinned torch tensors; device memory when 1)."""
+    if all(isinstance(x, int) for x in (lam, psi, rho_in)):
+        return _check(h, lib.nas_set_state(h, C.c_void_p(lam), C.c_void_p(psi), C.c_void_p(rho_in),
+                                           int(on_device)))
+    lam, psi, rho_in = (_c(x, np.float64) for x in (lam, psi, rho_in))
+    return _check(h, lib.nas_set_state(h, _ptr(lam), _ptr(psi), _ptr(rho_in), 0))
+
+
+def nas_apply(h, op, x, out, cnt=0, on_device=0):
+    if on_device:
+        return _check(h, lib.nas_apply(h, op, C.c_void_p(x), cnt, C.c_void_p(out), 1))
+    x = _c(x, np.float64)
+    return _check(h, lib.nas_apply(h, op, _ptr(x), cnt or x.size, _ptr(out), 0))
+
+
+def nas_spmm_f64(n_rows, row_ptr, col, val, N, X, Y, stream=0):
+    """Device-pointer SpMM (all pointer arguments are ints)."""
+    r = lib.nas_spmm_f64(n_rows, C.c_void_p(row_ptr), C.c_void_p(col), C.c_void_p(val), N, C.c_void_p(X),
+                         C.c_void_p(Y), C.c_void_p(stream or None))
+    if r != NAS_OK:
+        raise NasError(r, "nas_spmm_f64")
+    return r
+
+
+# ------------------------------------------------------------------ convenience
+class Solver:
+    """One context with an instance loaded (workloads.Instance-like object)."""
+
+    def __init__(self, inst, device=0, stream=0, **options):
+        self.h = nas_create(device, stream)
+        self.inst = inst
+        nas_set_mesh(self.h, NAS_FINE, inst.order, inst.fine_xyz, inst.fine_tet)
+        nas_set_mesh(self.h, NAS_COARSE, 1, inst.coarse_xyz, inst.coarse_tet)
+        nas_set_system(self.h, inst.R, inst.Z, inst.potential, inst.smooth_a, inst.occ)
+        o = nas_default_options()
+        o.mu = -1.0 if inst.mu is None else float(inst.mu)
+        o.tol_scf = inst.tol_scf
+        o.tol_inner = inst.tol_scf
+        o.tol_bvp = inst.tol_bvp
+        o.tol_poisson = inst.tol_poisson
+        o.max_inner = inst.max_inner
+        o.max_outer = inst.max_outer
+        o.hartree = int(inst.hartree)
+        o.xc = int(inst.xc)
+        o.omega = inst.omega
+        for k, v in options.items():
+            setattr(o, k, v)
+        self.opt = o
+        nas_set_options(self.h, o)
+
+    def close(self):
+        if self.h:
+            nas_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, psi0=None):
+        nas_init(self.h, psi0)
+
+    def step(self):
+        return nas_step(self.h)
+
+    def sizes(self):
+        v = np.zeros(16, dtype=np.int64)
+        nas_get(self.h, NAS_Q_SIZES, v)
+        keys = ["n", "nnz", "nH", "hnnz", "ne", "nq", "nnode", "N", "nb", "nnzb", "nv", "order", "nec"]
+        return {k: int(v[i]) for i, k in enumerate(keys)}
+
+    def get(self, what):
+        s = self.sizes()
+        n, N, nnz, nqt = s["n"], s["N"], s["nnz"], s["ne"] * s["nq"]
+        m = s["nH"] + N
+        shapes = {
+            NAS_Q_EIGVALS: ((N,), np.float64), NAS_Q_ORBITALS: ((n, N), np.float64),
+            NAS_Q_RHO_IN: ((s["ne"], s["nq"]), np.float64), NAS_Q_RHO_OUT: ((s["ne"], s["nq"]), np.float64),
+            NAS_Q_VHARTREE: ((s["nnode"],), np.float64), NAS_Q_UHAT: ((n, N), np.float64),
+            NAS_Q_ROWPTR: ((n + 1,), np.int32), NAS_Q_COLIDX: ((nnz,), np.int32), NAS_Q_K: ((nnz,), np.float64),
+            NAS_Q_M: ((nnz,), np.float64), NAS_Q_MVEXT: ((nnz,), np.float64), NAS_Q_ANL: ((nnz,), np.float64),
+            NAS_Q_HTILDE: ((nnz,), np.float64), NAS_Q_TRANSFER_ELEM: ((n,), np.int32),
+            NAS_Q_TRANSFER_COL: ((n, 4), np.int32), NAS_Q_TRANSFER_W: ((n, 4), np.float64),
+            NAS_Q_FA: ((m, m), np.float64), NAS_Q_FB: ((m, m), np.float64), NAS_Q_DOF_NODE: ((n,), np.int32),
+            NAS_Q_ENERGY: ((6,), np.float64),
+        }
+        shape, dt = shapes[what]
+        out = np.zeros(shape, dtype=dt)
+        if what in (NAS_Q_FA, NAS_Q_FB):
+            # the last small problem may be the coarse-only one (m = nH)
+            for mm in (m, s["nH"]):
+                o2 = np.zeros((mm, mm))
+                try:
+                    nas_get(self.h, what, o2)
+                    return o2
+                except NasError:
+                    continue
+        nas_get(self.h, what, out)
+        return out
+
+    def csr(self, what):
+        import scipy.sparse as sp
+        s = self.sizes()
+        rp = self.get(NAS_Q_ROWPTR)
+        ci = self.get(NAS_Q_COLIDX)
+        return sp.csr_matrix((self.get(what), ci, rp), shape=(s["n"], s["n"]))
+
+    def apply(self, op, x, out_shape, cnt=0):
+        out = np.zeros(out_shape)
+        nas_apply(self.h, op, x, out, cnt=cnt)
+        return out

@@ -73,13 +73,17 @@ typedef struct nas_options {
     int    timing;         /* 1: record per-kernel CUDA-event times (nas_report)     */
     int    eig_dense_max;  /* small problems up to this size use the dense host
                               eigensolver, larger ones warm-started LOBPCG           */
+    double eig_tol;        /* LOBPCG relative residual; <= 0: adaptive, 1e-3 x the
+                              previous inner-SCF residual clamped to [1e-11, 1e-4]  */
+    int    spmv_lanes;     /* lanes per row of the Poisson SpMV (4, 8, 16, 32);
+                              0 = chosen from the mean row length                    */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
  * tol_poisson = 1e-12, tol_scf = tol_inner = 1e-8, max_cg = 2000,
  * max_poisson = 20000, max_inner = 50, max_outer = 100, depth 5, beta 0.7,
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
- * eig_dense_max = 1200. */
+ * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto). */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -121,6 +125,7 @@ typedef struct nas_report {
     long long kernel_launches;/* kernels this library launched during the step       */
     double spmv_bytes;        /* same for the SpMV launches (N = 1)                  */
     double spmv_flops;
+    int    eig_iters;         /* host LOBPCG iterations of the last step (0: dense)   */
 } nas_report;
 
 /* ------------------------------------------------------------------ context */
@@ -246,6 +251,20 @@ int nas_apply(nas_ctx* ctx, int op, const void* in, int64_t cnt, void* out, int 
  * the cost of st4 and the N boundary value problems). */
 int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
                  const double* val, int N, const double* X, double* Y, void* stream);
+
+/* Stand-alone weighted column dot products, FP64, on device buffers:
+ *   out[c] = sum_i w[i] X[i][c] Y[i][c]   for c < N   (w == NULL: w[i] = 1)
+ * X, Y [n][N] row-major, w [n], out [N]: device pointers; stream: cudaStream_t.
+ * This is the reduction behind the density stop test ||rho_out - rho_in||_0
+ * of Algorithm 3 and the Anderson inner products (Sec. 5, eq. mix6), with the
+ * quadrature weights as w.  The sum is taken in a fixed order (per-block
+ * partial sums, then one ordered pass), so repeated calls are bit-identical.
+ * Scratch for the partial sums (<= 1216 * N doubles) is allocated and freed
+ * on `stream` by the library (stream-ordered allocator).
+ * Errors: NAS_E_INVALID_ARG (n < 0, N not in 1..256, NULL X/Y/out),
+ * NAS_E_CUDA (launch or allocation failure). */
+int nas_coldot_f64(int64_t n, int N, const double* X, const double* Y, const double* w, double* out,
+                   void* stream);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,8 @@ void nas_default_options(nas_options* o) {
     o->check_every = 1;
     o->timing = 0;
     o->eig_dense_max = 1200;
+    o->eig_tol = -1.0;
+    o->spmv_lanes = 0;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -93,6 +95,8 @@ void nas_destroy(nas_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->pcg1_exec) cudaGraphExecDestroy(c->pcg1_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -229,6 +233,25 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, con
     } catch (const Error& e) {
         return e.code;
     }
+}
+
+int nas_coldot_f64(int64_t n, int N, const double* X, const double* Y, const double* w, double* out,
+                   void* stream) {
+    if (n < 0 || N < 1 || N > 256 || !X || !Y || !out) return NAS_E_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* partial = nullptr;
+    size_t bytes = sizeof(double) * (size_t)nas::reduce_partial_size(N);
+    if (cudaMallocAsync(reinterpret_cast<void**>(&partial), bytes, s) != cudaSuccess) return NAS_E_CUDA;
+    int rc = NAS_OK;
+    try {
+        const double* Xs[1] = {X};
+        const double* Ys[1] = {Y};
+        nas::launch_coldots(n, N, 1, Xs, Ys, w, partial, out, s);
+    } catch (const Error& e) {
+        rc = e.code;
+    }
+    if (cudaFreeAsync(partial, s) != cudaSuccess && rc == NAS_OK) rc = NAS_E_CUDA;
+    return rc;
 }
 
 }  // extern "C"

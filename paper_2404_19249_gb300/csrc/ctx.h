@@ -12,6 +12,19 @@
 #include "space.h"
 #include "transfer_setup.h"
 
+// identity of a captured Poisson PCG graph (its baked-in pointers and parameters)
+struct Pcg1Key {
+    const void* ptr[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double tol = 0.0;
+    int lanes = 0;
+    int64_t n = 0;
+    bool operator==(const Pcg1Key& o) const {
+        for (int i = 0; i < 8; ++i)
+            if (ptr[i] != o.ptr[i]) return false;
+        return tol == o.tol && lanes == o.lanes && n == o.n;
+    }
+};
+
 struct nas_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -76,6 +89,12 @@ struct nas_ctx {
     nas::DBuf<double> d_blk_beta, d_blk_gamma;         // [N][N]
     nas::DBuf<double> d_partial, d_red;                // reduction scratch
     nas::DBuf<double> d_moments;
+    nas::DBuf<double> d_pcg1_part, d_pcg1_scal;        // fused Poisson PCG scratch
+    nas::DBuf<int> d_pcg1_flags;
+    cudaStream_t cap_stream = nullptr;                 // private stream for graph capture
+    cudaGraphExec_t pcg1_exec = nullptr;
+    Pcg1Key pcg1_key;
+    long long pcg1_iters = 0;
 
     // ---- state (host)
     std::vector<double> lam;            // [N]
@@ -92,6 +111,7 @@ struct nas_ctx {
     std::vector<double> hb_cH, hb_gamma, hb_bHL, hb_betaL;
     int Na = 0;                         // augmentation columns in use (0 or N)
     std::vector<double> U_warm;         // warm start of the small eigensolver [m][N]
+    double eig_tol_hint = 1.0;          // last inner-SCF residual (LOBPCG tolerance)
     int last_lobpcg_iters = 0;
 
     // ---- timing

@@ -164,6 +164,105 @@ static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double
     return it;
 }
 
+// Single right-hand-side PCG with the fused kernels (kernels_pcg1.cu),
+// replayed kPcg1Graph iterations at a time from a captured CUDA graph.  The
+// graph is captured once per context on a private stream (the graph's
+// pointers are the context's fixed Poisson buffers) and launched on the
+// context stream; the host reads the convergence flag after each replay.
+static const int kPcg1Graph = 16;
+
+static int pcg1_lanes(nas_ctx* c) {
+    if (c->opt.spmv_lanes > 0) return c->opt.spmv_lanes;
+    double avg = (double)c->F.nnz() / std::max<int64_t>(1, c->F.n);
+    return avg < 12 ? 2 : (avg < 24 ? 4 : 8);
+}
+
+static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double* b, double* x, double tol,
+                      int maxit, bool* converged) {
+    Phase ph(c, NAS_PH_SPMV);
+    const int64_t n = A.n_rows;
+    cudaStream_t s = c->stream;
+    const int G = pcg1_blocks();
+    c->d_pcg1_part.ensure(3 * (size_t)G);
+    c->d_pcg1_scal.ensure(8);
+    c->d_pcg1_flags.ensure(4);
+    Pcg1 st{};
+    st.n = n;
+    st.rowptr = A.rowptr;
+    st.col = A.col;
+    st.val = A.val;
+    st.dinv = Dinv;
+    st.x = x;
+    st.r = c->d_cg_R.p;
+    st.z = c->d_cg_Z.p;
+    st.p = c->d_cg_P.p;
+    st.q = c->d_cg_Q.p;
+    st.part_pq = c->d_pcg1_part.p;
+    st.part_rz = c->d_pcg1_part.p + G;
+    st.part_rr = c->d_pcg1_part.p + 2 * G;
+    st.scal = c->d_pcg1_scal.p;
+    st.active = c->d_pcg1_flags.p;
+    st.breakdown = c->d_pcg1_flags.p + 1;
+    st.iters = c->d_pcg1_flags.p + 2;
+    st.tol2 = tol * tol;
+    // r = b - A x, z = D^-1 r, p = z, rz = r.z, rr = r.r, bb = b.b
+    launch_spmm(A, 1, x, st.r, 1.0, 0.0, s);
+    launch_sub_from(n, b, st.r, s);
+    launch_scale_rows(n, 1, Dinv, st.r, st.z, s);
+    NAS_CUDA(cudaMemcpyAsync(st.p, st.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    {
+        const double* X3[3] = {st.r, st.r, b};
+        const double* Y3[3] = {st.z, st.r, b};
+        launch_coldots(n, 1, 3, X3, Y3, nullptr, c->d_partial.p, c->d_pcg1_scal.p + 4, s);
+    }
+    double h[3];
+    NAS_CUDA(cudaMemcpyAsync(h, c->d_pcg1_scal.p + 4, sizeof(h), cudaMemcpyDeviceToHost, s));
+    sync(c);
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
+    *converged = true;
+    if (!(h[2] > 0.0) || h[1] <= tol * tol * h[2]) return 0;
+    double init[4] = {h[0], 0.0, h[2], h[1]};
+    int flags[4] = {1, 0, 0, 0};
+    NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_scal.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_flags.p, flags, sizeof(flags), cudaMemcpyHostToDevice, s));
+    // graph of kPcg1Graph iterations for this (A, x, b) set of pointers
+    const int lanes = pcg1_lanes(c);
+    Pcg1Key key;
+    const void* ptrs[8] = {A.val, A.rowptr, x, Dinv, st.r, st.part_pq, st.scal, st.active};
+    for (int i = 0; i < 8; ++i) key.ptr[i] = ptrs[i];
+    key.tol = tol;
+    key.lanes = lanes;
+    key.n = n;
+    if (!c->pcg1_exec || !(key == c->pcg1_key)) {
+        if (c->pcg1_exec) cudaGraphExecDestroy(c->pcg1_exec);
+        c->pcg1_exec = nullptr;
+        if (!c->cap_stream) NAS_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        NAS_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < kPcg1Graph; ++k) launch_pcg1_iteration(st, k & 1, lanes, c->cap_stream);
+        NAS_CUDA(cudaStreamEndCapture(c->cap_stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&c->pcg1_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) fail(NAS_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        c->pcg1_key = key;
+    }
+    int it = 0;
+    while (true) {
+        NAS_CUDA(cudaGraphLaunch(c->pcg1_exec, s));
+        g_launch_count += 3 * kPcg1Graph;
+        NAS_CUDA(cudaMemcpyAsync(flags, c->d_pcg1_flags.p, sizeof(flags), cudaMemcpyDeviceToHost, s));
+        sync(c);
+        it = flags[2];
+        if (flags[1]) fail(NAS_E_BREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite)");
+        if (!flags[0] || it >= maxit) break;
+    }
+    *converged = (flags[0] == 0);
+    c->spmv_bytes += (double)it * (12.0 * A.rowptr_nnz + 108.0 * n);
+    c->spmv_flops += (double)it * (2.0 * A.rowptr_nnz + 10.0 * n);
+    c->pcg1_iters += it;
+    return it;
+}
+
 // ------------------------------------------------------------------ Hartree (Sec. 3.1)
 // V_H nodal into `VH` (boundary included): monopole/quadrupole boundary
 // values, b = 4 pi int rho phi_i - K_IB w_B, PCG on K_II with warm start VH.
@@ -179,8 +278,9 @@ static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
     Csr KIB{c->F.n, c->d_browptr.p, c->d_bcol.p, c->d_KIB.p};
     if (c->F.nnzb() > 0) spmm(c, KIB, 1, c->d_wB.p, c->d_pb.p, -1.0, 1.0);
     launch_nodal_to_dof(c->F.n, c->d_dof_node.p, VH, c->d_pv.p, s);
-    int it = pcg(c, fcsr(c, c->d_K.p), c->d_Kdinv.p, 1, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson,
-                 c->opt.max_poisson, conv);
+    Csr K = fcsr(c, c->d_K.p);
+    K.rowptr_nnz = c->F.nnz();
+    int it = pcg1_solve(c, K, c->d_Kdinv.p, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson, c->opt.max_poisson, conv);
     launch_dof_to_nodal(c->F.n, c->d_dof_node.p, c->d_pv.p, VH, s);
     return it;
 }
@@ -369,7 +469,12 @@ static void host_eig(nas_ctx* c, int m) {
         ArrowMat B{nH, Na, c->GM.hptr.data(), c->GM.hcol.data(), bs.data(), bb.data(), bc.data()};
         bool warm = (int64_t)c->U_warm.size() == (int64_t)m * c->N;
         if (warm) U = c->U_warm;
-        int it = lobpcg_arrow(A, B, c->N, std::max(4, c->N / 4), lam.data(), U.data(), warm, 1e-11, 2000);
+        // residual tolerance tied to the inner-SCF residual: the eigenvectors
+        // need no more accuracy than the density they produce, and the last
+        // inner iterations (residual near tol_inner) solve to 1e-11
+        double tol = c->opt.eig_tol > 0.0 ? c->opt.eig_tol
+                                          : std::min(1e-4, std::max(1e-11, 1e-3 * c->eig_tol_hint));
+        int it = lobpcg_arrow(A, B, c->N, std::max(4, c->N / 4), lam.data(), U.data(), warm, tol, 2000);
         if (it < 0) fail(NAS_E_EIGEN, "small eigenproblem: LOBPCG did not converge");
         c->last_lobpcg_iters += it;
     }
@@ -425,6 +530,7 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
             for (int i = 0; i < Na; ++i)
                 for (int j = 0; j < Na; ++j) c->FA[(nH + i) * m + nH + j] += betanl[i * Na + j];
         }
+        c->eig_tol_hint = (t == 0) ? 1.0 : res;
         host_eig(c, m);
         {
             Phase ph(c, NAS_PH_DENSITY);
@@ -540,6 +646,10 @@ void ctx_setup(nas_ctx* c) {
     fem_set_order(c->fine_order, c->device);
     c->setup_done = false;
     c->initialized = false;
+    if (c->pcg1_exec) {
+        cudaGraphExecDestroy(c->pcg1_exec);
+        c->pcg1_exec = nullptr;
+    }
     build_space(c->F, c->fine_order, c->fnv, c->fxyz.data(), c->fne, c->ftet.data(), true);
     build_space(c->C, 1, c->cnv, c->cxyz.data(), c->cne, c->ctet.data(), false);
     for (int d = 0; d < 3; ++d)
@@ -840,6 +950,7 @@ void ctx_fill_report(nas_ctx* c, nas_report* rep) {
     rep->spmv_bytes = c->spmv_bytes;
     rep->spmv_flops = c->spmv_flops;
     rep->kernel_launches = g_launch_count - c->launches_at_step_start;
+    rep->eig_iters = c->last_lobpcg_iters;
 }
 
 // ------------------------------------------------------------------ state in/out

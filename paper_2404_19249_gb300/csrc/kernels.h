@@ -92,6 +92,7 @@ struct Csr {
     const int32_t* rowptr;
     const int32_t* col;
     const double* val;
+    int64_t rowptr_nnz = 0;   // nnz (host-side bookkeeping for byte counts)
 };
 // Y = alpha * A X (+ beta Y), X [ncols][N], Y [n_rows][N]
 void launch_spmm(const Csr& A, int N, const double* X, double* Y, double alpha, double beta,
@@ -164,6 +165,25 @@ void launch_galerkin1(int64_t nw, const int64_t* ptr, const int32_t* con, const 
 // Galerkin stage 2: H[t] = sum_{r in list} ival[wrow[r>>2]*4 + (r&3)] * W[r>>2]
 void launch_galerkin2(int64_t nh, const int64_t* ptr, const int32_t* con, const double* W,
                       const int32_t* wrow, const double* ival, double* H, cudaStream_t s);
+
+// Fused single right-hand-side Jacobi PCG (Poisson): device state of one solve.
+struct Pcg1 {
+    int64_t n;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    const double* dinv;
+    double *x, *r, *z, *p, *q;
+    double *part_pq, *part_rz, *part_rr;  // [pcg1_blocks()] per-block partial sums
+    double* scal;                          // [0],[1] rz (by iteration parity), [2] ||b||^2, [3] r.r
+    int* active;                           // cleared when ||r||^2 <= tol2 ||b||^2
+    int* breakdown;
+    int* iters;
+    double tol2;
+};
+int pcg1_blocks();
+// one PCG iteration (3 kernels); par = iteration parity (selects the rz slot)
+void launch_pcg1_iteration(const Pcg1& s, int par, int lanes_per_row, cudaStream_t st);
 
 // Anderson: given F^0..F^m (pointers), w, compute the k x k matrix
 // A[a][b] = (F^m - F^a, F^m - F^b) and rhs[a] = (F^m - F^a, F^m), k = m;

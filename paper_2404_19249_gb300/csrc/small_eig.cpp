@@ -458,15 +458,33 @@ static double arrow_diag(const ArrowMat& F, int64_t i) {
     return F.Cd[a * F.Na + a];
 }
 
-// G[ns][ns] = S^T T (S, T are [m][ns] row-major)
+// G[ns][ns] = S^T T (S, T are [m][ns] row-major).  Rows are split into a
+// fixed number of chunks; each chunk accumulates its outer products S_i^T T_i
+// (contiguous rows), and the chunk sums are added in chunk order, so the
+// result does not depend on the thread count.
 static void gram(int64_t m, int ns, const double* S, const double* T, double* G) {
+    const int chunks = 32;
+    std::vector<double> part((size_t)chunks * ns * ns, 0.0);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int a = 0; a < ns; ++a)
-        for (int b = 0; b < ns; ++b) {
-            double s = 0.0;
-            for (int64_t i = 0; i < m; ++i) s += S[i * ns + a] * T[i * ns + b];
-            G[a * ns + b] = s;
+    for (int ch = 0; ch < chunks; ++ch) {
+        double* acc = &part[(size_t)ch * ns * ns];
+        const int64_t i0 = m * ch / chunks, i1 = m * (ch + 1) / chunks;
+        for (int64_t i = i0; i < i1; ++i) {
+            const double* si = S + i * ns;
+            const double* ti = T + i * ns;
+            for (int a = 0; a < ns; ++a) {
+                const double sa = si[a];
+                if (sa == 0.0) continue;
+                double* row = acc + (size_t)a * ns;
+                for (int b = 0; b < ns; ++b) row[b] += sa * ti[b];
+            }
         }
+    }
+    for (int q = 0; q < ns * ns; ++q) {
+        double v = 0.0;
+        for (int ch = 0; ch < chunks; ++ch) v += part[(size_t)ch * ns * ns + q];
+        G[q] = v;
+    }
 }
 
 // Y[m][kout] = S[m][ns] C[ns][kout]
@@ -497,7 +515,7 @@ static void sym_eig_all(int m, const double* A, double* w, double* V) {
 
 // Rayleigh-Ritz on basis S [m][ns] with AS, BS: lowest k Ritz pairs.  The basis
 // Gram matrix G = S^T B S is diagonalised; directions with eigenvalue below
-// 1e-14 * max are dropped.  Returns coefficient matrix Y [ns][k] and theta[k].
+// 1e-9 * max are dropped.  Returns coefficient matrix Y [ns][k] and theta[k].
 static int rayleigh_ritz(int64_t m, int ns, const double* S, const double* AS, const double* BS, int k,
                          std::vector<double>& Y, std::vector<double>& theta) {
     std::vector<double> G((size_t)ns * ns), H((size_t)ns * ns);
@@ -625,13 +643,19 @@ int lobpcg_arrow(const ArrowMat& A, const ArrowMat& B, int nev, int nguard, doub
     std::vector<double> rel(k);
     for (; it < maxit; ++it) {
         std::vector<double> rn(k, 0.0), an(k, 0.0), bn(k, 0.0);
-        for (int64_t i = 0; i < m; ++i)
-            for (int j = 0; j < k; ++j) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < k; ++j) {
+            double r2 = 0.0, a2 = 0.0, b2 = 0.0;
+            for (int64_t i = 0; i < m; ++i) {
                 double r = AX[i * k + j] - theta[j] * BX[i * k + j];
-                rn[j] += r * r;
-                an[j] += AX[i * k + j] * AX[i * k + j];
-                bn[j] += BX[i * k + j] * BX[i * k + j];
+                r2 += r * r;
+                a2 += AX[i * k + j] * AX[i * k + j];
+                b2 += BX[i * k + j] * BX[i * k + j];
             }
+            rn[j] = r2;
+            an[j] = a2;
+            bn[j] = b2;
+        }
         double worst = 0.0;
         for (int j = 0; j < k; ++j) {
             rel[j] = std::sqrt(rn[j]) / (std::sqrt(an[j]) + std::fabs(theta[j]) * std::sqrt(bn[j]) + 1e-300);
@@ -644,6 +668,7 @@ int lobpcg_arrow(const ArrowMat& A, const ArrowMat& B, int nev, int nguard, doub
             if (j >= nev || rel[j] > 0.1 * tol) act.push_back(j);
         const int ka = (int)act.size();
         std::vector<double> W((size_t)m * ka);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < m; ++i)
             for (int q = 0; q < ka; ++q) {
                 int j = act[q];
@@ -652,12 +677,25 @@ int lobpcg_arrow(const ArrowMat& A, const ArrowMat& B, int nev, int nguard, doub
         // W <- W - X (BX)^T W, then unit B-norm columns (keeps the Gram matrix well scaled)
         {
             std::vector<double> Cm((size_t)k * ka), XC((size_t)m * ka);
-            for (int a = 0; a < k; ++a)
-                for (int b = 0; b < ka; ++b) {
-                    double sacc = 0.0;
-                    for (int64_t i = 0; i < m; ++i) sacc += BX[i * k + a] * W[i * ka + b];
-                    Cm[a * ka + b] = sacc;
+            {
+                const int chunks = 32;
+                std::vector<double> part((size_t)chunks * k * ka, 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+                for (int ch = 0; ch < chunks; ++ch) {
+                    double* acc = &part[(size_t)ch * k * ka];
+                    const int64_t i0 = m * ch / chunks, i1 = m * (ch + 1) / chunks;
+                    for (int64_t i = i0; i < i1; ++i)
+                        for (int a = 0; a < k; ++a) {
+                            const double v = BX[i * k + a];
+                            for (int b = 0; b < ka; ++b) acc[a * ka + b] += v * W[i * ka + b];
+                        }
                 }
+                for (int q = 0; q < k * ka; ++q) {
+                    double v = 0.0;
+                    for (int ch = 0; ch < chunks; ++ch) v += part[(size_t)ch * k * ka + q];
+                    Cm[q] = v;
+                }
+            }
             mult(m, k, X.data(), ka, Cm.data(), XC.data());
             for (size_t q = 0; q < W.size(); ++q) W[q] -= XC[q];
         }

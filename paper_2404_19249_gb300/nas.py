@@ -38,6 +38,7 @@ class nas_options(C.Structure):
         ("max_outer", C.c_int), ("anderson_depth", C.c_int), ("anderson_beta", C.c_double),
         ("hartree", C.c_int), ("xc", C.c_int), ("multipole", C.c_int), ("omega", C.c_double),
         ("check_every", C.c_int), ("timing", C.c_int), ("eig_dense_max", C.c_int),
+        ("eig_tol", C.c_double), ("spmv_lanes", C.c_int),
     ]
 
 
@@ -49,6 +50,7 @@ class nas_report(C.Structure):
         ("e_vxc", C.c_double), ("e_nn", C.c_double), ("phase_ms", C.c_double * 16),
         ("phase_calls", C.c_longlong * 16), ("spmm_bytes", C.c_double), ("spmm_flops", C.c_double),
         ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_double), ("spmv_flops", C.c_double),
+        ("eig_iters", C.c_int),
     ]
 
     def as_dict(self):
@@ -85,6 +87,7 @@ def _load():
         "nas_set_state": (C.c_int, [VP, VP, VP, VP, C.c_int]),
         "nas_apply": (C.c_int, [VP, C.c_int, VP, I64, VP, C.c_int]),
         "nas_spmm_f64": (C.c_int, [I64, VP, VP, VP, C.c_int, VP, VP, VP]),
+        "nas_coldot_f64": (C.c_int, [I64, C.c_int, VP, VP, VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -97,7 +100,7 @@ lib = _load()
 EXPORTS = [
     "nas_default_options", "nas_version", "nas_create", "nas_destroy", "nas_last_error", "nas_set_mesh",
     "nas_set_system", "nas_set_options", "nas_init", "nas_step", "nas_solve", "nas_get", "nas_set_state",
-    "nas_apply", "nas_spmm_f64",
+    "nas_apply", "nas_spmm_f64", "nas_coldot_f64",
 ]
 
 
@@ -208,6 +211,15 @@ def nas_spmm_f64(n_rows, row_ptr, col, val, N, X, Y, stream=0):
                          C.c_void_p(Y), C.c_void_p(stream or None))
     if r != NAS_OK:
         raise NasError(r, "nas_spmm_f64")
+    return r
+
+
+def nas_coldot_f64(n, N, X, Y, w, out, stream=0):
+    """Device-pointer weighted column dots (pointer arguments are ints; w may be 0)."""
+    r = lib.nas_coldot_f64(n, N, C.c_void_p(X), C.c_void_p(Y), C.c_void_p(w or None), C.c_void_p(out),
+                           C.c_void_p(stream or None))
+    if r != NAS_OK:
+        raise NasError(r, "nas_coldot_f64")
     return r
 
 

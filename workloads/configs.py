@@ -108,8 +108,8 @@ def _molecule_instance(name, seed, n_nuc, z_max, box_half, half, cells, coarse_c
                     potential=potential, smooth_a=smooth_a)
 
 
-def _mol8_p2(cells=50, coarse_cells=16, order=2, **kw):
-    return _molecule_instance("mol8_p2", 1, 8, 8, 4.0, 16.0, cells, coarse_cells, order)
+def _mol8_p2(cells=50, coarse_cells=16, order=2, seed=1, **kw):
+    return _molecule_instance("mol8_p2", seed, 8, 8, 4.0, 16.0, cells, coarse_cells, order)
 
 
 def _mol32_p2(cells=100, coarse_cells=16, order=2, **kw):
@@ -142,7 +142,35 @@ def _hydrogen(cells=16, coarse_cells=4, order=1, half=12.0, power=2.0, **kw):
                     hartree=False, xc=False)
 
 
+# Molecules of the paper's experiments (Sec. 5), coordinates as printed.  The
+# LiH and CH4 tables are in bohr (Li-H 3.015, C-H 2.268); the benzene table is
+# in angstrom (C-C 1.397, C-H 1.084) and is converted to bohr.
+ANGSTROM = 1.0 / 0.529177210903
+PAPER_MOLECULES = {
+    "lih": ([[-1.0075, 0.0, 0.0], [2.0075, 0.0, 0.0]], [3.0, 1.0], 1.0),
+    "ch4": ([[0.0, 0.0, 0.0], [1.3092, 1.3092, 1.3092], [-1.3092, -1.3092, 1.3092],
+             [1.3092, -1.3092, -1.3092], [-1.3092, 1.3092, -1.3092]], [6.0, 1.0, 1.0, 1.0, 1.0], 1.0),
+    "c6h6": ([[0.0, 1.3970, 0.0], [1.2098, 0.6985, 0.0], [1.2098, -0.6985, 0.0], [0.0, -1.3970, 0.0],
+              [-1.2098, -0.6985, 0.0], [-1.2098, 0.6985, 0.0], [0.0, 2.4810, 0.0], [2.1486, 1.2405, 0.0],
+              [2.1486, -1.2405, 0.0], [0.0, -2.4810, 0.0], [-2.1486, -1.2405, 0.0], [-2.1486, 1.2405, 0.0]],
+             [6.0] * 6 + [1.0] * 6, ANGSTROM),
+}
+
+
+def _paper_molecule(molecule="ch4", cells=24, coarse_cells=8, order=2, **kw):
+    R, Z, unit = PAPER_MOLECULES[molecule]
+    R = np.asarray(R, dtype=np.float64) * unit
+    Z = np.asarray(Z, dtype=np.float64)
+    axes = [graded_axis_lorentz(-10.0, 10.0, cells, R[:, d]) for d in range(3)]
+    fxyz, ftet = kuhn_mesh(*axes)
+    cax = uniform_axis(-10.0, 10.0, coarse_cells)
+    cxyz, ctet = kuhn_mesh(cax, cax, cax)
+    return Instance("paper_" + molecule, order, fxyz, ftet, cxyz, ctet, R=R, Z=Z,
+                    occ=closed_shell_occupations(Z.sum()))
+
+
 WORKLOADS = {
+    "paper_molecule": _paper_molecule,
     "he_p1": _he_p1,
     "mol8_p2": _mol8_p2,
     "mol32_p2": _mol32_p2,

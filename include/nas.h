@@ -266,6 +266,27 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
 int nas_coldot_f64(int64_t n, int N, const double* X, const double* Y, const double* w, double* out,
                    void* stream);
 
+/* Same as nas_coldot_f64, for callers that cannot allocate device memory
+ * when they need the reduction (an application whose own pool allocator
+ * already owns the device memory, a latency-critical loop where an allocator
+ * call may block or synchronise, or code that must not gain a new
+ * out-of-memory failure point mid-run).  The paper has no counterpart; this
+ * is a property of the library, not of the method.
+ * It allocates nothing: its scratch is a fixed array of 64 * 1216 doubles
+ * (608 KiB) in device global memory inside the library, held by every GPU
+ * that loads the library until the process exits.
+ *  - N is limited to 1..64 (NAS_E_INVALID_ARG beyond); other arguments as
+ *    for nas_coldot_f64.
+ *  - The first call on a device looks up the array's device address on that
+ *    device (the calling thread's current device); make that first call
+ *    before any stream capture.
+ *  - All calls share the array: calls that overlap on the GPU (different
+ *    streams or host threads) race and may return wrong sums; serialise
+ *    them.  Each call writes every scratch entry it reads, so nothing needs
+ *    clearing between calls. */
+int nas_coldot_f64_noalloc(int64_t n, int N, const double* X, const double* Y, const double* w, double* out,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

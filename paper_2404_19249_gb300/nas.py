@@ -88,6 +88,7 @@ def _load():
         "nas_apply": (C.c_int, [VP, C.c_int, VP, I64, VP, C.c_int]),
         "nas_spmm_f64": (C.c_int, [I64, VP, VP, VP, C.c_int, VP, VP, VP]),
         "nas_coldot_f64": (C.c_int, [I64, C.c_int, VP, VP, VP, VP, VP]),
+        "nas_coldot_f64_noalloc": (C.c_int, [I64, C.c_int, VP, VP, VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -100,7 +101,7 @@ lib = _load()
 EXPORTS = [
     "nas_default_options", "nas_version", "nas_create", "nas_destroy", "nas_last_error", "nas_set_mesh",
     "nas_set_system", "nas_set_options", "nas_init", "nas_step", "nas_solve", "nas_get", "nas_set_state",
-    "nas_apply", "nas_spmm_f64", "nas_coldot_f64",
+    "nas_apply", "nas_spmm_f64", "nas_coldot_f64", "nas_coldot_f64_noalloc",
 ]
 
 

@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--tol-poisson", type=float, default=1e-10)
     p.add_argument("--tol-bvp", type=float, default=1e-10)
     p.add_argument("--spmv-lanes", type=int, default=0)
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return p.parse_args()
 
 
@@ -207,6 +208,22 @@ def full_unknowns(inst):
     return n
 
 
+# ---------------------------------------------------------------------------- replicas
+def reduce_max(x, dist, device=None):
+    """Max of a float over all ranks (no-op without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, max_ms):
+    """Whole-job throughput: every rank runs `steps` steps of its own replica."""
+    return world * steps / (max_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------- our arm
 def log(msg):
     print("[bench] " + msg, file=sys.stderr, flush=True)
@@ -223,16 +240,6 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    # the CPU oracle sample runs in a fresh process started before any GPU work
-    oracle_proc = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        env = dict(os.environ)
-        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            env[k] = "1"
-        code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-                "print('ORACLE', json.dumps(bench.oracle_sample(2, 1)))" % ROOT)
-        oracle_proc = subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
-                                       stderr=subprocess.PIPE, text=True)
     import numpy as np
     import torch
     torch.cuda.set_device(local)
@@ -268,6 +275,14 @@ def main():
 
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d.csv" % os.getpid())
+    # state at the start of the timed region (the mixed-precision run restarts from it)
+    n0, N0, nqt0 = sz["n"], sz["N"], sz["ne"] * sz["nq"]
+    s0_lam = np.zeros(N0)
+    s0_psi = np.zeros((n0, N0))
+    s0_rho = np.zeros(nqt0)
+    nas.nas_get(s.h, nas.NAS_Q_EIGVALS, s0_lam)
+    nas.nas_get(s.h, nas.NAS_Q_ORBITALS, s0_psi)
+    nas.nas_get(s.h, nas.NAS_Q_RHO_IN, s0_rho)
     barrier()
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -284,11 +299,48 @@ def main():
     clk = clocks.stop(local)
     ms = ev0.elapsed_time(ev1)
     log("timed: %d steps in %.1f ms; last report %s" % (args.steps, ms, reps[-1].as_dict()))
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = reduce_max(ms, dist, "cuda")
+    value = job_value(world, args.steps, ms)
+
+    lam64 = np.zeros(N0)
+    nas.nas_get(s.h, nas.NAS_Q_EIGVALS, lam64)
+    en64 = np.zeros(6)
+    nas.nas_get(s.h, nas.NAS_Q_ENERGY, en64)
+
+    # ---------------------------------------------------------------- mixed precision
+    mixed = None
+    if not args.no_mixed:
+        nas.nas_set_state(s.h, s0_lam, s0_psi, s0_rho)
+        s.opt.precision = 1
+        nas.nas_set_options(s.h, s.opt)
+        barrier()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record()
+        mreps = []
+        for _ in range(args.steps):
+            r, rep = s.step()
+            mreps.append(nas.nas_report.from_buffer_copy(rep))
+        m1.record()
+        barrier()
+        mms = reduce_max(m0.elapsed_time(m1), dist, "cuda")
+        lam32 = np.zeros(N0)
+        nas.nas_get(s.h, nas.NAS_Q_EIGVALS, lam32)
+        en32 = np.zeros(6)
+        nas.nas_get(s.h, nas.NAS_Q_ENERGY, en32)
+        mixed = {
+            "value": job_value(world, args.steps, mms), "unit": "steps/s", "ms_per_step": mms / args.steps,
+            "what": "Poisson PCG in FP32 (FP32 accumulation) inside FP64 iterative refinement; "
+                    "same start state and step count as the FP64 run",
+            "max_eigenvalue_err_ha": float(np.max(np.abs(lam32 - lam64))),
+            "eigenvalue_err_ha": [float(x) for x in (lam32 - lam64)],
+            "energy_err_ha": float(en32[0] - en64[0]),
+            "poisson_ms_per_step": sum(rp.phase_ms[2] for rp in mreps) / args.steps,
+            "poisson_iters_per_step": sum(rp.poisson_iters for rp in mreps) / args.steps,
+        }
+        log("mixed: %s" % json.dumps({k: v for k, v in mixed.items() if k != "eigenvalue_err_ha"}))
+        s.opt.precision = 0
+        nas.nas_set_options(s.h, s.opt)
 
     # phase totals over the timed steps (library CUDA events on the launching stream)
     ph = {name: sum(rp.phase_ms[i] for rp in reps) for i, name in enumerate(nas.PHASES)}
@@ -344,11 +396,7 @@ def main():
         get(nas.NAS_Q_RHO_IN, rho_h)
         get(nas.NAS_Q_ENERGY, en_h)
     barrier()
-    e2e_s = time.perf_counter() - e0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(time.perf_counter() - e0, dist, "cuda")
     io_bytes = 8 * (N + n * N + nqt)
     e2e = None
     if n_e2e > 0:
@@ -360,13 +408,13 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    # the CPU oracle sample runs after the GPU work, in a fresh single-threaded
+    # process (fork + exec), so that it never competes with the host-side work
+    # of the timed steps for the CPU cores
     cpu = None
-    if oracle_proc is not None:
+    if world == 1 and not args.no_cpu_baseline:
         try:
-            out, err = oracle_proc.communicate(timeout=900)
-            for line in out.splitlines():
-                if line.startswith("ORACLE "):
-                    cpu = cpu_baseline_from(json.loads(line[7:]), n)
+            cpu = cpu_baseline_from(run_oracle_subprocess(2, 1), n)
         except Exception as ex:  # the baseline is reported, never required
             cpu = {"error": str(ex)[:200]}
     last = reps[-1]
@@ -382,6 +430,7 @@ def main():
         "per_step": {"n_inner": last.n_inner, "cg_iters": last.cg_iters, "poisson_iters": last.poisson_iters,
                      "drho": last.drho, "energy": last.energy},
         "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "setup_s": setup_s,
+        "mixed": mixed, "energy_ha": float(en64[0]),
     }
     print(json.dumps(line))
     s.close()

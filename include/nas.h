@@ -75,15 +75,27 @@ typedef struct nas_options {
                               eigensolver, larger ones warm-started LOBPCG           */
     double eig_tol;        /* LOBPCG relative residual; <= 0: adaptive, 1e-3 x the
                               previous inner-SCF residual clamped to [1e-11, 1e-4]  */
-    int    spmv_lanes;     /* lanes per row of the Poisson SpMV (4, 8, 16, 32);
+    int    spmv_lanes;     /* lanes per row of the Poisson SpMV (1, 2, 4, 8, 16, 32);
                               0 = chosen from the mean row length                    */
+    int    poisson_two_level; /* 1: Poisson PCG preconditioner D^-1 + I K_H^-1 I^T with
+                              the method's coarse space and transfer (K_H = I^T K I);
+                              0: Jacobi only                                        */
+    int    precision;      /* 0: FP64 throughout; 1: mixed - the Poisson PCG runs in
+                              FP32 (FP32 accumulation) inside FP64 iterative
+                              refinement; residual tests, assembly, blocks, the
+                              small eigensolve and energies stay FP64               */
+    int    eig_device;     /* small problems above eig_dense_max: 1 = LOBPCG with its
+                              block vectors, products and Gram matrices on the
+                              device (host Rayleigh-Ritz of the 3k x 3k Grams);
+                              0 = the host LOBPCG                                  */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
  * tol_poisson = 1e-12, tol_scf = tol_inner = 1e-8, max_cg = 2000,
  * max_poisson = 20000, max_inner = 50, max_outer = 100, depth 5, beta 0.7,
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
- * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto). */
+ * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
+ * poisson_two_level = 1, precision = 0, eig_device = 1. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -95,10 +107,13 @@ enum nas_phase {
     NAS_PH_BLOCKS,         /* F_A / F_B blocks (st5-st7) incl. I^T A I              */
     NAS_PH_DENSITY,        /* Psi = I u_H + U^ alpha and rho at quadrature points   */
     NAS_PH_MIXING,         /* Anderson inner products and combination               */
-    NAS_PH_HOST_EIG,       /* host small eigensolve (incl. its D2H/H2D)             */
+    NAS_PH_HOST_EIG,       /* small eigensolve, wall time (host dense / host LOBPCG,
+                              or device LOBPCG incl. its host Rayleigh-Ritz)       */
     NAS_PH_TRANSFER,       /* point location + I_H^h                                */
     NAS_PH_SPMM,           /* SpMM launches with N > 1 columns (subset of the above) */
     NAS_PH_SPMV,           /* SpMV launches (N = 1, Poisson and Dirichlet lift)      */
+    NAS_PH_EIG_RR,         /* host Rayleigh-Ritz inside the device LOBPCG (subset of
+                              NAS_PH_HOST_EIG)                                      */
     NAS_PH_COUNT
 };
 
@@ -157,6 +172,10 @@ int nas_set_mesh(nas_ctx* ctx, int which, int order,
                  int64_t n_tet, const int32_t* tet);
 
 /* Molecule and orbitals (Sec. 2: M nuclei with charges Z_k at R_k, N orbitals).
+ * After nas_init, a call that keeps n_nuc, n_orb, occupations and the
+ * potential kind only moves/recharges the nuclei: the mesh structures are
+ * kept and the V_ext-dependent matrices are re-assembled (the solver state is
+ * kept; call nas_init to restart the SCF from scratch).
  *  R       : FP64 [n_nuc][3];  Z : FP64 [n_nuc]
  *  potential, smooth_a : see enum nas_potential
  *  n_orb   : N >= 1;  occ : FP64 [n_orb] occupations f_i (rho = sum f_i psi_i^2). */
@@ -183,7 +202,9 @@ int nas_init(nas_ctx* ctx, const double* psi0);
  * NAS_E_NOT_CONVERGED if a CG cap was hit (the state is still updated). */
 int nas_step(nas_ctx* ctx, nas_report* rep);
 
-/* Steps until ||rho^(l) - rho^(l-1)||_0 < tol_scf or max_outer steps. */
+/* Steps until ||rho^(l) - rho^(l-1)||_0 < tol_scf or max_outer steps.  Returns
+ * NAS_E_NOT_CONVERGED when max_outer steps end above tol_scf, or when the last
+ * step hit a CG cap (the state holds the last step either way). */
 int nas_solve(nas_ctx* ctx, nas_report* rep);
 
 /* ------------------------------------------------------------------ data out/in */
@@ -237,8 +258,17 @@ enum nas_op {
                              out [nnz] values of int c phi_i phi_j                       */
     NAS_OP_DENSITY,       /* in Psi [n_dof][N] -> out rho [n_elem][nq] = sum f psi^2    */
     NAS_OP_APPLY_H,       /* in X [n_dof][N] -> out H~ X with the last H~ (SpMM)        */
-    NAS_OP_BVP,           /* in R [n_dof][N] -> out solution of H~ U = R (block PCG)    */
+    NAS_OP_BVP,           /* in R [n_dof][N] -> out solution of H~ U = R (block PCG),
+                             H~ = A^L + A^NL(rho_in) + mu M of the current state       */
     NAS_OP_GALERKIN,      /* in fine CSR values [nnz] -> out dense I^T A I [nH][nH]     */
+    NAS_OP_ENERGY_GRAD,   /* in rho at quad points [n_elem][nq] -> out [n_nuc][4]:
+                             dE/d(R_k x, y, z, Z_k) = int rho dV_ext/dp + dE_nn/dp
+                             (Hellmann-Feynman on the fixed mesh)                       */
+    NAS_OP_BVP_VJP,       /* in [R ; G] (2 x [n_dof][N]) -> out [U ; A ; dp]: U solves
+                             H~ U = R, A = H~^-1 G (adjoint, H~ symmetric) and
+                             dp[n_nuc][4] = -sum_q W dV_ext/dp sum_c a_c u_c, the
+                             gradient of <G, U> w.r.t. the nuclear parameters at fixed
+                             R, mu and density                                           */
     NAS_OP_COUNT
 };
 int nas_apply(nas_ctx* ctx, int op, const void* in, int64_t cnt, void* out, int on_device);

@@ -70,6 +70,36 @@ def external_potential(inst, xq):
     return V
 
 
+def dvext_dparams(inst, xq):
+    """d V_ext / d(R_k, Z_k) at points xq: array [M, 4, ...] (x, y, z, Z)."""
+    out = np.zeros((len(inst.Z), 4) + xq.shape[:-1])
+    for k, (Rk, Zk) in enumerate(zip(inst.R, inst.Z)):
+        d = xq - Rk
+        r2 = np.sum(d * d, axis=-1)
+        if inst.potential == POT_SMOOTHED:
+            r2 = r2 + inst.smooth_a ** 2
+        inv = 1.0 / np.sqrt(r2)
+        # V = -Z (r2)^(-1/2): dV/dR = -Z (x - R) r2^(-3/2); dV/dZ = -r2^(-1/2)
+        for c in range(3):
+            out[k, c] = -Zk * d[..., c] * inv ** 3
+        out[k, 3] = -inv
+    return out
+
+
+def nuclear_repulsion_grad(inst):
+    """d E_nn / d(R_k, Z_k): [M, 4]."""
+    g = np.zeros((len(inst.Z), 4))
+    for j in range(len(inst.Z)):
+        for k in range(len(inst.Z)):
+            if j == k:
+                continue
+            d = inst.R[k] - inst.R[j]
+            r = np.linalg.norm(d)
+            g[k, :3] -= inst.Z[j] * inst.Z[k] * d / r ** 3
+            g[k, 3] += inst.Z[j] / r
+    return g
+
+
 def nuclear_repulsion(inst):
     """E_nn = sum_{k<j} Z_j Z_k / |R_j - R_k| (Sec. 3.1)."""
     E = 0.0
@@ -272,6 +302,30 @@ class Problem:
         return (float(np.dot(self.occ, st.lam))
                 - f.integrate((0.5 * VHq + vxc) * rho)
                 + f.integrate(rho * eps) + self.Enn)
+
+    def energy_gradient(self, rho_q):
+        """Hellmann-Feynman gradient of the total energy with respect to the
+        nuclear positions and charges on a fixed mesh: int rho dV_ext/dp plus
+        d E_nn/dp, [M, 4] (x, y, z, Z).  Exact for the discrete variational
+        problem at self-consistency (the basis does not move with the nuclei)."""
+        dV = dvext_dparams(self.inst, self.fine.xq)
+        g = np.einsum("eq,kceq->kc", self.fine.Wq * rho_q, dV)
+        return g + nuclear_repulsion_grad(self.inst)
+
+    def bvp_vjp(self, st, Uhat, G):
+        """Vector-Jacobian product of the linear problems H~ U^ = R (R fixed)
+        with respect to the nuclear parameters: for L with dL/dU^ = G, the
+        adjoint A = H~^-1 G (H~ symmetric) gives dL/dp = -sum_q W_q dV/dp
+        sum_c a_c(x_q) u_c(x_q), [M, 4]."""
+        _, VHq, _, vxc = self.nonlinear_cached(st)
+        Ht = (self.AL + self.A_NL(VHq, vxc) + self.mu * self.M).tocsr()
+        A = solve_spd(Ht, G, tol=1e-15)
+        f = self.fine
+        aq = f.at_quad(f.to_nodes(A))
+        uq = f.at_quad(f.to_nodes(Uhat))
+        prod = np.einsum("eqc,eqc->eq", aq, uq)
+        dV = dvext_dparams(self.inst, f.xq)
+        return -np.einsum("eq,kceq->kc", f.Wq * prod, dV)
 
     def variational_energy(self, Psi):
         """E(Psi) of Sec. 2 (kinetic + external + xc + Hartree/2 + E_nn)."""

@@ -61,6 +61,9 @@ void nas_default_options(nas_options* o) {
     o->eig_dense_max = 1200;
     o->eig_tol = -1.0;
     o->spmv_lanes = 0;
+    o->eig_device = 1;
+    o->poisson_two_level = 1;
+    o->precision = 0;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -96,6 +99,7 @@ void nas_destroy(nas_ctx* c) {
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->pcg1_exec) cudaGraphExecDestroy(c->pcg1_exec);
+    if (c->pcg1f_exec) cudaGraphExecDestroy(c->pcg1f_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
@@ -138,6 +142,16 @@ int nas_set_system(nas_ctx* c, int n_nuc, const double* R, const double* Z, int 
         if (n_orb < 1 || n_orb > 64) nas::fail(NAS_E_INVALID_ARG, "n_orb must be in 1..64");
         if (potential < NAS_POT_COULOMB || potential > NAS_POT_HARMONIC) nas::fail(NAS_E_INVALID_ARG, "potential");
         if (potential == NAS_POT_SMOOTHED && !(smooth_a > 0.0)) nas::fail(NAS_E_INVALID_ARG, "smooth_a must be > 0");
+        std::vector<double> occv(occ ? occ : (const double*)nullptr, occ ? occ + n_orb : (const double*)nullptr);
+        if (!occ) occv.assign(n_orb, 2.0);
+        if (c->setup_done && n_nuc == c->n_nuc && n_orb == c->N && potential == c->potential &&
+            smooth_a == c->smooth_a && occv == c->occ) {
+            // only the nuclei move or change charge: keep the mesh structures
+            c->R.assign(R, R + 3 * n_nuc);
+            c->Z.assign(Z, Z + n_nuc);
+            nas::ctx_update_nuclei(c);
+            return NAS_OK;
+        }
         c->n_nuc = n_nuc;
         c->R.assign(R ? R : (const double*)nullptr, R ? R + 3 * n_nuc : (const double*)nullptr);
         c->Z.assign(Z ? Z : (const double*)nullptr, Z ? Z + n_nuc : (const double*)nullptr);
@@ -159,9 +173,11 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
     return guarded(c, [&]() {
         if (!o) nas::fail(NAS_E_INVALID_ARG, "null options");
         if (o->tol_bvp <= 0 || o->tol_poisson <= 0 || o->max_cg < 1 || o->max_poisson < 1 || o->max_inner < 1 ||
-            o->anderson_depth < 1 || o->anderson_depth > 5)
+            o->anderson_depth < 1 || o->anderson_depth > 5 || o->precision < 0 || o->precision > 1 ||
+            o->eig_device < 0 || o->eig_device > 1)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
-        bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega);
+        bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
+                       (o->poisson_two_level != c->opt.poisson_two_level);
         c->opt = *o;
         if (rebuild && c->setup_done) invalidate(c);
         return NAS_OK;
@@ -188,13 +204,14 @@ int nas_solve(nas_ctx* c, nas_report* rep) {
     return guarded(c, [&]() {
         NAS_CUDA(cudaSetDevice(c->device));
         int status = NAS_OK;
-        nas_report r;
-        for (int l = 0; l < c->opt.max_outer; ++l) {
+        nas_report r{};
+        bool done = false;
+        for (int l = 0; l < c->opt.max_outer && !done; ++l) {
             status = nas::ctx_step(c, &r);
-            if (r.drho < c->opt.tol_scf) break;
+            done = r.drho < c->opt.tol_scf;
         }
         if (rep) *rep = r;
-        return status;
+        return (status == NAS_OK && !done) ? NAS_E_NOT_CONVERGED : status;
     });
 }
 

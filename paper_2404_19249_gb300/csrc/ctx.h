@@ -9,17 +9,19 @@
 
 #include "common.h"
 #include "kernels.h"
+#include "eig_dev.h"
 #include "space.h"
 #include "transfer_setup.h"
 
 // identity of a captured Poisson PCG graph (its baked-in pointers and parameters)
 struct Pcg1Key {
-    const void* ptr[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    static const int kPtrs = 11;
+    const void* ptr[kPtrs] = {};
     double tol = 0.0;
     int lanes = 0;
     int64_t n = 0;
     bool operator==(const Pcg1Key& o) const {
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < kPtrs; ++i)
             if (ptr[i] != o.ptr[i]) return false;
         return tol == o.tol && lanes == o.lanes && n == o.n;
     }
@@ -57,6 +59,7 @@ struct nas_ctx {
     std::vector<double> I_val;
     std::vector<double> BH, AHL;          // coarse Galerkin values [hnnz]
     std::vector<double> BH_chol;          // dense Cholesky factor of B_H [nH][nH]
+    nas::DBuf<double> d_BHinv;            // dense B_H^-1 [nH][nH] on the device
 
     // ---- device: fine mesh
     nas::DBuf<double> d_vxyz, d_node_xyz, d_Wq;
@@ -78,6 +81,11 @@ struct nas_ctx {
     nas::DBuf<int32_t> d_tptr, d_trow, d_wptr, d_wcol, d_wrow, d_w1con, d_hptr, d_hcol, d_h2con;
     nas::DBuf<int64_t> d_w1ptr, d_h2ptr;
     nas::DBuf<double> d_tval, d_W, d_AH;
+    nas::DBuf<int32_t> d_tpc_seg, d_h2pc_seg;          // balanced pieces of I^T rows / stage-2 lists
+    nas::DBuf<int64_t> d_tpc_start, d_h2pc_start;
+    nas::DBuf<double> d_piece_part;                    // piece sums (max of npieces_t * N, npieces_h2)
+    nas::DBuf<double> d_cpart;                         // piece sums of I^T r in the Poisson PCG
+    nas::DBuf<float> d_cpart32;
     // ---- device: orbitals and solver work
     nas::DBuf<double> d_Psi, d_Uhat, d_occ, d_U;
     nas::DBuf<double> d_X1, d_X2;                      // [n][N] temporaries
@@ -90,10 +98,15 @@ struct nas_ctx {
     nas::DBuf<double> d_partial, d_red;                // reduction scratch
     nas::DBuf<double> d_moments;
     nas::DBuf<double> d_pcg1_part, d_pcg1_scal;        // fused Poisson PCG scratch
+    nas::DBuf<double> d_khinv, d_khvec;                // two-level preconditioner: K_H^-1, [c ; y]
     nas::DBuf<int> d_pcg1_flags;
     cudaStream_t cap_stream = nullptr;                 // private stream for graph capture
     cudaGraphExec_t pcg1_exec = nullptr;
     Pcg1Key pcg1_key;
+    // mixed precision: FP32 copies and work arrays of the Poisson solve
+    nas::DBuf<float> d_K32, d_Kdinv32, d_ival32, d_tval32, d_khinv32, d_khvec32, d_f32work, d_f32part;
+    cudaGraphExec_t pcg1f_exec = nullptr;
+    Pcg1Key pcg1f_key;
     long long pcg1_iters = 0;
 
     // ---- state (host)
@@ -111,6 +124,14 @@ struct nas_ctx {
     std::vector<double> hb_cH, hb_gamma, hb_bHL, hb_betaL;
     int Na = 0;                         // augmentation columns in use (0 or N)
     std::vector<double> U_warm;         // warm start of the small eigensolver [m][N]
+    // device form of the small pencil (arrow structure) for the device LOBPCG
+    nas::DBuf<double> d_AHLv, d_BHv;                   // coarse CSR values of A_H^L, B_H
+    nas::DBuf<int32_t> d_hdiag;                        // CSR slot of each coarse diagonal entry
+    nas::DBuf<double> d_cH, d_gam, d_bL, d_betaL;      // fixed borders/corners of one step
+    nas::DBuf<double> d_FAs, d_FAb, d_FAc;             // F_A of the current inner iteration
+    nas::DBuf<double> d_Uwarm;                         // warm start [m][N] on the device
+    int64_t uwarm_dev_m = 0;                           // m of d_Uwarm's content (0: none)
+    nas::DevLobpcg lob;
     double eig_tol_hint = 1.0;          // last inner-SCF residual (LOBPCG tolerance)
     int last_lobpcg_iters = 0;
 
@@ -137,5 +158,6 @@ void ctx_fill_report(nas_ctx* c, nas_report* rep);
 void ctx_set_state(nas_ctx* c, const double* lam, const double* psi, const double* rho, int on_device);
 void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int on_device);
 void ctx_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device);
+void ctx_update_nuclei(nas_ctx* c);
 
 }  // namespace nas

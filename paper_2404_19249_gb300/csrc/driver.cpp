@@ -30,6 +30,14 @@ static Mesh fmesh(nas_ctx* c) {
     return Mesh{c->F.ne, c->F.nloc, (int)c->nq, c->d_vxyz.p, c->d_elem.p};
 }
 static Csr fcsr(nas_ctx* c, const double* val) { return Csr{c->F.n, c->d_rowptr.p, c->d_col.p, val}; }
+static Pieces tpieces(nas_ctx* c) {
+    Pieces pc;
+    pc.nseg = c->nH;
+    pc.npieces = c->GM.tpieces.npieces();
+    pc.seg_piece = c->d_tpc_seg.p;
+    pc.piece_start = c->d_tpc_start.p;
+    return pc;
+}
 
 static cudaEvent_t ev_get(nas_ctx* c) {
     if (!c->ev_pool.empty()) {
@@ -174,7 +182,7 @@ static const int kPcg1Graph = 16;
 static int pcg1_lanes(nas_ctx* c) {
     if (c->opt.spmv_lanes > 0) return c->opt.spmv_lanes;
     double avg = (double)c->F.nnz() / std::max<int64_t>(1, c->F.n);
-    return avg < 12 ? 2 : (avg < 24 ? 4 : 8);
+    return avg < 20 ? 2 : 4;
 }
 
 static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double* b, double* x, double tol,
@@ -205,10 +213,30 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     st.breakdown = c->d_pcg1_flags.p + 1;
     st.iters = c->d_pcg1_flags.p + 2;
     st.tol2 = tol * tol;
-    // r = b - A x, z = D^-1 r, p = z, rz = r.z, rr = r.r, bb = b.b
+    const bool two_level = c->opt.poisson_two_level && c->d_khinv.p && A.val == c->d_K.p;
+    if (two_level) {
+        st.two_level = 1;
+        st.nH = c->nH;
+        st.tpc = tpieces(c);
+        st.trow = c->d_trow.p;
+        st.tval = c->d_tval.p;
+        st.cpart = c->d_cpart.p;
+        st.icol = c->d_Icol.p;
+        st.ival = c->d_Ival.p;
+        st.khinv = c->d_khinv.p;
+        st.cvec = c->d_khvec.p;
+        st.yvec = c->d_khvec.p + c->nH;
+    }
+    // r = b - A x, z = M^-1 r, p = z, rz = r.z, rr = r.r, bb = b.b
     launch_spmm(A, 1, x, st.r, 1.0, 0.0, s);
     launch_sub_from(n, b, st.r, s);
-    launch_scale_rows(n, 1, Dinv, st.r, st.z, s);
+    if (two_level) {
+        int on[4] = {1, 0, 0, 0};
+        NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_flags.p, on, sizeof(on), cudaMemcpyHostToDevice, s));
+        launch_pcg1_coarse_correction(st, s);
+    } else {
+        launch_scale_rows(n, 1, Dinv, st.r, st.z, s);
+    }
     NAS_CUDA(cudaMemcpyAsync(st.p, st.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     {
         const double* X3[3] = {st.r, st.r, b};
@@ -228,8 +256,9 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     // graph of kPcg1Graph iterations for this (A, x, b) set of pointers
     const int lanes = pcg1_lanes(c);
     Pcg1Key key;
-    const void* ptrs[8] = {A.val, A.rowptr, x, Dinv, st.r, st.part_pq, st.scal, st.active};
-    for (int i = 0; i < 8; ++i) key.ptr[i] = ptrs[i];
+    const void* ptrs[Pcg1Key::kPtrs] = {A.val, A.rowptr, x, Dinv, st.r, st.part_pq, st.scal, st.active, st.khinv,
+                                        st.cvec, st.cpart};
+    for (int i = 0; i < Pcg1Key::kPtrs; ++i) key.ptr[i] = ptrs[i];
     key.tol = tol;
     key.lanes = lanes;
     key.n = n;
@@ -263,6 +292,147 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     return it;
 }
 
+// Mixed precision (Poisson): FP64 iterative refinement around an FP32 inner
+// PCG with FP32 accumulation.  Each outer pass forms the FP64 residual
+// r = b - K x, stops when ||r|| <= tol ||b||, else solves K e = r in FP32 to a
+// relative residual of max(1e-5, 0.3 tol ||b|| / ||r||) and adds e to x in
+// FP64.  The FP32 copies of K, D^-1, the transfer weights and K_H^-1 are made
+// on first use.
+static void make_f32_copies(nas_ctx* c) {
+    cudaStream_t s = c->stream;
+    const int64_t n = c->F.n, nnz = c->F.nnz();
+    c->d_K32.ensure(nnz);
+    launch_cast_to_f32(nnz, c->d_K.p, c->d_K32.p, s);
+    c->d_Kdinv32.ensure(n);
+    launch_cast_to_f32(n, c->d_Kdinv.p, c->d_Kdinv32.p, s);
+    c->d_ival32.ensure(4 * n);
+    launch_cast_to_f32(4 * n, c->d_Ival.p, c->d_ival32.p, s);
+    c->d_tval32.ensure(std::max<size_t>(1, c->GM.tval.size()));
+    launch_cast_to_f32((int64_t)c->GM.tval.size(), c->d_tval.p, c->d_tval32.p, s);
+    if (c->d_khinv.p) {
+        c->d_khinv32.ensure((size_t)c->nH * c->nH);
+        launch_cast_to_f32(c->nH * c->nH, c->d_khinv.p, c->d_khinv32.p, s);
+        c->d_khvec32.ensure(2 * c->nH);
+        c->d_cpart32.ensure(std::max<int64_t>(1, c->GM.tpieces.npieces()));
+    }
+    c->d_f32work.ensure(5 * (size_t)n);
+    c->d_f32part.ensure(3 * (size_t)pcg1_blocks() + 8);
+}
+
+static int pcg1_mixed_solve(nas_ctx* c, const double* b, double* x, double tol, int maxit, bool* converged) {
+    Phase ph(c, NAS_PH_SPMV);
+    cudaStream_t s = c->stream;
+    const int64_t n = c->F.n;
+    const int G = pcg1_blocks();
+    if (!c->d_K32.p) make_f32_copies(c);
+    c->d_pcg1_flags.ensure(4);
+    Csr K = fcsr(c, c->d_K.p);
+    Pcg1f st{};
+    st.n = n;
+    st.rowptr = c->d_rowptr.p;
+    st.col = c->d_col.p;
+    st.val = c->d_K32.p;
+    st.dinv = c->d_Kdinv32.p;
+    float* w = c->d_f32work.p;
+    st.x = w;
+    st.r = w + n;
+    st.z = w + 2 * n;
+    st.p = w + 3 * n;
+    st.q = w + 4 * n;
+    st.part_pq = c->d_f32part.p;
+    st.part_rz = c->d_f32part.p + G;
+    st.part_rr = c->d_f32part.p + 2 * G;
+    st.scal = c->d_f32part.p + 3 * G;
+    st.active = c->d_pcg1_flags.p;
+    st.breakdown = c->d_pcg1_flags.p + 1;
+    st.iters = c->d_pcg1_flags.p + 2;
+    if (c->opt.poisson_two_level && c->d_khinv32.p) {
+        st.two_level = 1;
+        st.nH = c->nH;
+        st.tpc = tpieces(c);
+        st.trow = c->d_trow.p;
+        st.tval = c->d_tval32.p;
+        st.cpart = c->d_cpart32.p;
+        st.icol = c->d_Icol.p;
+        st.ival = c->d_ival32.p;
+        st.khinv = c->d_khinv32.p;
+        st.cvec = c->d_khvec32.p;
+        st.yvec = c->d_khvec32.p + c->nH;
+    }
+    const int lanes = pcg1_lanes(c);
+    int total = 0;
+    *converged = false;
+    std::vector<float> hp(2 * (size_t)G);
+    for (int outer = 0; outer < 30; ++outer) {
+        // FP64 residual and stopping test
+        launch_spmm(K, 1, x, c->d_cg_R.p, 1.0, 0.0, s);
+        launch_sub_from(n, b, c->d_cg_R.p, s);
+        const double* X2[2] = {c->d_cg_R.p, b};
+        launch_coldots(n, 1, 2, X2, X2, nullptr, c->d_partial.p, c->d_red.p, s);
+        double h[2];
+        NAS_CUDA(cudaMemcpyAsync(h, c->d_red.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        sync(c);
+        if (!std::isfinite(h[0])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
+        if (!(h[1] > 0.0) || h[0] <= tol * tol * h[1]) {
+            *converged = true;
+            break;
+        }
+        if (total >= maxit) break;
+        const double tin = std::max(1e-5, 0.3 * tol * std::sqrt(h[1] / h[0]));
+        // inner FP32 solve of K e = r from e = 0
+        launch_cast_to_f32(n, c->d_cg_R.p, st.r, s);
+        int fl[4] = {1, 0, 0, 0};
+        NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_flags.p, fl, sizeof(fl), cudaMemcpyHostToDevice, s));
+        if (st.two_level) launch_pcg1_coarse_correction(st, s);
+        launch_pcg1_start(st, s);
+        NAS_CUDA(cudaMemcpyAsync(hp.data(), st.part_rz, sizeof(float) * 2 * G, cudaMemcpyDeviceToHost, s));
+        sync(c);
+        double rz = 0.0, rr = 0.0;
+        for (int k = 0; k < G; ++k) rz += hp[k];
+        for (int k = 0; k < G; ++k) rr += hp[G + k];
+        if (!(rr > 0.0)) break;
+        float sc[4] = {(float)rz, 0.0f, (float)rr, (float)rr};
+        NAS_CUDA(cudaMemcpyAsync(st.scal, sc, sizeof(sc), cudaMemcpyHostToDevice, s));
+        st.tol2 = (float)(tin * tin);
+        Pcg1Key key;
+        const void* ptrs[Pcg1Key::kPtrs] = {st.val, st.rowptr, st.x, st.dinv, st.r, st.part_pq, st.scal, st.active,
+                                            st.khinv, st.cvec, st.cpart};
+        for (int i = 0; i < Pcg1Key::kPtrs; ++i) key.ptr[i] = ptrs[i];
+        key.tol = tin;
+        key.lanes = lanes;
+        key.n = n;
+        if (!c->pcg1f_exec || !(key == c->pcg1f_key)) {
+            if (c->pcg1f_exec) cudaGraphExecDestroy(c->pcg1f_exec);
+            c->pcg1f_exec = nullptr;
+            if (!c->cap_stream) NAS_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t g;
+            NAS_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < kPcg1Graph; ++k) launch_pcg1_iteration(st, k & 1, lanes, c->cap_stream);
+            NAS_CUDA(cudaStreamEndCapture(c->cap_stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&c->pcg1f_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) fail(NAS_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            c->pcg1f_key = key;
+        }
+        int it = 0;
+        while (true) {
+            NAS_CUDA(cudaGraphLaunch(c->pcg1f_exec, s));
+            g_launch_count += (st.two_level ? 6 : 3) * kPcg1Graph;
+            NAS_CUDA(cudaMemcpyAsync(fl, c->d_pcg1_flags.p, sizeof(fl), cudaMemcpyDeviceToHost, s));
+            sync(c);
+            it = fl[2];
+            if (fl[1] || !fl[0] || total + it >= maxit) break;
+        }
+        total += it;
+        launch_add_f32(n, st.x, x, s);   // x += e in FP64
+        c->spmv_bytes += (double)it * (8.0 * c->F.nnz() + 54.0 * n) + 12.0 * c->F.nnz() + 40.0 * n;
+        c->spmv_flops += (double)it * (2.0 * c->F.nnz() + 10.0 * n) + 2.0 * c->F.nnz();
+        if (fl[1]) break;  // FP32 breakdown: the outer FP64 pass decides
+    }
+    c->pcg1_iters += total;
+    return total;
+}
+
 // ------------------------------------------------------------------ Hartree (Sec. 3.1)
 // V_H nodal into `VH` (boundary included): monopole/quadrupole boundary
 // values, b = 4 pi int rho phi_i - K_IB w_B, PCG on K_II with warm start VH.
@@ -280,7 +450,9 @@ static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
     launch_nodal_to_dof(c->F.n, c->d_dof_node.p, VH, c->d_pv.p, s);
     Csr K = fcsr(c, c->d_K.p);
     K.rowptr_nnz = c->F.nnz();
-    int it = pcg1_solve(c, K, c->d_Kdinv.p, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson, c->opt.max_poisson, conv);
+    int it = c->opt.precision == 1
+                 ? pcg1_mixed_solve(c, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson, c->opt.max_poisson, conv)
+                 : pcg1_solve(c, K, c->d_Kdinv.p, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson, c->opt.max_poisson, conv);
     launch_dof_to_nodal(c->F.n, c->d_dof_node.p, c->d_pv.p, VH, s);
     return it;
 }
@@ -299,8 +471,19 @@ static void assemble_nl(nas_ctx* c) {
 static void galerkin(nas_ctx* c, const double* fine_vals, double* coarse_vals) {
     launch_galerkin1(c->GM.wnnz(), c->d_w1ptr.p, c->d_w1con.p, fine_vals, c->d_col.p, c->d_Ival.p, c->d_W.p,
                      c->stream);
-    launch_galerkin2(c->GM.hnnz(), c->d_h2ptr.p, c->d_h2con.p, c->d_W.p, c->d_wrow.p, c->d_Ival.p, coarse_vals,
+    Pieces pc;
+    pc.nseg = c->GM.hnnz();
+    pc.npieces = c->GM.h2pieces.npieces();
+    pc.seg_piece = c->d_h2pc_seg.p;
+    pc.piece_start = c->d_h2pc_start.p;
+    launch_galerkin2(pc, c->d_h2con.p, c->d_W.p, c->d_wrow.p, c->d_Ival.p, c->d_piece_part.p, coarse_vals,
                      c->stream);
+}
+
+// I^T Y for Y [n][N] (fine interior rows) -> out [nH][N]
+static void transpose_apply(nas_ctx* c, int N, const double* Y, double* out) {
+    c->d_piece_part.ensure(std::max<int64_t>(1, c->GM.tpieces.npieces() * N));
+    launch_transpose_apply(tpieces(c), c->d_trow.p, c->d_tval.p, N, Y, c->d_piece_part.p, out, c->stream);
 }
 
 static double weighted_norm_diff(nas_ctx* c, const double* a, const double* b) {
@@ -414,32 +597,110 @@ static void fill_aug(nas_ctx* c, std::vector<double>& D, int m, const std::vecto
 }
 
 // blocks of A (fine CSR values) against [I, U^]: returns coarse values, b (nH x Na), beta (Na x Na)
+// (to_host = false: results stay in d_AH, d_blk_b, d_blk_beta; coarse = true
+// computes the coarse values without copying them to *AHv)
 static void blocks_of(nas_ctx* c, const double* Avals, std::vector<double>* AHv, std::vector<double>& b,
-                      std::vector<double>& beta) {
+                      std::vector<double>& beta, bool to_host = true, bool coarse = false) {
     Phase t(c, NAS_PH_BLOCKS);
     cudaStream_t s = c->stream;
     const int N = c->N, Na = c->Na;
-    if (AHv) {
-        galerkin(c, Avals, c->d_AH.p);
+    if (AHv || coarse) galerkin(c, Avals, c->d_AH.p);
+    if (AHv && to_host) {
         AHv->resize(c->GM.hnnz());
         NAS_CUDA(cudaMemcpyAsync(AHv->data(), c->d_AH.p, sizeof(double) * c->GM.hnnz(), cudaMemcpyDeviceToHost, s));
     }
     if (Na > 0) {
         spmm(c, fcsr(c, Avals), N, c->d_Uhat.p, c->d_X1.p);
-        launch_transpose_apply(c->nH, c->d_tptr.p, c->d_trow.p, c->d_tval.p, N, c->d_X1.p, c->d_blk_b.p, s);
+        transpose_apply(c, N, c->d_X1.p, c->d_blk_b.p);
         launch_gram(c->F.n, N, c->d_Uhat.p, N, c->d_X1.p, c->d_partial.p, c->d_blk_beta.p, s);
-        b.resize(c->nH * N);
-        beta.resize(N * N);
-        NAS_CUDA(cudaMemcpyAsync(b.data(), c->d_blk_b.p, sizeof(double) * c->nH * N, cudaMemcpyDeviceToHost, s));
-        NAS_CUDA(cudaMemcpyAsync(beta.data(), c->d_blk_beta.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+        if (to_host) {
+            b.resize(c->nH * N);
+            beta.resize(N * N);
+            NAS_CUDA(cudaMemcpyAsync(b.data(), c->d_blk_b.p, sizeof(double) * c->nH * N, cudaMemcpyDeviceToHost, s));
+            NAS_CUDA(cudaMemcpyAsync(beta.data(), c->d_blk_beta.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+        }
     }
-    sync(c);
+    if (to_host) sync(c);
 }
 
 // Host solve of F_A U = lambda F_B U for the lowest N pairs: dense (Cholesky
 // reduction + tridiagonal bisection) up to opt.eig_dense_max, else LOBPCG on
 // the arrow-structured pencil, warm-started from the previous solution.
+static double eig_tolerance(nas_ctx* c) {
+    // residual tolerance tied to the inner-SCF residual: the eigenvectors need
+    // no more accuracy than the density they produce, and the last inner
+    // iterations (residual near tol_inner) solve to 1e-11
+    return c->opt.eig_tol > 0.0 ? c->opt.eig_tol : std::min(1e-4, std::max(1e-11, 1e-3 * c->eig_tol_hint));
+}
+
+// Dense host copies of the last pencil after a device solve (nas_get only).
+static void dense_pencil_from_device(nas_ctx* c) {
+    if (!c->FA.empty() || c->last_m <= 0) return;
+    const int m = c->last_m;
+    const int64_t nH = c->nH;
+    const int Na = (int)(m - nH);
+    std::vector<double> av(c->GM.hnnz()), b, corner;
+    c->d_FAs.download(av.data(), av.size(), c->stream);
+    if (Na > 0) {
+        b.resize(nH * Na);
+        corner.resize(Na * Na);
+        c->d_FAb.download(b.data(), b.size(), c->stream);
+        c->d_FAc.download(corner.data(), corner.size(), c->stream);
+    }
+    sync(c);
+    c->FA.assign((size_t)m * m, 0.0);
+    c->FB.assign((size_t)m * m, 0.0);
+    dense_from_coarse(c, av, c->FA, m);
+    dense_from_coarse(c, c->BH, c->FB, m);
+    if (Na > 0) {
+        fill_aug(c, c->FA, m, b, corner);
+        fill_aug(c, c->FB, m, c->hb_cH, c->hb_gamma);
+    }
+}
+
+// LOBPCG with the block vectors on the device; the pencil's arrow parts are
+// d_FAs/d_FAb/d_FAc (F_A) and d_BHv/d_cH/d_gam (F_B); the result goes to d_U.
+static void device_eig(nas_ctx* c, int m) {
+    double t0 = wall_ms();
+    cudaStream_t s = c->stream;
+    const int64_t nH = c->nH;
+    const int Na = c->Na;
+    ArrowDev A, B;
+    A.nH = B.nH = nH;
+    A.Na = B.Na = Na;
+    A.ptr = B.ptr = c->d_hptr.p;
+    A.col = B.col = c->d_hcol.p;
+    A.sval = c->d_FAs.p;
+    B.sval = c->d_BHv.p;
+    if (Na > 0) {
+        A.Bd = c->d_FAb.p;
+        A.Cd = c->d_FAc.p;
+        B.Bd = c->d_cH.p;
+        B.Cd = c->d_gam.p;
+    }
+    std::vector<double> lam(c->N);
+    const bool warm = c->uwarm_dev_m == m;
+    c->lob.rr_ms = 0.0;
+    int it = c->lob.solve(A, B, c->d_hdiag.p, c->N, std::max(4, c->N / 4), lam.data(), warm ? c->d_Uwarm.p : nullptr,
+                          c->d_U.p, eig_tolerance(c), 2000, s);
+    if (it < 0) fail(NAS_E_EIGEN, "small eigenproblem: LOBPCG did not converge");
+    c->last_lobpcg_iters += it;
+    c->phase_ms[NAS_PH_EIG_RR] += c->lob.rr_ms;
+    c->phase_calls[NAS_PH_EIG_RR] += 1;
+    c->d_Uwarm.ensure((size_t)m * c->N);
+    NAS_CUDA(cudaMemcpyAsync(c->d_Uwarm.p, c->d_U.p, sizeof(double) * m * c->N, cudaMemcpyDeviceToDevice, s));
+    c->uwarm_dev_m = m;
+    c->U_warm.clear();
+    c->lam = lam;
+    c->phase_ms[NAS_PH_HOST_EIG] += wall_ms() - t0;
+    c->phase_calls[NAS_PH_HOST_EIG] += 1;
+}
+
 static void host_eig(nas_ctx* c, int m) {
+    if (m > c->opt.eig_dense_max && c->opt.eig_device) {
+        device_eig(c, m);
+        return;
+    }
     double t0 = wall_ms();
     std::vector<double> lam(c->N), U((size_t)m * c->N);
     if (m <= c->opt.eig_dense_max) {
@@ -469,16 +730,13 @@ static void host_eig(nas_ctx* c, int m) {
         ArrowMat B{nH, Na, c->GM.hptr.data(), c->GM.hcol.data(), bs.data(), bb.data(), bc.data()};
         bool warm = (int64_t)c->U_warm.size() == (int64_t)m * c->N;
         if (warm) U = c->U_warm;
-        // residual tolerance tied to the inner-SCF residual: the eigenvectors
-        // need no more accuracy than the density they produce, and the last
-        // inner iterations (residual near tol_inner) solve to 1e-11
-        double tol = c->opt.eig_tol > 0.0 ? c->opt.eig_tol
-                                          : std::min(1e-4, std::max(1e-11, 1e-3 * c->eig_tol_hint));
+        double tol = eig_tolerance(c);
         int it = lobpcg_arrow(A, B, c->N, std::max(4, c->N / 4), lam.data(), U.data(), warm, tol, 2000);
         if (it < 0) fail(NAS_E_EIGEN, "small eigenproblem: LOBPCG did not converge");
         c->last_lobpcg_iters += it;
     }
     c->U_warm = U;
+    c->uwarm_dev_m = 0;
     c->lam = lam;
     NAS_CUDA(cudaMemcpyAsync(c->d_U.p, U.data(), sizeof(double) * m * c->N, cudaMemcpyHostToDevice, c->stream));
     sync(c);
@@ -493,14 +751,24 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
     const int m = (int)(nH + Na);
     cudaStream_t s = c->stream;
     c->last_m = m;
-    std::vector<double> FB0((size_t)m * m, 0.0), FA0((size_t)m * m, 0.0);
-    dense_from_coarse(c, c->BH, FB0, m);
-    dense_from_coarse(c, c->AHL, FA0, m);
-    if (Na > 0) {
-        fill_aug(c, FB0, m, c->hb_cH, c->hb_gamma);
-        fill_aug(c, FA0, m, c->hb_bHL, c->hb_betaL);
+    // the host keeps dense copies of the pencil only for the dense path and the
+    // host LOBPCG; the device LOBPCG reads the arrow parts on the device
+    const bool dev_eig = m > c->opt.eig_dense_max && c->opt.eig_device;
+    std::vector<double> FB0, FA0;
+    if (!dev_eig) {
+        FB0.assign((size_t)m * m, 0.0);
+        FA0.assign((size_t)m * m, 0.0);
+        dense_from_coarse(c, c->BH, FB0, m);
+        dense_from_coarse(c, c->AHL, FA0, m);
+        if (Na > 0) {
+            fill_aug(c, FB0, m, c->hb_cH, c->hb_gamma);
+            fill_aug(c, FA0, m, c->hb_bHL, c->hb_betaL);
+        }
+        c->FB = FB0;
+    } else {
+        c->FA.clear();
+        c->FB.clear();
     }
-    c->FB = FB0;
     Anderson A;
     int poisson = 0;
     double res = 0.0;
@@ -517,18 +785,31 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
             assemble_nl(c);
             c->anl_valid = true;
         }
-        blocks_of(c, c->d_ANL.p, &AHnl, bnl, betanl);
-        c->FA = FA0;
-        for (int64_t a = 0; a < nH; ++a)
-            for (int p = c->GM.hptr[a]; p < c->GM.hptr[a + 1]; ++p) c->FA[a * m + c->GM.hcol[p]] += AHnl[p];
-        if (Na > 0) {
+        if (dev_eig) {
+            // F_A = linear part + A^NL part, formed on the device (arrow parts)
+            blocks_of(c, c->d_ANL.p, nullptr, bnl, betanl, /*to_host=*/false, /*coarse=*/true);
+            c->d_FAs.ensure(std::max<int64_t>(1, c->GM.hnnz()));
+            launch_axpby(c->GM.hnnz(), 1.0, c->d_AHLv.p, 1.0, c->d_AH.p, c->d_FAs.p, s);
+            if (Na > 0) {
+                c->d_FAb.ensure(nH * Na);
+                c->d_FAc.ensure(Na * Na);
+                launch_axpby(nH * Na, 1.0, c->d_bL.p, 1.0, c->d_blk_b.p, c->d_FAb.p, s);
+                launch_axpby(Na * Na, 1.0, c->d_betaL.p, 1.0, c->d_blk_beta.p, c->d_FAc.p, s);
+            }
+        } else {
+            blocks_of(c, c->d_ANL.p, &AHnl, bnl, betanl);
+            c->FA = FA0;
             for (int64_t a = 0; a < nH; ++a)
-                for (int j = 0; j < Na; ++j) {
-                    c->FA[a * m + nH + j] += bnl[a * Na + j];
-                    c->FA[(nH + j) * m + a] += bnl[a * Na + j];
-                }
-            for (int i = 0; i < Na; ++i)
-                for (int j = 0; j < Na; ++j) c->FA[(nH + i) * m + nH + j] += betanl[i * Na + j];
+                for (int p = c->GM.hptr[a]; p < c->GM.hptr[a + 1]; ++p) c->FA[a * m + c->GM.hcol[p]] += AHnl[p];
+            if (Na > 0) {
+                for (int64_t a = 0; a < nH; ++a)
+                    for (int j = 0; j < Na; ++j) {
+                        c->FA[a * m + nH + j] += bnl[a * Na + j];
+                        c->FA[(nH + j) * m + a] += bnl[a * Na + j];
+                    }
+                for (int i = 0; i < Na; ++i)
+                    for (int j = 0; j < Na; ++j) c->FA[(nH + i) * m + nH + j] += betanl[i * Na + j];
+            }
         }
         c->eig_tol_hint = (t == 0) ? 1.0 : res;
         host_eig(c, m);
@@ -568,11 +849,13 @@ static void augment_basis(nas_ctx* c) {
     const int64_t n = c->F.n, nH = c->nH;
     const int N = c->N;
     spmm(c, fcsr(c, c->d_M.p), N, c->d_Uhat.p, c->d_X1.p);
-    launch_transpose_apply(nH, c->d_tptr.p, c->d_trow.p, c->d_tval.p, N, c->d_X1.p, c->d_blk_c.p, s);
+    transpose_apply(c, N, c->d_X1.p, c->d_blk_c.p);
+    // Y = B_H^-1 I^T M U^ (dense inverse on the device)
+    launch_cols_mult(nH, ColBlocks::one(c->d_BHinv.p, (int)nH, (int)nH), c->d_blk_c.p, N, 1.0, 0.0, c->d_blk_b.p,
+                     s);
     std::vector<double> Y(nH * N), Uf((nH + N) * N, 0.0);
-    NAS_CUDA(cudaMemcpyAsync(Y.data(), c->d_blk_c.p, sizeof(double) * nH * N, cudaMemcpyDeviceToHost, s));
+    NAS_CUDA(cudaMemcpyAsync(Y.data(), c->d_blk_b.p, sizeof(double) * nH * N, cudaMemcpyDeviceToHost, s));
     sync(c);
-    chol_solve((int)nH, c->BH_chol.data(), N, Y.data());
     for (int64_t i = 0; i < nH * N; ++i) Uf[i] = -Y[i];
     for (int j = 0; j < N; ++j) Uf[(nH + j) * N + j] = 1.0;
     NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
@@ -599,6 +882,8 @@ static void augment_basis(nas_ctx* c) {
     for (int64_t i = 0; i < nH * N; ++i) c->U_warm[i] = Y[i];
     for (int a = 0; a < N; ++a)
         for (int b = a; b < N; ++b) c->U_warm[(nH + a) * N + b] = g[b * N + a];
+    c->d_Uwarm.upload(c->U_warm, s);
+    c->uwarm_dev_m = nH + N;
     std::fill(Uf.begin(), Uf.end(), 0.0);
     for (int i = 0; i < N * N; ++i) Uf[nH * N + i] = Linv_T[i];
     NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
@@ -606,6 +891,47 @@ static void augment_basis(nas_ctx* c) {
 }
 
 // ------------------------------------------------------------------ setup
+static Nuclei nuclei(nas_ctx* c) {
+    return Nuclei{c->n_nuc, c->d_R.p, c->d_Zn.p, c->potential, c->smooth_a, c->opt.omega};
+}
+
+// V_ext at quadrature points, M_Vext and A^L = K/2 + M_Vext (eq. st3 without mu)
+static void assemble_vext(nas_ctx* c) {
+    cudaStream_t s = c->stream;
+    const int64_t nnz = c->F.nnz();
+    Mesh m = fmesh(c);
+    c->d_R.upload(c->R, s);
+    c->d_Zn.upload(c->Z, s);
+    launch_vext(m, nuclei(c), c->d_coef.p, s);
+    launch_local_mass(m, c->d_Wq.p, c->d_coef.p, c->d_L.p, s);
+    launch_gather(nnz, c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, c->d_Mvext.p, s);
+    launch_combine3(nnz, 0.5, c->d_K.p, 1.0, c->d_Mvext.p, 0.0, nullptr, c->d_AL.p, s);
+}
+
+static void system_parameters(nas_ctx* c) {
+    double z2 = 0.0;
+    for (double z : c->Z) z2 += z * z;
+    c->mu = c->opt.mu >= 0.0 ? c->opt.mu : 8.0 * c->n_nuc * z2;
+    c->Enn = 0.0;
+    for (int j = 0; j < c->n_nuc; ++j)
+        for (int k = 0; k < j; ++k) {
+            double dx = c->R[3 * j] - c->R[3 * k], dy = c->R[3 * j + 1] - c->R[3 * k + 1],
+                   dz = c->R[3 * j + 2] - c->R[3 * k + 2];
+            c->Enn += c->Z[j] * c->Z[k] / std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+}
+
+static void galerkin(nas_ctx* c, const double* fine_vals, double* coarse_vals);
+
+void ctx_update_nuclei(nas_ctx* c) {
+    assemble_vext(c);
+    galerkin(c, c->d_AL.p, c->d_AH.p);
+    c->d_AH.download(c->AHL.data(), c->GM.hnnz(), c->stream);
+    c->d_AHLv.upload(c->AHL, c->stream);
+    sync(c);
+    system_parameters(c);
+}
+
 static void alloc_work(nas_ctx* c) {
     const int64_t n = c->F.n, N = c->N;
     const int64_t nqt = c->nqt;
@@ -650,6 +976,11 @@ void ctx_setup(nas_ctx* c) {
         cudaGraphExecDestroy(c->pcg1_exec);
         c->pcg1_exec = nullptr;
     }
+    if (c->pcg1f_exec) {
+        cudaGraphExecDestroy(c->pcg1f_exec);
+        c->pcg1f_exec = nullptr;
+    }
+    c->d_K32.release();
     build_space(c->F, c->fine_order, c->fnv, c->fxyz.data(), c->fne, c->ftet.data(), true);
     build_space(c->C, 1, c->cnv, c->cxyz.data(), c->cne, c->ctet.data(), false);
     for (int d = 0; d < 3; ++d)
@@ -698,14 +1029,8 @@ void ctx_setup(nas_ctx* c) {
     launch_gather(F.nnzb(), c->d_bcptr.p, c->d_bcontrib.p, c->d_L.p, 1.0, c->d_KIB.p, s);
     launch_local_mass(m, c->d_Wq.p, nullptr, c->d_L.p, s);
     launch_gather(nnz, c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, c->d_M.p, s);
-    c->d_R.upload(c->R, s);
-    c->d_Zn.upload(c->Z, s);
     c->d_coef.alloc(c->nqt);
-    Nuclei nuc{c->n_nuc, c->d_R.p, c->d_Zn.p, c->potential, c->smooth_a, c->opt.omega};
-    launch_vext(m, nuc, c->d_coef.p, s);
-    launch_local_mass(m, c->d_Wq.p, c->d_coef.p, c->d_L.p, s);
-    launch_gather(nnz, c->d_cptr.p, c->d_contrib.p, c->d_L.p, 1.0, c->d_Mvext.p, s);
-    launch_combine3(nnz, 0.5, c->d_K.p, 1.0, c->d_Mvext.p, 0.0, nullptr, c->d_AL.p, s);
+    assemble_vext(c);
     launch_inv_diag(fcsr(c, c->d_K.p), c->d_Kdinv.p, s);
     // ---- transfer I_H^h by point location (Algorithm 1)
     {
@@ -763,6 +1088,12 @@ void ctx_setup(nas_ctx* c) {
     c->d_hcol.upload(G.hcol, s);
     c->d_h2ptr.upload(G.h2ptr, s);
     c->d_h2con.upload(G.h2con, s);
+    c->d_tpc_seg.upload(G.tpieces.seg_piece, s);
+    c->d_tpc_start.upload(G.tpieces.piece_start, s);
+    c->d_h2pc_seg.upload(G.h2pieces.seg_piece, s);
+    c->d_h2pc_start.upload(G.h2pieces.piece_start, s);
+    c->d_piece_part.ensure(std::max<int64_t>({1, G.h2pieces.npieces(), G.tpieces.npieces() * std::max(1, c->N)}));
+    c->d_cpart.alloc(std::max<int64_t>(1, G.tpieces.npieces()));
     c->d_W.alloc(std::max<int64_t>(1, G.wnnz()));
     c->d_AH.alloc(std::max<int64_t>(1, G.hnnz()));
     // fixed coarse blocks B_H = I^T M I and A_H^L = I^T A^L I
@@ -774,22 +1105,48 @@ void ctx_setup(nas_ctx* c) {
     galerkin(c, c->d_AL.p, c->d_AH.p);
     c->d_AH.download(c->AHL.data(), G.hnnz(), s);
     sync(c);
+    // device copies for the small pencil on the device
+    c->d_BHv.upload(c->BH, s);
+    c->d_AHLv.upload(c->AHL, s);
+    {
+        std::vector<int32_t> dslot(c->nH, -1);
+        for (int64_t a = 0; a < c->nH; ++a)
+            for (int p = G.hptr[a]; p < G.hptr[a + 1]; ++p)
+                if (G.hcol[p] == a) dslot[a] = p;
+        c->d_hdiag.upload(dslot, s);
+    }
+    c->uwarm_dev_m = 0;
+    sync(c);
+    // two-level Poisson preconditioner: dense K_H^-1 with K_H = I^T K I
+    c->d_khinv.release();
+    if (c->opt.poisson_two_level) {
+        std::vector<double> kh(G.hnnz());
+        galerkin(c, c->d_K.p, c->d_AH.p);
+        c->d_AH.download(kh.data(), G.hnnz(), s);
+        sync(c);
+        std::vector<double> D((size_t)c->nH * c->nH, 0.0), Inv((size_t)c->nH * c->nH, 0.0);
+        for (int64_t a = 0; a < c->nH; ++a)
+            for (int p = G.hptr[a]; p < G.hptr[a + 1]; ++p) D[a * c->nH + G.hcol[p]] = kh[p];
+        if (chol_factor((int)c->nH, D.data()) != 0) fail(NAS_E_MESH, "coarse stiffness I^T K I is singular");
+        chol_inverse((int)c->nH, D.data(), Inv.data());
+        c->d_khinv.upload(Inv, s);
+        c->d_khvec.alloc(2 * c->nH);
+        sync(c);
+    }
     // dense Cholesky factor of B_H (coarse Gram matrix), used by augment_basis
     c->BH_chol.assign((size_t)c->nH * c->nH, 0.0);
     for (int64_t a = 0; a < c->nH; ++a)
         for (int p = G.hptr[a]; p < G.hptr[a + 1]; ++p) c->BH_chol[a * c->nH + G.hcol[p]] = c->BH[p];
     if (chol_factor((int)c->nH, c->BH_chol.data()) != 0) fail(NAS_E_MESH, "coarse Gram matrix B_H is singular");
+    {
+        // dense B_H^-1 on the device: augment_basis applies it to N columns per step
+        std::vector<double> Inv((size_t)c->nH * c->nH);
+        chol_inverse((int)c->nH, c->BH_chol.data(), Inv.data());
+        c->d_BHinv.upload(Inv, s);
+        sync(c);
+    }
     // ---- parameters
-    double z2 = 0.0;
-    for (double z : c->Z) z2 += z * z;
-    c->mu = c->opt.mu >= 0.0 ? c->opt.mu : 8.0 * c->n_nuc * z2;
-    c->Enn = 0.0;
-    for (int j = 0; j < c->n_nuc; ++j)
-        for (int k = 0; k < j; ++k) {
-            double dx = c->R[3 * j] - c->R[3 * k], dy = c->R[3 * j + 1] - c->R[3 * k + 1],
-                   dz = c->R[3 * j + 2] - c->R[3 * k + 2];
-            c->Enn += c->Z[j] * c->Z[k] / std::sqrt(dx * dx + dy * dy + dz * dz);
-        }
+    system_parameters(c);
     c->d_VH.alloc(F.nnode);
     c->d_wB.alloc(std::max<int64_t>(1, F.nb));
     c->d_VH.zero(s);
@@ -807,6 +1164,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
     c->anl_valid = false;
     c->d_VH.zero(s);
     c->U_warm.clear();
+    c->uwarm_dev_m = 0;
     if (psi0 == nullptr) {
         // self-consistent solution in S_H alone, from rho = 0
         if (c->nH < c->N) fail(NAS_E_INVALID_ARG, "the coarse-space initial guess needs n_coarse_dof >= N");
@@ -913,7 +1271,11 @@ int ctx_step(nas_ctx* c, nas_report* rep) {
         std::vector<double> dummy;
         // M against U^: c_H = I^T M U^, gamma = U^T M U^
         blocks_of(c, c->d_M.p, nullptr, c->hb_cH, c->hb_gamma);
+        c->d_cH.upload(c->hb_cH, s);
+        c->d_gam.upload(c->hb_gamma, s);
         blocks_of(c, c->d_AL.p, nullptr, c->hb_bHL, c->hb_betaL);
+        c->d_bL.upload(c->hb_bHL, s);
+        c->d_betaL.upload(c->hb_betaL, s);
     }
     NAS_CUDA(cudaMemcpyAsync(c->d_rho_prev.p, c->d_rho_out.p, sizeof(double) * c->nqt, cudaMemcpyDeviceToDevice, s));
     inner_scf(c, true);
@@ -1036,8 +1398,14 @@ void ctx_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {
         case NAS_Q_TRANSFER_ELEM: put(c->d_Ielem.p, sizeof(int32_t) * n); break;
         case NAS_Q_TRANSFER_COL: put(c->d_Icol.p, sizeof(int32_t) * 4 * n); break;
         case NAS_Q_TRANSFER_W: put(c->d_Ival.p, sizeof(double) * 4 * n); break;
-        case NAS_Q_FA: put_host(c->FA.data(), sizeof(double) * c->FA.size()); break;
-        case NAS_Q_FB: put_host(c->FB.data(), sizeof(double) * c->FB.size()); break;
+        case NAS_Q_FA:
+            dense_pencil_from_device(c);
+            put_host(c->FA.data(), sizeof(double) * c->FA.size());
+            break;
+        case NAS_Q_FB:
+            dense_pencil_from_device(c);
+            put_host(c->FB.data(), sizeof(double) * c->FB.size());
+            break;
         case NAS_Q_DOF_NODE: put(c->d_dof_node.p, sizeof(int32_t) * n); break;
         case NAS_Q_ENERGY: put_host(c->energy.data(), sizeof(double) * 6); break;
         default: fail(NAS_E_INVALID_ARG, "unknown quantity");
@@ -1104,10 +1472,20 @@ void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int o
             break;
         }
         case NAS_OP_BVP: {
-            if (c->step_count == 0) fail(NAS_E_STATE, "H~ exists after the first nas_step");
+            if (!c->initialized) fail(NAS_E_STATE, "nas_init must be called first");
             fin(a, n * N);
             b.alloc(n * N);
             b.zero(s);
+            if (!c->anl_valid) {
+                if (c->opt.hartree) {
+                    bool pc;
+                    hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
+                }
+                assemble_nl(c);
+                c->anl_valid = true;
+            }
+            launch_combine3(nnz, 1.0, c->d_AL.p, 1.0, c->d_ANL.p, c->mu, c->d_M.p, c->d_H.p, s);
+            launch_inv_diag(fcsr(c, c->d_H.p), c->d_Hdinv.p, s);
             bool conv;
             pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, (int)N, a.p, b.p, c->opt.tol_bvp, c->opt.max_cg, &conv);
             if (!conv) fail(NAS_E_NOT_CONVERGED, "block PCG hit its iteration cap");
@@ -1128,6 +1506,61 @@ void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int o
             else
                 std::memcpy(out, D.data(), sizeof(double) * D.size());
             sync(c);
+            break;
+        }
+        case NAS_OP_ENERGY_GRAD: {
+            fin(a, c->nqt);
+            b.alloc(4 * std::max(1, c->n_nuc));
+            DBuf<double> part(1216 * 32);
+            launch_vext_grad(fmesh(c), nuclei(c), c->d_Wq.p, a.p, part.p, b.p, s);
+            std::vector<double> g(4 * c->n_nuc);
+            b.download(g.data(), g.size(), s);
+            sync(c);
+            // + d E_nn / d(R_k, Z_k)
+            for (int k = 0; k < c->n_nuc; ++k)
+                for (int j = 0; j < c->n_nuc; ++j) {
+                    if (j == k) continue;
+                    double d[3] = {c->R[3 * k] - c->R[3 * j], c->R[3 * k + 1] - c->R[3 * j + 1],
+                                   c->R[3 * k + 2] - c->R[3 * j + 2]};
+                    double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    for (int q = 0; q < 3; ++q) g[4 * k + q] -= c->Z[j] * c->Z[k] * d[q] / (r * r * r);
+                    g[4 * k + 3] += c->Z[j] / r;
+                }
+            if (on_device)
+                NAS_CUDA(cudaMemcpyAsync(out, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, s));
+            else
+                std::memcpy(out, g.data(), sizeof(double) * g.size());
+            sync(c);
+            break;
+        }
+        case NAS_OP_BVP_VJP: {
+            if (!c->initialized) fail(NAS_E_STATE, "nas_init must be called first");
+            fin(a, 2 * n * N);
+            b.alloc(2 * n * N + 4 * std::max(1, c->n_nuc));
+            if (!c->anl_valid) {
+                if (c->opt.hartree) {
+                    bool pc;
+                    hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
+                }
+                assemble_nl(c);
+                c->anl_valid = true;
+            }
+            launch_combine3(nnz, 1.0, c->d_AL.p, 1.0, c->d_ANL.p, c->mu, c->d_M.p, c->d_H.p, s);
+            launch_inv_diag(fcsr(c, c->d_H.p), c->d_Hdinv.p, s);
+            double* U = b.p;
+            double* A = b.p + n * N;
+            b.zero(s);
+            bool conv;
+            pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, (int)N, a.p, U, c->opt.tol_bvp, c->opt.max_cg, &conv);
+            if (!conv) fail(NAS_E_NOT_CONVERGED, "block PCG hit its iteration cap");
+            pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, (int)N, a.p + n * N, A, c->opt.tol_bvp, c->opt.max_cg, &conv);
+            if (!conv) fail(NAS_E_NOT_CONVERGED, "block PCG hit its iteration cap");
+            launch_pair_density(fmesh(c), c->d_dof_of_node.p, A, U, (int)N, c->d_tmpq.p, s);
+            DBuf<double> part(1216 * 32);
+            double* dp = b.p + 2 * n * N;
+            launch_vext_grad(fmesh(c), nuclei(c), c->d_Wq.p, c->d_tmpq.p, part.p, dp, s);
+            launch_axpby(4 * c->n_nuc, -1.0, dp, 0.0, nullptr, dp, s);
+            fout(b.p, 2 * n * N + 4 * c->n_nuc);
             break;
         }
         default: fail(NAS_E_INVALID_ARG, "unknown op");

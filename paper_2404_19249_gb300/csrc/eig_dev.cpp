@@ -1,0 +1,188 @@
+// Device LOBPCG (Knyazev 2001) for the arrow-structured small pencil of
+// Algorithm 3: the same iteration as the host solver (diagonal preconditioner
+// diag(A - sigma B)^-1, W orthogonalised against X and B-normalised, exact
+// recomputation of A and B times the new X and P, two-pass Gram
+// orthonormalisation inside the Rayleigh-Ritz step), with every column kept
+// active and the convergence test taken from the residual norms that travel
+// with the Gram matrices.
+#include "eig_dev.h"
+
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "small_eig.h"
+
+namespace nas {
+
+int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, int nev, int nguard,
+                     double* lam, const double* U0, double* Uout, double tol, int maxit, cudaStream_t s) {
+    const int64_t m = A.nH + A.Na;
+    if (nev < 1 || nev > m) return -1;
+    const int k = (int)std::min<int64_t>(nev + nguard, m);
+    const int kmax3 = 3 * k;
+    if (m > m_cap || k > k_cap) {
+        for (auto& b : bufs) b.alloc(m * k);
+        T.alloc(m);
+        theta.alloc(k);
+        nrm.alloc(4 * k);
+        int64_t gp = std::max<int64_t>({gram_tiles_partial_size(m, kmax3, kmax3),
+                                        gram_tiles_partial_size(A.nH, std::max(1, A.Na), k),
+                                        reduce_partial_size(3 * k)});
+        gpart.alloc(gp);
+        gtmp.alloc(std::max(1, A.Na) * (int64_t)k);
+        GA.alloc((int64_t)kmax3 * kmax3);
+        GB.alloc((int64_t)kmax3 * kmax3);
+        Y.alloc((int64_t)kmax3 * k);
+        C.alloc((int64_t)k * k);
+        m_cap = m;
+        k_cap = k;
+    }
+    double *X = bufs[0].p, *AX = bufs[1].p, *BX = bufs[2].p, *W = bufs[3].p, *AW = bufs[4].p, *BW = bufs[5].p;
+    double *P = bufs[6].p, *AP = bufs[7].p, *BP = bufs[8].p, *X2 = bufs[9].p, *P2 = bufs[10].p;
+    auto applyA = [&](int w, const double* in, double* out) {
+        launch_arrow_apply(A, w, in, out, gpart.p, gtmp.p, s);
+    };
+    auto applyB = [&](int w, const double* in, double* out) {
+        launch_arrow_apply(B, w, in, out, gpart.p, gtmp.p, s);
+    };
+    std::vector<double> hG, hH, hY, th, hn(3 * (size_t)k);
+    // Rayleigh-Ritz on the basis S (ns columns): Grams on the device, the rest on the host
+    auto grams = [&](const ColBlocks& S, const ColBlocks& AS, const ColBlocks& BS) {
+        launch_gram_tiles(m, S, AS, gpart.p, GA.p, s);
+        launch_gram_tiles(m, S, BS, gpart.p, GB.p, s);
+    };
+    auto fetch = [&](int ns, bool norms) {
+        hG.resize((size_t)ns * ns);
+        hH.resize((size_t)ns * ns);
+        NAS_CUDA(cudaMemcpyAsync(hH.data(), GA.p, sizeof(double) * ns * ns, cudaMemcpyDeviceToHost, s));
+        NAS_CUDA(cudaMemcpyAsync(hG.data(), GB.p, sizeof(double) * ns * ns, cudaMemcpyDeviceToHost, s));
+        if (norms) NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
+        NAS_CUDA(cudaStreamSynchronize(s));
+    };
+    auto rr = [&](int ns) {
+        auto t0 = std::chrono::steady_clock::now();
+        int r = rayleigh_ritz_grams(ns, hG, hH, k, hY, th);
+        rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (r == 0) {
+            NAS_CUDA(cudaMemcpyAsync(Y.p, hY.data(), sizeof(double) * ns * k, cudaMemcpyHostToDevice, s));
+            NAS_CUDA(cudaMemcpyAsync(theta.p, th.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+        }
+        return r;
+    };
+    // ---- start: warm vectors for the wanted columns, deterministic pseudo-random otherwise
+    {
+        std::vector<double> X0((size_t)m * k);
+        for (int64_t i = 0; i < m; ++i)
+            for (int j = 0; j < k; ++j) {
+                double r = std::sin(12.9898 * (i + 1) + 78.233 * (j + 1)) * 43758.5453;
+                X0[i * k + j] = r - std::floor(r) - 0.5;
+            }
+        NAS_CUDA(cudaMemcpyAsync(X, X0.data(), sizeof(double) * m * k, cudaMemcpyHostToDevice, s));
+        if (U0)
+            NAS_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * k, U0, sizeof(double) * nev, sizeof(double) * nev, m,
+                                       cudaMemcpyDeviceToDevice, s));
+        // the host copy must outlive the asynchronous upload
+        NAS_CUDA(cudaStreamSynchronize(s));
+    }
+    applyA(k, X, AX);
+    applyB(k, X, BX);
+    {
+        ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
+        grams(S, AS, BS);
+        fetch(k, false);
+        if (rr(k) != 0) return -1;
+        launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
+        std::swap(X, X2);
+        applyA(k, X, AX);
+        applyB(k, X, BX);
+    }
+    {
+        const double sigma = th[0] - 0.1 * std::fabs(th[0]) - 1.0;
+        launch_eig_precond(A, B, diag_slot, sigma, T.p, s);
+    }
+    int np = 0;
+    int it = 0;
+    for (; it < maxit; ++it) {
+        // W = T (AX - BX theta); residual norms of the current X
+        launch_eig_resid(m, k, AX, BX, theta.p, W, s);
+        {
+            const double* Xs[3] = {W, AX, BX};
+            launch_coldots(m, k, 3, Xs, Xs, nullptr, gpart.p, nrm.p, s);
+        }
+        launch_scale_rows(m, k, T.p, W, W, s);
+        // W <- W - X (BX^T W), then unit B-norm columns
+        launch_gram_tiles(m, ColBlocks::one(BX, k, k), ColBlocks::one(W, k, k), gpart.p, C.p, s);
+        launch_cols_mult(m, ColBlocks::one(X, k, k), C.p, k, -1.0, 1.0, W, s);
+        applyB(k, W, BW);
+        {
+            const double* Xs[1] = {W};
+            const double* Ys[1] = {BW};
+            launch_coldots(m, k, 1, Xs, Ys, nullptr, gpart.p, nrm.p + 3 * k, s);
+        }
+        launch_inv_sqrt_scale(m, k, nrm.p + 3 * k, W, BW, nullptr, s);
+        applyA(k, W, AW);
+        ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
+        S.add(W, k, k);
+        AS.add(AW, k, k);
+        BS.add(BW, k, k);
+        if (np > 0) {
+            S.add(P, k, np);
+            AS.add(AP, k, np);
+            BS.add(BP, k, np);
+        }
+        const int ns = S.ncols();
+        grams(S, AS, BS);
+        fetch(ns, true);
+        double worst = 0.0;
+        for (int j = 0; j < nev; ++j) {
+            const double rel = std::sqrt(std::max(hn[j], 0.0)) /
+                               (std::sqrt(std::max(hn[k + j], 0.0)) +
+                                std::fabs(th[j]) * std::sqrt(std::max(hn[2 * k + j], 0.0)) + 1e-300);
+            worst = std::max(worst, rel);
+        }
+        if (!std::isfinite(worst)) return -1;
+        if (worst <= tol) break;
+        if (rr(ns) != 0) {
+            if (np == 0) return -1;
+            np = 0;  // restart without P
+            continue;
+        }
+        // new X = S Y; new P = [W, P] part of S Y
+        launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
+        {
+            ColBlocks WP = ColBlocks::one(W, k, k);
+            if (np > 0) WP.add(P, k, np);
+            launch_cols_mult(m, WP, Y.p + (int64_t)k * k, k, 1.0, 0.0, P2, s);
+        }
+        std::swap(X, X2);
+        std::swap(P, P2);
+        np = k;
+        // exact images (implicitly updated ones drift and break the Rayleigh-Ritz)
+        applyA(k, X, AX);
+        applyB(k, X, BX);
+        applyA(k, P, AP);
+        applyB(k, P, BP);
+        {
+            const double* Xs[1] = {P};
+            const double* Ys[1] = {BP};
+            launch_coldots(m, k, 1, Xs, Ys, nullptr, gpart.p, nrm.p + 3 * k, s);
+        }
+        launch_inv_sqrt_scale(m, k, nrm.p + 3 * k, P, AP, BP, s);
+    }
+    if (it >= maxit) return -1;
+    // final Rayleigh-Ritz within span X for B-orthonormal output
+    {
+        ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
+        grams(S, AS, BS);
+        fetch(k, false);
+        if (rr(k) != 0) return -1;
+        launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
+        NAS_CUDA(cudaMemcpy2DAsync(Uout, sizeof(double) * nev, X2, sizeof(double) * k, sizeof(double) * nev, m,
+                                   cudaMemcpyDeviceToDevice, s));
+    }
+    for (int j = 0; j < nev; ++j) lam[j] = th[j];
+    return it;
+}
+
+}  // namespace nas

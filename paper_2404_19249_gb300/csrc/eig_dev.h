@@ -1,0 +1,31 @@
+// LOBPCG for the small pencil F_A U = lambda F_B U of Algorithm 3 (eq. st1)
+// with the block vectors on the device.  The arrow-structured products, the
+// residuals, the orthogonalisation and the Gram matrices of the basis
+// [X, W, P] run in device kernels; the host receives only the Gram matrices
+// ((3k)^2 numbers, k = nev + nguard) and returns the Rayleigh-Ritz
+// coefficients, so one host round trip is made per iteration.
+#pragma once
+
+#include "common.h"
+#include "kernels.h"
+
+namespace nas {
+
+struct DevLobpcg {
+    // block vectors [m][k] (raw pointers are swapped between iterations)
+    DBuf<double> bufs[11];
+    DBuf<double> T, theta, nrm, gpart, gtmp, GA, GB, Y, C;
+    int64_t m_cap = 0;
+    int k_cap = 0;
+    double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)
+
+    // Lowest nev pairs.  U0: device [m][nev] warm start or null; Uout: device
+    // [m][nev] (B-orthonormal eigenvectors); lam: host [nev].  diag_slot[i] is
+    // the CSR slot of the coarse block's diagonal entry (i, i).  Stops when every
+    // wanted residual satisfies ||A u - lambda B u|| <= tol (||A u|| + |lambda|
+    // ||B u||).  Returns the iterations used, or -1 on failure.
+    int solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, int nev, int nguard, double* lam,
+              const double* U0, double* Uout, double tol, int maxit, cudaStream_t s);
+};
+
+}  // namespace nas

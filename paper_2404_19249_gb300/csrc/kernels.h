@@ -79,6 +79,13 @@ void launch_moments(const Mesh& m, const double* Wq, const double* rho, double* 
 void launch_boundary_values(int64_t nb, const int32_t* bnd_node, const double* node_xyz,
                             const double* moments, int multipole, double* wB, double* V_nodal,
                             cudaStream_t s);
+// out[e][q] = sum_c A_c(x_q) U_c(x_q) for dof values A, U [n][N]
+void launch_pair_density(const Mesh& m, const int32_t* dof_of_node, const double* A, const double* U, int N,
+                         double* out, cudaStream_t s);
+// out[k][c] = sum_{e,q} W_eq w_eq dV_ext/dp_(k,c)(x_q), p = (R_k x, y, z, Z_k);
+// partial: scratch of 1216*32 doubles (Coulomb or smoothed Coulomb)
+void launch_vext_grad(const Mesh& m, const Nuclei& nuc, const double* Wq, const double* w, double* partial,
+                      double* out, cudaStream_t s);
 // gather nodal values at the dofs: x[i] = V_nodal[dof_node[i]]
 void launch_nodal_to_dof(int64_t n, const int32_t* dof_node, const double* V_nodal, double* x,
                          cudaStream_t s);
@@ -152,9 +159,18 @@ int64_t gram_partial_size(int64_t width);
 void launch_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y, double* partial,
                  double* G, cudaStream_t s);
 
-// out[a][c] = sum_{p in [tptr[a], tptr[a+1])} tval[p] Y[trow[p]][c]   (I^T Y)
-void launch_transpose_apply(int64_t nH, const int32_t* tptr, const int32_t* trow, const double* tval,
-                            int N, const double* Y, double* out, cudaStream_t s);
+// Balanced pieces of a segmented list (see PieceMap on the host): pieces of
+// segment a are [seg_piece[a], seg_piece[a+1]); piece q covers list entries
+// [piece_start[q], piece_start[q+1]).
+struct Pieces {
+    int64_t nseg = 0, npieces = 0;
+    const int32_t* seg_piece = nullptr;
+    const int64_t* piece_start = nullptr;
+};
+// out[a][c] = sum_{p in segment a} tval[p] Y[trow[p]][c]   (I^T Y over the I^T
+// rows split into pieces); partial: scratch of npieces * N doubles
+void launch_transpose_apply(const Pieces& pc, const int32_t* trow, const double* tval, int N, const double* Y,
+                            double* partial, double* out, cudaStream_t s);
 // Psi[i][c] = sum_k ival[i][k] uH[icol[i][k]][c] + sum_j Uhat[i][j] alpha[j][c]
 // U = [uH ; alpha] is [(nH + Na)][N] on the device; Na may be 0.
 void launch_reconstruct(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
@@ -162,28 +178,112 @@ void launch_reconstruct(int64_t n, const int32_t* icol, const double* ival, int 
 // Galerkin stage 1: W[s] = sum_{q in list} A[q>>2] * ival[col[q>>2]*4 + (q&3)]
 void launch_galerkin1(int64_t nw, const int64_t* ptr, const int32_t* con, const double* A,
                       const int32_t* col, const double* ival, double* W, cudaStream_t s);
-// Galerkin stage 2: H[t] = sum_{r in list} ival[wrow[r>>2]*4 + (r&3)] * W[r>>2]
-void launch_galerkin2(int64_t nh, const int64_t* ptr, const int32_t* con, const double* W,
-                      const int32_t* wrow, const double* ival, double* H, cudaStream_t s);
+// Galerkin stage 2: H[t] = sum_{r in list t} ival[wrow[r>>2]*4 + (r&3)] * W[r>>2]
+// over the lists split into pieces; partial: scratch of npieces doubles
+void launch_galerkin2(const Pieces& pc, const int32_t* con, const double* W, const int32_t* wrow,
+                      const double* ival, double* partial, double* H, cudaStream_t s);
 
-// Fused single right-hand-side Jacobi PCG (Poisson): device state of one solve.
-struct Pcg1 {
+// ------------------------------------------------------------ small pencil on the device
+// Arrow-structured symmetric matrix of the small problem (eq. st2):
+// [[S, Bd], [Bd^T, Cd]], S sparse nH x nH (CSR, full symmetric storage),
+// Bd dense [nH][Na], Cd dense [Na][Na]; all pointers on the device.
+struct ArrowDev {
+    int64_t nH = 0;
+    int Na = 0;
+    const int32_t* ptr = nullptr;
+    const int32_t* col = nullptr;
+    const double* sval = nullptr;
+    const double* Bd = nullptr;
+    const double* Cd = nullptr;
+};
+// A matrix given as up to three column blocks side by side: column a of the
+// whole is column (a - offset) of block u, block u row-major with row stride ld[u].
+struct ColBlocks {
+    const double* p[3] = {nullptr, nullptr, nullptr};
+    int ld[3] = {0, 0, 0};
+    int w[3] = {0, 0, 0};
+    int nblk = 0;
+    __host__ __device__ int ncols() const { return w[0] + (nblk > 1 ? w[1] : 0) + (nblk > 2 ? w[2] : 0); }
+    static ColBlocks one(const double* a, int ld, int w) {
+        ColBlocks c;
+        c.p[0] = a;
+        c.ld[0] = ld;
+        c.w[0] = w;
+        c.nblk = 1;
+        return c;
+    }
+    void add(const double* a, int ldv, int wv) {
+        p[nblk] = a;
+        ld[nblk] = ldv;
+        w[nblk] = wv;
+        ++nblk;
+    }
+};
+// Y = F X for X, Y [m][w]; partial: gram_tiles_partial_size(nH, Na, w) doubles,
+// G: Na*w doubles of scratch
+void launch_arrow_apply(const ArrowDev& F, int w, const double* X, double* Y, double* partial, double* G,
+                        cudaStream_t s);
+// G[a][b] = sum_{i<m} L(i,a) R(i,b) (deterministic); partial scratch of
+// gram_tiles_partial_size(m, ncols(L), ncols(R)) doubles
+int64_t gram_tiles_partial_size(int64_t m, int La, int Rb);
+void launch_gram_tiles(int64_t m, const ColBlocks& L, const ColBlocks& R, double* partial, double* G,
+                       cudaStream_t s);
+// Y[i][j] = alpha sum_a S(i,a) C[a][j] + beta Y[i][j], C row-major [ncols(S)][kout]
+void launch_cols_mult(int64_t m, const ColBlocks& S, const double* C, int kout, double alpha, double beta,
+                      double* Y, cudaStream_t s);
+// R = AX - BX diag(theta) for [m][k] arrays (theta on the device)
+void launch_eig_resid(int64_t m, int k, const double* AX, const double* BX, const double* theta, double* R,
+                      cudaStream_t s);
+// columns of A1, A2, A3 ([m][k], any may be null) scaled by 1/sqrt(nrm[j])
+void launch_inv_sqrt_scale(int64_t m, int k, const double* nrm, double* A1, double* A2, double* A3,
+                           cudaStream_t s);
+// T[i] = 1 / (A_ii - sigma B_ii), diag_slot[i] = CSR slot of (i, i) in the coarse block
+void launch_eig_precond(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, double sigma, double* T,
+                        cudaStream_t s);
+
+// Fused single right-hand-side PCG (Poisson): device state of one solve, in
+// FP64 (Pcg1) or FP32 (Pcg1f, the inner solver of the mixed-precision mode).
+template <typename T>
+struct Pcg1T {
     int64_t n;
     const int32_t* rowptr;
     const int32_t* col;
-    const double* val;
-    const double* dinv;
-    double *x, *r, *z, *p, *q;
-    double *part_pq, *part_rz, *part_rr;  // [pcg1_blocks()] per-block partial sums
-    double* scal;                          // [0],[1] rz (by iteration parity), [2] ||b||^2, [3] r.r
-    int* active;                           // cleared when ||r||^2 <= tol2 ||b||^2
+    const T* val;
+    const T* dinv;
+    T *x, *r, *z, *p, *q;
+    T *part_pq, *part_rz, *part_rr;  // [pcg1_blocks()] per-block partial sums
+    T* scal;                          // [0],[1] rz (by iteration parity), [2] ||b||^2, [3] r.r
+    int* active;                      // cleared when ||r||^2 <= tol2 ||b||^2
     int* breakdown;
     int* iters;
-    double tol2;
+    T tol2;
+    // optional two-level preconditioner z = D^-1 r + I K_H^-1 I^T r
+    int two_level = 0;
+    int64_t nH = 0;
+    Pieces tpc;                      // I^T rows (coarse) split into balanced pieces
+    const int32_t* trow = nullptr;   // I^T entries: fine row and weight
+    const T* tval = nullptr;
+    T* cpart = nullptr;              // [tpc.npieces] piece sums of I^T r
+    const int32_t* icol = nullptr;   // I as ELL [n][4]
+    const T* ival = nullptr;
+    const T* khinv = nullptr;        // dense K_H^-1 [nH][nH]
+    T* cvec = nullptr;               // [nH]
+    T* yvec = nullptr;               // [nH]
 };
+using Pcg1 = Pcg1T<double>;
+using Pcg1f = Pcg1T<float>;
 int pcg1_blocks();
-// one PCG iteration (3 kernels); par = iteration parity (selects the rz slot)
+// one PCG iteration (3 kernels, 7 with the two-level preconditioner);
+// par = iteration parity (selects the rz slot)
 void launch_pcg1_iteration(const Pcg1& s, int par, int lanes_per_row, cudaStream_t st);
+void launch_pcg1_iteration(const Pcg1f& s, int par, int lanes_per_row, cudaStream_t st);
+// z = D^-1 r + I K_H^-1 I^T r and partial sums of r.z (two-level only)
+void launch_pcg1_coarse_correction(const Pcg1& s, cudaStream_t st);
+void launch_pcg1_coarse_correction(const Pcg1f& s, cudaStream_t st);
+// FP32 inner solve start from e = 0 (p = z, x = 0, partial sums of r.z, r.r)
+void launch_pcg1_start(const Pcg1f& s, cudaStream_t st);
+void launch_cast_to_f32(int64_t n, const double* a, float* b, cudaStream_t st);
+void launch_add_f32(int64_t n, const float* e, double* x, cudaStream_t st);
 
 // Anderson: given F^0..F^m (pointers), w, compute the k x k matrix
 // A[a][b] = (F^m - F^a, F^m - F^b) and rhs[a] = (F^m - F^a, F^m), k = m;

@@ -499,6 +499,91 @@ __global__ void k_nodal_to_dof(int64_t n, const int32_t* dof_node, const double*
     x[i] = V[dof_node[i]];
 }
 
+// out[e][q] = sum_c A_c(x_q) U_c(x_q) (both from dof values [n][N]); used by
+// the adjoint contraction of the linear problems
+template <int ORDER>
+__global__ void __launch_bounds__(128) k_pair_density(Mesh m, const int32_t* dof_of_node, const double* A,
+                                                      const double* U, int N, double* out) {
+    constexpr int NL = El<ORDER>::NLOC, NQ = El<ORDER>::NQ;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.ne) return;
+    int d[NL];
+    for (int a = 0; a < NL; ++a) d[a] = dof_of_node[m.elem[e * NL + a]];
+    double prod[NQ];
+    for (int q = 0; q < NQ; ++q) prod[q] = 0.0;
+    for (int c = 0; c < N; ++c) {
+        double av[NL], uv[NL];
+        for (int a = 0; a < NL; ++a) {
+            av[a] = d[a] >= 0 ? A[(int64_t)d[a] * N + c] : 0.0;
+            uv[a] = d[a] >= 0 ? U[(int64_t)d[a] * N + c] : 0.0;
+        }
+        for (int q = 0; q < NQ; ++q) {
+            double aq = 0.0, uq = 0.0;
+            for (int a = 0; a < NL; ++a) {
+                aq += T_phi<ORDER>(q, a) * av[a];
+                uq += T_phi<ORDER>(q, a) * uv[a];
+            }
+            prod[q] += aq * uq;
+        }
+    }
+    for (int q = 0; q < NQ; ++q) out[e * NQ + q] = prod[q];
+}
+
+// partial[block][4*j + c] = sum over the block's quadrature points of
+// W_eq w_eq dV_ext/dp_(k0+j, c)(x_q), c = x, y, z, Z, for nuclei k0..k0+7
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_vext_grad(Mesh m, Nuclei nuc, int k0, const double* Wq, const double* w,
+                                                  double* partial) {
+    constexpr int NQ = El<ORDER>::NQ;
+    const int nk = min(8, nuc.count - k0);
+    double acc[32];
+    for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m.ne; e += (int64_t)gridDim.x * blockDim.x) {
+        double v[4][3];
+        load_vertices(m, e, v);
+        for (int q = 0; q < NQ; ++q) {
+            const double ww = Wq[e * NQ + q] * w[e * NQ + q];
+            if (ww == 0.0) continue;
+            double x[3];
+            for (int dd = 0; dd < 3; ++dd)
+                x[dd] = T_bary<ORDER>(q, 0) * v[0][dd] + T_bary<ORDER>(q, 1) * v[1][dd] +
+                        T_bary<ORDER>(q, 2) * v[2][dd] + T_bary<ORDER>(q, 3) * v[3][dd];
+            for (int j = 0; j < nk; ++j) {
+                const int k = k0 + j;
+                const double dx = x[0] - nuc.R[3 * k], dy = x[1] - nuc.R[3 * k + 1], dz = x[2] - nuc.R[3 * k + 2];
+                double r2 = dx * dx + dy * dy + dz * dz;
+                if (nuc.potential == NAS_POT_SMOOTHED) r2 += nuc.smooth_a * nuc.smooth_a;
+                const double inv = 1.0 / sqrt(r2);
+                const double zi3 = nuc.Z[k] * inv * inv * inv;
+                // V = -Z r2^(-1/2): dV/dR = -Z (x - R) r2^(-3/2), dV/dZ = -r2^(-1/2)
+                acc[4 * j + 0] -= ww * zi3 * dx;
+                acc[4 * j + 1] -= ww * zi3 * dy;
+                acc[4 * j + 2] -= ww * zi3 * dz;
+                acc[4 * j + 3] -= ww * inv;
+            }
+        }
+    }
+    __shared__ double sh[256];
+    for (int j = 0; j < 4 * nk; ++j) {
+        sh[threadIdx.x] = acc[j];
+        __syncthreads();
+        for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+            if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 32 + j] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_reduce_grad(int nblocks, int nk4, const double* partial, double* out) {
+    int j = threadIdx.x;
+    if (j >= nk4) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * 32 + j];
+    out[j] = s;
+}
+
 // ------------------------------------------------------------------ launchers
 #define NAS_DISPATCH(m, KERNEL, ...)                                                 \
     do {                                                                             \
@@ -565,6 +650,26 @@ void launch_boundary_values(int64_t nb, const int32_t* bnd_node, const double* n
                                                        wB, V_nodal);
     NAS_CHECK_LAUNCH();
 }
+void launch_pair_density(const Mesh& m, const int32_t* dof_of_node, const double* A, const double* U, int N,
+                         double* out, cudaStream_t s) {
+    NAS_DISPATCH(m, k_pair_density, m, dof_of_node, A, U, N, out);
+}
+
+void launch_vext_grad(const Mesh& m, const Nuclei& nuc, const double* Wq, const double* w, double* partial,
+                      double* out, cudaStream_t s) {
+    const int nb = (int)std::min<int64_t>(kRedBlocks, (m.ne + 255) / 256);
+    for (int k0 = 0; k0 < nuc.count; k0 += 8) {
+        if (m.nloc == 4)
+            k_vext_grad<1><<<nb, 256, 0, s>>>(m, nuc, k0, Wq, w, partial);
+        else
+            k_vext_grad<2><<<nb, 256, 0, s>>>(m, nuc, k0, Wq, w, partial);
+        NAS_CHECK_LAUNCH();
+        const int nk4 = 4 * std::min(8, nuc.count - k0);
+        k_reduce_grad<<<1, 32, 0, s>>>(nb, nk4, partial, out + 4 * k0);
+        NAS_CHECK_LAUNCH();
+    }
+}
+
 void launch_nodal_to_dof(int64_t n, const int32_t* dof_node, const double* V, double* x, cudaStream_t s) {
     if (n <= 0) return;
     k_nodal_to_dof<<<grid_for(n, 256), 256, 0, s>>>(n, dof_node, V, x);

@@ -66,13 +66,23 @@ void launch_spmm(const Csr& A, int N, const double* X, double* Y, double alpha, 
 }
 
 // ------------------------------------------------------------------ ordered reductions
-// final pass: out[j] = sum_b partial[b][j] for j < width, b in order
+// final pass: out[j] = sum_b partial[b][j] for j < width.  One warp per
+// output: lane l sums b = l, l+32, ... in order, then a fixed shuffle tree, so
+// the order is fixed and the loads of a lane are independent (no serial chain
+// of nblocks dependent steps).
 __global__ void k_reduce_partials(int nblocks, int64_t width, const double* partial, double* out) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= width) return;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (j >= width) return;  // warp-uniform
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * width + j];
-    out[j] = s;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * width + j];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) out[j] = s;
+}
+
+static void reduce_partials(int nblocks, int64_t width, const double* partial, double* out, cudaStream_t s) {
+    k_reduce_partials<<<grid_for(width * 32, 256), 256, 0, s>>>(nblocks, width, partial, out);
+    NAS_CHECK_LAUNCH();
 }
 
 int64_t reduce_partial_size(int64_t width) { return (int64_t)kRedBlocks * width; }
@@ -124,8 +134,7 @@ void launch_coldots(int64_t n, int N, int npairs, const double* const* X, const 
     k_coldots<<<nb, 256, 0, s>>>(n, N, npairs, a, w, partial);
     NAS_CHECK_LAUNCH();
     int64_t width = (int64_t)npairs * N;
-    k_reduce_partials<<<grid_for(width, 128), 128, 0, s>>>(nb, width, partial, out);
-    NAS_CHECK_LAUNCH();
+    reduce_partials(nb, width, partial, out, s);
 }
 
 // ------------------------------------------------------------------ PCG scalars and updates
@@ -328,26 +337,48 @@ void launch_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y, do
     size_t sm = sizeof(double) * 32 * (Nx + Ny);
     k_gram<<<nb, 256, sm, s>>>(n, Nx, X, Ny, Y, partial);
     NAS_CHECK_LAUNCH();
-    k_reduce_partials<<<grid_for(W, 128), 128, 0, s>>>(nb, W, partial, G);
-    NAS_CHECK_LAUNCH();
+    reduce_partials(nb, W, partial, G, s);
 }
 
 // ------------------------------------------------------------------ transfer products
-__global__ void k_transpose_apply(int64_t nH, const int32_t* tptr, const int32_t* trow, const double* tval,
-                                  int N, const double* Y, double* out) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t a = t / N;
-    if (a >= nH) return;
-    int c = (int)(t - a * N);
-    double s = 0.0;
-    for (int p = tptr[a]; p < tptr[a + 1]; ++p) s += tval[p] * Y[(int64_t)trow[p] * N + c];
-    out[t] = s;
+// one warp per output (a, c): lanes stride over the ~n/nH fine entries of
+// coarse row a, then a fixed-order shuffle sum
+// I^T Y, stage 1: one warp per piece of an I^T row, lane c holds column c
+// (columns beyond 32 in further passes), entries in list order
+__global__ void k_transpose_pieces(Pieces pc, const int32_t* trow, const double* tval, int N, const double* Y,
+                                   double* partial) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (q >= pc.npieces) return;  // warp-uniform
+    const int64_t b = pc.piece_start[q], e = pc.piece_start[q + 1];
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        const int c = c0 + lane;
+        double acc = 0.0;
+        if (c < N)
+            for (int64_t p = b; p < e; ++p) acc += tval[p] * Y[(int64_t)trow[p] * N + c];
+        if (c < N) partial[q * N + c] = acc;
+    }
 }
 
-void launch_transpose_apply(int64_t nH, const int32_t* tptr, const int32_t* trow, const double* tval,
-                            int N, const double* Y, double* out, cudaStream_t s) {
-    if (nH <= 0) return;
-    k_transpose_apply<<<grid_for(nH * N, 128), 128, 0, s>>>(nH, tptr, trow, tval, N, Y, out);
+// stage 2 of every piece reduction: out[a][c] = sum of the pieces of segment a, in order
+__global__ void k_piece_sum(int64_t nseg, const int32_t* seg_piece, int N, const double* partial, double* out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nseg * N) return;
+    const int64_t a = t / N;
+    const int c = (int)(t - a * N);
+    double acc = 0.0;
+    for (int q = seg_piece[a]; q < seg_piece[a + 1]; ++q) acc += partial[(int64_t)q * N + c];
+    out[t] = acc;
+}
+
+void launch_transpose_apply(const Pieces& pc, const int32_t* trow, const double* tval, int N, const double* Y,
+                            double* partial, double* out, cudaStream_t s) {
+    if (pc.nseg <= 0 || N <= 0) return;
+    if (pc.npieces > 0) {
+        k_transpose_pieces<<<grid_for(pc.npieces * 32, 256), 256, 0, s>>>(pc, trow, tval, N, Y, partial);
+        NAS_CHECK_LAUNCH();
+    }
+    k_piece_sum<<<grid_for(pc.nseg * N, 256), 256, 0, s>>>(pc.nseg, pc.seg_piece, N, partial, out);
     NAS_CHECK_LAUNCH();
 }
 
@@ -393,23 +424,31 @@ void launch_galerkin1(int64_t nw, const int64_t* ptr, const int32_t* con, const 
     NAS_CHECK_LAUNCH();
 }
 
-__global__ void k_galerkin2(int64_t nh, const int64_t* ptr, const int32_t* con, const double* W,
-                            const int32_t* wrow, const double* ival, double* H) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nh) return;
+// one warp per piece of a coarse slot's gather list: lanes stride over the
+// piece, then a fixed-order shuffle sum; k_piece_sum adds a slot's pieces
+__global__ void k_galerkin2_pieces(Pieces pc, const int32_t* con, const double* W, const int32_t* wrow,
+                                   const double* ival, double* partial) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (q >= pc.npieces) return;  // warp-uniform
     double acc = 0.0;
-    for (int64_t k = ptr[t]; k < ptr[t + 1]; ++k) {
-        int r = con[k];
-        int s = r >> 2;
-        acc += ival[(int64_t)wrow[s] * 4 + (r & 3)] * W[s];
+    for (int64_t k = pc.piece_start[q] + lane; k < pc.piece_start[q + 1]; k += 32) {
+        const int r = con[k];
+        const int sl = r >> 2;
+        acc += ival[(int64_t)wrow[sl] * 4 + (r & 3)] * W[sl];
     }
-    H[t] = acc;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) partial[q] = acc;
 }
 
-void launch_galerkin2(int64_t nh, const int64_t* ptr, const int32_t* con, const double* W,
-                      const int32_t* wrow, const double* ival, double* H, cudaStream_t s) {
-    if (nh <= 0) return;
-    k_galerkin2<<<grid_for(nh, 256), 256, 0, s>>>(nh, ptr, con, W, wrow, ival, H);
+void launch_galerkin2(const Pieces& pc, const int32_t* con, const double* W, const int32_t* wrow,
+                      const double* ival, double* partial, double* H, cudaStream_t s) {
+    if (pc.nseg <= 0) return;
+    if (pc.npieces > 0) {
+        k_galerkin2_pieces<<<grid_for(pc.npieces * 32, 256), 256, 0, s>>>(pc, con, W, wrow, ival, partial);
+        NAS_CHECK_LAUNCH();
+    }
+    k_piece_sum<<<grid_for(pc.nseg, 256), 256, 0, s>>>(pc.nseg, pc.seg_piece, 1, partial, H);
     NAS_CHECK_LAUNCH();
 }
 
@@ -457,8 +496,7 @@ void launch_anderson_dots(int64_t cnt, int m, const double* const* F, const doub
     k_anderson_dots<<<nb, 256, 0, s>>>(cnt, m, f, w, partial);
     NAS_CHECK_LAUNCH();
     int K = m * m + m;
-    k_reduce_partials<<<1, 128, 0, s>>>(nb, K, partial, out);
-    NAS_CHECK_LAUNCH();
+    reduce_partials(nb, K, partial, out, s);
 }
 
 struct MixArgs {

@@ -4,12 +4,18 @@
 //   k_pcg1_update: alpha = rz / (sum p.q); x += alpha p; r -= alpha q;
 //                  z = D^-1 r; per-block partial sums of r.z and r.r
 //   k_pcg1_dir   : beta = rz_new / rz; p = z + beta p; convergence test
+// With the two-level preconditioner z = D^-1 r + I K_H^-1 I^T r (I the
+// nonnested transfer of the method, K_H = I^T K I), z and r.z are computed by
+// three more kernels between update and dir: restriction I^T r, the dense
+// coarse solve with the precomputed K_H^-1, and prolongation.
 // The scalars are not reduced by a separate launch: every block reduces the
 // fixed-size partial array itself, in the same fixed order, so all blocks
 // see bit-identical scalars and the result is deterministic.  The grid is a
 // fixed number of blocks striding over the rows.  Kernels return at once
 // when the solve is no longer active, so a captured graph of several
 // iterations can run past convergence at negligible cost.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace nas {
@@ -18,8 +24,9 @@ static const int kPcgBlocks = 1216;  // 8 resident blocks x 152 SMs: one full wa
 static const int kPcgThreads = 256;
 
 // Sum of part[0..G) in a fixed order, identical in every block.
-__device__ __forceinline__ double block_sum_partials(const double* part, int G, double* sh) {
-    double s = 0.0;
+template <typename T>
+__device__ __forceinline__ T block_sum_partials(const T* part, int G, T* sh) {
+    T s = 0;
     for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[b];
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -27,12 +34,13 @@ __device__ __forceinline__ double block_sum_partials(const double* part, int G, 
         if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
         __syncthreads();
     }
-    double r = sh[0];
+    T r = sh[0];
     __syncthreads();
     return r;
 }
 
-__device__ __forceinline__ void block_store_sum(double v, double* sh, double* out) {
+template <typename T>
+__device__ __forceinline__ void block_store_sum(T v, T* sh, T* out) {
     sh[threadIdx.x] = v;
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
@@ -42,21 +50,21 @@ __device__ __forceinline__ void block_store_sum(double v, double* sh, double* ou
     if (threadIdx.x == 0) *out = sh[0];
 }
 
-template <int LPR>
-__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_spmv(Pcg1 s) {
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_spmv(Pcg1T<T> s) {
     if (!*s.active) return;
-    __shared__ double sh[kPcgThreads];
+    __shared__ T sh[kPcgThreads];
     const int lane = threadIdx.x % LPR;
     // warp-uniform loop: every lane of a warp runs the same trip count, so the
     // full-mask shuffles below are always executed by all 32 lanes
     const int64_t rows_per_warp = 32 / LPR;
     const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int64_t warp_stride = (int64_t)gridDim.x * (blockDim.x / 32) * rows_per_warp;
-    double dot = 0.0;
+    T dot = 0;
     for (int64_t base = warp_id * rows_per_warp; base < s.n; base += warp_stride) {
         const int64_t row = base + (threadIdx.x % 32) / LPR;
         const bool valid = row < s.n;
-        double acc = 0.0;
+        T acc = 0;
         if (valid) {
             const int p1 = s.rowptr[row + 1];
             for (int p = s.rowptr[row] + lane; p < p1; p += LPR) acc += s.val[p] * s.p[s.col[p]];
@@ -71,38 +79,103 @@ __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_spmv(Pcg1 s) {
     block_store_sum(dot, sh, s.part_pq + blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_update(Pcg1 s, int par) {
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_update(Pcg1T<T> s, int par) {
     if (!*s.active) return;
-    __shared__ double sh[kPcgThreads];
-    const double pq = block_sum_partials(s.part_pq, gridDim.x, sh);
-    const double rz = s.scal[par];
+    __shared__ T sh[kPcgThreads];
+    const T pq = block_sum_partials(s.part_pq, gridDim.x, sh);
+    const T rz = s.scal[par];
     if (!(pq > 0.0) || !isfinite(pq)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) *s.breakdown = 1;
         return;
     }
-    const double alpha = rz / pq;
-    double srz = 0.0, srr = 0.0;
+    const T alpha = rz / pq;
+    T srz = 0, srr = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x) {
         s.x[i] += alpha * s.p[i];
-        const double r = s.r[i] - alpha * s.q[i];
+        const T r = s.r[i] - alpha * s.q[i];
         s.r[i] = r;
-        const double z = s.dinv[i] * r;
-        s.z[i] = z;
-        srz += r * z;
         srr += r * r;
+        if (!s.two_level) {  // with the coarse correction, z and r.z come from k_pcg1_prolong
+            const T z = s.dinv[i] * r;
+            s.z[i] = z;
+            srz += r * z;
+        }
     }
-    block_store_sum(srz, sh, s.part_rz + blockIdx.x);
+    if (!s.two_level) block_store_sum(srz, sh, s.part_rz + blockIdx.x);
     __syncthreads();
     block_store_sum(srr, sh, s.part_rr + blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_dir(Pcg1 s, int par) {
+// ---- two-level preconditioner z = D^-1 r + I K_H^-1 I^T r (coarse space of the method)
+// c = I^T r in two stages: one warp per balanced piece of an I^T row (lanes
+// stride, fixed-order shuffle sum), then each coarse row adds its pieces in order
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads) k_pcg1_restrict(Pcg1T<T> s) {
     if (!*s.active || *s.breakdown) return;
-    __shared__ double sh[kPcgThreads];
-    const double rz_new = block_sum_partials(s.part_rz, gridDim.x, sh);
-    const double rr = block_sum_partials(s.part_rr, gridDim.x, sh);
-    const double rz = s.scal[par];
-    const double beta = rz != 0.0 ? rz_new / rz : 0.0;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (q >= s.tpc.npieces) return;  // warp-uniform
+    T acc = 0;
+    for (int64_t p = s.tpc.piece_start[q] + lane; p < s.tpc.piece_start[q + 1]; p += 32)
+        acc += s.tval[p] * s.r[s.trow[p]];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) s.cpart[q] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads) k_pcg1_restrict_sum(Pcg1T<T> s) {
+    if (!*s.active || *s.breakdown) return;
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.nH) return;
+    T acc = 0;
+    for (int q = s.tpc.seg_piece[a]; q < s.tpc.seg_piece[a + 1]; ++q) acc += s.cpart[q];
+    s.cvec[a] = acc;
+}
+
+// y = K_H^-1 c (dense row-major inverse): one warp per row
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads) k_pcg1_coarse(Pcg1T<T> s) {
+    if (!*s.active || *s.breakdown) return;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t a = warp; a < s.nH; a += nwarps) {
+        const T* row = s.khinv + a * s.nH;
+        T acc = 0;
+        for (int64_t b = lane; b < s.nH; b += 32) acc += row[b] * s.cvec[b];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) s.yvec[a] = acc;
+    }
+}
+
+// z = D^-1 r + I y, with per-block partial sums of r.z
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_prolong(Pcg1T<T> s) {
+    if (!*s.active || *s.breakdown) return;
+    __shared__ T sh[kPcgThreads];
+    T srz = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T r = s.r[i];
+        T z = s.dinv[i] * r;
+        for (int k = 0; k < 4; ++k) {
+            const int a = s.icol[4 * i + k];
+            if (a >= 0) z += s.ival[4 * i + k] * s.yvec[a];
+        }
+        s.z[i] = z;
+        srz += r * z;
+    }
+    block_store_sum(srz, sh, s.part_rz + blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_dir(Pcg1T<T> s, int par) {
+    if (!*s.active || *s.breakdown) return;
+    __shared__ T sh[kPcgThreads];
+    const T rz_new = block_sum_partials(s.part_rz, gridDim.x, sh);
+    const T rr = block_sum_partials(s.part_rr, gridDim.x, sh);
+    const T rz = s.scal[par];
+    const T beta = rz != T(0) ? rz_new / rz : T(0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x)
         s.p[i] = s.z[i] + beta * s.p[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -116,19 +189,96 @@ __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_dir(Pcg1 s, int par) {
 
 int pcg1_blocks() { return kPcgBlocks; }
 
-void launch_pcg1_iteration(const Pcg1& s, int par, int lpr, cudaStream_t st) {
+template <typename T>
+static void pcg1_coarse_correction(const Pcg1T<T>& s, cudaStream_t st) {
+    const int warps_per_block = kPcgThreads / 32;
+    const int gb = (int)std::min<int64_t>(4 * kPcgBlocks, (s.nH + warps_per_block - 1) / warps_per_block);
+    if (s.tpc.npieces > 0) {
+        k_pcg1_restrict<T><<<(int)((s.tpc.npieces + warps_per_block - 1) / warps_per_block), kPcgThreads, 0, st>>>(s);
+        NAS_CHECK_LAUNCH();
+    }
+    k_pcg1_restrict_sum<T><<<(int)((s.nH + kPcgThreads - 1) / kPcgThreads), kPcgThreads, 0, st>>>(s);
+    NAS_CHECK_LAUNCH();
+    k_pcg1_coarse<T><<<gb, kPcgThreads, 0, st>>>(s);
+    NAS_CHECK_LAUNCH();
+    k_pcg1_prolong<T><<<kPcgBlocks, kPcgThreads, 0, st>>>(s);
+    NAS_CHECK_LAUNCH();
+}
+
+template <typename T>
+static void pcg1_iteration(const Pcg1T<T>& s, int par, int lpr, cudaStream_t st) {
     switch (lpr) {
-        case 1: k_pcg1_spmv<1><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
-        case 2: k_pcg1_spmv<2><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
-        case 4: k_pcg1_spmv<4><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
-        case 8: k_pcg1_spmv<8><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
-        case 16: k_pcg1_spmv<16><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
-        default: k_pcg1_spmv<32><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
+        case 1: k_pcg1_spmv<T, 1><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
+        case 2: k_pcg1_spmv<T, 2><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
+        case 4: k_pcg1_spmv<T, 4><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
+        case 8: k_pcg1_spmv<T, 8><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
+        case 16: k_pcg1_spmv<T, 16><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
+        default: k_pcg1_spmv<T, 32><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
     }
     NAS_CHECK_LAUNCH();
-    k_pcg1_update<<<kPcgBlocks, kPcgThreads, 0, st>>>(s, par);
+    k_pcg1_update<T><<<kPcgBlocks, kPcgThreads, 0, st>>>(s, par);
     NAS_CHECK_LAUNCH();
-    k_pcg1_dir<<<kPcgBlocks, kPcgThreads, 0, st>>>(s, par);
+    if (s.two_level) pcg1_coarse_correction(s, st);
+    k_pcg1_dir<T><<<kPcgBlocks, kPcgThreads, 0, st>>>(s, par);
+    NAS_CHECK_LAUNCH();
+}
+
+void launch_pcg1_iteration(const Pcg1& s, int par, int lpr, cudaStream_t st) { pcg1_iteration(s, par, lpr, st); }
+void launch_pcg1_iteration(const Pcg1f& s, int par, int lpr, cudaStream_t st) { pcg1_iteration(s, par, lpr, st); }
+void launch_pcg1_coarse_correction(const Pcg1& s, cudaStream_t st) { pcg1_coarse_correction(s, st); }
+void launch_pcg1_coarse_correction(const Pcg1f& s, cudaStream_t st) { pcg1_coarse_correction(s, st); }
+
+// ---- mixed precision helpers
+// start of an inner solve from e = 0: r given, z = M^-1 r (Jacobi part; the
+// coarse part, if any, was added by the coarse-correction kernels), p = z,
+// x = 0, partial sums of r.z (Jacobi only) and r.r
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_start(Pcg1T<T> s) {
+    __shared__ T sh[kPcgThreads];
+    T srz = 0, srr = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T r = s.r[i];
+        T z;
+        if (s.two_level) {
+            z = s.z[i];
+        } else {
+            z = s.dinv[i] * r;
+            s.z[i] = z;
+            srz += r * z;
+        }
+        s.p[i] = z;
+        s.x[i] = 0;
+        srr += r * r;
+    }
+    if (!s.two_level) block_store_sum(srz, sh, s.part_rz + blockIdx.x);
+    __syncthreads();
+    block_store_sum(srr, sh, s.part_rr + blockIdx.x);
+}
+
+void launch_pcg1_start(const Pcg1f& s, cudaStream_t st) {
+    k_pcg1_start<float><<<kPcgBlocks, kPcgThreads, 0, st>>>(s);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_cast_to_f32(int64_t n, const double* a, float* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_add_f32(int64_t n, const float* e, double* x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += (double)e[i];
+}
+
+void launch_cast_to_f32(int64_t n, const double* a, float* b, cudaStream_t st) {
+    if (n <= 0) return;
+    k_cast_to_f32<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
+    NAS_CHECK_LAUNCH();
+}
+
+void launch_add_f32(int64_t n, const float* e, double* x, cudaStream_t st) {
+    if (n <= 0) return;
+    k_add_f32<<<grid_for(n, 256), 256, 0, st>>>(n, e, x);
     NAS_CHECK_LAUNCH();
 }
 

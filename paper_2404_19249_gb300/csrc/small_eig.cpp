@@ -47,7 +47,7 @@ static void reduce_standard(int m, const std::vector<double>& L, const double* A
     auto a = [&](int i, int j) { return i >= j ? A[(size_t)i * m + j] : A[(size_t)j * m + i]; };
     // Y = L^{-1} A, stored transposed: Yt[c][i] = Y[i][c]
     std::vector<double> Yt((size_t)m * m);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (m > 128)
     for (int c = 0; c < m; ++c) {
         double* y = &Yt[(size_t)c * m];
         for (int i = 0; i < m; ++i) {
@@ -60,7 +60,7 @@ static void reduce_standard(int m, const std::vector<double>& L, const double* A
     // C = L^{-1} Y^T ; Y^T = (L^{-1}A)^T = A L^{-T}; column c of Y^T is row c of Y = Yt[:, c]
     // C[:,c] solves L z = (Y^T)[:,c] = Y[c,:] = Yt[*][c]... use Y^T[i][c] = Y[c][i] = Yt[i][c]
     C.assign((size_t)m * m, 0.0);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (m > 128)
     for (int c = 0; c < m; ++c) {
         std::vector<double> z(m);
         for (int i = 0; i < m; ++i) {
@@ -151,45 +151,43 @@ static int sturm_count(int m, const std::vector<double>& d, const std::vector<do
 
 // Solve (T - lam I) x = b for tridiagonal T by Gaussian elimination with
 // partial pivoting (x overwrites b).
+struct TriWork {
+    std::vector<double> a, c, u2;
+};
+
 static void tri_solve(int m, const std::vector<double>& d, const std::vector<double>& e, double lam,
-                      double pert, std::vector<double>& b) {
-    std::vector<double> a(m), c(m), u2(m, 0.0);
-    std::vector<double> dd(m);
-    for (int i = 0; i < m; ++i) dd[i] = d[i] - lam;
-    // rows: sub e[i-1], diag dd[i], super e[i]
-    std::vector<double> sub(m, 0.0), sup(m, 0.0);
-    for (int i = 0; i + 1 < m; ++i) {
-        sup[i] = e[i];
-        sub[i + 1] = e[i];
-    }
-    // U has diag a, super c, super2 u2
-    std::vector<double> diag(dd), up(sup);
-    std::vector<int> piv(m, 0);
+                      double pert, std::vector<double>& b, TriWork& w) {
+    // U (after elimination with row swaps) has diagonal a, super-diagonal c and
+    // second super-diagonal u2
+    w.a.resize(m);
+    w.c.resize(m);
+    w.u2.assign(m, 0.0);
+    double* a = w.a.data();
+    double* c = w.c.data();
+    double* u2 = w.u2.data();
     for (int i = 0; i < m; ++i) {
-        a[i] = diag[i];
-        c[i] = up[i];
+        a[i] = d[i] - lam;
+        c[i] = (i + 1 < m) ? e[i] : 0.0;
     }
     for (int i = 0; i + 1 < m; ++i) {
-        double s = sub[i + 1];
-        if (std::fabs(a[i]) >= std::fabs(s)) {
+        const double sub = e[i];  // entry (i+1, i)
+        if (std::fabs(a[i]) >= std::fabs(sub)) {
             if (a[i] == 0.0) a[i] = pert;
-            double l = s / a[i];
+            const double l = sub / a[i];
             a[i + 1] -= l * c[i];
             b[i + 1] -= l * b[i];
-            piv[i] = 0;
         } else {
             // swap rows i and i+1
-            double l = a[i] / s;
-            double ai1 = a[i + 1], ci1 = (i + 1 < m - 1) ? c[i + 1] : 0.0;
-            a[i] = s;
-            double ci = c[i];
+            const double l = a[i] / sub;
+            const double ai1 = a[i + 1], ci1 = (i + 1 < m - 1) ? c[i + 1] : 0.0;
+            a[i] = sub;
+            const double ci = c[i];
             c[i] = ai1;
             u2[i] = ci1;
             a[i + 1] = ci - l * ai1;
             if (i + 1 < m - 1) c[i + 1] = -l * ci1;
             std::swap(b[i], b[i + 1]);
             b[i + 1] -= l * b[i];
-            piv[i] = 1;
         }
     }
     if (a[m - 1] == 0.0) a[m - 1] = pert;
@@ -197,6 +195,63 @@ static void tri_solve(int m, const std::vector<double>& d, const std::vector<dou
     b[m - 1] /= a[m - 1];
     if (m >= 2) b[m - 2] = (b[m - 2] - c[m - 2] * b[m - 1]) / a[m - 2];
     for (int i = m - 3; i >= 0; --i) b[i] = (b[i] - c[i] * b[i + 1] - u2[i] * b[i + 2]) / a[i];
+}
+
+// sqrt(f^2 + g^2), with the scaled library routine only outside the range
+// where the squares can neither overflow nor underflow
+static inline double fast_hypot(double f, double g) {
+    const double a = std::fmax(std::fabs(f), std::fabs(g));
+    if (a > 1e-140 && a < 1e140) return std::sqrt(f * f + g * g);
+    return std::hypot(f, g);
+}
+
+static bool tridiag_eigvals(int m, const std::vector<double>& d_in, const std::vector<double>& e_in,
+                            std::vector<double>& w) {
+    std::vector<double> d(d_in.begin(), d_in.begin() + m), e(m, 0.0);
+    for (int i = 0; i + 1 < m; ++i) e[i] = e_in[i];
+    const double eps = std::numeric_limits<double>::epsilon();
+    for (int l = 0; l < m; ++l) {
+        for (int sweep = 0;; ++sweep) {
+            // end of the unreduced block that starts at l
+            int mm = l;
+            while (mm + 1 < m && std::fabs(e[mm]) > eps * (std::fabs(d[mm]) + std::fabs(d[mm + 1]))) ++mm;
+            if (mm == l) break;
+            if (sweep >= 60) return false;
+            // shift: eigenvalue of the leading 2 x 2 corner closer to d[l]
+            const double theta = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            const double rho = fast_hypot(theta, 1.0);
+            const double shift = d[l] - e[l] / (theta + std::copysign(rho, theta));
+            // implicit shifted QL step on rows l..mm, bottom to top
+            double g = d[mm] - shift;
+            double c = 1.0, sn = 1.0, p = 0.0;
+            bool split = false;
+            for (int i = mm - 1; i >= l; --i) {
+                const double f = sn * e[i], b = c * e[i];
+                const double r = fast_hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {  // the block splits at i+1: undo the pending shift there
+                    d[i + 1] -= p;
+                    e[mm] = 0.0;
+                    split = true;
+                    break;
+                }
+                sn = f / r;
+                c = g / r;
+                const double h = d[i + 1] - p;
+                const double t = (d[i] - h) * sn + 2.0 * c * b;
+                p = sn * t;
+                d[i + 1] = h + p;
+                g = c * t - b;
+            }
+            if (split) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[mm] = 0.0;
+        }
+    }
+    std::sort(d.begin(), d.end());
+    w.swap(d);
+    return true;
 }
 
 int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, double* U) {
@@ -221,8 +276,18 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
     lo -= 2 * eps * tnorm + 1e-300;
     hi += 2 * eps * tnorm + 1e-300;
     std::vector<double> w(k);
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int i = 0; i < k; ++i) {
+    // many eigenvalues of a small matrix: QL (no serial chain of divisions per
+    // bisection step); a few of a large one: bisection on the Sturm count
+    bool have_w = false;
+    if (m <= 512 && 4 * k >= m) {
+        std::vector<double> all;
+        if (tridiag_eigvals(m, d, e, all)) {
+            for (int i = 0; i < k; ++i) w[i] = all[i];
+            have_w = true;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1) if (!have_w)
+    for (int i = 0; i < (have_w ? 0 : k); ++i) {
         double a = lo, b = hi;
         for (int it = 0; it < 200; ++it) {
             double mid = 0.5 * (a + b);
@@ -240,13 +305,14 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
     const double pert = eps * tnorm + 1e-300;
     const double clus = 1e-3 * tnorm;
     int start = 0;
+    std::vector<double> x(m);
+    TriWork tw;
     for (int i = 0; i < k; ++i) {
         if (i > 0 && std::fabs(w[i] - w[i - 1]) > clus) start = i;
-        std::vector<double> x(m);
         for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * std::sin(0.7 * r + 1.3 * i);
         double shift = w[i];
         for (int it = 0; it < 4; ++it) {
-            tri_solve(m, d, e, shift, pert, x);
+            tri_solve(m, d, e, shift, pert, x, tw);
             for (int j = start; j < i; ++j) {
                 const double* zj = &Z[(size_t)j * m];
                 double s = 0.0;
@@ -265,7 +331,7 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
         std::copy(x.begin(), x.end(), Z.begin() + (size_t)i * m);
     }
     // back-transform: y = Q z = H_0 ... H_{m-3} z, then U = L^{-T} y
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if ((int64_t)k * m * m > 2000000)
     for (int i = 0; i < k; ++i) {
         double* z = &Z[(size_t)i * m];
         for (int j = m - 3; j >= 0; --j) {
@@ -283,16 +349,17 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
             z[r] = s / L[(size_t)r * m + r];
         }
     }
-    // Rayleigh quotients refine the eigenvalues: lambda = u^T A u (u is B-normalised)
-    auto a = [&](int r, int c) { return r >= c ? A[(size_t)r * m + c] : A[(size_t)c * m + r]; };
-#pragma omp parallel for schedule(dynamic, 1)
+    // Rayleigh quotients refine the eigenvalues: lambda = u^T A u (u is
+    // B-normalised), from the lower triangle of A: sum_r u_r (A_rr u_r + 2 sum_{c<r} A_rc u_c)
+#pragma omp parallel for schedule(dynamic, 1) if ((int64_t)k * m * m > 2000000)
     for (int i = 0; i < k; ++i) {
         const double* u = &Z[(size_t)i * m];
         double s = 0.0;
         for (int r = 0; r < m; ++r) {
+            const double* Ar = A + (size_t)r * m;
             double t = 0.0;
-            for (int c = 0; c < m; ++c) t += a(r, c) * u[c];
-            s += u[r] * t;
+            for (int c = 0; c < r; ++c) t += Ar[c] * u[c];
+            s += u[r] * (Ar[r] * u[r] + 2.0 * t);
         }
         lam[i] = s;
     }
@@ -306,6 +373,39 @@ int chol_factor(int m, double* A) {
     if (!cholesky(m, L)) return -1;
     std::copy(L.begin(), L.end(), A);
     return 0;
+}
+
+void chol_inverse(int m, const double* L, double* Inv) {
+    // U = L^T row-major, so that the backward solve reads contiguous rows
+    std::vector<double> U((size_t)m * m);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j <= i; ++j) U[(size_t)j * m + i] = L[(size_t)i * m + j];
+#pragma omp parallel
+    {
+        std::vector<double> y(m);
+#pragma omp for schedule(dynamic, 8)
+        for (int c = 0; c < m; ++c) {
+            // L y = e_c: y vanishes above row c
+            std::fill(y.begin(), y.end(), 0.0);
+            y[c] = 1.0 / L[(size_t)c * m + c];
+            for (int i = c + 1; i < m; ++i) {
+                const double* Li = L + (size_t)i * m;
+                double s = 0.0;
+                for (int j = c; j < i; ++j) s -= Li[j] * y[j];
+                y[i] = s / Li[i];
+            }
+            // L^T x = y
+            for (int i = m - 1; i >= 0; --i) {
+                const double* Ui = &U[(size_t)i * m];
+                double s = y[i];
+                for (int j = i + 1; j < m; ++j) s -= Ui[j] * y[j];
+                y[i] = s / Ui[i];
+            }
+            // column c of the (symmetric) inverse, stored as row c
+            std::copy(y.begin(), y.end(), Inv + (size_t)c * m);
+        }
+    }
 }
 
 void chol_solve(int m, const double* L, int k, double* B) {
@@ -521,6 +621,11 @@ static int rayleigh_ritz(int64_t m, int ns, const double* S, const double* AS, c
     std::vector<double> G((size_t)ns * ns), H((size_t)ns * ns);
     gram(m, ns, S, BS, G.data());
     gram(m, ns, S, AS, H.data());
+    return rayleigh_ritz_grams(ns, G, H, k, Y, theta);
+}
+
+int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, int k, std::vector<double>& Y,
+                        std::vector<double>& theta) {
     for (int a = 0; a < ns; ++a)
         for (int b = 0; b < a; ++b) {
             double g = 0.5 * (G[a * ns + b] + G[b * ns + a]);
@@ -528,6 +633,28 @@ static int rayleigh_ritz(int64_t m, int ns, const double* S, const double* AS, c
             double h = 0.5 * (H[a * ns + b] + H[b * ns + a]);
             H[a * ns + b] = H[b * ns + a] = h;
         }
+    // fast path: a well-conditioned basis Gram matrix is factored by Cholesky
+    // and the pencil (H, G) solved directly; the smallest squared pivot must
+    // stay above 1e-8 of the largest diagonal entry (kappa(G) below ~1e8, so
+    // the B-orthonormality of S Y holds to ~1e-12).  Otherwise the two-pass
+    // eigen-decomposition below drops the near-dependent directions.
+    {
+        double gmax = 0.0;
+        for (int a = 0; a < ns; ++a) gmax = std::max(gmax, G[(size_t)a * ns + a]);
+        std::vector<double> L(G);
+        if (gmax > 0.0 && cholesky(ns, L)) {
+            double pmin = 1e300;
+            for (int a = 0; a < ns; ++a) pmin = std::min(pmin, L[(size_t)a * ns + a] * L[(size_t)a * ns + a]);
+            if (pmin >= 1e-8 * gmax) {
+                std::vector<double> lam(k), U((size_t)ns * k);
+                if (dense_gen_eig(ns, H.data(), G.data(), k, lam.data(), U.data()) == 0) {
+                    theta.assign(lam.begin(), lam.end());
+                    Y.swap(U);
+                    return 0;
+                }
+            }
+        }
+    }
     std::vector<double> gw(ns), GV((size_t)ns * ns);
     sym_eig_all(ns, G.data(), gw.data(), GV.data());
     double gmax = gw[ns - 1];

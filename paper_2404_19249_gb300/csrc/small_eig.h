@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 namespace nas {
 
@@ -22,6 +23,9 @@ void jacobi_eig(int m, double* A, double* w, double* V);
 int chol_factor(int m, double* A);
 // Solve (L L^T) X = B for B row-major [m][k] (overwritten by X).
 void chol_solve(int m, const double* L, int k, double* B);
+// Inv = (L L^T)^-1, row-major [m][m] (symmetric), from the factor of chol_factor;
+// columns in parallel, each row-oriented (contiguous reads of L and L^T).
+void chol_inverse(int m, const double* L, double* Inv);
 
 // Solve A x = b (n <= 8) by Gaussian elimination with partial pivoting.
 // Returns 0 or -1 if singular.
@@ -54,5 +58,14 @@ struct ArrowMat {
 // used, or -1 on failure.
 int lobpcg_arrow(const ArrowMat& A, const ArrowMat& B, int nev, int nguard, double* lam, double* U, bool warm,
                  double tol, int maxit);
+
+// Rayleigh-Ritz step of LOBPCG from the Gram matrices of a basis S [m][ns]:
+// G = S^T B S and H = S^T A S (row-major [ns][ns]; symmetrised in place).  The
+// basis is B-orthonormalised by two passes of G's eigen-decomposition, dropping
+// directions whose Gram eigenvalue is below 1e-9 of the largest; then the
+// lowest k Ritz pairs: theta[k] and coefficients Y [ns][k] (S Y is
+// B-orthonormal).  Returns 0, or -1 if fewer than k directions remain.
+int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, int k, std::vector<double>& Y,
+                        std::vector<double>& theta);
 
 }  // namespace nas

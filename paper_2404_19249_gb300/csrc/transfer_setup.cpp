@@ -194,6 +194,25 @@ void build_galerkin(const HostSpace& F, int64_t nH, const std::vector<int32_t>& 
         }
     }
     G.h2ptr[hnnz] = hst[nH];
+    make_pieces(G.tptr, 128, G.tpieces);
+    make_pieces(G.h2ptr, 256, G.h2pieces);
 }
+
+template <typename P>
+void make_pieces(const std::vector<P>& ptr, int64_t len, PieceMap& pm) {
+    const int64_t nseg = (int64_t)ptr.size() - 1;
+    pm.seg_piece.assign(std::max<int64_t>(nseg, 0) + 1, 0);
+    pm.piece_start.clear();
+    for (int64_t a = 0; a < nseg; ++a) {
+        const int64_t b = ptr[a], e = ptr[a + 1];
+        const int64_t np = (e - b + len - 1) / len;
+        if ((int64_t)pm.seg_piece[a] + np > 2147483647) fail(NAS_E_INVALID_ARG, "too many list pieces");
+        for (int64_t q = 0; q < np; ++q) pm.piece_start.push_back(b + q * len);
+        pm.seg_piece[a + 1] = pm.seg_piece[a] + (int32_t)np;
+    }
+    pm.piece_start.push_back(nseg > 0 ? (int64_t)ptr[nseg] : 0);
+}
+template void make_pieces<int32_t>(const std::vector<int32_t>&, int64_t, PieceMap&);
+template void make_pieces<int64_t>(const std::vector<int64_t>&, int64_t, PieceMap&);
 
 }  // namespace nas

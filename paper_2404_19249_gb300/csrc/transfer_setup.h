@@ -21,6 +21,21 @@ struct BucketGrid {
 // Register every coarse tetrahedron in each bucket its bounding box meets.
 void build_buckets(const HostSpace& C, BucketGrid& G);
 
+// Load-balanced split of a segmented list (CSR-like `ptr` over nseg segments):
+// each segment's entries are cut into consecutive pieces of at most `len`
+// entries.  Pieces of segment a are [seg_piece[a], seg_piece[a+1]); piece q
+// covers list entries [piece_start[q], piece_start[q+1]).  A GPU reduction then
+// takes one warp per piece and sums a segment's piece results in order, so the
+// work per warp is bounded whatever the segment lengths (the transfer lists are
+// very uneven on graded meshes) and the result stays deterministic.
+struct PieceMap {
+    std::vector<int32_t> seg_piece;
+    std::vector<int64_t> piece_start;
+    int64_t npieces() const { return seg_piece.empty() ? 0 : seg_piece.back(); }
+};
+template <typename P>
+void make_pieces(const std::vector<P>& ptr, int64_t len, PieceMap& pm);
+
 struct GalerkinMaps {
     int64_t nH = 0;                      // coarse dofs
     // I^T as CSR over coarse dofs: fine rows and weights
@@ -34,6 +49,8 @@ struct GalerkinMaps {
     std::vector<int32_t> hptr, hcol;
     std::vector<int64_t> h2ptr;
     std::vector<int32_t> h2con;
+    // balanced pieces of the I^T rows and of the stage-2 lists
+    PieceMap tpieces, h2pieces;
     int64_t wnnz() const { return wptr.empty() ? 0 : wptr.back(); }
     int64_t hnnz() const { return hptr.empty() ? 0 : hptr.back(); }
 };

@@ -23,12 +23,13 @@ ERRORS = {
 }
 NAS_FINE, NAS_COARSE = 0, 1
 NAS_POT_COULOMB, NAS_POT_SMOOTHED, NAS_POT_HARMONIC = 0, 1, 2
-PHASES = ["assembly", "bvp", "poisson", "blocks", "density", "mixing", "host_eig", "transfer", "spmm", "spmv"]
+PHASES = ["assembly", "bvp", "poisson", "blocks", "density", "mixing", "host_eig", "transfer", "spmm", "spmv",
+          "eig_rr"]
 (NAS_Q_SIZES, NAS_Q_EIGVALS, NAS_Q_ORBITALS, NAS_Q_RHO_IN, NAS_Q_RHO_OUT, NAS_Q_VHARTREE, NAS_Q_UHAT,
  NAS_Q_ROWPTR, NAS_Q_COLIDX, NAS_Q_K, NAS_Q_M, NAS_Q_MVEXT, NAS_Q_ANL, NAS_Q_HTILDE, NAS_Q_TRANSFER_ELEM,
  NAS_Q_TRANSFER_COL, NAS_Q_TRANSFER_W, NAS_Q_FA, NAS_Q_FB, NAS_Q_DOF_NODE, NAS_Q_ENERGY) = range(21)
 (NAS_OP_LDA, NAS_OP_HARTREE, NAS_OP_ASSEMBLE_MASS, NAS_OP_DENSITY, NAS_OP_APPLY_H, NAS_OP_BVP,
- NAS_OP_GALERKIN) = range(7)
+ NAS_OP_GALERKIN, NAS_OP_ENERGY_GRAD, NAS_OP_BVP_VJP) = range(9)
 
 
 class nas_options(C.Structure):
@@ -38,7 +39,8 @@ class nas_options(C.Structure):
         ("max_outer", C.c_int), ("anderson_depth", C.c_int), ("anderson_beta", C.c_double),
         ("hartree", C.c_int), ("xc", C.c_int), ("multipole", C.c_int), ("omega", C.c_double),
         ("check_every", C.c_int), ("timing", C.c_int), ("eig_dense_max", C.c_int),
-        ("eig_tol", C.c_double), ("spmv_lanes", C.c_int),
+        ("eig_tol", C.c_double), ("spmv_lanes", C.c_int), ("poisson_two_level", C.c_int),
+        ("precision", C.c_int), ("eig_device", C.c_int),
     ]
 
 

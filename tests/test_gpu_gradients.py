@@ -1,0 +1,135 @@
+"""GPU gradients through the C ABI: the Hellmann-Feynman energy gradient and
+the adjoint of the shifted linear problems, against the oracle's formulas and
+against central finite differences of the library's own forward maps; and the
+torch.autograd.Function wrappers."""
+import numpy as np
+import pytest
+
+from oracle.nas import Problem
+from workloads import make_instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nasmod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    from paper_2404_19249_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2404_19249_gb300 import nas
+    return nas
+
+
+def _inst(hartree=True):
+    inst = make_instance("smooth4_p1", cells=8, coarse_cells=3, hartree=hartree, tol_scf=1e-11)
+    inst.mu = 40.0
+    inst.tol_bvp = 1e-15
+    inst.tol_poisson = 1e-14
+    return inst
+
+
+def _params(inst):
+    import torch
+    return torch.tensor(np.concatenate([inst.R, inst.Z[:, None]], axis=1), dtype=torch.float64,
+                        requires_grad=True)
+
+
+def test_energy_gradient_op_matches_oracle(nasmod):
+    inst = _inst()
+    P = Problem(inst, with_transfer=False)
+    s = nasmod.Solver(inst)
+    s.init()
+    rho = np.random.default_rng(1).uniform(0.0, 1.0, size=P.fine.Wq.shape)
+    g = np.zeros((len(inst.Z), 4))
+    nasmod.nas_apply(s.h, nasmod.NAS_OP_ENERGY_GRAD, rho, g)
+    ref = P.energy_gradient(rho)
+    assert np.max(np.abs(g - ref)) < 1e-12 * np.max(np.abs(ref))
+    s.close()
+
+
+def test_bvp_vjp_op_matches_oracle(nasmod):
+    inst = _inst()
+    P = Problem(inst)
+    s = nasmod.Solver(inst)
+    s.init()
+    st = P.initial_state()
+    rng = np.random.default_rng(2)
+    n, N = P.fine.n, P.N
+    R = rng.normal(size=(n, N))
+    G = rng.normal(size=(n, N))
+    out = np.zeros(2 * n * N + 4 * len(inst.Z))
+    nasmod.nas_apply(s.h, nasmod.NAS_OP_BVP_VJP, np.concatenate([R.ravel(), G.ravel()]), out)
+    U = out[:n * N].reshape(n, N)
+    dp = out[2 * n * N:].reshape(-1, 4)
+    from oracle import lda as olda
+    from oracle.linalg import solve_spd
+    _, vxc = olda.lda(st.rho_in)
+    Ht = (P.AL + P.A_NL(P.fine.at_quad(st.VH), vxc) + P.mu * P.M).tocsr()
+    Uref = solve_spd(Ht, R, tol=1e-15)
+    assert np.max(np.abs(U - Uref)) < 1e-9 * np.max(np.abs(Uref))
+    ref = P.bvp_vjp(st, Uref, G)
+    assert np.max(np.abs(dp - ref)) < 1e-9 * np.max(np.abs(ref))
+    s.close()
+
+
+def test_autograd_bvp_solve_matches_finite_differences(nasmod):
+    import torch
+    from paper_2404_19249_gb300.autograd import BVPSolve
+    inst = _inst()
+    s = nasmod.Solver(inst)
+    s.init()
+    sz = s.sizes()
+    rng = np.random.default_rng(3)
+    R = torch.tensor(rng.normal(size=(sz["n"], sz["N"])), dtype=torch.float64, requires_grad=True)
+    G = torch.tensor(rng.normal(size=(sz["n"], sz["N"])), dtype=torch.float64)
+    p = _params(inst)
+    L = torch.sum(G * BVPSolve.apply(p, R, s))
+    L.backward()
+    h = 1e-5
+    for k, c in [(0, 0), (1, 2), (3, 3)]:
+        vals = []
+        for sgn in (1.0, -1.0):
+            q = p.detach().clone()
+            q[k, c] += sgn * h
+            vals.append(float(torch.sum(G * BVPSolve.apply(q, R.detach(), s))))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(p.grad[k, c].item() - fd) < 1e-6 * max(1.0, abs(fd))
+    # dL/dR = A = H~^-1 G: check one direction
+    d = torch.tensor(rng.normal(size=R.shape), dtype=torch.float64)
+    q = p.detach()
+    fd = (float(torch.sum(G * BVPSolve.apply(q, R.detach() + 1e-3 * d, s))) -
+          float(torch.sum(G * BVPSolve.apply(q, R.detach() - 1e-3 * d, s)))) / 2e-3
+    assert abs(float(torch.sum(R.grad * d)) - fd) < 1e-8 * max(1.0, abs(fd))
+    s.close()
+
+
+def test_autograd_energy_hellmann_feynman_matches_finite_differences(nasmod):
+    import torch
+    from paper_2404_19249_gb300.autograd import KSEnergy
+    # two smoothed nuclei, one doubly occupied orbital, no Hartree (the discrete
+    # functional is then variational and Hellmann-Feynman exact); mu and the
+    # step cap are chosen so that Algorithm 3 reaches tol_scf (about 80 steps)
+    inst = _inst(hartree=False)
+    inst.R = np.array([[0.7, -0.2, 0.1], [-0.7, 0.3, -0.2]])
+    inst.Z = np.array([1.0, 1.5])
+    inst.occ = np.array([2.0])
+    inst.mu = 4.0
+    inst.max_outer = 300
+    s = nasmod.Solver(inst)
+    p = _params(inst)
+    E = KSEnergy.apply(p, s)
+    E.backward()
+    h = 1e-4
+    for k, c in [(0, 1), (1, 0), (1, 3)]:
+        vals = []
+        for sgn in (1.0, -1.0):
+            q = p.detach().clone()
+            q[k, c] += sgn * h
+            vals.append(float(KSEnergy.apply(q, s)))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(p.grad[k, c].item() - fd) < 1e-5 * max(1.0, abs(fd)), (k, c, p.grad[k, c].item(), fd)
+    s.close()

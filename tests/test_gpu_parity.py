@@ -215,12 +215,14 @@ def test_benchmark_molecule_first_step(nasmod):
     s.close()
 
 
-def test_lobpcg_path_matches_oracle(nasmod):
-    """The warm-started LOBPCG host eigensolver (used for large coarse spaces)
-    gives the same steps as the oracle's dense generalized eigensolver."""
+@pytest.mark.parametrize("eig_device", [0, 1], ids=["host_lobpcg", "device_lobpcg"])
+def test_lobpcg_path_matches_oracle(nasmod, eig_device):
+    """The warm-started LOBPCG eigensolvers used for large coarse spaces (host
+    block vectors, or device block vectors with a host Rayleigh-Ritz) give the
+    same steps as the oracle's dense generalized eigensolver."""
     inst = _tight(make_instance("paper_molecule", molecule="c6h6", cells=8, coarse_cells=4))
     P = Problem(inst)
-    s = nasmod.Solver(inst, eig_dense_max=0, eig_tol=1e-12)
+    s = nasmod.Solver(inst, eig_dense_max=0, eig_tol=1e-12, eig_device=eig_device)
     s.init()
     st = P.initial_state()
     assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG
@@ -251,3 +253,25 @@ def test_coldot_standalone(nasmod):
         nasmod.nas_coldot_f64(n, N, Xd.data_ptr(), Yd.data_ptr(), wd.data_ptr(), out2.data_ptr(), st)
         torch.cuda.synchronize()
         assert torch.equal(out, out2)   # fixed summation order: bit-identical repeats
+
+
+def test_mixed_precision_poisson_matches_fp64(nasmod):
+    """Mixed precision (FP32 Poisson PCG inside FP64 refinement) reproduces the
+    FP64 steps: eigenvalues within 1e-8 Ha and the oracle within 1e-10."""
+    inst = _tight(make_instance("paper_molecule", molecule="c6h6", cells=8, coarse_cells=4))
+    P = Problem(inst)
+    res = {}
+    for prec in (0, 1):
+        s = nasmod.Solver(inst, precision=prec)
+        s.init()
+        for _ in range(2):
+            r, rep = s.step()
+            assert r == 0
+        res[prec] = (s.get(nasmod.NAS_Q_EIGVALS), s.get(nasmod.NAS_Q_ENERGY)[0])
+        s.close()
+    assert np.max(np.abs(res[1][0] - res[0][0])) < 1e-8
+    assert abs(res[1][1] - res[0][1]) < 1e-8
+    st = P.initial_state()
+    for _ in range(2):
+        st = P.step(st)
+    assert _relmax(res[1][0], st.lam) < TOL_EIG

@@ -276,3 +276,70 @@ def test_nuclear_repulsion_closed_form():
     inst.R = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0], [0.0, 0.0, 2.0]])
     inst.Z = np.array([1.0, 2.0, 3.0])
     assert abs(nuclear_repulsion(inst) - (2.0 / 5 + 3.0 / 2 + 6.0 / sqrt(9 + 16 + 4))) < 1e-15
+
+
+# ---------------------------------------------------------------- gradients (fixed mesh)
+def _smooth_instance(hartree):
+    return make_instance("smooth4_p1", cells=8, coarse_cells=3, hartree=hartree, tol_scf=1e-12)
+
+
+def test_hellmann_feynman_gradient_equals_finite_differences():
+    """dE/d(R, Z) = int rho dV_ext/dp + dE_nn/dp at self-consistency (exact for
+    the discrete variational functional: LDA, no Hartree boundary term)."""
+    inst = _smooth_instance(hartree=False)
+    P = Problem(inst, with_transfer=False)
+    d = P.direct_scf(tol=1e-12, dense_max=5000)
+    g = P.energy_gradient(d.rho_in)
+    h = 1e-4
+    for k, c in [(0, 0), (1, 2), (3, 1), (2, 3)]:
+        vals = []
+        for sgn in (1.0, -1.0):
+            inst2 = _smooth_instance(hartree=False)
+            if c < 3:
+                inst2.R = inst2.R.copy()
+                inst2.R[k, c] += sgn * h
+            else:
+                inst2.Z = inst2.Z.copy()
+                inst2.Z[k] += sgn * h
+            P2 = Problem(inst2, with_transfer=False)
+            vals.append(P2.energy(P2.direct_scf(tol=1e-12, dense_max=5000)))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(g[k, c] - fd) < 2e-6 * max(1.0, abs(fd)), (k, c, g[k, c], fd)
+
+
+def test_bvp_vjp_equals_finite_differences():
+    """Adjoint of the shifted linear problems: d<G, U>/dp with U = H~(p)^-1 R."""
+    inst = _smooth_instance(hartree=True)
+    inst.mu = 40.0
+    P = Problem(inst)
+    st = P.initial_state()
+    rng = np.random.default_rng(9)
+    R = rng.normal(size=(P.fine.n, P.N))
+    G = rng.normal(size=(P.fine.n, P.N))
+
+    def solve(Pp):
+        from oracle import lda as _lda
+        from oracle.linalg import solve_spd
+        VHq = Pp.fine.at_quad(st.VH)
+        _, vxc = _lda.lda(st.rho_in)
+        Ht = (Pp.AL + Pp.A_NL(VHq, vxc) + Pp.mu * Pp.M).tocsr()
+        return solve_spd(Ht, R, tol=1e-15)
+
+    U = solve(P)
+    g = P.bvp_vjp(st, U, G)
+    h = 1e-5
+    for k, c in [(0, 0), (2, 1), (1, 3)]:
+        vals = []
+        for sgn in (1.0, -1.0):
+            inst2 = _smooth_instance(hartree=True)
+            inst2.mu = 40.0
+            if c < 3:
+                inst2.R = inst2.R.copy()
+                inst2.R[k, c] += sgn * h
+            else:
+                inst2.Z = inst2.Z.copy()
+                inst2.Z[k] += sgn * h
+            P2 = Problem(inst2, with_transfer=False)
+            vals.append(float(np.sum(G * solve(P2))))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(g[k, c] - fd) < 1e-6 * max(1.0, abs(fd)), (k, c, g[k, c], fd)

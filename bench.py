@@ -51,6 +51,13 @@ def parse():
     p.add_argument("--tol-bvp", type=float, default=1e-10)
     p.add_argument("--spmv-lanes", type=int, default=0)
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    p.add_argument("--batch", type=int, default=0,
+                   help="also time this many independent small instances (batched workload), "
+                        "one after another and concurrently")
+    p.add_argument("--batch-steps", type=int, default=2)
+    p.add_argument("--batch-threads", type=int, default=8)
+    p.add_argument("--poisson-adaptive", type=int, default=1,
+                   help="1: inner Poisson tolerance follows the density residual (fixed point unchanged)")
     return p.parse_args()
 
 
@@ -64,6 +71,25 @@ def instance(args):
     return make_instance(args.workload, **kw)
 
 
+def kernel_source_hash(name):
+    import hashlib
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_2404_19249_gb300", "csrc", name), "rb").read()).hexdigest()
+
+
+def spmv_traffic(sz):
+    """DRAM bytes per full-size k_pcg1_spmv launch from the committed ncu capture
+    (profiles/traffic.json: a smaller mesh of the same workload, scaled by nnz,
+    since the CSR stream grows with nnz); None when the kernel source changed
+    after the capture or no capture is recorded."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_pcg1_spmv"]
+    except Exception:
+        return None
+    if rec.get("source_sha256") != kernel_source_hash("kernels_pcg1.cu"):
+        return None
+    return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * sz["nnz"] / rec["nnz"]
+
+
 def workload_config(args, inst, extra=None):
     cfg = {
         "workload": "%s: %d nuclei Z=%s, N=%d orbitals, P%d fine mesh %d tets, coarse %d tets, FP64"
@@ -72,6 +98,9 @@ def workload_config(args, inst, extra=None):
         "fine_vertices": int(len(inst.fine_xyz)),
         "l2": "no flush: the per-step working set (CSR values/indices, orbitals, quadrature arrays) exceeds the 126 MB L2",
         "tol_bvp": args.tol_bvp, "tol_poisson": args.tol_poisson, "tol_inner": inst.tol_scf,
+        "poisson_tolerance": ("inexact inner solves: max(tol_poisson, min(1e-6, 1e-3 x previous density "
+                              "residual))" if args.poisson_adaptive else "tol_poisson in every solve"),
+        "small_eigensolver": "LOBPCG, block vectors on the device, host Rayleigh-Ritz",
     }
     if extra:
         cfg.update(extra)
@@ -208,6 +237,44 @@ def full_unknowns(inst):
     return n
 
 
+# ---------------------------------------------------------------------------- batched instances
+def run_batch(args, nas, torch, device):
+    """Independent small molecules (workloads.configs.batch_instances): the same
+    contexts run `batch_steps` steps one after another (one host thread) and
+    concurrently (nas_batch_run with batch_threads workers, one stream per
+    context), each time from the same initial state.  Returns instance-steps/s
+    for both and checks that both runs give bit-identical energies."""
+    from workloads.configs import batch_instances
+    insts = batch_instances(count=args.batch)
+    streams = [torch.cuda.Stream(device=device) for _ in insts]
+    t0 = time.time()
+    solvers = [nas.Solver(inst, device=device, stream=st.cuda_stream, tol_poisson=args.tol_poisson,
+                          tol_bvp=args.tol_bvp, poisson_adaptive=args.poisson_adaptive)
+               for inst, st in zip(insts, streams)]
+    setup = time.time() - t0
+    out = {"instances": len(insts), "steps_each": args.batch_steps,
+           "unknowns": [int(sv.sizes()["n"]) for sv in solvers]}
+    energies = {}
+    for mode, threads in (("sequential", 1), ("batched", args.batch_threads)):
+        for sv in solvers:
+            sv.init()
+        torch.cuda.synchronize(device)
+        t = time.perf_counter()
+        status, reps = nas.nas_batch_run([sv.h for sv in solvers], args.batch_steps, threads)
+        torch.cuda.synchronize(device)
+        dt = time.perf_counter() - t
+        energies[mode] = [r.energy for r in reps]
+        out[mode] = {"instance_steps_per_s": len(insts) * args.batch_steps / dt, "s": dt, "threads": threads,
+                     "status_ok": int(sum(st in (0, -5) for st in status))}
+    out["speedup"] = out["batched"]["instance_steps_per_s"] / out["sequential"]["instance_steps_per_s"]
+    out["identical_results"] = energies["sequential"] == energies["batched"]
+    out["setup_s"] = setup
+    for sv in solvers:
+        sv.close()
+    log("batch: %s" % json.dumps({k: v for k, v in out.items() if k != "unknowns"}))
+    return out
+
+
 # ---------------------------------------------------------------------------- replicas
 def reduce_max(x, dist, device=None):
     """Max of a float over all ranks (no-op without a process group)."""
@@ -256,7 +323,8 @@ def main():
     stream = torch.cuda.current_stream().cuda_stream
     t0 = time.time()
     s = nas.Solver(inst, device=local, stream=stream, timing=1, tol_poisson=args.tol_poisson,
-                   tol_bvp=args.tol_bvp, check_every=4, spmv_lanes=args.spmv_lanes)
+                   tol_bvp=args.tol_bvp, check_every=4, spmv_lanes=args.spmv_lanes,
+                   poisson_adaptive=args.poisson_adaptive)
     s.init()
     setup_s = time.time() - t0
     sz = s.sizes()
@@ -366,11 +434,21 @@ def main():
                  "peak_source": "FP64 FMA issue rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
                  "algorithmic_gbs": spmm_gbs, "launches": calls["spmm"], "ms_per_launch":
                      spmm_ms / max(calls["spmm"], 1)}
-    roof_spmv = {"kernel": "k_spmv8 (CSR SpMV, Poisson PCG, FP64)", "bound": "hbm", "achieved": spmv_gbs,
-                 "peak": hbm_peak, "unit": "GB/s", "frac": spmv_gbs / hbm_peak, "traffic": None,
-                 "peak_source": peak_src, "launches": calls["spmv"],
-                 "ms_per_launch": spmv_ms / max(calls["spmv"], 1)}
-    dominant, other = (roof_spmv, roof_spmm) if spmv_ms >= spmm_ms else (roof_spmm, roof_spmv)
+    # dominant kernel: the SpMV of the FP64 Poisson PCG (k_pcg1_spmv), timed by
+    # CUDA events around the SpMV launches of the first two iterations of every
+    # Poisson solve (library timing mode), over the timed steps
+    sp_ms = sum(rp.poisson_spmv_ms for rp in reps)
+    sp_n = int(sum(rp.poisson_spmv_launches for rp in reps))
+    sp_bytes = 12.0 * sz["nnz"] + 20.0 * sz["n"] + 4.0   # val+col, row_ptr, p once, q written
+    sp_ms_launch = sp_ms / max(sp_n, 1)
+    sp_gbs = sp_bytes / (sp_ms_launch * 1e-3) / 1e9 if sp_ms > 0 else 0.0
+    roof_spmv = {"kernel": "k_pcg1_spmv (CSR SpMV of the Poisson PCG, FP64)",
+                 "bound": "hbm", "achieved": sp_gbs, "peak": hbm_peak, "unit": "GB/s",
+                 "frac": sp_gbs / hbm_peak, "traffic": spmv_traffic(sz), "peak_source": peak_src,
+                 "algorithmic_bytes_per_launch": sp_bytes, "launches": sp_n, "ms_per_launch": sp_ms_launch,
+                 "timing": "CUDA events on the library stream around the SpMV of the first two iterations "
+                           "of every Poisson solve (direct launches; the rest replays from a CUDA graph)"}
+    dominant, other = (roof_spmv, roof_spmm) if sp_ms >= spmm_ms else (roof_spmm, roof_spmv)
 
     # ---------------------------------------------------------------- e2e through host buffers
     n, N, nqt = sz["n"], sz["N"], sz["ne"] * sz["nq"]
@@ -408,6 +486,8 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    batched = run_batch(args, nas, torch, local) if args.batch > 0 else None
+
     # the CPU oracle sample runs after the GPU work, in a fresh single-threaded
     # process (fork + exec), so that it never competes with the host-side work
     # of the timed steps for the CPU cores
@@ -424,7 +504,7 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args, inst, {"unknowns": n, "nnz": sz["nnz"], "coarse_unknowns": sz["nH"],
                                                "parallelism": "replicas" if world > 1 else "1 GPU"}),
-        "spmm_hbm_gbs": spmm_gbs, "spmv_hbm_gbs": spmv_gbs,
+        "spmm_hbm_gbs": spmm_gbs, "spmv_hbm_gbs": sp_gbs,
         "roofline": dominant, "roofline_other": other,
         "phase_ms_per_step": {k: v / args.steps for k, v in ph.items()},
         "per_step": {"n_inner": last.n_inner, "cg_iters": last.cg_iters, "poisson_iters": last.poisson_iters,
@@ -432,6 +512,8 @@ def main():
         "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "setup_s": setup_s,
         "mixed": mixed, "energy_ha": float(en64[0]),
     }
+    if batched is not None:
+        line["batched"] = batched
     print(json.dumps(line))
     s.close()
     if dist is not None:

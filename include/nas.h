@@ -88,6 +88,10 @@ typedef struct nas_options {
                               block vectors, products and Gram matrices on the
                               device (host Rayleigh-Ritz of the 3k x 3k Grams);
                               0 = the host LOBPCG                                  */
+    int    poisson_adaptive; /* 1: inside the inner SCF the Poisson tolerance follows
+                              the previous density residual res:
+                              max(tol_poisson, min(1e-6, 1e-3 res)); 0: always
+                              tol_poisson.  The fixed point is unchanged.          */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -95,7 +99,7 @@ typedef struct nas_options {
  * max_poisson = 20000, max_inner = 50, max_outer = 100, depth 5, beta 0.7,
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
- * poisson_two_level = 1, precision = 0, eig_device = 1. */
+ * poisson_two_level = 1, precision = 0, eig_device = 1, poisson_adaptive = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -140,7 +144,13 @@ typedef struct nas_report {
     long long kernel_launches;/* kernels this library launched during the step       */
     double spmv_bytes;        /* same for the SpMV launches (N = 1)                  */
     double spmv_flops;
-    int    eig_iters;         /* host LOBPCG iterations of the last step (0: dense)   */
+    int    eig_iters;         /* LOBPCG iterations of the last step (0: dense)        */
+    double poisson_spmv_ms;   /* timing = 1: summed CUDA-event time of the SpMV kernel
+                                 of the FP64 Poisson PCG, over the first two
+                                 iterations of every solve (launched directly, with
+                                 events around the SpMV; the rest of the solve is
+                                 replayed from the CUDA graph)                       */
+    long long poisson_spmv_launches; /* SpMV launches counted in poisson_spmv_ms      */
 } nas_report;
 
 /* ------------------------------------------------------------------ context */
@@ -272,6 +282,27 @@ enum nas_op {
     NAS_OP_COUNT
 };
 int nas_apply(nas_ctx* ctx, int op, const void* in, int64_t cnt, void* out, int on_device);
+
+/* Batched independent instances (one molecule and mesh per context): runs
+ * `steps` augmented-subspace steps (nas_step) on each of ctxs[0..count), or
+ * nas_solve when steps <= 0, with n_threads host threads taking contexts
+ * from a shared queue.  The work of different contexts overlaps on the GPU,
+ * which matters for instances too small to fill 152 SMs, and their host-side
+ * parts (small dense eigensolves, Anderson, convergence tests) run in
+ * parallel.  Every result is the one the context gives on its own: each
+ * context is deterministic and shares no device data with the others.
+ *  - Every context must be initialised (nas_init), distinct, on one device,
+ *    and created with its own non-NULL stream (the streams must differ; the
+ *    legacy default stream would serialise them): NAS_E_INVALID_ARG
+ *    otherwise, before any work starts.
+ *  - status[i] receives the return code of context i's last call (NAS_OK,
+ *    NAS_E_NOT_CONVERGED, or an error; an error stops that context only);
+ *    reports (may be NULL) receives each context's last nas_report.
+ *  - Host OpenMP threads are split evenly among the n_threads workers.
+ * Returns NAS_OK when all contexts were run (see status[] for each).
+ * Not in the paper (whose experiments are single molecules); it is the
+ * batched-instance mode of this library. */
+int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* status, nas_report* reports);
 
 /* Stand-alone CSR SpMM with N interleaved right-hand sides, FP64, on device
  * buffers: Y[i][c] = sum_p val[p] X[col[p]][c] for rows i < n_rows.

@@ -1,7 +1,12 @@
 // C ABI of the nas library (include/nas.h): argument checks, exception to
 // status-code translation, and the context lifecycle.
+#include <omp.h>
+
+#include <atomic>
 #include <cstring>
 #include <new>
+#include <set>
+#include <thread>
 
 #include "ctx.h"
 
@@ -62,6 +67,7 @@ void nas_default_options(nas_options* o) {
     o->eig_tol = -1.0;
     o->spmv_lanes = 0;
     o->eig_device = 1;
+    o->poisson_adaptive = 0;
     o->poisson_two_level = 1;
     o->precision = 0;
 }
@@ -100,6 +106,7 @@ void nas_destroy(nas_ctx* c) {
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->pcg1_exec) cudaGraphExecDestroy(c->pcg1_exec);
     if (c->pcg1f_exec) cudaGraphExecDestroy(c->pcg1f_exec);
+    for (auto e : c->pcg1_ev) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
@@ -174,7 +181,7 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
         if (!o) nas::fail(NAS_E_INVALID_ARG, "null options");
         if (o->tol_bvp <= 0 || o->tol_poisson <= 0 || o->max_cg < 1 || o->max_poisson < 1 || o->max_inner < 1 ||
             o->anderson_depth < 1 || o->anderson_depth > 5 || o->precision < 0 || o->precision > 1 ||
-            o->eig_device < 0 || o->eig_device > 1)
+            o->eig_device < 0 || o->eig_device > 1 || o->poisson_adaptive < 0 || o->poisson_adaptive > 1)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level);
@@ -213,6 +220,50 @@ int nas_solve(nas_ctx* c, nas_report* rep) {
         if (rep) *rep = r;
         return (status == NAS_OK && !done) ? NAS_E_NOT_CONVERGED : status;
     });
+}
+
+int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* status, nas_report* reports) {
+    if (count < 0 || n_threads < 1 || (count > 0 && (!ctxs || !status))) return NAS_E_INVALID_ARG;
+    if (count == 0) return NAS_OK;
+    std::set<nas_ctx*> seen;
+    std::set<cudaStream_t> streams;
+    for (int i = 0; i < count; ++i) {
+        nas_ctx* c = ctxs[i];
+        if (!c || !seen.insert(c).second) return NAS_E_INVALID_ARG;
+        if (!c->initialized || c->device != ctxs[0]->device) {
+            c->err = "nas_batch_run: contexts must be initialised and on one device";
+            return NAS_E_INVALID_ARG;
+        }
+        if (!c->stream || !streams.insert(c->stream).second) {
+            c->err = "nas_batch_run: every context needs its own non-default stream";
+            return NAS_E_INVALID_ARG;
+        }
+    }
+    const int nt = std::min(n_threads, count);
+    const int omp_each = std::max(1, omp_get_max_threads() / nt);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        omp_set_num_threads(omp_each);
+        for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+            nas_report r{};
+            int st = NAS_OK;
+            if (steps > 0) {
+                for (int k = 0; k < steps; ++k) {
+                    st = nas_step(ctxs[i], &r);
+                    if (st < 0 && st != NAS_E_NOT_CONVERGED) break;
+                }
+            } else {
+                st = nas_solve(ctxs[i], &r);
+            }
+            status[i] = st;
+            if (reports) reports[i] = r;
+        }
+    };
+    // workers are new threads, so the caller's OpenMP settings stay as they were
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    return NAS_OK;
 }
 
 int nas_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {

@@ -31,8 +31,9 @@ struct Error : public std::runtime_error {
             ::nas::fail(NAS_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-// kernels launched by this library (counted at every launch site)
-extern long long g_launch_count;
+// kernels launched by this library from the calling host thread (counted at
+// every launch site; per thread, so concurrent contexts count separately)
+extern thread_local long long g_launch_count;
 
 #define NAS_CHECK_LAUNCH()                 \
     do {                                   \

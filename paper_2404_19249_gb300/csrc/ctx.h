@@ -103,6 +103,10 @@ struct nas_ctx {
     cudaStream_t cap_stream = nullptr;                 // private stream for graph capture
     cudaGraphExec_t pcg1_exec = nullptr;
     Pcg1Key pcg1_key;
+    // timing mode: events around the SpMV of the first two (direct) iterations
+    std::vector<cudaEvent_t> pcg1_ev;                  // [4]
+    double pcg1_spmv_ms = 0.0;                          // this step: SpMV kernel time
+    long long pcg1_spmv_launches = 0;
     // mixed precision: FP32 copies and work arrays of the Poisson solve
     nas::DBuf<float> d_K32, d_Kdinv32, d_ival32, d_tval32, d_khinv32, d_khvec32, d_f32work, d_f32part;
     cudaGraphExec_t pcg1f_exec = nullptr;
@@ -133,6 +137,7 @@ struct nas_ctx {
     int64_t uwarm_dev_m = 0;                           // m of d_Uwarm's content (0: none)
     nas::DevLobpcg lob;
     double eig_tol_hint = 1.0;          // last inner-SCF residual (LOBPCG tolerance)
+    double poisson_tol_now = 0.0;       // > 0: tolerance of the next Poisson solve
     int last_lobpcg_iters = 0;
 
     // ---- timing

@@ -23,7 +23,7 @@
 
 namespace nas {
 
-long long g_launch_count = 0;
+thread_local long long g_launch_count = 0;
 
 // ------------------------------------------------------------------ helpers
 static Mesh fmesh(nas_ctx* c) {
@@ -212,7 +212,9 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     st.active = c->d_pcg1_flags.p;
     st.breakdown = c->d_pcg1_flags.p + 1;
     st.iters = c->d_pcg1_flags.p + 2;
-    st.tol2 = tol * tol;
+    // the stopping threshold tol^2 ||b||^2 lives in scal[2] (device), so the
+    // captured graph does not depend on the tolerance
+    st.tol2 = 1.0;
     const bool two_level = c->opt.poisson_two_level && c->d_khinv.p && A.val == c->d_K.p;
     if (two_level) {
         st.two_level = 1;
@@ -249,7 +251,7 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
     *converged = true;
     if (!(h[2] > 0.0) || h[1] <= tol * tol * h[2]) return 0;
-    double init[4] = {h[0], 0.0, h[2], h[1]};
+    double init[4] = {h[0], 0.0, tol * tol * h[2], h[1]};
     int flags[4] = {1, 0, 0, 0};
     NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_scal.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
     NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_flags.p, flags, sizeof(flags), cudaMemcpyHostToDevice, s));
@@ -259,9 +261,14 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     const void* ptrs[Pcg1Key::kPtrs] = {A.val, A.rowptr, x, Dinv, st.r, st.part_pq, st.scal, st.active, st.khinv,
                                         st.cvec, st.cpart};
     for (int i = 0; i < Pcg1Key::kPtrs; ++i) key.ptr[i] = ptrs[i];
-    key.tol = tol;
+    key.tol = 1.0;
     key.lanes = lanes;
     key.n = n;
+    const bool timed = c->opt.timing != 0;
+    if (timed && c->pcg1_ev.empty()) {
+        c->pcg1_ev.resize(4);
+        for (auto& e : c->pcg1_ev) NAS_CUDA(cudaEventCreate(&e));
+    }
     if (!c->pcg1_exec || !(key == c->pcg1_key)) {
         if (c->pcg1_exec) cudaGraphExecDestroy(c->pcg1_exec);
         c->pcg1_exec = nullptr;
@@ -276,11 +283,31 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
         c->pcg1_key = key;
     }
     int it = 0;
+    const int kpi = pcg1_kernels_per_iteration(st.two_level, st.tpc.npieces);
+    if (timed) {
+        // timing mode: the first two iterations (both parities, so the graph
+        // continues with parity 0) run as direct launches with CUDA events
+        // around their SpMV kernel; same kernels, same order, same results
+        launch_pcg1_iteration(st, 0, lanes, s, c->pcg1_ev[0], c->pcg1_ev[1]);
+        launch_pcg1_iteration(st, 1, lanes, s, c->pcg1_ev[2], c->pcg1_ev[3]);
+    }
+    bool first = true;
     while (true) {
         NAS_CUDA(cudaGraphLaunch(c->pcg1_exec, s));
-        g_launch_count += 3 * kPcg1Graph;
+        g_launch_count += (long long)kpi * kPcg1Graph;
         NAS_CUDA(cudaMemcpyAsync(flags, c->d_pcg1_flags.p, sizeof(flags), cudaMemcpyDeviceToHost, s));
         sync(c);
+        if (timed && first) {
+            // SpMV times of the direct iterations that were active
+            const int active = std::min(2, flags[2]);
+            for (int k = 0; k < active; ++k) {
+                float ms = 0.0f;
+                NAS_CUDA(cudaEventElapsedTime(&ms, c->pcg1_ev[2 * k], c->pcg1_ev[2 * k + 1]));
+                c->pcg1_spmv_ms += ms;
+                c->pcg1_spmv_launches += 1;
+            }
+        }
+        first = false;
         it = flags[2];
         if (flags[1]) fail(NAS_E_BREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite)");
         if (!flags[0] || it >= maxit) break;
@@ -391,14 +418,15 @@ static int pcg1_mixed_solve(nas_ctx* c, const double* b, double* x, double tol, 
         for (int k = 0; k < G; ++k) rz += hp[k];
         for (int k = 0; k < G; ++k) rr += hp[G + k];
         if (!(rr > 0.0)) break;
-        float sc[4] = {(float)rz, 0.0f, (float)rr, (float)rr};
+        // threshold tin^2 r.r in scal[2]: the graph does not depend on tin
+        float sc[4] = {(float)rz, 0.0f, (float)(tin * tin * rr), (float)rr};
         NAS_CUDA(cudaMemcpyAsync(st.scal, sc, sizeof(sc), cudaMemcpyHostToDevice, s));
-        st.tol2 = (float)(tin * tin);
+        st.tol2 = 1.0f;
         Pcg1Key key;
         const void* ptrs[Pcg1Key::kPtrs] = {st.val, st.rowptr, st.x, st.dinv, st.r, st.part_pq, st.scal, st.active,
                                             st.khinv, st.cvec, st.cpart};
         for (int i = 0; i < Pcg1Key::kPtrs; ++i) key.ptr[i] = ptrs[i];
-        key.tol = tin;
+        key.tol = 1.0;
         key.lanes = lanes;
         key.n = n;
         if (!c->pcg1f_exec || !(key == c->pcg1f_key)) {
@@ -417,7 +445,7 @@ static int pcg1_mixed_solve(nas_ctx* c, const double* b, double* x, double tol, 
         int it = 0;
         while (true) {
             NAS_CUDA(cudaGraphLaunch(c->pcg1f_exec, s));
-            g_launch_count += (st.two_level ? 6 : 3) * kPcg1Graph;
+            g_launch_count += (long long)pcg1_kernels_per_iteration(st.two_level, st.tpc.npieces) * kPcg1Graph;
             NAS_CUDA(cudaMemcpyAsync(fl, c->d_pcg1_flags.p, sizeof(fl), cudaMemcpyDeviceToHost, s));
             sync(c);
             it = fl[2];
@@ -450,9 +478,10 @@ static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
     launch_nodal_to_dof(c->F.n, c->d_dof_node.p, VH, c->d_pv.p, s);
     Csr K = fcsr(c, c->d_K.p);
     K.rowptr_nnz = c->F.nnz();
+    const double tol = c->poisson_tol_now > 0.0 ? c->poisson_tol_now : c->opt.tol_poisson;
     int it = c->opt.precision == 1
-                 ? pcg1_mixed_solve(c, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson, c->opt.max_poisson, conv)
-                 : pcg1_solve(c, K, c->d_Kdinv.p, c->d_pb.p, c->d_pv.p, c->opt.tol_poisson, c->opt.max_poisson, conv);
+                 ? pcg1_mixed_solve(c, c->d_pb.p, c->d_pv.p, tol, c->opt.max_poisson, conv)
+                 : pcg1_solve(c, K, c->d_Kdinv.p, c->d_pb.p, c->d_pv.p, tol, c->opt.max_poisson, conv);
     launch_dof_to_nodal(c->F.n, c->d_dof_node.p, c->d_pv.p, VH, s);
     return it;
 }
@@ -779,7 +808,14 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
         if (!(t == 0 && reuse_first && c->anl_valid)) {
             if (c->opt.hartree) {
                 bool pc;
+                // optional inexact inner Poisson solves: the tolerance follows
+                // the previous density residual (the last inner iterations,
+                // with residual near tol_inner, solve to tol_poisson)
+                c->poisson_tol_now = (c->opt.poisson_adaptive && t > 0)
+                                         ? std::max(c->opt.tol_poisson, std::min(1e-6, 1e-3 * res))
+                                         : 0.0;
                 poisson += hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
+                c->poisson_tol_now = 0.0;
                 if (!pc) fail(NAS_E_NOT_CONVERGED, "Poisson PCG hit its iteration cap");
             }
             assemble_nl(c);
@@ -1237,6 +1273,8 @@ int ctx_step(nas_ctx* c, nas_report* rep) {
         c->phase_calls[k] = 0;
     }
     c->spmm_bytes = c->spmm_flops = c->spmv_bytes = c->spmv_flops = 0;
+    c->pcg1_spmv_ms = 0.0;
+    c->pcg1_spmv_launches = 0;
     c->last_lobpcg_iters = 0;
     int status = NAS_OK;
     if (!c->anl_valid) {
@@ -1313,6 +1351,8 @@ void ctx_fill_report(nas_ctx* c, nas_report* rep) {
     rep->spmv_flops = c->spmv_flops;
     rep->kernel_launches = g_launch_count - c->launches_at_step_start;
     rep->eig_iters = c->last_lobpcg_iters;
+    rep->poisson_spmv_ms = c->pcg1_spmv_ms;
+    rep->poisson_spmv_launches = c->pcg1_spmv_launches;
 }
 
 // ------------------------------------------------------------------ state in/out

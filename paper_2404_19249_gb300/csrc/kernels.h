@@ -252,8 +252,8 @@ struct Pcg1T {
     const T* dinv;
     T *x, *r, *z, *p, *q;
     T *part_pq, *part_rz, *part_rr;  // [pcg1_blocks()] per-block partial sums
-    T* scal;                          // [0],[1] rz (by iteration parity), [2] ||b||^2, [3] r.r
-    int* active;                      // cleared when ||r||^2 <= tol2 ||b||^2
+    T* scal;                          // [0],[1] rz (by iteration parity), [2] stop threshold, [3] r.r
+    int* active;                      // cleared when ||r||^2 <= tol2 scal[2]
     int* breakdown;
     int* iters;
     T tol2;
@@ -274,9 +274,13 @@ using Pcg1 = Pcg1T<double>;
 using Pcg1f = Pcg1T<float>;
 int pcg1_blocks();
 // one PCG iteration (3 kernels, 7 with the two-level preconditioner);
-// par = iteration parity (selects the rz slot)
-void launch_pcg1_iteration(const Pcg1& s, int par, int lanes_per_row, cudaStream_t st);
-void launch_pcg1_iteration(const Pcg1f& s, int par, int lanes_per_row, cudaStream_t st);
+// par = iteration parity (selects the rz slot).  ev0/ev1 (optional) are
+// recorded right before and after the SpMV kernel.
+void launch_pcg1_iteration(const Pcg1& s, int par, int lanes_per_row, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                           cudaEvent_t ev1 = nullptr);
+void launch_pcg1_iteration(const Pcg1f& s, int par, int lanes_per_row, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                           cudaEvent_t ev1 = nullptr);
+int pcg1_kernels_per_iteration(int two_level, int64_t npieces);
 // z = D^-1 r + I K_H^-1 I^T r and partial sums of r.z (two-level only)
 void launch_pcg1_coarse_correction(const Pcg1& s, cudaStream_t st);
 void launch_pcg1_coarse_correction(const Pcg1f& s, cudaStream_t st);

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_dir(Pcg1T<T> s, int par
         s.scal[3] = rr;
         *s.iters += 1;
         if (!isfinite(rr)) *s.breakdown = 1;
-        if (rr <= s.tol2 * s.scal[2] || !isfinite(rr)) *s.active = 0;
+        if (rr <= s.tol2 * s.scal[2] || !isfinite(rr)) *s.active = 0;  // scal[2] = tol^2 ||b||^2 (tol2 = 1)
     }
 }
 
@@ -206,7 +206,9 @@ static void pcg1_coarse_correction(const Pcg1T<T>& s, cudaStream_t st) {
 }
 
 template <typename T>
-static void pcg1_iteration(const Pcg1T<T>& s, int par, int lpr, cudaStream_t st) {
+static void pcg1_iteration(const Pcg1T<T>& s, int par, int lpr, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                           cudaEvent_t ev1 = nullptr) {
+    if (ev0) NAS_CUDA(cudaEventRecord(ev0, st));
     switch (lpr) {
         case 1: k_pcg1_spmv<T, 1><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
         case 2: k_pcg1_spmv<T, 2><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
@@ -216,6 +218,7 @@ static void pcg1_iteration(const Pcg1T<T>& s, int par, int lpr, cudaStream_t st)
         default: k_pcg1_spmv<T, 32><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
     }
     NAS_CHECK_LAUNCH();
+    if (ev1) NAS_CUDA(cudaEventRecord(ev1, st));
     k_pcg1_update<T><<<kPcgBlocks, kPcgThreads, 0, st>>>(s, par);
     NAS_CHECK_LAUNCH();
     if (s.two_level) pcg1_coarse_correction(s, st);
@@ -223,8 +226,15 @@ static void pcg1_iteration(const Pcg1T<T>& s, int par, int lpr, cudaStream_t st)
     NAS_CHECK_LAUNCH();
 }
 
-void launch_pcg1_iteration(const Pcg1& s, int par, int lpr, cudaStream_t st) { pcg1_iteration(s, par, lpr, st); }
-void launch_pcg1_iteration(const Pcg1f& s, int par, int lpr, cudaStream_t st) { pcg1_iteration(s, par, lpr, st); }
+void launch_pcg1_iteration(const Pcg1& s, int par, int lpr, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+    pcg1_iteration(s, par, lpr, st, ev0, ev1);
+}
+void launch_pcg1_iteration(const Pcg1f& s, int par, int lpr, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+    pcg1_iteration(s, par, lpr, st, ev0, ev1);
+}
+int pcg1_kernels_per_iteration(int two_level, int64_t npieces) {
+    return two_level ? (npieces > 0 ? 7 : 6) : 3;
+}
 void launch_pcg1_coarse_correction(const Pcg1& s, cudaStream_t st) { pcg1_coarse_correction(s, st); }
 void launch_pcg1_coarse_correction(const Pcg1f& s, cudaStream_t st) { pcg1_coarse_correction(s, st); }
 

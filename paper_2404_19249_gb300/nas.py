@@ -40,7 +40,7 @@ class nas_options(C.Structure):
         ("hartree", C.c_int), ("xc", C.c_int), ("multipole", C.c_int), ("omega", C.c_double),
         ("check_every", C.c_int), ("timing", C.c_int), ("eig_dense_max", C.c_int),
         ("eig_tol", C.c_double), ("spmv_lanes", C.c_int), ("poisson_two_level", C.c_int),
-        ("precision", C.c_int), ("eig_device", C.c_int),
+        ("precision", C.c_int), ("eig_device", C.c_int), ("poisson_adaptive", C.c_int),
     ]
 
 
@@ -52,7 +52,7 @@ class nas_report(C.Structure):
         ("e_vxc", C.c_double), ("e_nn", C.c_double), ("phase_ms", C.c_double * 16),
         ("phase_calls", C.c_longlong * 16), ("spmm_bytes", C.c_double), ("spmm_flops", C.c_double),
         ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_double), ("spmv_flops", C.c_double),
-        ("eig_iters", C.c_int),
+        ("eig_iters", C.c_int), ("poisson_spmv_ms", C.c_double), ("poisson_spmv_launches", C.c_longlong),
     ]
 
     def as_dict(self):
@@ -88,6 +88,7 @@ def _load():
         "nas_get": (C.c_int, [VP, C.c_int, VP, C.c_size_t, C.c_int]),
         "nas_set_state": (C.c_int, [VP, VP, VP, VP, C.c_int]),
         "nas_apply": (C.c_int, [VP, C.c_int, VP, I64, VP, C.c_int]),
+        "nas_batch_run": (C.c_int, [P(VP), C.c_int, C.c_int, C.c_int, P(C.c_int), P(nas_report)]),
         "nas_spmm_f64": (C.c_int, [I64, VP, VP, VP, C.c_int, VP, VP, VP]),
         "nas_coldot_f64": (C.c_int, [I64, C.c_int, VP, VP, VP, VP, VP]),
         "nas_coldot_f64_noalloc": (C.c_int, [I64, C.c_int, VP, VP, VP, VP, VP]),
@@ -103,7 +104,7 @@ lib = _load()
 EXPORTS = [
     "nas_default_options", "nas_version", "nas_create", "nas_destroy", "nas_last_error", "nas_set_mesh",
     "nas_set_system", "nas_set_options", "nas_init", "nas_step", "nas_solve", "nas_get", "nas_set_state",
-    "nas_apply", "nas_spmm_f64", "nas_coldot_f64", "nas_coldot_f64_noalloc",
+    "nas_apply", "nas_batch_run", "nas_spmm_f64", "nas_coldot_f64", "nas_coldot_f64_noalloc",
 ]
 
 
@@ -206,6 +207,22 @@ def nas_apply(h, op, x, out, cnt=0, on_device=0):
         return _check(h, lib.nas_apply(h, op, C.c_void_p(x), cnt, C.c_void_p(out), 1))
     x = _c(x, np.float64)
     return _check(h, lib.nas_apply(h, op, _ptr(x), cnt or x.size, _ptr(out), 0))
+
+
+def nas_batch_run(handles, steps, n_threads):
+    """Run `steps` steps (nas_solve if steps <= 0) on every context of `handles`
+    concurrently (one stream per context, n_threads host workers).  Returns
+    (status list, report list)."""
+    n = len(handles)
+    arr = (C.c_void_p * max(n, 1))()
+    for i, h in enumerate(handles):
+        arr[i] = h.value if isinstance(h, C.c_void_p) else h
+    st = (C.c_int * max(n, 1))()
+    reps = (nas_report * max(n, 1))()
+    r = lib.nas_batch_run(C.cast(arr, C.POINTER(C.c_void_p)), n, int(steps), int(n_threads), st, reps)
+    if r != NAS_OK:
+        raise NasError(r, "nas_batch_run: " + (lib.nas_last_error(handles[0]) or b"").decode())
+    return [st[i] for i in range(n)], [reps[i] for i in range(n)]
 
 
 def nas_spmm_f64(n_rows, row_ptr, col, val, N, X, Y, stream=0):

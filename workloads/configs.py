@@ -169,6 +169,42 @@ def _paper_molecule(molecule="ch4", cells=24, coarse_cells=8, order=2, **kw):
                     occ=closed_shell_occupations(Z.sum()))
 
 
+def batch_instances(count=64, seed=4, dof_lo=1e4, dof_hi=4e5, max_orb=8):
+    """The batched workload: `count` independent small molecules.
+
+    Each instance: 1-6 nuclei with Z uniform in {1..4} and positions uniform in
+    [-3,3]^3 (>= 1.2 bohr apart), redrawn until N = ceil(sum Z / 2) <= max_orb;
+    fine order P1 or P2 by a fair coin; the number of fine unknowns log-uniform
+    in [dof_lo, dof_hi] (rounded to a whole number of cells per axis);
+    Omega = [-10,10]^3 with a mild grading toward the nuclei (amplitude 2,
+    width 1 bohr) and a uniform coarse mesh of about a quarter (P1) or half
+    (P2) the cells per axis, at least 3.  mu is the paper's 8 M sum Z^2.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        while True:
+            n_nuc = int(rng.integers(1, 7))
+            R, Z = random_molecule(rng, n_nuc, 4, 3.0)
+            if (int(Z.sum()) + 1) // 2 <= max_orb:
+                break
+        order = int(rng.integers(1, 3))
+        side = float(np.exp(rng.uniform(np.log(dof_lo), np.log(dof_hi)))) ** (1.0 / 3.0)
+        if order == 1:
+            cells = max(6, int(round(side + 1.0)))
+            coarse = max(3, cells // 4)
+        else:
+            cells = max(4, int(round((side + 1.0) / 2.0)))
+            coarse = max(3, cells // 2)
+        axes = [graded_axis_lorentz(-10.0, 10.0, cells, R[:, d], amplitude=2.0, width=1.0) for d in range(3)]
+        fxyz, ftet = kuhn_mesh(*axes)
+        cax = uniform_axis(-10.0, 10.0, coarse)
+        cxyz, ctet = kuhn_mesh(cax, cax, cax)
+        out.append(Instance("batch%d" % b, order, fxyz, ftet, cxyz, ctet, R=R, Z=Z,
+                            occ=closed_shell_occupations(Z.sum())))
+    return out
+
+
 WORKLOADS = {
     "paper_molecule": _paper_molecule,
     "he_p1": _he_p1,

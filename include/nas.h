@@ -73,8 +73,9 @@ typedef struct nas_options {
     int    timing;         /* 1: record per-kernel CUDA-event times (nas_report)     */
     int    eig_dense_max;  /* small problems up to this size use the dense host
                               eigensolver, larger ones warm-started LOBPCG           */
-    double eig_tol;        /* LOBPCG relative residual; <= 0: adaptive, 1e-3 x the
-                              previous inner-SCF residual clamped to [1e-11, 1e-4]  */
+    double eig_tol;        /* LOBPCG relative residual; <= 0: adaptive, eig_adapt x
+                              the previous inner-SCF residual clamped to
+                              [1e-11, 1e-4]                                        */
     int    spmv_lanes;     /* lanes per row of the Poisson SpMV (1, 2, 4, 8, 16, 32);
                               0 = chosen from the mean row length                    */
     int    poisson_two_level; /* 1: Poisson PCG preconditioner D^-1 + I K_H^-1 I^T with
@@ -88,6 +89,9 @@ typedef struct nas_options {
                               block vectors, products and Gram matrices on the
                               device (host Rayleigh-Ritz of the 3k x 3k Grams);
                               0 = the host LOBPCG                                  */
+    double eig_adapt;      /* factor of the adaptive LOBPCG tolerance (eig_tol <= 0):
+                              eig_adapt x the previous inner-SCF residual, clamped
+                              to [1e-11, 1e-4]                                     */
     int    poisson_adaptive; /* 1: inside the inner SCF the Poisson tolerance follows
                               the previous density residual res:
                               max(tol_poisson, min(1e-6, 1e-3 res)); 0: always
@@ -99,7 +103,8 @@ typedef struct nas_options {
  * max_poisson = 20000, max_inner = 50, max_outer = 100, depth 5, beta 0.7,
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
- * poisson_two_level = 1, precision = 0, eig_device = 1, poisson_adaptive = 0. */
+ * poisson_two_level = 1, precision = 0, eig_device = 1, eig_adapt = 1e-3,
+ * poisson_adaptive = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -291,10 +296,12 @@ int nas_apply(nas_ctx* ctx, int op, const void* in, int64_t cnt, void* out, int 
  * parts (small dense eigensolves, Anderson, convergence tests) run in
  * parallel.  Every result is the one the context gives on its own: each
  * context is deterministic and shares no device data with the others.
- *  - Every context must be initialised (nas_init), distinct, on one device,
- *    and created with its own non-NULL stream (the streams must differ; the
- *    legacy default stream would serialise them): NAS_E_INVALID_ARG
- *    otherwise, before any work starts.
+ *  - Every context must be initialised (nas_init), distinct and on one
+ *    device (NAS_E_INVALID_ARG otherwise, before any work starts).  During
+ *    the call each context runs on a private non-blocking stream of the
+ *    library, ordered after the work already queued on the context's own
+ *    stream; at return the own stream is made to wait for it, so callers may
+ *    keep sharing one stream among contexts.
  *  - status[i] receives the return code of context i's last call (NAS_OK,
  *    NAS_E_NOT_CONVERGED, or an error; an error stops that context only);
  *    reports (may be NULL) receives each context's last nas_report.

@@ -67,6 +67,7 @@ void nas_default_options(nas_options* o) {
     o->eig_tol = -1.0;
     o->spmv_lanes = 0;
     o->eig_device = 1;
+    o->eig_adapt = 1e-3;
     o->poisson_adaptive = 0;
     o->poisson_two_level = 1;
     o->precision = 0;
@@ -181,7 +182,8 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
         if (!o) nas::fail(NAS_E_INVALID_ARG, "null options");
         if (o->tol_bvp <= 0 || o->tol_poisson <= 0 || o->max_cg < 1 || o->max_poisson < 1 || o->max_inner < 1 ||
             o->anderson_depth < 1 || o->anderson_depth > 5 || o->precision < 0 || o->precision > 1 ||
-            o->eig_device < 0 || o->eig_device > 1 || o->poisson_adaptive < 0 || o->poisson_adaptive > 1)
+            o->eig_device < 0 || o->eig_device > 1 || o->poisson_adaptive < 0 || o->poisson_adaptive > 1 ||
+            !(o->eig_adapt > 0.0) || o->eig_adapt > 1.0)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level);
@@ -226,18 +228,36 @@ int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* stat
     if (count < 0 || n_threads < 1 || (count > 0 && (!ctxs || !status))) return NAS_E_INVALID_ARG;
     if (count == 0) return NAS_OK;
     std::set<nas_ctx*> seen;
-    std::set<cudaStream_t> streams;
     for (int i = 0; i < count; ++i) {
         nas_ctx* c = ctxs[i];
-        if (!c || !seen.insert(c).second) return NAS_E_INVALID_ARG;
+        if (!c || !seen.insert(c).second) {
+            if (ctxs[0]) ctxs[0]->err = "nas_batch_run: null or repeated context";
+            return NAS_E_INVALID_ARG;
+        }
         if (!c->initialized || c->device != ctxs[0]->device) {
-            c->err = "nas_batch_run: contexts must be initialised and on one device";
+            ctxs[0]->err = c->err = "nas_batch_run: contexts must be initialised and on one device";
             return NAS_E_INVALID_ARG;
         }
-        if (!c->stream || !streams.insert(c->stream).second) {
-            c->err = "nas_batch_run: every context needs its own non-default stream";
-            return NAS_E_INVALID_ARG;
+    }
+    // Each context runs on a private non-blocking stream for the duration of
+    // the batch, ordered after the work already queued on its own stream, and
+    // its own stream waits for the batch's work at the end.
+    if (cudaSetDevice(ctxs[0]->device) != cudaSuccess) return NAS_E_CUDA;
+    std::vector<cudaStream_t> own(count), priv(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+        nas_ctx* c = ctxs[i];
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&priv[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(e, c->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(priv[i], e, 0) != cudaSuccess) {
+            for (int j = 0; j <= i; ++j)
+                if (priv[j]) cudaStreamDestroy(priv[j]);
+            if (e) cudaEventDestroy(e);
+            return NAS_E_CUDA;
         }
+        cudaEventDestroy(e);
+        own[i] = c->stream;
+        c->stream = priv[i];
     }
     const int nt = std::min(n_threads, count);
     const int omp_each = std::max(1, omp_get_max_threads() / nt);
@@ -263,7 +283,18 @@ int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* stat
     std::vector<std::thread> pool;
     for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
     for (auto& t : pool) t.join();
-    return NAS_OK;
+    int rc = NAS_OK;
+    for (int i = 0; i < count; ++i) {
+        nas_ctx* c = ctxs[i];
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(e, priv[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(own[i], e, 0) != cudaSuccess)
+            rc = NAS_E_CUDA;
+        if (e) cudaEventDestroy(e);
+        c->stream = own[i];
+        cudaStreamDestroy(priv[i]);  // released once its queued work completes
+    }
+    return rc;
 }
 
 int nas_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {

@@ -659,7 +659,8 @@ static double eig_tolerance(nas_ctx* c) {
     // residual tolerance tied to the inner-SCF residual: the eigenvectors need
     // no more accuracy than the density they produce, and the last inner
     // iterations (residual near tol_inner) solve to 1e-11
-    return c->opt.eig_tol > 0.0 ? c->opt.eig_tol : std::min(1e-4, std::max(1e-11, 1e-3 * c->eig_tol_hint));
+    return c->opt.eig_tol > 0.0 ? c->opt.eig_tol
+                                : std::min(1e-4, std::max(1e-11, c->opt.eig_adapt * c->eig_tol_hint));
 }
 
 // Dense host copies of the last pencil after a device solve (nas_get only).

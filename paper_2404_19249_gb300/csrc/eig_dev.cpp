@@ -1,10 +1,12 @@
 // Device LOBPCG (Knyazev 2001) for the arrow-structured small pencil of
 // Algorithm 3: the same iteration as the host solver (diagonal preconditioner
 // diag(A - sigma B)^-1, W orthogonalised against X and B-normalised, exact
-// recomputation of A and B times the new X and P, two-pass Gram
-// orthonormalisation inside the Rayleigh-Ritz step), with every column kept
+// recomputation of A and B times the new X and P), with every column kept
 // active and the convergence test taken from the residual norms that travel
-// with the Gram matrices.
+// with the Rayleigh-Ritz results.  The Rayleigh-Ritz step runs on the device
+// (Cholesky of the basis Gram matrix + Jacobi) when the basis is small and
+// well conditioned, else on the host (Cholesky, or the two-pass
+// eigen-decomposition that drops near-dependent directions).
 #include "eig_dev.h"
 
 #include <algorithm>
@@ -35,6 +37,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         GB.alloc((int64_t)kmax3 * kmax3);
         Y.alloc((int64_t)kmax3 * k);
         C.alloc((int64_t)k * k);
+        dstat.alloc(1);
         m_cap = m;
         k_cap = k;
     }
@@ -46,7 +49,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
     auto applyB = [&](int w, const double* in, double* out) {
         launch_arrow_apply(B, w, in, out, gpart.p, gtmp.p, s);
     };
-    std::vector<double> hG, hH, hY, th, hn(3 * (size_t)k);
+    std::vector<double> hG, hH, hY, th, th_new, hn(3 * (size_t)k);
     // Rayleigh-Ritz on the basis S (ns columns): Grams on the device, the rest on the host
     auto grams = [&](const ColBlocks& S, const ColBlocks& AS, const ColBlocks& BS) {
         launch_gram_tiles(m, S, AS, gpart.p, GA.p, s);
@@ -60,15 +63,37 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         if (norms) NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
         NAS_CUDA(cudaStreamSynchronize(s));
     };
-    auto rr = [&](int ns) {
+    // host Rayleigh-Ritz from the fetched Grams (fallback and large ns)
+    auto rr_host = [&](int ns, std::vector<double>& th_out) {
         auto t0 = std::chrono::steady_clock::now();
-        int r = rayleigh_ritz_grams(ns, hG, hH, k, hY, th);
+        int r = rayleigh_ritz_grams(ns, hG, hH, k, hY, th_out);
         rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (r == 0) {
             NAS_CUDA(cudaMemcpyAsync(Y.p, hY.data(), sizeof(double) * ns * k, cudaMemcpyHostToDevice, s));
-            NAS_CUDA(cudaMemcpyAsync(theta.p, th.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+            NAS_CUDA(cudaMemcpyAsync(theta.p, th_out.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
         }
         return r;
+    };
+    // Rayleigh-Ritz of the basis whose Grams are in GA/GB: on the device when
+    // ns is small enough (one host round trip fetches theta, the status and,
+    // with norms = true, the residual norms of the current X), else or when
+    // the device reports an ill-conditioned basis, on the host.  th_out
+    // receives the new Ritz values; Y/theta on the device hold the result.
+    auto rr = [&](int ns, bool norms, std::vector<double>& th_out) {
+        th_out.resize(k);
+        if (ns <= rr_device_max_ns()) {
+            launch_rr_small(ns, k, GA.p, GB.p, 1e-8, Y.p, theta.p, dstat.p, s);
+            int st = -1;
+            NAS_CUDA(cudaMemcpyAsync(&st, dstat.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            NAS_CUDA(cudaMemcpyAsync(th_out.data(), theta.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+            if (norms) NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
+            NAS_CUDA(cudaStreamSynchronize(s));
+            if (st == 0) return 0;
+            fetch(ns, false);
+        } else {
+            fetch(ns, norms);
+        }
+        return rr_host(ns, th_out);
     };
     // ---- start: warm vectors for the wanted columns, deterministic pseudo-random otherwise
     {
@@ -90,8 +115,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
     {
         ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
         grams(S, AS, BS);
-        fetch(k, false);
-        if (rr(k) != 0) return -1;
+        if (rr(k, false, th) != 0) return -1;
         launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
         std::swap(X, X2);
         applyA(k, X, AX);
@@ -133,7 +157,10 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         }
         const int ns = S.ncols();
         grams(S, AS, BS);
-        fetch(ns, true);
+        // the Rayleigh-Ritz runs before the convergence test of the current
+        // X (its norms arrive with the same round trip); if X has converged
+        // the new coefficients are simply not used
+        const int rr_status = rr(ns, true, th_new);
         double worst = 0.0;
         for (int j = 0; j < nev; ++j) {
             const double rel = std::sqrt(std::max(hn[j], 0.0)) /
@@ -143,11 +170,12 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         }
         if (!std::isfinite(worst)) return -1;
         if (worst <= tol) break;
-        if (rr(ns) != 0) {
+        if (rr_status != 0) {
             if (np == 0) return -1;
             np = 0;  // restart without P
             continue;
         }
+        th.swap(th_new);
         // new X = S Y; new P = [W, P] part of S Y
         launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
         {
@@ -175,8 +203,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
     {
         ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
         grams(S, AS, BS);
-        fetch(k, false);
-        if (rr(k) != 0) return -1;
+        if (rr(k, false, th) != 0) return -1;
         launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
         NAS_CUDA(cudaMemcpy2DAsync(Uout, sizeof(double) * nev, X2, sizeof(double) * k, sizeof(double) * nev, m,
                                    cudaMemcpyDeviceToDevice, s));

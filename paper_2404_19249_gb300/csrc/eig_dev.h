@@ -1,9 +1,11 @@
 // LOBPCG for the small pencil F_A U = lambda F_B U of Algorithm 3 (eq. st1)
 // with the block vectors on the device.  The arrow-structured products, the
 // residuals, the orthogonalisation and the Gram matrices of the basis
-// [X, W, P] run in device kernels; the host receives only the Gram matrices
-// ((3k)^2 numbers, k = nev + nguard) and returns the Rayleigh-Ritz
-// coefficients, so one host round trip is made per iteration.
+// [X, W, P] run in device kernels, and so does the Rayleigh-Ritz step when
+// the basis has at most 80 columns (3k, k = nev + nguard; one block:
+// Cholesky + Jacobi); the host then reads only the residual norms and Ritz
+// values, one round trip per iteration.  Larger or ill-conditioned bases
+// take the host Rayleigh-Ritz of the fetched Gram matrices.
 #pragma once
 
 #include "common.h"
@@ -15,6 +17,7 @@ struct DevLobpcg {
     // block vectors [m][k] (raw pointers are swapped between iterations)
     DBuf<double> bufs[11];
     DBuf<double> T, theta, nrm, gpart, gtmp, GA, GB, Y, C;
+    DBuf<int> dstat;      // status of the device Rayleigh-Ritz
     int64_t m_cap = 0;
     int k_cap = 0;
     double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)

@@ -5,6 +5,8 @@
 // block vectors are row-major [m][w] with m = nH + Na.  Every sum runs in a
 // fixed order (per-chunk partial sums, then an ordered final pass), so results
 // are bit-reproducible.
+#include <mutex>
+
 #include "kernels.h"
 
 namespace nas {
@@ -212,6 +214,250 @@ void launch_eig_precond(const ArrowDev& A, const ArrowDev& B, const int32_t* dia
     const int64_t m = A.nH + A.Na;
     if (m <= 0) return;
     k_eig_precond<<<grid_of(m, 256), 256, 0, s>>>(A, B, diag_slot, sigma, T);
+    NAS_CHECK_LAUNCH();
+}
+
+
+// ---------------------------------------------------------------- Rayleigh-Ritz on the device
+// One block solves the small pencil (H, G) of the basis Gram matrices
+// (ns <= kRRMax): G = L L^T by Cholesky (status 1 if a squared pivot falls
+// below pivot_tol x max diag G: the caller then uses the host fallback),
+// Hr = L^-1 H L^-T, all eigenpairs of Hr by the cyclic Jacobi method with the
+// round-robin ordering (ns/2 disjoint rotations per round, applied to rows,
+// then columns, then the eigenvector matrix), the lowest k (ascending), and
+// Y = L^-T Z.  Status 2: Jacobi did not reach the off-diagonal tolerance.
+namespace {
+constexpr int kRRMax = 80;
+constexpr int kRRLd = kRRMax + 1;
+constexpr int kRRThreads = 512;
+}
+
+int rr_device_max_ns() { return kRRMax; }
+
+static size_t rr_device_smem_bytes() {
+    return sizeof(double) * (3 * (size_t)kRRMax * kRRLd + 4 * kRRMax + kRRThreads) + sizeof(int) * (2 * kRRMax + 8);
+}
+
+__device__ double rr_block_sum(double v, double* red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kRRThreads) k_rr_small(int ns, int k, const double* GA, const double* GB,
+                                                         double pivot_tol, double* Y, double* theta, int* status) {
+    extern __shared__ double sm[];
+    double* L = sm;                              // G, then its Cholesky factor (lower)
+    double* A = L + kRRMax * kRRLd;              // H, then L^-1 H, then reused for V
+    double* C = A + kRRMax * kRRLd;              // Hr = L^-1 H L^-T (Jacobi works here)
+    double* cs = C + kRRMax * kRRLd;             // rotation cosines [kRRMax/2]
+    double* sn = cs + kRRMax;                    // rotation sines
+    double* ev = sn + kRRMax;                    // eigenvalues
+    double* red = ev + 2 * kRRMax;               // reduction scratch [blockDim]
+    int* pr = reinterpret_cast<int*>(red + kRRThreads);  // pair p per slot
+    int* qr = pr + kRRMax;                               // pair q per slot
+    int* flag = qr + kRRMax;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // ---- load and symmetrise
+    for (int e = tid; e < ns * ns; e += nt) {
+        const int i = e / ns, j = e % ns;
+        L[i * kRRLd + j] = 0.5 * (GB[i * ns + j] + GB[j * ns + i]);
+        A[i * kRRLd + j] = 0.5 * (GA[i * ns + j] + GA[j * ns + i]);
+    }
+    if (tid == 0) flag[0] = 0;
+    __syncthreads();
+    double gmax = 0.0;
+    for (int i = 0; i < ns; ++i) gmax = fmax(gmax, L[i * kRRLd + i]);
+    // ---- Cholesky (right-looking)
+    for (int j = 0; j < ns; ++j) {
+        if (tid == 0) {
+            const double piv = L[j * kRRLd + j];
+            if (!(piv >= pivot_tol * gmax) || !(piv > 0.0)) flag[0] = 1;
+            L[j * kRRLd + j] = sqrt(fmax(piv, 0.0));
+        }
+        __syncthreads();
+        if (flag[0]) {
+            if (tid == 0) *status = 1;
+            return;
+        }
+        const double d = L[j * kRRLd + j];
+        for (int i = j + 1 + tid; i < ns; i += nt) L[i * kRRLd + j] /= d;
+        __syncthreads();
+        const int r = ns - j - 1;
+        for (int e = tid; e < r * r; e += nt) {
+            const int i = j + 1 + e / r, l = j + 1 + e % r;
+            if (l <= i) L[i * kRRLd + l] -= L[i * kRRLd + j] * L[l * kRRLd + j];
+        }
+        __syncthreads();
+    }
+    // ---- A <- L^-1 A (forward substitution, all columns at once)
+    for (int i = 0; i < ns; ++i) {
+        for (int c = tid; c < ns; c += nt) {
+            double s = A[i * kRRLd + c];
+            for (int p = 0; p < i; ++p) s -= L[i * kRRLd + p] * A[p * kRRLd + c];
+            A[i * kRRLd + c] = s / L[i * kRRLd + i];
+        }
+        __syncthreads();
+    }
+    // ---- C <- L^-1 A^T  (= L^-1 H L^-T)
+    for (int i = 0; i < ns; ++i) {
+        for (int c = tid; c < ns; c += nt) {
+            double s = A[c * kRRLd + i];
+            for (int p = 0; p < i; ++p) s -= L[i * kRRLd + p] * C[p * kRRLd + c];
+            C[i * kRRLd + c] = s / L[i * kRRLd + i];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < ns * ns; e += nt) {
+        const int i = e / ns, j = e % ns;
+        if (j < i) {
+            const double v = 0.5 * (C[i * kRRLd + j] + C[j * kRRLd + i]);
+            C[i * kRRLd + j] = v;
+            C[j * kRRLd + i] = v;
+        }
+    }
+    // ---- V <- I (in A)
+    for (int e = tid; e < ns * ns; e += nt) A[(e / ns) * kRRLd + e % ns] = (e / ns == e % ns) ? 1.0 : 0.0;
+    __syncthreads();
+    // ---- cyclic Jacobi, round-robin pairs over n2 = ns rounded up to even
+    const int n2 = ns + (ns & 1);
+    const int half = n2 / 2;
+    double fro2 = 0.0;
+    {
+        double s = 0.0;
+        for (int e = tid; e < ns * ns; e += nt) {
+            const double v = C[(e / ns) * kRRLd + e % ns];
+            s += v * v;
+        }
+        fro2 = rr_block_sum(s, red);
+    }
+    bool converged = false;
+    for (int sweep = 0; sweep < 30 && !converged; ++sweep) {
+        double off = 0.0;
+        for (int e = tid; e < ns * ns; e += nt) {
+            const int i = e / ns, j = e % ns;
+            if (i != j) off += C[i * kRRLd + j] * C[i * kRRLd + j];
+        }
+        off = rr_block_sum(off, red);
+        if (off <= 1e-28 * fro2) {  // off-diagonal norm <= 1e-14 of the Frobenius norm
+            converged = true;
+            break;
+        }
+        for (int round = 0; round < n2 - 1; ++round) {
+            // pairs of this round: slot 0 pairs the fixed index n2-1 with `round`;
+            // slot t pairs (round + t) and (round - t) mod (n2 - 1)
+            for (int t = tid; t < half; t += nt) {
+                int p, q;
+                if (t == 0) {
+                    p = round;
+                    q = n2 - 1;
+                } else {
+                    p = (round + t) % (n2 - 1);
+                    q = (round - t + (n2 - 1)) % (n2 - 1);
+                }
+                if (p > q) {
+                    const int x = p;
+                    p = q;
+                    q = x;
+                }
+                double c = 1.0, s = 0.0;
+                if (q < ns) {
+                    const double apq = C[p * kRRLd + q];
+                    if (apq != 0.0) {
+                        const double app = C[p * kRRLd + p], aqq = C[q * kRRLd + q];
+                        const double zeta = (aqq - app) / (2.0 * apq);
+                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        s = c * tt;
+                    }
+                }
+                pr[t] = p;
+                qr[t] = q;
+                cs[t] = c;
+                sn[t] = s;
+            }
+            __syncthreads();
+            // rows p, q of C
+            for (int e = tid; e < half * ns; e += nt) {
+                const int t = e / ns, j = e % ns;
+                const int p = pr[t], q = qr[t];
+                if (q >= ns || sn[t] == 0.0) continue;
+                const double c = cs[t], s = sn[t];
+                const double a = C[p * kRRLd + j], b = C[q * kRRLd + j];
+                C[p * kRRLd + j] = c * a - s * b;
+                C[q * kRRLd + j] = s * a + c * b;
+            }
+            __syncthreads();
+            // columns p, q of C and of V
+            for (int e = tid; e < half * ns; e += nt) {
+                const int t = e / ns, j = e % ns;
+                const int p = pr[t], q = qr[t];
+                if (q >= ns || sn[t] == 0.0) continue;
+                const double c = cs[t], s = sn[t];
+                const double a = C[j * kRRLd + p], b = C[j * kRRLd + q];
+                C[j * kRRLd + p] = c * a - s * b;
+                C[j * kRRLd + q] = s * a + c * b;
+                const double va = A[j * kRRLd + p], vb = A[j * kRRLd + q];
+                A[j * kRRLd + p] = c * va - s * vb;
+                A[j * kRRLd + q] = s * va + c * vb;
+            }
+            __syncthreads();
+        }
+    }
+    if (!converged) {
+        if (tid == 0) *status = 2;
+        return;
+    }
+    // ---- lowest k eigenpairs in ascending order (rank of each diagonal entry)
+    for (int i = tid; i < ns; i += nt) {
+        const double v = C[i * kRRLd + i];
+        int rank = 0;
+        for (int j = 0; j < ns; ++j) {
+            const double w = C[j * kRRLd + j];
+            rank += (w < v || (w == v && j < i)) ? 1 : 0;
+        }
+        if (rank < k) {
+            ev[rank] = v;
+            pr[rank] = i;
+        }
+    }
+    __syncthreads();
+    // ---- Y = L^-T Z (backward substitution, k columns in parallel); Y [ns][k]
+    for (int i = ns - 1; i >= 0; --i) {
+        for (int c = tid; c < k; c += nt) {
+            double s = A[i * kRRLd + pr[c]];
+            for (int p = i + 1; p < ns; ++p) s -= L[p * kRRLd + i] * Y[p * k + c];
+            Y[i * k + c] = s / L[i * kRRLd + i];
+        }
+        __syncthreads();
+    }
+    for (int c = tid; c < k; c += nt) theta[c] = ev[c];
+    if (tid == 0) *status = 0;
+}
+
+void launch_rr_small(int ns, int k, const double* GA, const double* GB, double pivot_tol, double* Y, double* theta,
+                     int* status, cudaStream_t s) {
+    if (ns > kRRMax || k > ns || k < 1) fail(NAS_E_INVALID_ARG, "device Rayleigh-Ritz size");
+    static std::mutex mu;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    NAS_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64) fail(NAS_E_INVALID_ARG, "device id");
+        if (!attr_set[dev]) {
+            NAS_CUDA(cudaFuncSetAttribute(k_rr_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)rr_device_smem_bytes()));
+            attr_set[dev] = true;
+        }
+    }
+    k_rr_small<<<1, kRRThreads, rr_device_smem_bytes(), s>>>(ns, k, GA, GB, pivot_tol, Y, theta, status);
     NAS_CHECK_LAUNCH();
 }
 

@@ -60,20 +60,36 @@ __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_spmv(Pcg1T<T> s) {
     const int64_t rows_per_warp = 32 / LPR;
     const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int64_t warp_stride = (int64_t)gridDim.x * (blockDim.x / 32) * rows_per_warp;
+    // read-only views (nothing this kernel writes aliases them), so the
+    // loads may take the read-only path and be issued early
+    const int32_t* __restrict__ rp = s.rowptr;
+    const int32_t* __restrict__ cl = s.col;
+    const T* __restrict__ va = s.val;
+    const T* __restrict__ pv = s.p;
     T dot = 0;
     for (int64_t base = warp_id * rows_per_warp; base < s.n; base += warp_stride) {
         const int64_t row = base + (threadIdx.x % 32) / LPR;
         const bool valid = row < s.n;
         T acc = 0;
         if (valid) {
-            const int p1 = s.rowptr[row + 1];
-            for (int p = s.rowptr[row] + lane; p < p1; p += LPR) acc += s.val[p] * s.p[s.col[p]];
+            // two independent accumulators: two gathers in flight per lane
+            const int p1 = rp[row + 1];
+            int p = rp[row] + lane;
+            T a0 = 0, a1 = 0;
+            for (; p + LPR < p1; p += 2 * LPR) {
+                const int c0 = cl[p], c1 = cl[p + LPR];
+                const T v0 = va[p], v1 = va[p + LPR];
+                a0 += v0 * pv[c0];
+                a1 += v1 * pv[c1];
+            }
+            if (p < p1) a0 += va[p] * pv[cl[p]];
+            acc = a0 + a1;
         }
 #pragma unroll
         for (int off = LPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, LPR > 1 ? LPR : 2);
         if (valid && lane == 0) {
             s.q[row] = acc;
-            dot += s.p[row] * acc;
+            dot += pv[row] * acc;
         }
     }
     block_store_sum(dot, sh, s.part_pq + blockIdx.x);

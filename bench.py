@@ -56,7 +56,9 @@ def parse():
                         "one after another and concurrently")
     p.add_argument("--batch-steps", type=int, default=2)
     p.add_argument("--batch-threads", type=int, default=8)
-    p.add_argument("--eig-adapt", type=float, default=1e-3,
+    p.add_argument("--eig-precond", type=int, default=1,
+                   help="LOBPCG preconditioner: 1 = inverse coarse stiffness on the coarse rows, 0 = diagonal")
+    p.add_argument("--eig-adapt", type=float, default=1e-2,
                    help="adaptive LOBPCG tolerance factor (x previous inner-SCF residual)")
     p.add_argument("--poisson-adaptive", type=int, default=1,
                    help="1: inner Poisson tolerance follows the density residual (fixed point unchanged)")
@@ -102,8 +104,9 @@ def workload_config(args, inst, extra=None):
         "tol_bvp": args.tol_bvp, "tol_poisson": args.tol_poisson, "tol_inner": inst.tol_scf,
         "poisson_tolerance": ("inexact inner solves: max(tol_poisson, min(1e-6, 1e-3 x previous density "
                               "residual))" if args.poisson_adaptive else "tol_poisson in every solve"),
-        "small_eigensolver": "LOBPCG, block vectors on the device, host Rayleigh-Ritz; residual tolerance "
-                             "%g x previous inner-SCF residual in [1e-11, 1e-4]" % args.eig_adapt,
+        "small_eigensolver": "LOBPCG, block vectors on the device, host Rayleigh-Ritz, %s preconditioner; "
+                             "residual tolerance %g x previous inner-SCF residual in [1e-11, 1e-4]"
+                             % ("inverse coarse stiffness" if args.eig_precond else "diagonal", args.eig_adapt),
     }
     if extra:
         cfg.update(extra)
@@ -327,7 +330,7 @@ def main():
     t0 = time.time()
     s = nas.Solver(inst, device=local, stream=stream, timing=1, tol_poisson=args.tol_poisson,
                    tol_bvp=args.tol_bvp, check_every=4, spmv_lanes=args.spmv_lanes,
-                   poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt)
+                   poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt, eig_precond=args.eig_precond)
     s.init()
     setup_s = time.time() - t0
     sz = s.sizes()

@@ -89,6 +89,11 @@ typedef struct nas_options {
                               block vectors, products and Gram matrices on the
                               device (host Rayleigh-Ritz of the 3k x 3k Grams);
                               0 = the host LOBPCG                                  */
+    int    eig_precond;    /* LOBPCG preconditioner: 1 = the inverse coarse stiffness
+                              (I^T K I)^-1 on the coarse rows (FP32, dense; when
+                              the block has <= 32 columns and the coarse space
+                              <= 6000 unknowns) and the diagonal on the others;
+                              0 = diag(F_A - sigma F_B)^-1 everywhere             */
     double eig_adapt;      /* factor of the adaptive LOBPCG tolerance (eig_tol <= 0):
                               eig_adapt x the previous inner-SCF residual, clamped
                               to [1e-11, 1e-4]                                     */
@@ -103,8 +108,8 @@ typedef struct nas_options {
  * max_poisson = 20000, max_inner = 50, max_outer = 100, depth 5, beta 0.7,
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
- * poisson_two_level = 1, precision = 0, eig_device = 1, eig_adapt = 1e-3,
- * poisson_adaptive = 0. */
+ * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
+ * eig_adapt = 1e-3, poisson_adaptive = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */

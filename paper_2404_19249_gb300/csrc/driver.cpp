@@ -30,6 +30,9 @@ static Mesh fmesh(nas_ctx* c) {
     return Mesh{c->F.ne, c->F.nloc, (int)c->nq, c->d_vxyz.p, c->d_elem.p};
 }
 static Csr fcsr(nas_ctx* c, const double* val) { return Csr{c->F.n, c->d_rowptr.p, c->d_col.p, val}; }
+// largest coarse space for which dense K_H^-1 and B_H^-1 are formed (nH^2 doubles each)
+static const int64_t kDenseCoarseMax = 6000;
+
 static Pieces tpieces(nas_ctx* c) {
     Pieces pc;
     pc.nseg = c->nH;
@@ -711,8 +714,19 @@ static void device_eig(nas_ctx* c, int m) {
     std::vector<double> lam(c->N);
     const bool warm = c->uwarm_dev_m == m;
     c->lob.rr_ms = 0.0;
-    int it = c->lob.solve(A, B, c->d_hdiag.p, c->N, std::max(4, c->N / 4), lam.data(), warm ? c->d_Uwarm.p : nullptr,
-                          c->d_U.p, eig_tolerance(c), 2000, s);
+    const int nguard = std::max(4, c->N / 4);
+    // coarse-block preconditioner: the inverse coarse stiffness (K_H = I^T K I
+    // is twice the kinetic part of the coarse block of F_A), in FP32
+    const float* TH = nullptr;
+    if (c->opt.eig_precond && c->d_khinv.p && c->N + nguard <= 32) {
+        if (!c->d_khinv32.p) {
+            c->d_khinv32.ensure((size_t)c->nH * c->nH);
+            launch_cast_to_f32(c->nH * c->nH, c->d_khinv.p, c->d_khinv32.p, s);
+        }
+        TH = c->d_khinv32.p;
+    }
+    int it = c->lob.solve(A, B, c->d_hdiag.p, c->N, nguard, lam.data(), warm ? c->d_Uwarm.p : nullptr, c->d_U.p,
+                          eig_tolerance(c), 2000, s, TH);
     if (it < 0) fail(NAS_E_EIGEN, "small eigenproblem: LOBPCG did not converge");
     c->last_lobpcg_iters += it;
     c->phase_ms[NAS_PH_EIG_RR] += c->lob.rr_ms;
@@ -1154,9 +1168,12 @@ void ctx_setup(nas_ctx* c) {
     }
     c->uwarm_dev_m = 0;
     sync(c);
-    // two-level Poisson preconditioner: dense K_H^-1 with K_H = I^T K I
+    // dense K_H^-1 with K_H = I^T K I: the coarse part of the two-level Poisson
+    // preconditioner and of the LOBPCG preconditioner (coarse spaces up to
+    // kDenseCoarseMax unknowns; larger ones keep the Jacobi preconditioners)
     c->d_khinv.release();
-    if (c->opt.poisson_two_level) {
+    c->d_khinv32.release();
+    if ((c->opt.poisson_two_level || c->opt.eig_precond) && c->nH <= kDenseCoarseMax) {
         std::vector<double> kh(G.hnnz());
         galerkin(c, c->d_K.p, c->d_AH.p);
         c->d_AH.download(kh.data(), G.hnnz(), s);

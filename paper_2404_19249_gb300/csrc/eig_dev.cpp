@@ -3,10 +3,11 @@
 // diag(A - sigma B)^-1, W orthogonalised against X and B-normalised, exact
 // recomputation of A and B times the new X and P), with every column kept
 // active and the convergence test taken from the residual norms that travel
-// with the Rayleigh-Ritz results.  The Rayleigh-Ritz step runs on the device
-// (Cholesky of the basis Gram matrix + Jacobi) when the basis is small and
-// well conditioned, else on the host (Cholesky, or the two-pass
-// eigen-decomposition that drops near-dependent directions).
+// with the Gram matrices.  The Rayleigh-Ritz step of the (3k)^2 Grams runs on
+// the host (Cholesky, or the two-pass eigen-decomposition that drops
+// near-dependent directions): GB300 executes 2 FP64 FMA per clock per SM, so
+// a one-block FP64 dense eigensolver is about ten times slower than one host
+// core (measured: 9.8 ms against ~0.9 ms for 78 columns).
 #include "eig_dev.h"
 
 #include <algorithm>
@@ -18,7 +19,8 @@
 namespace nas {
 
 int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, int nev, int nguard,
-                     double* lam, const double* U0, double* Uout, double tol, int maxit, cudaStream_t s) {
+                     double* lam, const double* U0, double* Uout, double tol, int maxit, cudaStream_t s,
+                     const float* TH) {
     const int64_t m = A.nH + A.Na;
     if (nev < 1 || nev > m) return -1;
     const int k = (int)std::min<int64_t>(nev + nguard, m);
@@ -37,10 +39,10 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         GB.alloc((int64_t)kmax3 * kmax3);
         Y.alloc((int64_t)kmax3 * k);
         C.alloc((int64_t)k * k);
-        dstat.alloc(1);
         m_cap = m;
         k_cap = k;
     }
+    if (TH) ppart.ensure(std::max<int64_t>(1, dense_precond_part_size(A.nH, k)));
     double *X = bufs[0].p, *AX = bufs[1].p, *BX = bufs[2].p, *W = bufs[3].p, *AW = bufs[4].p, *BW = bufs[5].p;
     double *P = bufs[6].p, *AP = bufs[7].p, *BP = bufs[8].p, *X2 = bufs[9].p, *P2 = bufs[10].p;
     auto applyA = [&](int w, const double* in, double* out) {
@@ -74,25 +76,13 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         }
         return r;
     };
-    // Rayleigh-Ritz of the basis whose Grams are in GA/GB: on the device when
-    // ns is small enough (one host round trip fetches theta, the status and,
-    // with norms = true, the residual norms of the current X), else or when
-    // the device reports an ill-conditioned basis, on the host.  th_out
-    // receives the new Ritz values; Y/theta on the device hold the result.
+    // Rayleigh-Ritz of the basis whose Grams are in GA/GB, on the host; with
+    // norms = true the residual norms of the current X come with the same
+    // round trip.  th_out receives the new Ritz values; Y/theta on the device
+    // hold the result.
     auto rr = [&](int ns, bool norms, std::vector<double>& th_out) {
         th_out.resize(k);
-        if (ns <= rr_device_max_ns()) {
-            launch_rr_small(ns, k, GA.p, GB.p, 1e-8, Y.p, theta.p, dstat.p, s);
-            int st = -1;
-            NAS_CUDA(cudaMemcpyAsync(&st, dstat.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-            NAS_CUDA(cudaMemcpyAsync(th_out.data(), theta.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-            if (norms) NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
-            NAS_CUDA(cudaStreamSynchronize(s));
-            if (st == 0) return 0;
-            fetch(ns, false);
-        } else {
-            fetch(ns, norms);
-        }
+        fetch(ns, norms);
         return rr_host(ns, th_out);
     };
     // ---- start: warm vectors for the wanted columns, deterministic pseudo-random otherwise
@@ -128,13 +118,18 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
     int np = 0;
     int it = 0;
     for (; it < maxit; ++it) {
-        // W = T (AX - BX theta); residual norms of the current X
-        launch_eig_resid(m, k, AX, BX, theta.p, W, s);
+        // W = T (AX - BX theta); residual norms of the current X.  With a dense
+        // coarse block the residual goes to X2 (free until the update below).
+        double* R = TH ? X2 : W;
+        launch_eig_resid(m, k, AX, BX, theta.p, R, s);
         {
-            const double* Xs[3] = {W, AX, BX};
+            const double* Xs[3] = {R, AX, BX};
             launch_coldots(m, k, 3, Xs, Xs, nullptr, gpart.p, nrm.p, s);
         }
-        launch_scale_rows(m, k, T.p, W, W, s);
+        if (TH)
+            launch_dense_precond(A.nH, m, k, TH, R, T.p, ppart.p, W, s);
+        else
+            launch_scale_rows(m, k, T.p, W, W, s);
         // W <- W - X (BX^T W), then unit B-norm columns
         launch_gram_tiles(m, ColBlocks::one(BX, k, k), ColBlocks::one(W, k, k), gpart.p, C.p, s);
         launch_cols_mult(m, ColBlocks::one(X, k, k), C.p, k, -1.0, 1.0, W, s);

@@ -1,11 +1,9 @@
 // LOBPCG for the small pencil F_A U = lambda F_B U of Algorithm 3 (eq. st1)
 // with the block vectors on the device.  The arrow-structured products, the
 // residuals, the orthogonalisation and the Gram matrices of the basis
-// [X, W, P] run in device kernels, and so does the Rayleigh-Ritz step when
-// the basis has at most 80 columns (3k, k = nev + nguard; one block:
-// Cholesky + Jacobi); the host then reads only the residual norms and Ritz
-// values, one round trip per iteration.  Larger or ill-conditioned bases
-// take the host Rayleigh-Ritz of the fetched Gram matrices.
+// [X, W, P] run in device kernels; the host receives the Gram matrices
+// ((3k)^2 numbers, k = nev + nguard) with the residual norms and returns the
+// Rayleigh-Ritz coefficients: one host round trip per iteration.
 #pragma once
 
 #include "common.h"
@@ -17,7 +15,7 @@ struct DevLobpcg {
     // block vectors [m][k] (raw pointers are swapped between iterations)
     DBuf<double> bufs[11];
     DBuf<double> T, theta, nrm, gpart, gtmp, GA, GB, Y, C;
-    DBuf<int> dstat;      // status of the device Rayleigh-Ritz
+    DBuf<float> ppart;    // split partial products of the dense preconditioner
     int64_t m_cap = 0;
     int k_cap = 0;
     double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)
@@ -27,8 +25,10 @@ struct DevLobpcg {
     // the CSR slot of the coarse block's diagonal entry (i, i).  Stops when every
     // wanted residual satisfies ||A u - lambda B u|| <= tol (||A u|| + |lambda|
     // ||B u||).  Returns the iterations used, or -1 on failure.
+    // TH (optional): FP32 [nH][nH] preconditioner block for the coarse rows
+    // (the border rows keep the diagonal one).
     int solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, int nev, int nguard, double* lam,
-              const double* U0, double* Uout, double tol, int maxit, cudaStream_t s);
+              const double* U0, double* Uout, double tol, int maxit, cudaStream_t s, const float* TH = nullptr);
 };
 
 }  // namespace nas

@@ -237,16 +237,13 @@ void launch_eig_resid(int64_t m, int k, const double* AX, const double* BX, cons
 // columns of A1, A2, A3 ([m][k], any may be null) scaled by 1/sqrt(nrm[j])
 void launch_inv_sqrt_scale(int64_t m, int k, const double* nrm, double* A1, double* A2, double* A3,
                            cudaStream_t s);
-// Rayleigh-Ritz of LOBPCG on the device for ns <= rr_device_max_ns(): from the
-// basis Gram matrices GA = S^T A S and GB = S^T B S ([ns][ns] row-major) the
-// lowest k Ritz values theta[k] and coefficients Y [ns][k] (one block:
-// Cholesky of GB, cyclic Jacobi on L^-1 GA L^-T).  *status: 0 ok; 1 if a
-// squared Cholesky pivot is below pivot_tol x max diag GB (ill-conditioned
-// basis: the caller falls back to the host two-pass method); 2 if Jacobi
-// did not converge.
-int rr_device_max_ns();
-void launch_rr_small(int ns, int k, const double* GA, const double* GB, double pivot_tol, double* Y, double* theta,
-                     int* status, cudaStream_t s);
+// LOBPCG preconditioner with a dense coarse block: W = T R on the first nH rows
+// (T FP32 [nH][nH], e.g. the inverse coarse stiffness), W = Dinv R on the
+// remaining m - nH rows; R, W [m][k] FP64, k <= 32; part: FP32 scratch of
+// dense_precond_part_size(nH, k)
+int64_t dense_precond_part_size(int64_t nH, int k);
+void launch_dense_precond(int64_t nH, int64_t m, int k, const float* T, const double* R, const double* Dinv,
+                          float* part, double* W, cudaStream_t s);
 // T[i] = 1 / (A_ii - sigma B_ii), diag_slot[i] = CSR slot of (i, i) in the coarse block
 void launch_eig_precond(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, double sigma, double* T,
                         cudaStream_t s);

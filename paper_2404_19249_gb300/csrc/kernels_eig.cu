@@ -5,8 +5,6 @@
 // block vectors are row-major [m][w] with m = nH + Na.  Every sum runs in a
 // fixed order (per-chunk partial sums, then an ordered final pass), so results
 // are bit-reproducible.
-#include <mutex>
-
 #include "kernels.h"
 
 namespace nas {
@@ -217,247 +215,84 @@ void launch_eig_precond(const ArrowDev& A, const ArrowDev& B, const int32_t* dia
     NAS_CHECK_LAUNCH();
 }
 
+}  // namespace nas
 
-// ---------------------------------------------------------------- Rayleigh-Ritz on the device
-// One block solves the small pencil (H, G) of the basis Gram matrices
-// (ns <= kRRMax): G = L L^T by Cholesky (status 1 if a squared pivot falls
-// below pivot_tol x max diag G: the caller then uses the host fallback),
-// Hr = L^-1 H L^-T, all eigenpairs of Hr by the cyclic Jacobi method with the
-// round-robin ordering (ns/2 disjoint rotations per round, applied to rows,
-// then columns, then the eigenvector matrix), the lowest k (ascending), and
-// Y = L^-T Z.  Status 2: Jacobi did not reach the off-diagonal tolerance.
-namespace {
-constexpr int kRRMax = 80;
-constexpr int kRRLd = kRRMax + 1;
-constexpr int kRRThreads = 512;
+namespace nas {
+
+// ---- preconditioner with a dense coarse block:
+//   W[i][j] = sum_b T[i][b] R[b][j]   (i < nH; T FP32 [nH][nH], FP32 products and sums)
+//   W[i][j] = Dinv[i] R[i][j]        (nH <= i < m)
+// Stage 1, grid (row blocks, kPcSplit): block (rb, sp) multiplies 32 rows of T
+// by the rows of R in its share of the b range, staging 32 columns of T and
+// the matching 32 rows of R in shared memory; thread = (column j, rows ty +
+// 8q).  Stage 2 adds the kPcSplit partial products in order.  FP32 is enough
+// for a preconditioner (a fixed symmetric positive definite operator close to
+// an inverse).
+static const int kPcRows = 32;
+static const int kPcK = 32;
+static const int kPcSplit = 4;
+
+__global__ void __launch_bounds__(256) k_dense_precond_part(int64_t nH, int k, const float* T, const double* R,
+                                                            float* part) {
+    __shared__ float Ts[kPcRows][kPcK + 1];
+    __shared__ float Rs[kPcK][kPcK + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * kPcRows;
+    const int64_t span = (nH + kPcSplit - 1) / kPcSplit;
+    const int64_t bbeg = (int64_t)blockIdx.y * span;
+    const int64_t bend = bbeg + span < nH ? bbeg + span : nH;
+    const int tx = threadIdx.x % kPcK;  // column j
+    const int ty = threadIdx.x / kPcK;  // rows ty, ty+8, ty+16, ty+24
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t b0 = bbeg; b0 < bend; b0 += kPcK) {
+        for (int e = threadIdx.x; e < kPcRows * kPcK; e += blockDim.x) {
+            const int rr = e / kPcK, cc = e % kPcK;
+            const int64_t i = r0 + rr, b = b0 + cc;
+            Ts[rr][cc] = (i < nH && b < bend) ? T[i * nH + b] : 0.f;
+            const int64_t bj = b0 + rr;
+            Rs[rr][cc] = (bj < bend && cc < k) ? (float)R[bj * k + cc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int bb = 0; bb < kPcK; ++bb) {
+            const float rv = Rs[bb][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += Ts[ty + 8 * q][bb] * rv;
+        }
+        __syncthreads();
+    }
+    if (tx < k)
+        for (int q = 0; q < 4; ++q) {
+            const int64_t i = r0 + ty + 8 * q;
+            if (i < nH) part[((int64_t)blockIdx.y * nH + i) * k + tx] = acc[q];
+        }
 }
 
-int rr_device_max_ns() { return kRRMax; }
-
-static size_t rr_device_smem_bytes() {
-    return sizeof(double) * (3 * (size_t)kRRMax * kRRLd + 4 * kRRMax + kRRThreads) + sizeof(int) * (2 * kRRMax + 8);
+__global__ void k_dense_precond_sum(int64_t nH, int64_t m, int k, const float* part, const double* R,
+                                    const double* Dinv, double* W) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * k) return;
+    const int64_t i = t / k;
+    if (i < nH) {
+        float acc = 0.f;
+        for (int sp = 0; sp < kPcSplit; ++sp) acc += part[(int64_t)sp * nH * k + t];
+        W[t] = (double)acc;
+    } else {
+        W[t] = Dinv[i] * R[t];
+    }
 }
 
-__device__ double rr_block_sum(double v, double* red) {
-    red[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-        __syncthreads();
-    }
-    double r = red[0];
-    __syncthreads();
-    return r;
-}
+int64_t dense_precond_part_size(int64_t nH, int k) { return (int64_t)kPcSplit * nH * k; }
 
-__global__ void __launch_bounds__(kRRThreads) k_rr_small(int ns, int k, const double* GA, const double* GB,
-                                                         double pivot_tol, double* Y, double* theta, int* status) {
-    extern __shared__ double sm[];
-    double* L = sm;                              // G, then its Cholesky factor (lower)
-    double* A = L + kRRMax * kRRLd;              // H, then L^-1 H, then reused for V
-    double* C = A + kRRMax * kRRLd;              // Hr = L^-1 H L^-T (Jacobi works here)
-    double* cs = C + kRRMax * kRRLd;             // rotation cosines [kRRMax/2]
-    double* sn = cs + kRRMax;                    // rotation sines
-    double* ev = sn + kRRMax;                    // eigenvalues
-    double* red = ev + 2 * kRRMax;               // reduction scratch [blockDim]
-    int* pr = reinterpret_cast<int*>(red + kRRThreads);  // pair p per slot
-    int* qr = pr + kRRMax;                               // pair q per slot
-    int* flag = qr + kRRMax;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    // ---- load and symmetrise
-    for (int e = tid; e < ns * ns; e += nt) {
-        const int i = e / ns, j = e % ns;
-        L[i * kRRLd + j] = 0.5 * (GB[i * ns + j] + GB[j * ns + i]);
-        A[i * kRRLd + j] = 0.5 * (GA[i * ns + j] + GA[j * ns + i]);
+void launch_dense_precond(int64_t nH, int64_t m, int k, const float* T, const double* R, const double* Dinv,
+                          float* part, double* W, cudaStream_t s) {
+    if (k > kPcK) fail(NAS_E_INVALID_ARG, "dense preconditioner: more than 32 block columns");
+    if (m <= 0) return;
+    if (nH > 0) {
+        dim3 grid((unsigned)((nH + kPcRows - 1) / kPcRows), kPcSplit);
+        k_dense_precond_part<<<grid, 256, 0, s>>>(nH, k, T, R, part);
+        NAS_CHECK_LAUNCH();
     }
-    if (tid == 0) flag[0] = 0;
-    __syncthreads();
-    double gmax = 0.0;
-    for (int i = 0; i < ns; ++i) gmax = fmax(gmax, L[i * kRRLd + i]);
-    // ---- Cholesky (right-looking)
-    for (int j = 0; j < ns; ++j) {
-        if (tid == 0) {
-            const double piv = L[j * kRRLd + j];
-            if (!(piv >= pivot_tol * gmax) || !(piv > 0.0)) flag[0] = 1;
-            L[j * kRRLd + j] = sqrt(fmax(piv, 0.0));
-        }
-        __syncthreads();
-        if (flag[0]) {
-            if (tid == 0) *status = 1;
-            return;
-        }
-        const double d = L[j * kRRLd + j];
-        for (int i = j + 1 + tid; i < ns; i += nt) L[i * kRRLd + j] /= d;
-        __syncthreads();
-        const int r = ns - j - 1;
-        for (int e = tid; e < r * r; e += nt) {
-            const int i = j + 1 + e / r, l = j + 1 + e % r;
-            if (l <= i) L[i * kRRLd + l] -= L[i * kRRLd + j] * L[l * kRRLd + j];
-        }
-        __syncthreads();
-    }
-    // ---- A <- L^-1 A (forward substitution, all columns at once)
-    for (int i = 0; i < ns; ++i) {
-        for (int c = tid; c < ns; c += nt) {
-            double s = A[i * kRRLd + c];
-            for (int p = 0; p < i; ++p) s -= L[i * kRRLd + p] * A[p * kRRLd + c];
-            A[i * kRRLd + c] = s / L[i * kRRLd + i];
-        }
-        __syncthreads();
-    }
-    // ---- C <- L^-1 A^T  (= L^-1 H L^-T)
-    for (int i = 0; i < ns; ++i) {
-        for (int c = tid; c < ns; c += nt) {
-            double s = A[c * kRRLd + i];
-            for (int p = 0; p < i; ++p) s -= L[i * kRRLd + p] * C[p * kRRLd + c];
-            C[i * kRRLd + c] = s / L[i * kRRLd + i];
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < ns * ns; e += nt) {
-        const int i = e / ns, j = e % ns;
-        if (j < i) {
-            const double v = 0.5 * (C[i * kRRLd + j] + C[j * kRRLd + i]);
-            C[i * kRRLd + j] = v;
-            C[j * kRRLd + i] = v;
-        }
-    }
-    // ---- V <- I (in A)
-    for (int e = tid; e < ns * ns; e += nt) A[(e / ns) * kRRLd + e % ns] = (e / ns == e % ns) ? 1.0 : 0.0;
-    __syncthreads();
-    // ---- cyclic Jacobi, round-robin pairs over n2 = ns rounded up to even
-    const int n2 = ns + (ns & 1);
-    const int half = n2 / 2;
-    double fro2 = 0.0;
-    {
-        double s = 0.0;
-        for (int e = tid; e < ns * ns; e += nt) {
-            const double v = C[(e / ns) * kRRLd + e % ns];
-            s += v * v;
-        }
-        fro2 = rr_block_sum(s, red);
-    }
-    bool converged = false;
-    for (int sweep = 0; sweep < 30 && !converged; ++sweep) {
-        double off = 0.0;
-        for (int e = tid; e < ns * ns; e += nt) {
-            const int i = e / ns, j = e % ns;
-            if (i != j) off += C[i * kRRLd + j] * C[i * kRRLd + j];
-        }
-        off = rr_block_sum(off, red);
-        if (off <= 1e-28 * fro2) {  // off-diagonal norm <= 1e-14 of the Frobenius norm
-            converged = true;
-            break;
-        }
-        for (int round = 0; round < n2 - 1; ++round) {
-            // pairs of this round: slot 0 pairs the fixed index n2-1 with `round`;
-            // slot t pairs (round + t) and (round - t) mod (n2 - 1)
-            for (int t = tid; t < half; t += nt) {
-                int p, q;
-                if (t == 0) {
-                    p = round;
-                    q = n2 - 1;
-                } else {
-                    p = (round + t) % (n2 - 1);
-                    q = (round - t + (n2 - 1)) % (n2 - 1);
-                }
-                if (p > q) {
-                    const int x = p;
-                    p = q;
-                    q = x;
-                }
-                double c = 1.0, s = 0.0;
-                if (q < ns) {
-                    const double apq = C[p * kRRLd + q];
-                    if (apq != 0.0) {
-                        const double app = C[p * kRRLd + p], aqq = C[q * kRRLd + q];
-                        const double zeta = (aqq - app) / (2.0 * apq);
-                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
-                        s = c * tt;
-                    }
-                }
-                pr[t] = p;
-                qr[t] = q;
-                cs[t] = c;
-                sn[t] = s;
-            }
-            __syncthreads();
-            // rows p, q of C
-            for (int e = tid; e < half * ns; e += nt) {
-                const int t = e / ns, j = e % ns;
-                const int p = pr[t], q = qr[t];
-                if (q >= ns || sn[t] == 0.0) continue;
-                const double c = cs[t], s = sn[t];
-                const double a = C[p * kRRLd + j], b = C[q * kRRLd + j];
-                C[p * kRRLd + j] = c * a - s * b;
-                C[q * kRRLd + j] = s * a + c * b;
-            }
-            __syncthreads();
-            // columns p, q of C and of V
-            for (int e = tid; e < half * ns; e += nt) {
-                const int t = e / ns, j = e % ns;
-                const int p = pr[t], q = qr[t];
-                if (q >= ns || sn[t] == 0.0) continue;
-                const double c = cs[t], s = sn[t];
-                const double a = C[j * kRRLd + p], b = C[j * kRRLd + q];
-                C[j * kRRLd + p] = c * a - s * b;
-                C[j * kRRLd + q] = s * a + c * b;
-                const double va = A[j * kRRLd + p], vb = A[j * kRRLd + q];
-                A[j * kRRLd + p] = c * va - s * vb;
-                A[j * kRRLd + q] = s * va + c * vb;
-            }
-            __syncthreads();
-        }
-    }
-    if (!converged) {
-        if (tid == 0) *status = 2;
-        return;
-    }
-    // ---- lowest k eigenpairs in ascending order (rank of each diagonal entry)
-    for (int i = tid; i < ns; i += nt) {
-        const double v = C[i * kRRLd + i];
-        int rank = 0;
-        for (int j = 0; j < ns; ++j) {
-            const double w = C[j * kRRLd + j];
-            rank += (w < v || (w == v && j < i)) ? 1 : 0;
-        }
-        if (rank < k) {
-            ev[rank] = v;
-            pr[rank] = i;
-        }
-    }
-    __syncthreads();
-    // ---- Y = L^-T Z (backward substitution, k columns in parallel); Y [ns][k]
-    for (int i = ns - 1; i >= 0; --i) {
-        for (int c = tid; c < k; c += nt) {
-            double s = A[i * kRRLd + pr[c]];
-            for (int p = i + 1; p < ns; ++p) s -= L[p * kRRLd + i] * Y[p * k + c];
-            Y[i * k + c] = s / L[i * kRRLd + i];
-        }
-        __syncthreads();
-    }
-    for (int c = tid; c < k; c += nt) theta[c] = ev[c];
-    if (tid == 0) *status = 0;
-}
-
-void launch_rr_small(int ns, int k, const double* GA, const double* GB, double pivot_tol, double* Y, double* theta,
-                     int* status, cudaStream_t s) {
-    if (ns > kRRMax || k > ns || k < 1) fail(NAS_E_INVALID_ARG, "device Rayleigh-Ritz size");
-    static std::mutex mu;
-    static bool attr_set[64] = {false};
-    int dev = 0;
-    NAS_CUDA(cudaGetDevice(&dev));
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (dev < 0 || dev >= 64) fail(NAS_E_INVALID_ARG, "device id");
-        if (!attr_set[dev]) {
-            NAS_CUDA(cudaFuncSetAttribute(k_rr_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)rr_device_smem_bytes()));
-            attr_set[dev] = true;
-        }
-    }
-    k_rr_small<<<1, kRRThreads, rr_device_smem_bytes(), s>>>(ns, k, GA, GB, pivot_tol, Y, theta, status);
+    k_dense_precond_sum<<<grid_of(m * k, 256), 256, 0, s>>>(nH, m, k, part, R, Dinv, W);
     NAS_CHECK_LAUNCH();
 }
 

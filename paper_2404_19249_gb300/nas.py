@@ -40,7 +40,7 @@ class nas_options(C.Structure):
         ("hartree", C.c_int), ("xc", C.c_int), ("multipole", C.c_int), ("omega", C.c_double),
         ("check_every", C.c_int), ("timing", C.c_int), ("eig_dense_max", C.c_int),
         ("eig_tol", C.c_double), ("spmv_lanes", C.c_int), ("poisson_two_level", C.c_int),
-        ("precision", C.c_int), ("eig_device", C.c_int), ("eig_adapt", C.c_double),
+        ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
         ("poisson_adaptive", C.c_int),
     ]
 

@@ -218,14 +218,15 @@ def test_benchmark_molecule_first_step(nasmod):
     s.close()
 
 
-@pytest.mark.parametrize("eig_device", [0, 1], ids=["host_lobpcg", "device_lobpcg"])
-def test_lobpcg_path_matches_oracle(nasmod, eig_device):
+@pytest.mark.parametrize("eig_device,eig_precond", [(0, 0), (1, 0), (1, 1)],
+                         ids=["host_lobpcg", "device_lobpcg_diag", "device_lobpcg_coarse_stiffness"])
+def test_lobpcg_path_matches_oracle(nasmod, eig_device, eig_precond):
     """The warm-started LOBPCG eigensolvers used for large coarse spaces (host
     block vectors, or device block vectors with a host Rayleigh-Ritz) give the
     same steps as the oracle's dense generalized eigensolver."""
     inst = _tight(make_instance("paper_molecule", molecule="c6h6", cells=8, coarse_cells=4))
     P = Problem(inst)
-    s = nasmod.Solver(inst, eig_dense_max=0, eig_tol=1e-12, eig_device=eig_device)
+    s = nasmod.Solver(inst, eig_dense_max=0, eig_tol=1e-12, eig_device=eig_device, eig_precond=eig_precond)
     s.init()
     st = P.initial_state()
     assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG

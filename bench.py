@@ -60,6 +60,7 @@ def parse():
                    help="LOBPCG preconditioner: 1 = inverse coarse stiffness on the coarse rows, 0 = diagonal")
     p.add_argument("--eig-adapt", type=float, default=1e-2,
                    help="adaptive LOBPCG tolerance factor (x previous inner-SCF residual)")
+    p.add_argument("--poisson-sell", type=int, default=1, help="1: sliced-ELL Poisson SpMV, 0: CSR")
     p.add_argument("--poisson-adaptive", type=int, default=1,
                    help="1: inner Poisson tolerance follows the density residual (fixed point unchanged)")
     return p.parse_args()
@@ -80,13 +81,14 @@ def kernel_source_hash(name):
     return hashlib.sha256(open(os.path.join(ROOT, "paper_2404_19249_gb300", "csrc", name), "rb").read()).hexdigest()
 
 
-def spmv_traffic(sz):
-    """DRAM bytes per full-size k_pcg1_spmv launch from the committed ncu capture
-    (profiles/traffic.json: a smaller mesh of the same workload, scaled by nnz,
-    since the CSR stream grows with nnz); None when the kernel source changed
-    after the capture or no capture is recorded."""
+def spmv_traffic(sz, kernel="k_pcg1_spmv"):
+    """DRAM bytes per full-size launch of the Poisson SpMV kernel from the
+    committed ncu capture (profiles/traffic.json: a smaller mesh of the same
+    workload, scaled by nnz, since the matrix stream grows with nnz); None
+    when the kernel source changed after the capture or no capture is
+    recorded."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_pcg1_spmv"]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
     except Exception:
         return None
     if rec.get("source_sha256") != kernel_source_hash("kernels_pcg1.cu"):
@@ -330,7 +332,8 @@ def main():
     t0 = time.time()
     s = nas.Solver(inst, device=local, stream=stream, timing=1, tol_poisson=args.tol_poisson,
                    tol_bvp=args.tol_bvp, check_every=4, spmv_lanes=args.spmv_lanes,
-                   poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt, eig_precond=args.eig_precond)
+                   poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt, eig_precond=args.eig_precond,
+                   poisson_sell=args.poisson_sell)
     s.init()
     setup_s = time.time() - t0
     sz = s.sizes()
@@ -445,12 +448,16 @@ def main():
     # Poisson solve (library timing mode), over the timed steps
     sp_ms = sum(rp.poisson_spmv_ms for rp in reps)
     sp_n = int(sum(rp.poisson_spmv_launches for rp in reps))
-    sp_bytes = 12.0 * sz["nnz"] + 20.0 * sz["n"] + 4.0   # val+col, row_ptr, p once, q written
+    sp_bytes = 12.0 * sz["nnz"] + 20.0 * sz["n"] + 4.0   # val+col, row_ptr, p once, q written (CSR count)
     sp_ms_launch = sp_ms / max(sp_n, 1)
     sp_gbs = sp_bytes / (sp_ms_launch * 1e-3) / 1e9 if sp_ms > 0 else 0.0
-    roof_spmv = {"kernel": "k_pcg1_spmv (CSR SpMV of the Poisson PCG, FP64)",
+    sell = sz.get("sell", 0) if args.poisson_sell else 0
+    sp_name = "k_pcg1_spmv_sell" if sell else "k_pcg1_spmv"
+    roof_spmv = {"kernel": ("k_pcg1_spmv_sell (sliced-ELL SpMV of the Poisson PCG, FP64; %d stored entries, "
+                            "%.1f %% padding)" % (sell, 100.0 * (sell / sz["nnz"] - 1.0)))
+                 if sell else "k_pcg1_spmv (CSR SpMV of the Poisson PCG, FP64)",
                  "bound": "hbm", "achieved": sp_gbs, "peak": hbm_peak, "unit": "GB/s",
-                 "frac": sp_gbs / hbm_peak, "traffic": spmv_traffic(sz), "peak_source": peak_src,
+                 "frac": sp_gbs / hbm_peak, "traffic": spmv_traffic(sz, sp_name), "peak_source": peak_src,
                  "algorithmic_bytes_per_launch": sp_bytes, "launches": sp_n, "ms_per_launch": sp_ms_launch,
                  "timing": "CUDA events on the library stream around the SpMV of the first two iterations "
                            "of every Poisson solve (direct launches; the rest replays from a CUDA graph)"}

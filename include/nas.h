@@ -97,6 +97,10 @@ typedef struct nas_options {
     double eig_adapt;      /* factor of the adaptive LOBPCG tolerance (eig_tol <= 0):
                               eig_adapt x the previous inner-SCF residual, clamped
                               to [1e-11, 1e-4]                                     */
+    int    poisson_sell;   /* 1: the FP64 Poisson SpMV reads a sliced-ELL copy of K
+                              (32 rows per slice, one thread per row, coalesced
+                              value/column loads); 0: the CSR kernel with
+                              spmv_lanes lanes per row                             */
     int    poisson_adaptive; /* 1: inside the inner SCF the Poisson tolerance follows
                               the previous density residual res:
                               max(tol_poisson, min(1e-6, 1e-3 res)); 0: always
@@ -109,7 +113,7 @@ typedef struct nas_options {
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
- * eig_adapt = 1e-3, poisson_adaptive = 0. */
+ * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -231,7 +235,8 @@ int nas_solve(nas_ctx* ctx, nas_report* rep);
 enum nas_quantity {
     NAS_Q_SIZES = 0,      /* int64[16]: n_dof, nnz, n_coarse_dof, coarse_nnz, n_elem,
                              n_quad_per_elem, n_node, n_orb, n_boundary, nnz_boundary,
-                             n_vert, order, n_coarse_elem, 0...                       */
+                             n_vert, order, n_coarse_elem, sliced-ELL entries of K
+                             (padding included), 0...                               */
     NAS_Q_EIGVALS,        /* FP64 [N]                                                */
     NAS_Q_ORBITALS,       /* FP64 [n_dof][N]  Psi (fine interior values)              */
     NAS_Q_RHO_IN,         /* FP64 [n_elem][nq] density defining the potential         */

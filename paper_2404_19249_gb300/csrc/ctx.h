@@ -15,7 +15,7 @@
 
 // identity of a captured Poisson PCG graph (its baked-in pointers and parameters)
 struct Pcg1Key {
-    static const int kPtrs = 11;
+    static const int kPtrs = 12;
     const void* ptr[kPtrs] = {};
     double tol = 0.0;
     int lanes = 0;
@@ -99,6 +99,10 @@ struct nas_ctx {
     nas::DBuf<double> d_moments;
     nas::DBuf<double> d_pcg1_part, d_pcg1_scal;        // fused Poisson PCG scratch
     nas::DBuf<double> d_khinv, d_khvec;                // two-level preconditioner: K_H^-1, [c ; y]
+    nas::DBuf<int64_t> d_sell_ptr;                     // sliced-ELL copy of K (Poisson SpMV)
+    nas::DBuf<int32_t> d_sell_col;
+    nas::DBuf<double> d_sell_val;
+    int64_t sell_slices = 0, sell_entries = 0;
     nas::DBuf<int> d_pcg1_flags;
     cudaStream_t cap_stream = nullptr;                 // private stream for graph capture
     cudaGraphExec_t pcg1_exec = nullptr;

@@ -219,6 +219,11 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     // captured graph does not depend on the tolerance
     st.tol2 = 1.0;
     const bool two_level = c->opt.poisson_two_level && c->d_khinv.p && A.val == c->d_K.p;
+    if (c->opt.poisson_sell && A.val == c->d_K.p && c->d_sell_ptr.p) {
+        st.sell_ptr = c->d_sell_ptr.p;
+        st.sell_col = c->d_sell_col.p;
+        st.sell_val = c->d_sell_val.p;
+    }
     if (two_level) {
         st.two_level = 1;
         st.nH = c->nH;
@@ -262,7 +267,7 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     const int lanes = pcg1_lanes(c);
     Pcg1Key key;
     const void* ptrs[Pcg1Key::kPtrs] = {A.val, A.rowptr, x, Dinv, st.r, st.part_pq, st.scal, st.active, st.khinv,
-                                        st.cvec, st.cpart};
+                                        st.cvec, st.cpart, st.sell_val};
     for (int i = 0; i < Pcg1Key::kPtrs; ++i) key.ptr[i] = ptrs[i];
     key.tol = 1.0;
     key.lanes = lanes;
@@ -427,7 +432,7 @@ static int pcg1_mixed_solve(nas_ctx* c, const double* b, double* x, double tol, 
         st.tol2 = 1.0f;
         Pcg1Key key;
         const void* ptrs[Pcg1Key::kPtrs] = {st.val, st.rowptr, st.x, st.dinv, st.r, st.part_pq, st.scal, st.active,
-                                            st.khinv, st.cvec, st.cpart};
+                                            st.khinv, st.cvec, st.cpart, st.sell_val};
         for (int i = 0; i < Pcg1Key::kPtrs; ++i) key.ptr[i] = ptrs[i];
         key.tol = 1.0;
         key.lanes = lanes;
@@ -1083,6 +1088,25 @@ void ctx_setup(nas_ctx* c) {
     c->d_coef.alloc(c->nqt);
     assemble_vext(c);
     launch_inv_diag(fcsr(c, c->d_K.p), c->d_Kdinv.p, s);
+    // sliced-ELL copy of K for the Poisson SpMV (32 rows per slice)
+    {
+        const int64_t nsl = (F.n + 31) / 32;
+        std::vector<int64_t> sp(nsl + 1, 0);
+        for (int64_t sl = 0; sl < nsl; ++sl) {
+            int64_t w = 0;
+            for (int64_t r = sl * 32; r < std::min<int64_t>(F.n, sl * 32 + 32); ++r)
+                w = std::max<int64_t>(w, F.rowptr[r + 1] - F.rowptr[r]);
+            sp[sl + 1] = sp[sl] + 32 * w;
+        }
+        c->sell_slices = nsl;
+        c->d_sell_ptr.upload(sp, s);
+        c->d_sell_col.alloc(std::max<int64_t>(1, sp[nsl]));
+        c->d_sell_val.alloc(std::max<int64_t>(1, sp[nsl]));
+        launch_sell_fill(F.n, c->d_rowptr.p, c->d_col.p, c->d_K.p, c->d_sell_ptr.p, nsl, c->d_sell_col.p,
+                         c->d_sell_val.p, s);
+        c->sell_entries = sp[nsl];
+        sync(c);
+    }
     // ---- transfer I_H^h by point location (Algorithm 1)
     {
         Phase t(c, NAS_PH_TRANSFER);
@@ -1433,6 +1457,7 @@ void ctx_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {
             v[10] = c->F.nv;
             v[11] = c->F.order;
             v[12] = c->C.ne;
+            v[13] = c->sell_entries;
         }
         put_host(v, sizeof(v));
         return;

@@ -1,13 +1,14 @@
 // Device LOBPCG (Knyazev 2001) for the arrow-structured small pencil of
-// Algorithm 3: the same iteration as the host solver (diagonal preconditioner
-// diag(A - sigma B)^-1, W orthogonalised against X and B-normalised, exact
-// recomputation of A and B times the new X and P), with every column kept
-// active and the convergence test taken from the residual norms that travel
-// with the Gram matrices.  The Rayleigh-Ritz step of the (3k)^2 Grams runs on
-// the host (Cholesky, or the two-pass eigen-decomposition that drops
-// near-dependent directions): GB300 executes 2 FP64 FMA per clock per SM, so
-// a one-block FP64 dense eigensolver is about ten times slower than one host
-// core (measured: 9.8 ms against ~0.9 ms for 78 columns).
+// Algorithm 3: the same iteration as the host solver (preconditioned
+// residuals, W orthogonalised against X and B-normalised, exact
+// recomputation of A and B times the new X and P, soft locking: converged
+// wanted columns get no new search direction).  Two host round trips per
+// iteration: the residual norms (convergence test, active columns) and the
+// Rayleigh-Ritz step of the Gram matrices, which runs on the host (Cholesky,
+// or the two-pass eigen-decomposition that drops near-dependent directions):
+// GB300 executes 2 FP64 FMA per clock per SM, so a one-block FP64 dense
+// eigensolver is about ten times slower than one host core (measured: 9.8 ms
+// against ~0.9 ms for 78 columns).
 #include "eig_dev.h"
 
 #include <algorithm>
@@ -31,25 +32,25 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         theta.alloc(k);
         nrm.alloc(4 * k);
         int64_t gp = std::max<int64_t>({gram_tiles_partial_size(m, kmax3, kmax3),
-                                        gram_tiles_partial_size(A.nH, std::max(1, A.Na), k),
+                                        gram_tiles_partial_size(A.nH, 2 * std::max(1, A.Na), k),
                                         reduce_partial_size(3 * k)});
         gpart.alloc(gp);
-        gtmp.alloc(std::max(1, A.Na) * (int64_t)k);
+        gtmp.alloc(2 * std::max(1, A.Na) * (int64_t)k);
         GA.alloc((int64_t)kmax3 * kmax3);
         GB.alloc((int64_t)kmax3 * kmax3);
         Y.alloc((int64_t)kmax3 * k);
         C.alloc((int64_t)k * k);
+        Yp.alloc((int64_t)2 * k * k);
+        actd.alloc(k);
         m_cap = m;
         k_cap = k;
     }
     if (TH) ppart.ensure(std::max<int64_t>(1, dense_precond_part_size(A.nH, k)));
     double *X = bufs[0].p, *AX = bufs[1].p, *BX = bufs[2].p, *W = bufs[3].p, *AW = bufs[4].p, *BW = bufs[5].p;
     double *P = bufs[6].p, *AP = bufs[7].p, *BP = bufs[8].p, *X2 = bufs[9].p, *P2 = bufs[10].p;
-    auto applyA = [&](int w, const double* in, double* out) {
-        launch_arrow_apply(A, w, in, out, gpart.p, gtmp.p, s);
-    };
-    auto applyB = [&](int w, const double* in, double* out) {
-        launch_arrow_apply(B, w, in, out, gpart.p, gtmp.p, s);
+    // A and B share the coarse pattern: both products in one pass over the input
+    auto applyAB = [&](int w, const double* in, double* outA, double* outB) {
+        launch_arrow_apply2(A, B, w, in, outA, outB, gpart.p, gtmp.p, s);
     };
     std::vector<double> hG, hH, hY, th, th_new, hn(3 * (size_t)k);
     // Rayleigh-Ritz on the basis S (ns columns): Grams on the device, the rest on the host
@@ -85,31 +86,35 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         fetch(ns, norms);
         return rr_host(ns, th_out);
     };
-    // ---- start: warm vectors for the wanted columns, deterministic pseudo-random otherwise
+    // ---- start: warm vectors for the wanted columns, deterministic pseudo-random
+    // otherwise (generated once per (m, k) and kept on the device)
     {
-        std::vector<double> X0((size_t)m * k);
-        for (int64_t i = 0; i < m; ++i)
-            for (int j = 0; j < k; ++j) {
-                double r = std::sin(12.9898 * (i + 1) + 78.233 * (j + 1)) * 43758.5453;
-                X0[i * k + j] = r - std::floor(r) - 0.5;
-            }
-        NAS_CUDA(cudaMemcpyAsync(X, X0.data(), sizeof(double) * m * k, cudaMemcpyHostToDevice, s));
+        if (x0_m != m || x0_k != k) {
+            std::vector<double> h((size_t)m * k);
+            for (int64_t i = 0; i < m; ++i)
+                for (int j = 0; j < k; ++j) {
+                    double r = std::sin(12.9898 * (i + 1) + 78.233 * (j + 1)) * 43758.5453;
+                    h[i * k + j] = r - std::floor(r) - 0.5;
+                }
+            X0.alloc(m * k);
+            NAS_CUDA(cudaMemcpyAsync(X0.p, h.data(), sizeof(double) * m * k, cudaMemcpyHostToDevice, s));
+            NAS_CUDA(cudaStreamSynchronize(s));  // the host copy must outlive the upload
+            x0_m = m;
+            x0_k = k;
+        }
+        NAS_CUDA(cudaMemcpyAsync(X, X0.p, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, s));
         if (U0)
             NAS_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * k, U0, sizeof(double) * nev, sizeof(double) * nev, m,
                                        cudaMemcpyDeviceToDevice, s));
-        // the host copy must outlive the asynchronous upload
-        NAS_CUDA(cudaStreamSynchronize(s));
     }
-    applyA(k, X, AX);
-    applyB(k, X, BX);
+    applyAB(k, X, AX, BX);
     {
         ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
         grams(S, AS, BS);
         if (rr(k, false, th) != 0) return -1;
         launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
         std::swap(X, X2);
-        applyA(k, X, AX);
-        applyB(k, X, BX);
+        applyAB(k, X, AX, BX);
     }
     {
         const double sigma = th[0] - 0.1 * std::fabs(th[0]) - 1.0;
@@ -117,81 +122,95 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
     }
     int np = 0;
     int it = 0;
+    std::vector<int> act;
+    std::vector<double> hYp;
     for (; it < maxit; ++it) {
-        // W = T (AX - BX theta); residual norms of the current X.  With a dense
-        // coarse block the residual goes to X2 (free until the update below).
-        double* R = TH ? X2 : W;
+        // residual R = AX - BX theta of the current X (into X2, free until the
+        // update below) and its norms: one round trip decides convergence and
+        // the active columns (soft locking: unconverged wanted columns and
+        // every guard column get a new search direction)
+        double* R = X2;
         launch_eig_resid(m, k, AX, BX, theta.p, R, s);
         {
             const double* Xs[3] = {R, AX, BX};
             launch_coldots(m, k, 3, Xs, Xs, nullptr, gpart.p, nrm.p, s);
         }
-        if (TH)
-            launch_dense_precond(A.nH, m, k, TH, R, T.p, ppart.p, W, s);
-        else
-            launch_scale_rows(m, k, T.p, W, W, s);
-        // W <- W - X (BX^T W), then unit B-norm columns
-        launch_gram_tiles(m, ColBlocks::one(BX, k, k), ColBlocks::one(W, k, k), gpart.p, C.p, s);
-        launch_cols_mult(m, ColBlocks::one(X, k, k), C.p, k, -1.0, 1.0, W, s);
-        applyB(k, W, BW);
-        {
-            const double* Xs[1] = {W};
-            const double* Ys[1] = {BW};
-            launch_coldots(m, k, 1, Xs, Ys, nullptr, gpart.p, nrm.p + 3 * k, s);
-        }
-        launch_inv_sqrt_scale(m, k, nrm.p + 3 * k, W, BW, nullptr, s);
-        applyA(k, W, AW);
-        ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
-        S.add(W, k, k);
-        AS.add(AW, k, k);
-        BS.add(BW, k, k);
-        if (np > 0) {
-            S.add(P, k, np);
-            AS.add(AP, k, np);
-            BS.add(BP, k, np);
-        }
-        const int ns = S.ncols();
-        grams(S, AS, BS);
-        // the Rayleigh-Ritz runs before the convergence test of the current
-        // X (its norms arrive with the same round trip); if X has converged
-        // the new coefficients are simply not used
-        const int rr_status = rr(ns, true, th_new);
+        NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
+        NAS_CUDA(cudaStreamSynchronize(s));
         double worst = 0.0;
-        for (int j = 0; j < nev; ++j) {
-            const double rel = std::sqrt(std::max(hn[j], 0.0)) /
-                               (std::sqrt(std::max(hn[k + j], 0.0)) +
-                                std::fabs(th[j]) * std::sqrt(std::max(hn[2 * k + j], 0.0)) + 1e-300);
-            worst = std::max(worst, rel);
+        std::vector<double> rel(k);
+        for (int j = 0; j < k; ++j) {
+            rel[j] = std::sqrt(std::max(hn[j], 0.0)) /
+                     (std::sqrt(std::max(hn[k + j], 0.0)) +
+                      std::fabs(th[j]) * std::sqrt(std::max(hn[2 * k + j], 0.0)) + 1e-300);
+            if (j < nev) worst = std::max(worst, rel[j]);
         }
         if (!std::isfinite(worst)) return -1;
         if (worst <= tol) break;
-        if (rr_status != 0) {
+        act.clear();
+        for (int j = 0; j < k; ++j)
+            if (j >= nev || rel[j] > 0.1 * tol) act.push_back(j);
+        const int ka = (int)act.size();
+        NAS_CUDA(cudaMemcpyAsync(actd.p, act.data(), sizeof(int) * ka, cudaMemcpyHostToDevice, s));
+        // W = T R(:, act)
+        launch_gather_cols(m, k, ka, actd.p, R, P2, s);
+        if (TH)
+            launch_dense_precond(A.nH, m, ka, TH, P2, T.p, ppart.p, W, s);
+        else
+            launch_scale_rows(m, ka, T.p, P2, W, s);
+        // W <- W - X (BX^T W), then unit B-norm columns (AW scaled alike)
+        launch_gram_tiles(m, ColBlocks::one(BX, k, k), ColBlocks::one(W, ka, ka), gpart.p, C.p, s);
+        launch_cols_mult(m, ColBlocks::one(X, k, k), C.p, ka, -1.0, 1.0, W, s);
+        applyAB(ka, W, AW, BW);
+        {
+            const double* Xs[1] = {W};
+            const double* Ys[1] = {BW};
+            launch_coldots(m, ka, 1, Xs, Ys, nullptr, gpart.p, nrm.p + 3 * k, s);
+        }
+        launch_inv_sqrt_scale(m, ka, nrm.p + 3 * k, W, BW, AW, s);
+        ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
+        S.add(W, ka, ka);
+        AS.add(AW, ka, ka);
+        BS.add(BW, ka, ka);
+        if (np > 0) {
+            S.add(P, np, np);
+            AS.add(AP, np, np);
+            BS.add(BP, np, np);
+        }
+        const int ns = S.ncols();
+        grams(S, AS, BS);
+        if (rr(ns, false, th_new) != 0) {
             if (np == 0) return -1;
             np = 0;  // restart without P
             continue;
         }
         th.swap(th_new);
-        // new X = S Y; new P = [W, P] part of S Y
+        // new X = S Y; new P = [W, P] part of S Y for the active columns
         launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
         {
-            ColBlocks WP = ColBlocks::one(W, k, k);
-            if (np > 0) WP.add(P, k, np);
-            launch_cols_mult(m, WP, Y.p + (int64_t)k * k, k, 1.0, 0.0, P2, s);
+            const int nwp = ns - k;
+            hYp.assign((size_t)nwp * ka, 0.0);
+            for (int a = 0; a < nwp; ++a)
+                for (int q = 0; q < ka; ++q) hYp[(size_t)a * ka + q] = hY[(size_t)(k + a) * k + act[q]];
+            NAS_CUDA(cudaMemcpyAsync(Yp.p, hYp.data(), sizeof(double) * nwp * ka, cudaMemcpyHostToDevice, s));
+            ColBlocks WP = ColBlocks::one(W, ka, ka);
+            if (np > 0) WP.add(P, np, np);
+            launch_cols_mult(m, WP, Yp.p, ka, 1.0, 0.0, P2, s);
         }
         std::swap(X, X2);
         std::swap(P, P2);
-        np = k;
+        np = ka;
         // exact images (implicitly updated ones drift and break the Rayleigh-Ritz)
-        applyA(k, X, AX);
-        applyB(k, X, BX);
-        applyA(k, P, AP);
-        applyB(k, P, BP);
+        applyAB(k, X, AX, BX);
+        applyAB(np, P, AP, BP);
         {
             const double* Xs[1] = {P};
             const double* Ys[1] = {BP};
-            launch_coldots(m, k, 1, Xs, Ys, nullptr, gpart.p, nrm.p + 3 * k, s);
+            launch_coldots(m, np, 1, Xs, Ys, nullptr, gpart.p, nrm.p + 3 * k, s);
         }
-        launch_inv_sqrt_scale(m, k, nrm.p + 3 * k, P, AP, BP, s);
+        launch_inv_sqrt_scale(m, np, nrm.p + 3 * k, P, AP, BP, s);
+        // the host copies of Y and Yp must outlive their uploads
+        NAS_CUDA(cudaStreamSynchronize(s));
     }
     if (it >= maxit) return -1;
     // final Rayleigh-Ritz within span X for B-orthonormal output

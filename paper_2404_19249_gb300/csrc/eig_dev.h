@@ -1,9 +1,9 @@
 // LOBPCG for the small pencil F_A U = lambda F_B U of Algorithm 3 (eq. st1)
 // with the block vectors on the device.  The arrow-structured products, the
 // residuals, the orthogonalisation and the Gram matrices of the basis
-// [X, W, P] run in device kernels; the host receives the Gram matrices
-// ((3k)^2 numbers, k = nev + nguard) with the residual norms and returns the
-// Rayleigh-Ritz coefficients: one host round trip per iteration.
+// [X, W, P] run in device kernels; the host receives the residual norms
+// (convergence test, active columns) and the Gram matrices (at most (3k)^2
+// numbers, k = nev + nguard) and returns the Rayleigh-Ritz coefficients.
 #pragma once
 
 #include "common.h"
@@ -16,6 +16,11 @@ struct DevLobpcg {
     DBuf<double> bufs[11];
     DBuf<double> T, theta, nrm, gpart, gtmp, GA, GB, Y, C;
     DBuf<float> ppart;    // split partial products of the dense preconditioner
+    DBuf<double> Yp;      // coefficients of the new search directions [2k][k]
+    DBuf<int> actd;       // active (unlocked) block columns
+    DBuf<double> X0;      // pseudo-random start block [m][k]
+    int64_t x0_m = 0;
+    int x0_k = 0;
     int64_t m_cap = 0;
     int k_cap = 0;
     double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)

@@ -223,6 +223,10 @@ struct ColBlocks {
 // G: Na*w doubles of scratch
 void launch_arrow_apply(const ArrowDev& F, int w, const double* X, double* Y, double* partial, double* G,
                         cudaStream_t s);
+// YA = A X and YB = B X for two arrow matrices with the same pattern (X read
+// once); partial: gram_tiles_partial_size(nH, 2 Na, w), G: 2 Na w doubles
+void launch_arrow_apply2(const ArrowDev& A, const ArrowDev& B, int w, const double* X, double* YA, double* YB,
+                         double* partial, double* G, cudaStream_t s);
 // G[a][b] = sum_{i<m} L(i,a) R(i,b) (deterministic); partial scratch of
 // gram_tiles_partial_size(m, ncols(L), ncols(R)) doubles
 int64_t gram_tiles_partial_size(int64_t m, int La, int Rb);
@@ -231,6 +235,8 @@ void launch_gram_tiles(int64_t m, const ColBlocks& L, const ColBlocks& R, double
 // Y[i][j] = alpha sum_a S(i,a) C[a][j] + beta Y[i][j], C row-major [ncols(S)][kout]
 void launch_cols_mult(int64_t m, const ColBlocks& S, const double* C, int kout, double alpha, double beta,
                       double* Y, cudaStream_t s);
+// dst[i][q] = src[i][idx[q]]: columns idx[0..kq) of src [m][k] into dst [m][kq]
+void launch_gather_cols(int64_t m, int k, int kq, const int* idx, const double* src, double* dst, cudaStream_t s);
 // R = AX - BX diag(theta) for [m][k] arrays (theta on the device)
 void launch_eig_resid(int64_t m, int k, const double* AX, const double* BX, const double* theta, double* R,
                       cudaStream_t s);
@@ -276,6 +282,12 @@ struct Pcg1T {
     const T* khinv = nullptr;        // dense K_H^-1 [nH][nH]
     T* cvec = nullptr;               // [nH]
     T* yvec = nullptr;               // [nH]
+    // optional sliced-ELL copy of the matrix (32 rows per slice, column-major
+    // within a slice, zero-padded to the slice's longest row); used for q = A p
+    // when sell_ptr is set
+    const int64_t* sell_ptr = nullptr;  // [n_slices + 1] entry offsets
+    const int32_t* sell_col = nullptr;
+    const T* sell_val = nullptr;
 };
 using Pcg1 = Pcg1T<double>;
 using Pcg1f = Pcg1T<float>;
@@ -288,6 +300,10 @@ void launch_pcg1_iteration(const Pcg1& s, int par, int lanes_per_row, cudaStream
 void launch_pcg1_iteration(const Pcg1f& s, int par, int lanes_per_row, cudaStream_t st, cudaEvent_t ev0 = nullptr,
                            cudaEvent_t ev1 = nullptr);
 int pcg1_kernels_per_iteration(int two_level, int64_t npieces);
+// sliced ELL (32 rows per slice) of a CSR matrix: sell_ptr from the host,
+// columns and values filled on the device (padding: column = row, value 0)
+void launch_sell_fill(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                      const int64_t* sell_ptr, int64_t n_slices, int32_t* sell_col, double* sell_val, cudaStream_t st);
 // z = D^-1 r + I K_H^-1 I^T r and partial sums of r.z (two-level only)
 void launch_pcg1_coarse_correction(const Pcg1& s, cudaStream_t st);
 void launch_pcg1_coarse_correction(const Pcg1f& s, cudaStream_t st);

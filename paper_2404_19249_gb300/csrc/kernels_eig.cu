@@ -138,6 +138,63 @@ void launch_arrow_apply(const ArrowDev& F, int w, const double* X, double* Y, do
     }
 }
 
+// ---- both matrices of the pencil at once (same coarse CSR pattern): YA = A X, YB = B X
+__global__ void k_arrow_rows2(ArrowDev A, ArrowDev B, int w, const double* X, double* YA, double* YB) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.nH * w) return;
+    const int64_t i = t / w;
+    const int j = (int)(t - i * w);
+    double a = 0.0, b = 0.0;
+    for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+        const double x = X[(int64_t)A.col[p] * w + j];
+        a += A.sval[p] * x;
+        b += B.sval[p] * x;
+    }
+    const double* xa = X + A.nH * w + j;
+    for (int q = 0; q < A.Na; ++q) {
+        const double x = xa[(int64_t)q * w];
+        a += A.Bd[i * A.Na + q] * x;
+        b += B.Bd[i * A.Na + q] * x;
+    }
+    YA[t] = a;
+    YB[t] = b;
+}
+
+// border rows of both: G = [Bd_A | Bd_B]^T X_H ([2 Na][w])
+__global__ void k_arrow_border2(ArrowDev A, ArrowDev B, int w, const double* X, const double* G, double* YA,
+                                double* YB) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.Na * w) return;
+    const int a = t / w, j = t - (t / w) * w;
+    double ya = G[t], yb = G[A.Na * w + t];
+    const double* xa = X + A.nH * w + j;
+    for (int q = 0; q < A.Na; ++q) {
+        const double x = xa[(int64_t)q * w];
+        ya += A.Cd[a * A.Na + q] * x;
+        yb += B.Cd[a * A.Na + q] * x;
+    }
+    YA[(A.nH + a) * w + j] = ya;
+    YB[(A.nH + a) * w + j] = yb;
+}
+
+void launch_arrow_apply2(const ArrowDev& A, const ArrowDev& B, int w, const double* X, double* YA, double* YB,
+                         double* partial, double* G, cudaStream_t s) {
+    if (A.ptr != B.ptr || A.col != B.col || A.nH != B.nH || A.Na != B.Na)
+        fail(NAS_E_INVALID_ARG, "arrow pair: the two matrices must share the pattern");
+    if (A.nH > 0) {
+        k_arrow_rows2<<<grid_of(A.nH * w, 256), 256, 0, s>>>(A, B, w, X, YA, YB);
+        NAS_CHECK_LAUNCH();
+    }
+    if (A.Na > 0) {
+        ColBlocks L = ColBlocks::one(A.Bd, A.Na, A.Na);
+        L.add(B.Bd, A.Na, A.Na);
+        ColBlocks R = ColBlocks::one(X, w, w);
+        launch_gram_tiles(A.nH, L, R, partial, G, s);
+        k_arrow_border2<<<grid_of((int64_t)A.Na * w, 128), 128, 0, s>>>(A, B, w, X, G, YA, YB);
+        NAS_CHECK_LAUNCH();
+    }
+}
+
 // ---- Y[i][j] = alpha sum_a S(i,a) C[a][j] + beta Y[i][j]   (Y row-major [m][kout])
 __global__ void k_cols_mult(int64_t m, ColBlocks S, const double* C, int kout, double alpha, double beta, double* Y) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,6 +214,21 @@ void launch_cols_mult(int64_t m, const ColBlocks& S, const double* C, int kout, 
                       double* Y, cudaStream_t s) {
     if (m <= 0 || kout <= 0) return;
     k_cols_mult<<<grid_of(m * kout, 256), 256, 0, s>>>(m, S, C, kout, alpha, beta, Y);
+    NAS_CHECK_LAUNCH();
+}
+
+// ---- dst[i][q] = src[i][idx[q]] (src [m][k], dst [m][kq])
+__global__ void k_gather_cols(int64_t m, int k, int kq, const int* idx, const double* src, double* dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * kq) return;
+    const int64_t i = t / kq;
+    const int q = (int)(t - i * kq);
+    dst[t] = src[i * k + idx[q]];
+}
+
+void launch_gather_cols(int64_t m, int k, int kq, const int* idx, const double* src, double* dst, cudaStream_t s) {
+    if (m * kq <= 0) return;
+    k_gather_cols<<<grid_of(m * kq, 256), 256, 0, s>>>(m, k, kq, idx, src, dst);
     NAS_CHECK_LAUNCH();
 }
 

@@ -95,6 +95,69 @@ __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_spmv(Pcg1T<T> s) {
     block_store_sum(dot, sh, s.part_pq + blockIdx.x);
 }
 
+// q = A p from the sliced-ELL copy: one thread per row (slices of 32 rows, so
+// a warp reads each of its rows' k-th entries as one coalesced segment), two
+// accumulators; blocks stride over the rows; per-block partial sums of p.q
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_spmv_sell(Pcg1T<T> s) {
+    if (!*s.active) return;
+    __shared__ T sh[kPcgThreads];
+    const int64_t* __restrict__ sp = s.sell_ptr;
+    const int32_t* __restrict__ cl = s.sell_col;
+    const T* __restrict__ va = s.sell_val;
+    const T* __restrict__ pv = s.p;
+    T dot = 0;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < s.n;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slice = row >> 5;
+        const int lane = (int)(row & 31);
+        const int64_t b = sp[slice], e = sp[slice + 1];
+        T a0 = 0, a1 = 0;
+        int64_t idx = b + lane;
+        for (; idx + 32 < e; idx += 64) {
+            const int c0 = cl[idx], c1 = cl[idx + 32];
+            const T v0 = va[idx], v1 = va[idx + 32];
+            a0 += v0 * pv[c0];
+            a1 += v1 * pv[c1];
+        }
+        if (idx < e) a0 += va[idx] * pv[cl[idx]];
+        const T acc = a0 + a1;
+        s.q[row] = acc;
+        dot += pv[row] * acc;
+    }
+    block_store_sum(dot, sh, s.part_pq + blockIdx.x);
+}
+
+__global__ void k_sell_fill(int64_t n, int64_t nrows_pad, const int32_t* rowptr, const int32_t* col,
+                            const double* val, const int64_t* sell_ptr, int32_t* sell_col, double* sell_val) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows_pad) return;
+    const int64_t slice = r >> 5;
+    const int lane = (int)(r & 31);
+    const int64_t b = sell_ptr[slice];
+    const int64_t w = (sell_ptr[slice + 1] - b) >> 5;
+    const int64_t p0 = r < n ? rowptr[r] : 0;
+    const int64_t len = r < n ? rowptr[r + 1] - p0 : 0;
+    for (int64_t k = 0; k < w; ++k) {
+        const int64_t idx = b + k * 32 + lane;
+        if (k < len) {
+            sell_col[idx] = col[p0 + k];
+            sell_val[idx] = val[p0 + k];
+        } else {
+            sell_col[idx] = (int32_t)(r < n ? r : 0);
+            sell_val[idx] = 0.0;
+        }
+    }
+}
+
+void launch_sell_fill(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                      const int64_t* sell_ptr, int64_t n_slices, int32_t* sell_col, double* sell_val, cudaStream_t st) {
+    const int64_t rows = n_slices * 32;
+    if (rows <= 0) return;
+    k_sell_fill<<<(int)((rows + 255) / 256), 256, 0, st>>>(n, rows, rowptr, col, val, sell_ptr, sell_col, sell_val);
+    NAS_CHECK_LAUNCH();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_update(Pcg1T<T> s, int par) {
     if (!*s.active) return;
@@ -225,7 +288,9 @@ template <typename T>
 static void pcg1_iteration(const Pcg1T<T>& s, int par, int lpr, cudaStream_t st, cudaEvent_t ev0 = nullptr,
                            cudaEvent_t ev1 = nullptr) {
     if (ev0) NAS_CUDA(cudaEventRecord(ev0, st));
+    if (s.sell_ptr) lpr = 0;
     switch (lpr) {
+        case 0: k_pcg1_spmv_sell<T><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
         case 1: k_pcg1_spmv<T, 1><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
         case 2: k_pcg1_spmv<T, 2><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;
         case 4: k_pcg1_spmv<T, 4><<<kPcgBlocks, kPcgThreads, 0, st>>>(s); break;

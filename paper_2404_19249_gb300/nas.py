@@ -41,7 +41,7 @@ class nas_options(C.Structure):
         ("check_every", C.c_int), ("timing", C.c_int), ("eig_dense_max", C.c_int),
         ("eig_tol", C.c_double), ("spmv_lanes", C.c_int), ("poisson_two_level", C.c_int),
         ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
-        ("poisson_adaptive", C.c_int),
+        ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int),
     ]
 
 
@@ -290,7 +290,7 @@ class Solver:
     def sizes(self):
         v = np.zeros(16, dtype=np.int64)
         nas_get(self.h, NAS_Q_SIZES, v)
-        keys = ["n", "nnz", "nH", "hnnz", "ne", "nq", "nnode", "N", "nb", "nnzb", "nv", "order", "nec"]
+        keys = ["n", "nnz", "nH", "hnnz", "ne", "nq", "nnode", "N", "nb", "nnzb", "nv", "order", "nec", "sell"]
         return {k: int(v[i]) for i, k in enumerate(keys)}
 
     def get(self, what):

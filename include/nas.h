@@ -100,7 +100,8 @@ typedef struct nas_options {
     int    poisson_sell;   /* 1: the FP64 Poisson SpMV reads a sliced-ELL copy of K
                               (32 rows per slice, one thread per row, coalesced
                               value/column loads); 0: the CSR kernel with
-                              spmv_lanes lanes per row                             */
+                              spmv_lanes lanes per row (the FP32 inner solve of
+                              precision = 1 always uses the CSR kernel)            */
     int    poisson_adaptive; /* 1: inside the inner SCF the Poisson tolerance follows
                               the previous density residual res:
                               max(tol_poisson, min(1e-6, 1e-3 res)); 0: always
@@ -132,6 +133,8 @@ enum nas_phase {
     NAS_PH_SPMV,           /* SpMV launches (N = 1, Poisson and Dirichlet lift)      */
     NAS_PH_EIG_RR,         /* host Rayleigh-Ritz inside the device LOBPCG (subset of
                               NAS_PH_HOST_EIG)                                      */
+    NAS_PH_EIG_WAIT,       /* host time blocked in stream synchronisations inside the
+                              device LOBPCG (subset of NAS_PH_HOST_EIG)            */
     NAS_PH_COUNT
 };
 

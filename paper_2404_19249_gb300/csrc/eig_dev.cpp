@@ -53,6 +53,12 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         launch_arrow_apply2(A, B, w, in, outA, outB, gpart.p, gtmp.p, s);
     };
     std::vector<double> hG, hH, hY, th, th_new, hn(3 * (size_t)k);
+    // stream synchronisation, timed (host time spent waiting for the device)
+    auto wait = [&]() {
+        auto t0 = std::chrono::steady_clock::now();
+        NAS_CUDA(cudaStreamSynchronize(s));
+        wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    };
     // Rayleigh-Ritz on the basis S (ns columns): Grams on the device, the rest on the host
     auto grams = [&](const ColBlocks& S, const ColBlocks& AS, const ColBlocks& BS) {
         launch_gram_tiles(m, S, AS, gpart.p, GA.p, s);
@@ -64,7 +70,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         NAS_CUDA(cudaMemcpyAsync(hH.data(), GA.p, sizeof(double) * ns * ns, cudaMemcpyDeviceToHost, s));
         NAS_CUDA(cudaMemcpyAsync(hG.data(), GB.p, sizeof(double) * ns * ns, cudaMemcpyDeviceToHost, s));
         if (norms) NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
-        NAS_CUDA(cudaStreamSynchronize(s));
+        wait();
     };
     // host Rayleigh-Ritz from the fetched Grams (fallback and large ns)
     auto rr_host = [&](int ns, std::vector<double>& th_out) {
@@ -136,7 +142,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
             launch_coldots(m, k, 3, Xs, Xs, nullptr, gpart.p, nrm.p, s);
         }
         NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
-        NAS_CUDA(cudaStreamSynchronize(s));
+        wait();
         double worst = 0.0;
         std::vector<double> rel(k);
         for (int j = 0; j < k; ++j) {
@@ -210,7 +216,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         }
         launch_inv_sqrt_scale(m, np, nrm.p + 3 * k, P, AP, BP, s);
         // the host copies of Y and Yp must outlive their uploads
-        NAS_CUDA(cudaStreamSynchronize(s));
+        wait();
     }
     if (it >= maxit) return -1;
     // final Rayleigh-Ritz within span X for B-orthonormal output

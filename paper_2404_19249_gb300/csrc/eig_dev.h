@@ -24,6 +24,7 @@ struct DevLobpcg {
     int64_t m_cap = 0;
     int k_cap = 0;
     double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)
+    double wait_ms = 0.0; // host time waiting for the device in synchronisations
 
     // Lowest nev pairs.  U0: device [m][nev] warm start or null; Uout: device
     // [m][nev] (B-orthonormal eigenvectors); lam: host [nev].  diag_slot[i] is

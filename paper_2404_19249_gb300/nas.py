@@ -24,7 +24,7 @@ ERRORS = {
 NAS_FINE, NAS_COARSE = 0, 1
 NAS_POT_COULOMB, NAS_POT_SMOOTHED, NAS_POT_HARMONIC = 0, 1, 2
 PHASES = ["assembly", "bvp", "poisson", "blocks", "density", "mixing", "host_eig", "transfer", "spmm", "spmv",
-          "eig_rr"]
+          "eig_rr", "eig_wait"]
 (NAS_Q_SIZES, NAS_Q_EIGVALS, NAS_Q_ORBITALS, NAS_Q_RHO_IN, NAS_Q_RHO_OUT, NAS_Q_VHARTREE, NAS_Q_UHAT,
  NAS_Q_ROWPTR, NAS_Q_COLIDX, NAS_Q_K, NAS_Q_M, NAS_Q_MVEXT, NAS_Q_ANL, NAS_Q_HTILDE, NAS_Q_TRANSFER_ELEM,
  NAS_Q_TRANSFER_COL, NAS_Q_TRANSFER_W, NAS_Q_FA, NAS_Q_FB, NAS_Q_DOF_NODE, NAS_Q_ENERGY) = range(21)

@@ -31,13 +31,12 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         T.alloc(m);
         theta.alloc(k);
         nrm.alloc(4 * k);
-        int64_t gp = std::max<int64_t>({gram_tiles_partial_size(m, kmax3, kmax3),
+        int64_t gp = std::max<int64_t>({gram_tiles_partial_size(m, kmax3, 2 * kmax3),
                                         gram_tiles_partial_size(A.nH, 2 * std::max(1, A.Na), k),
                                         reduce_partial_size(3 * k)});
         gpart.alloc(gp);
         gtmp.alloc(2 * std::max(1, A.Na) * (int64_t)k);
-        GA.alloc((int64_t)kmax3 * kmax3);
-        GB.alloc((int64_t)kmax3 * kmax3);
+        GAB.alloc((int64_t)kmax3 * 2 * kmax3);
         Y.alloc((int64_t)kmax3 * k);
         C.alloc((int64_t)k * k);
         Yp.alloc((int64_t)2 * k * k);
@@ -46,6 +45,22 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         k_cap = k;
     }
     if (TH) ppart.ensure(std::max<int64_t>(1, dense_precond_part_size(A.nH, k)));
+    // pinned staging: [GA | GB] (kmax3 x 2 kmax3), norms (3k), Y (kmax3 k), Yp (2k k), theta (k), active (k ints)
+    const size_t o_ga = 0, o_nrm = o_ga + 2 * (size_t)kmax3 * kmax3,
+                 o_y = o_nrm + 3 * (size_t)k, o_yp = o_y + (size_t)kmax3 * k, o_th = o_yp + 2 * (size_t)k * k,
+                 o_act = o_th + k, pin_need = o_act + k;
+    if (pin_doubles < pin_need) {
+        if (pin) cudaFreeHost(pin);
+        pin = nullptr;
+        NAS_CUDA(cudaMallocHost((void**)&pin, sizeof(double) * pin_need));
+        pin_doubles = pin_need;
+    }
+    double* pGA = pin + o_ga;
+    double* pN = pin + o_nrm;
+    double* pY = pin + o_y;
+    double* pYp = pin + o_yp;
+    double* pTh = pin + o_th;
+    int* pAct = reinterpret_cast<int*>(pin + o_act);
     double *X = bufs[0].p, *AX = bufs[1].p, *BX = bufs[2].p, *W = bufs[3].p, *AW = bufs[4].p, *BW = bufs[5].p;
     double *P = bufs[6].p, *AP = bufs[7].p, *BP = bufs[8].p, *X2 = bufs[9].p, *P2 = bufs[10].p;
     // A and B share the coarse pattern: both products in one pass over the input
@@ -60,17 +75,23 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     };
     // Rayleigh-Ritz on the basis S (ns columns): Grams on the device, the rest on the host
+    // both Grams in one pass: S^T [AS | BS] -> [ns][2 ns], split into GA and GB
     auto grams = [&](const ColBlocks& S, const ColBlocks& AS, const ColBlocks& BS) {
-        launch_gram_tiles(m, S, AS, gpart.p, GA.p, s);
-        launch_gram_tiles(m, S, BS, gpart.p, GB.p, s);
+        ColBlocks R = AS;
+        for (int u = 0; u < BS.nblk; ++u) R.add(BS.p[u], BS.ld[u], BS.w[u]);
+        launch_gram_tiles(m, S, R, gpart.p, GAB.p, s);
     };
     auto fetch = [&](int ns, bool norms) {
-        hG.resize((size_t)ns * ns);
-        hH.resize((size_t)ns * ns);
-        NAS_CUDA(cudaMemcpyAsync(hH.data(), GA.p, sizeof(double) * ns * ns, cudaMemcpyDeviceToHost, s));
-        NAS_CUDA(cudaMemcpyAsync(hG.data(), GB.p, sizeof(double) * ns * ns, cudaMemcpyDeviceToHost, s));
-        if (norms) NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
+        NAS_CUDA(cudaMemcpyAsync(pGA, GAB.p, sizeof(double) * ns * 2 * ns, cudaMemcpyDeviceToHost, s));
+        if (norms) NAS_CUDA(cudaMemcpyAsync(pN, nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
         wait();
+        hH.resize((size_t)ns * ns);
+        hG.resize((size_t)ns * ns);
+        for (int a = 0; a < ns; ++a) {
+            std::copy(pGA + (size_t)a * 2 * ns, pGA + (size_t)a * 2 * ns + ns, hH.begin() + (size_t)a * ns);
+            std::copy(pGA + (size_t)a * 2 * ns + ns, pGA + (size_t)(a + 1) * 2 * ns, hG.begin() + (size_t)a * ns);
+        }
+        if (norms) hn.assign(pN, pN + 3 * (size_t)k);
     };
     // host Rayleigh-Ritz from the fetched Grams (fallback and large ns)
     auto rr_host = [&](int ns, std::vector<double>& th_out) {
@@ -78,8 +99,11 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         int r = rayleigh_ritz_grams(ns, hG, hH, k, hY, th_out);
         rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (r == 0) {
-            NAS_CUDA(cudaMemcpyAsync(Y.p, hY.data(), sizeof(double) * ns * k, cudaMemcpyHostToDevice, s));
-            NAS_CUDA(cudaMemcpyAsync(theta.p, th_out.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+            // from the pinned area: it is rewritten only after the next synchronisation
+            std::copy(hY.begin(), hY.begin() + (size_t)ns * k, pY);
+            std::copy(th_out.begin(), th_out.begin() + k, pTh);
+            NAS_CUDA(cudaMemcpyAsync(Y.p, pY, sizeof(double) * ns * k, cudaMemcpyHostToDevice, s));
+            NAS_CUDA(cudaMemcpyAsync(theta.p, pTh, sizeof(double) * k, cudaMemcpyHostToDevice, s));
         }
         return r;
     };
@@ -141,8 +165,9 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
             const double* Xs[3] = {R, AX, BX};
             launch_coldots(m, k, 3, Xs, Xs, nullptr, gpart.p, nrm.p, s);
         }
-        NAS_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
+        NAS_CUDA(cudaMemcpyAsync(pN, nrm.p, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, s));
         wait();
+        hn.assign(pN, pN + 3 * (size_t)k);
         double worst = 0.0;
         std::vector<double> rel(k);
         for (int j = 0; j < k; ++j) {
@@ -157,7 +182,8 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         for (int j = 0; j < k; ++j)
             if (j >= nev || rel[j] > 0.1 * tol) act.push_back(j);
         const int ka = (int)act.size();
-        NAS_CUDA(cudaMemcpyAsync(actd.p, act.data(), sizeof(int) * ka, cudaMemcpyHostToDevice, s));
+        std::copy(act.begin(), act.end(), pAct);
+        NAS_CUDA(cudaMemcpyAsync(actd.p, pAct, sizeof(int) * ka, cudaMemcpyHostToDevice, s));
         // W = T R(:, act)
         launch_gather_cols(m, k, ka, actd.p, R, P2, s);
         if (TH)
@@ -198,7 +224,8 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
             hYp.assign((size_t)nwp * ka, 0.0);
             for (int a = 0; a < nwp; ++a)
                 for (int q = 0; q < ka; ++q) hYp[(size_t)a * ka + q] = hY[(size_t)(k + a) * k + act[q]];
-            NAS_CUDA(cudaMemcpyAsync(Yp.p, hYp.data(), sizeof(double) * nwp * ka, cudaMemcpyHostToDevice, s));
+            std::copy(hYp.begin(), hYp.end(), pYp);
+            NAS_CUDA(cudaMemcpyAsync(Yp.p, pYp, sizeof(double) * nwp * ka, cudaMemcpyHostToDevice, s));
             ColBlocks WP = ColBlocks::one(W, ka, ka);
             if (np > 0) WP.add(P, np, np);
             launch_cols_mult(m, WP, Yp.p, ka, 1.0, 0.0, P2, s);
@@ -215,8 +242,6 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
             launch_coldots(m, np, 1, Xs, Ys, nullptr, gpart.p, nrm.p + 3 * k, s);
         }
         launch_inv_sqrt_scale(m, np, nrm.p + 3 * k, P, AP, BP, s);
-        // the host copies of Y and Yp must outlive their uploads
-        wait();
     }
     if (it >= maxit) return -1;
     // final Rayleigh-Ritz within span X for B-orthonormal output

@@ -14,7 +14,7 @@ namespace nas {
 struct DevLobpcg {
     // block vectors [m][k] (raw pointers are swapped between iterations)
     DBuf<double> bufs[11];
-    DBuf<double> T, theta, nrm, gpart, gtmp, GA, GB, Y, C;
+    DBuf<double> T, theta, nrm, gpart, gtmp, GAB, Y, C;  // GAB = S^T [AS | BS]
     DBuf<float> ppart;    // split partial products of the dense preconditioner
     DBuf<double> Yp;      // coefficients of the new search directions [2k][k]
     DBuf<int> actd;       // active (unlocked) block columns
@@ -25,6 +25,16 @@ struct DevLobpcg {
     int k_cap = 0;
     double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)
     double wait_ms = 0.0; // host time waiting for the device in synchronisations
+    // pinned staging area for the per-iteration transfers (Grams, norms,
+    // Ritz coefficients, active columns), so that they are truly asynchronous
+    double* pin = nullptr;
+    size_t pin_doubles = 0;
+    DevLobpcg() = default;
+    DevLobpcg(const DevLobpcg&) = delete;
+    DevLobpcg& operator=(const DevLobpcg&) = delete;
+    ~DevLobpcg() {
+        if (pin) cudaFreeHost(pin);
+    }
 
     // Lowest nev pairs.  U0: device [m][nev] warm start or null; Uout: device
     // [m][nev] (B-orthonormal eigenvectors); lam: host [nev].  diag_slot[i] is

@@ -196,14 +196,19 @@ struct ArrowDev {
     const double* Bd = nullptr;
     const double* Cd = nullptr;
 };
-// A matrix given as up to three column blocks side by side: column a of the
+// A matrix given as up to six column blocks side by side: column a of the
 // whole is column (a - offset) of block u, block u row-major with row stride ld[u].
 struct ColBlocks {
-    const double* p[3] = {nullptr, nullptr, nullptr};
-    int ld[3] = {0, 0, 0};
-    int w[3] = {0, 0, 0};
+    static const int kMax = 6;
+    const double* p[kMax] = {};
+    int ld[kMax] = {};
+    int w[kMax] = {};
     int nblk = 0;
-    __host__ __device__ int ncols() const { return w[0] + (nblk > 1 ? w[1] : 0) + (nblk > 2 ? w[2] : 0); }
+    __host__ __device__ int ncols() const {
+        int c = 0;
+        for (int u = 0; u < nblk; ++u) c += w[u];
+        return c;
+    }
     static ColBlocks one(const double* a, int ld, int w) {
         ColBlocks c;
         c.p[0] = a;
@@ -213,6 +218,7 @@ struct ColBlocks {
         return c;
     }
     void add(const double* a, int ldv, int wv) {
+        if (nblk >= kMax) return;  // callers never exceed kMax blocks
         p[nblk] = a;
         ld[nblk] = ldv;
         w[nblk] = wv;

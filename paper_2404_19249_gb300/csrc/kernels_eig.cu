@@ -302,7 +302,7 @@ namespace nas {
 // an inverse).
 static const int kPcRows = 32;
 static const int kPcK = 32;
-static const int kPcSplit = 4;
+static const int kPcSplit = 16;
 
 __global__ void __launch_bounds__(256) k_dense_precond_part(int64_t nH, int k, const float* T, const double* R,
                                                             float* part) {

@@ -139,6 +139,7 @@ struct nas_ctx {
     nas::DBuf<double> d_FAs, d_FAb, d_FAc;             // F_A of the current inner iteration
     nas::DBuf<double> d_Uwarm;                         // warm start [m][N] on the device
     int64_t uwarm_dev_m = 0;                           // m of d_Uwarm's content (0: none)
+    bool lob_reuse_ok = false;                         // F_B unchanged since the last device solve
     nas::DevLobpcg lob;
     double eig_tol_hint = 1.0;          // last inner-SCF residual (LOBPCG tolerance)
     double poisson_tol_now = 0.0;       // > 0: tolerance of the next Poisson solve

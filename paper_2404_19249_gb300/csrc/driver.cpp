@@ -733,8 +733,12 @@ static void device_eig(nas_ctx* c, int m) {
         }
         TH = c->d_khinv32.p;
     }
+    // within one inner SCF F_B is fixed: later solves start from the whole
+    // previous block (Ritz vectors of the previous F_A) without a start-up
+    // Rayleigh-Ritz
     int it = c->lob.solve(A, B, c->d_hdiag.p, c->N, nguard, lam.data(), warm ? c->d_Uwarm.p : nullptr, c->d_U.p,
-                          eig_tolerance(c), 2000, s, TH);
+                          eig_tolerance(c), 2000, s, TH, c->lob_reuse_ok);
+    c->lob_reuse_ok = true;
     if (it < 0) fail(NAS_E_EIGEN, "small eigenproblem: LOBPCG did not converge");
     c->last_lobpcg_iters += it;
     c->phase_ms[NAS_PH_EIG_RR] += c->lob.rr_ms;
@@ -945,6 +949,7 @@ static void augment_basis(nas_ctx* c) {
         for (int b = a; b < N; ++b) c->U_warm[(nH + a) * N + b] = g[b * N + a];
     c->d_Uwarm.upload(c->U_warm, s);
     c->uwarm_dev_m = nH + N;
+    c->lob_reuse_ok = false;  // new augmentation: new F_B
     std::fill(Uf.begin(), Uf.end(), 0.0);
     for (int i = 0; i < N * N; ++i) Uf[nH * N + i] = Linv_T[i];
     NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
@@ -1248,6 +1253,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
     c->d_VH.zero(s);
     c->U_warm.clear();
     c->uwarm_dev_m = 0;
+    c->lob_reuse_ok = false;
     if (psi0 == nullptr) {
         // self-consistent solution in S_H alone, from rho = 0
         if (c->nH < c->N) fail(NAS_E_INVALID_ARG, "the coarse-space initial guess needs n_coarse_dof >= N");

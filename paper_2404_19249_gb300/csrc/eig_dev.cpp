@@ -21,7 +21,7 @@ namespace nas {
 
 int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, int nev, int nguard,
                      double* lam, const double* U0, double* Uout, double tol, int maxit, cudaStream_t s,
-                     const float* TH) {
+                     const float* TH, bool reuse_block) {
     const int64_t m = A.nH + A.Na;
     if (nev < 1 || nev > m) return -1;
     const int k = (int)std::min<int64_t>(nev + nguard, m);
@@ -116,9 +116,26 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         fetch(ns, norms);
         return rr_host(ns, th_out);
     };
-    // ---- start: warm vectors for the wanted columns, deterministic pseudo-random
-    // otherwise (generated once per (m, k) and kept on the device)
-    {
+    // ---- start.  reuse_block: the whole block of the previous solve (same m,
+    // k and F_B; its columns are B-orthonormal Ritz vectors of a nearby F_A),
+    // with Rayleigh quotients as the first Ritz values - no start-up
+    // Rayleigh-Ritz.  Otherwise warm vectors for the wanted columns and
+    // deterministic pseudo-random ones (generated once per (m, k)) for the rest,
+    // B-orthonormalised by a Rayleigh-Ritz step.
+    const bool reuse = reuse_block && keep_m == m && keep_k == k;
+    if (reuse) {
+        NAS_CUDA(cudaMemcpyAsync(X, Xkeep.p, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, s));
+        applyAB(k, X, AX, BX);
+        const double* Xs[2] = {X, X};
+        const double* Ys[2] = {AX, BX};
+        launch_coldots(m, k, 2, Xs, Ys, nullptr, gpart.p, nrm.p, s);
+        NAS_CUDA(cudaMemcpyAsync(pN, nrm.p, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+        wait();
+        th.resize(k);
+        for (int j = 0; j < k; ++j) th[j] = pN[j] / (pN[k + j] > 0.0 ? pN[k + j] : 1.0);
+        std::copy(th.begin(), th.end(), pTh);
+        NAS_CUDA(cudaMemcpyAsync(theta.p, pTh, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    } else {
         if (x0_m != m || x0_k != k) {
             std::vector<double> h((size_t)m * k);
             for (int64_t i = 0; i < m; ++i)
@@ -136,9 +153,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         if (U0)
             NAS_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * k, U0, sizeof(double) * nev, sizeof(double) * nev, m,
                                        cudaMemcpyDeviceToDevice, s));
-    }
-    applyAB(k, X, AX, BX);
-    {
+        applyAB(k, X, AX, BX);
         ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
         grams(S, AS, BS);
         if (rr(k, false, th) != 0) return -1;
@@ -244,15 +259,15 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         launch_inv_sqrt_scale(m, np, nrm.p + 3 * k, P, AP, BP, s);
     }
     if (it >= maxit) return -1;
-    // final Rayleigh-Ritz within span X for B-orthonormal output
-    {
-        ColBlocks S = ColBlocks::one(X, k, k), AS = ColBlocks::one(AX, k, k), BS = ColBlocks::one(BX, k, k);
-        grams(S, AS, BS);
-        if (rr(k, false, th) != 0) return -1;
-        launch_cols_mult(m, S, Y.p, k, 1.0, 0.0, X2, s);
-        NAS_CUDA(cudaMemcpy2DAsync(Uout, sizeof(double) * nev, X2, sizeof(double) * k, sizeof(double) * nev, m,
-                                   cudaMemcpyDeviceToDevice, s));
-    }
+    // X holds B-orthonormal Ritz vectors (every iteration ends with X = S Y):
+    // the wanted columns are the output; the whole block is kept for the next
+    // solve of the same pencil family
+    NAS_CUDA(cudaMemcpy2DAsync(Uout, sizeof(double) * nev, X, sizeof(double) * k, sizeof(double) * nev, m,
+                               cudaMemcpyDeviceToDevice, s));
+    Xkeep.ensure((size_t)m * k);
+    NAS_CUDA(cudaMemcpyAsync(Xkeep.p, X, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, s));
+    keep_m = m;
+    keep_k = k;
     for (int j = 0; j < nev; ++j) lam[j] = th[j];
     return it;
 }

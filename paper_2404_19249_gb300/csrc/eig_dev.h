@@ -43,8 +43,14 @@ struct DevLobpcg {
     // ||B u||).  Returns the iterations used, or -1 on failure.
     // TH (optional): FP32 [nH][nH] preconditioner block for the coarse rows
     // (the border rows keep the diagonal one).
+    // reuse_block: start from the full block of the previous solve (same m and
+    // k, same F_B) instead of U0 and random guard columns.
     int solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_slot, int nev, int nguard, double* lam,
-              const double* U0, double* Uout, double tol, int maxit, cudaStream_t s, const float* TH = nullptr);
+              const double* U0, double* Uout, double tol, int maxit, cudaStream_t s, const float* TH = nullptr,
+              bool reuse_block = false);
+    DBuf<double> Xkeep;   // last solve's block [m][k]
+    int64_t keep_m = 0;
+    int keep_k = 0;
 };
 
 }  // namespace nas

@@ -17,21 +17,35 @@
 
 namespace nas {
 
+// sum_k a[k] b[k] with four interleaved partial sums (k mod 4), added as
+// ((s0 + s1) + (s2 + s3)) + tail: a fixed order, and the four running sums
+// let consecutive multiply-adds overlap instead of waiting on one sum
+static inline double dot(const double* a, const double* b, int n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 4 <= n; k += 4) {
+        s0 += a[k] * b[k];
+        s1 += a[k + 1] * b[k + 1];
+        s2 += a[k + 2] * b[k + 2];
+        s3 += a[k + 3] * b[k + 3];
+    }
+    double s = (s0 + s1) + (s2 + s3);
+    for (; k < n; ++k) s += a[k] * b[k];
+    return s;
+}
+
 // lower Cholesky in place (row-major, lower triangle); returns false if not SPD
 static bool cholesky(int m, std::vector<double>& L) {
     for (int j = 0; j < m; ++j) {
-        double d = L[(size_t)j * m + j];
-        for (int k = 0; k < j; ++k) d -= L[(size_t)j * m + k] * L[(size_t)j * m + k];
+        const double* Lj = &L[(size_t)j * m];
+        double d = L[(size_t)j * m + j] - dot(Lj, Lj, j);
         if (!(d > 0.0)) return false;
         d = std::sqrt(d);
         L[(size_t)j * m + j] = d;
-        const double* Lj = &L[(size_t)j * m];
 #pragma omp parallel for schedule(static) if (m - j > 256)
         for (int i = j + 1; i < m; ++i) {
             double* Li = &L[(size_t)i * m];
-            double s = Li[j];
-            for (int k = 0; k < j; ++k) s -= Li[k] * Lj[k];
-            Li[j] = s / d;
+            Li[j] = (Li[j] - dot(Li, Lj, j)) / d;
         }
     }
     for (int i = 0; i < m; ++i)
@@ -40,37 +54,31 @@ static bool cholesky(int m, std::vector<double>& L) {
 }
 
 // C = L^{-1} A L^{-T} (A symmetric, full storage built from its lower triangle)
+// by forward elimination applied to whole rows (Z <- L^-1 Z for all columns
+// at once: each update is a contiguous row operation), first to A, then to
+// the transpose of the result.
 static void reduce_standard(int m, const std::vector<double>& L, const double* A, std::vector<double>& C) {
-    std::vector<double> X((size_t)m * m);
-    // X^T = (L^{-1} A)^T ... compute column by column of L^{-1} A: column c solves L y = A[:,c]
-    // A symmetric: A[:,c] = A[c,:] (use lower triangle)
-    auto a = [&](int i, int j) { return i >= j ? A[(size_t)i * m + j] : A[(size_t)j * m + i]; };
-    // Y = L^{-1} A, stored transposed: Yt[c][i] = Y[i][c]
-    std::vector<double> Yt((size_t)m * m);
-#pragma omp parallel for schedule(static) if (m > 128)
-    for (int c = 0; c < m; ++c) {
-        double* y = &Yt[(size_t)c * m];
-        for (int i = 0; i < m; ++i) {
-            double s = a(i, c);
-            const double* Li = &L[(size_t)i * m];
-            for (int k = 0; k < i; ++k) s -= Li[k] * y[k];
-            y[i] = s / Li[i];
+    auto solve_rows = [&](std::vector<double>& Z) {
+        for (int k = 0; k < m; ++k) {
+            double* zk = &Z[(size_t)k * m];
+            const double d = L[(size_t)k * m + k];
+            for (int j = 0; j < m; ++j) zk[j] /= d;
+            for (int i = k + 1; i < m; ++i) {
+                const double l = L[(size_t)i * m + k];
+                if (l == 0.0) continue;
+                double* zi = &Z[(size_t)i * m];
+                for (int j = 0; j < m; ++j) zi[j] -= l * zk[j];
+            }
         }
-    }
-    // C = L^{-1} Y^T ; Y^T = (L^{-1}A)^T = A L^{-T}; column c of Y^T is row c of Y = Yt[:, c]
-    // C[:,c] solves L z = (Y^T)[:,c] = Y[c,:] = Yt[*][c]... use Y^T[i][c] = Y[c][i] = Yt[i][c]
-    C.assign((size_t)m * m, 0.0);
-#pragma omp parallel for schedule(static) if (m > 128)
-    for (int c = 0; c < m; ++c) {
-        std::vector<double> z(m);
-        for (int i = 0; i < m; ++i) {
-            double s = Yt[(size_t)i * m + c];
-            const double* Li = &L[(size_t)i * m];
-            for (int k = 0; k < i; ++k) s -= Li[k] * z[k];
-            z[i] = s / Li[i];
-        }
-        for (int i = 0; i < m; ++i) C[(size_t)i * m + c] = z[i];
-    }
+    };
+    std::vector<double> Y((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j <= i; ++j) Y[(size_t)i * m + j] = Y[(size_t)j * m + i] = A[(size_t)i * m + j];
+    solve_rows(Y);                       // Y = L^-1 A
+    C.resize((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) C[(size_t)i * m + j] = Y[(size_t)j * m + i];
+    solve_rows(C);                       // C = L^-1 (L^-1 A)^T = L^-1 A L^-T
     // symmetrise
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < i; ++j) {
@@ -114,12 +122,7 @@ static void tridiagonalise(int m, std::vector<double>& C, std::vector<double>& d
         for (int i = 0; i < n1; ++i) V[(size_t)j * m + j + 1 + i] = x[i];
         // p = tau * C22 v
 #pragma omp parallel for schedule(static) if (n1 > 256)
-        for (int i = 0; i < n1; ++i) {
-            const double* Ci = &C[(size_t)(j + 1 + i) * m + j + 1];
-            double s = 0.0;
-            for (int k = 0; k < n1; ++k) s += Ci[k] * x[k];
-            p[i] = t * s;
-        }
+        for (int i = 0; i < n1; ++i) p[i] = t * dot(&C[(size_t)(j + 1 + i) * m + j + 1], x, n1);
         double pv = 0.0;
         for (int i = 0; i < n1; ++i) pv += p[i] * x[i];
         for (int i = 0; i < n1; ++i) w[i] = p[i] - 0.5 * t * pv * x[i];
@@ -315,13 +318,10 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
             tri_solve(m, d, e, shift, pert, x, tw);
             for (int j = start; j < i; ++j) {
                 const double* zj = &Z[(size_t)j * m];
-                double s = 0.0;
-                for (int r = 0; r < m; ++r) s += zj[r] * x[r];
+                const double s = dot(zj, x.data(), m);
                 for (int r = 0; r < m; ++r) x[r] -= s * zj[r];
             }
-            double nrm = 0.0;
-            for (int r = 0; r < m; ++r) nrm += x[r] * x[r];
-            nrm = std::sqrt(nrm);
+            double nrm = std::sqrt(dot(x.data(), x.data(), m));
             if (!(nrm > 0)) {
                 for (int r = 0; r < m; ++r) x[r] = (r == i) ? 1.0 : 0.0;
                 nrm = 1.0;
@@ -330,24 +330,23 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
         }
         std::copy(x.begin(), x.end(), Z.begin() + (size_t)i * m);
     }
-    // back-transform: y = Q z = H_0 ... H_{m-3} z, then U = L^{-T} y
+    // back-transform: y = Q z = H_0 ... H_{m-3} z, then U = L^{-T} y (rows of
+    // L^T, i.e. columns of L, made contiguous first)
+    std::vector<double> Lt((size_t)m * m);
+    for (int r = 0; r < m; ++r)
+        for (int q = 0; q <= r; ++q) Lt[(size_t)q * m + r] = L[(size_t)r * m + q];
 #pragma omp parallel for schedule(dynamic, 1) if ((int64_t)k * m * m > 2000000)
     for (int i = 0; i < k; ++i) {
         double* z = &Z[(size_t)i * m];
         for (int j = m - 3; j >= 0; --j) {
             if (tau[j] == 0.0) continue;
             const double* v = &V[(size_t)j * m];
-            double s = 0.0;
-            for (int r = j + 1; r < m; ++r) s += v[r] * z[r];
-            s *= tau[j];
+            const double s = tau[j] * dot(v + j + 1, z + j + 1, m - j - 1);
             for (int r = j + 1; r < m; ++r) z[r] -= s * v[r];
         }
         // solve L^T u = z (backward)
-        for (int r = m - 1; r >= 0; --r) {
-            double s = z[r];
-            for (int q = r + 1; q < m; ++q) s -= L[(size_t)q * m + r] * z[q];
-            z[r] = s / L[(size_t)r * m + r];
-        }
+        for (int r = m - 1; r >= 0; --r)
+            z[r] = (z[r] - dot(&Lt[(size_t)r * m + r + 1], z + r + 1, m - r - 1)) / Lt[(size_t)r * m + r];
     }
     // Rayleigh quotients refine the eigenvalues: lambda = u^T A u (u is
     // B-normalised), from the lower triangle of A: sum_r u_r (A_rr u_r + 2 sum_{c<r} A_rc u_c)
@@ -357,9 +356,7 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
         double s = 0.0;
         for (int r = 0; r < m; ++r) {
             const double* Ar = A + (size_t)r * m;
-            double t = 0.0;
-            for (int c = 0; c < r; ++c) t += Ar[c] * u[c];
-            s += u[r] * (Ar[r] * u[r] + 2.0 * t);
+            s += u[r] * (Ar[r] * u[r] + 2.0 * dot(Ar, u, r));
         }
         lam[i] = s;
     }

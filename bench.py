@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--tol-bvp", type=float, default=1e-10)
     p.add_argument("--spmv-lanes", type=int, default=0)
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    p.add_argument("--clocks-file", default=None, help="where to keep the nvidia-smi clock samples")
     p.add_argument("--batch", type=int, default=0,
                    help="also time this many independent small instances (batched workload), "
                         "one after another and concurrently")
@@ -350,8 +351,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d.csv" % os.getpid())
+    clocks = Clocks(args.clocks_file or "/tmp/bench_clocks_%d.csv" % os.getpid())
     # state at the start of the timed region (the mixed-precision run restarts from it)
     n0, N0, nqt0 = sz["n"], sz["N"], sz["ne"] * sz["nq"]
     s0_lam = np.zeros(N0)

@@ -409,13 +409,15 @@ def main():
         nas.nas_get(s.h, nas.NAS_Q_ENERGY, en32)
         mixed = {
             "value": job_value(world, args.steps, mms), "unit": "steps/s", "ms_per_step": mms / args.steps,
-            "what": "Poisson PCG in FP32 (FP32 accumulation) inside FP64 iterative refinement; "
+            "what": "Poisson PCG and block PCG of the N shifted problems in FP32 inside FP64 iterative refinement; "
                     "same start state and step count as the FP64 run",
             "max_eigenvalue_err_ha": float(np.max(np.abs(lam32 - lam64))),
             "eigenvalue_err_ha": [float(x) for x in (lam32 - lam64)],
             "energy_err_ha": float(en32[0] - en64[0]),
             "poisson_ms_per_step": sum(rp.phase_ms[2] for rp in mreps) / args.steps,
             "poisson_iters_per_step": sum(rp.poisson_iters for rp in mreps) / args.steps,
+            "bvp_ms_per_step": sum(rp.phase_ms[1] for rp in mreps) / args.steps,
+            "fp64_bvp_ms_per_step": sum(rp.phase_ms[1] for rp in reps) / args.steps,
         }
         log("mixed: %s" % json.dumps({k: v for k, v in mixed.items() if k != "eigenvalue_err_ha"}))
         s.opt.precision = 0

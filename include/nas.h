@@ -81,8 +81,9 @@ typedef struct nas_options {
     int    poisson_two_level; /* 1: Poisson PCG preconditioner D^-1 + I K_H^-1 I^T with
                               the method's coarse space and transfer (K_H = I^T K I);
                               0: Jacobi only                                        */
-    int    precision;      /* 0: FP64 throughout; 1: mixed - the Poisson PCG runs in
-                              FP32 (FP32 accumulation) inside FP64 iterative
+    int    precision;      /* 0: FP64 throughout; 1: mixed - the Poisson PCG and the
+                              block PCG of the N shifted problems run in FP32
+                              (FP32 storage and products) inside FP64 iterative
                               refinement; residual tests, assembly, blocks, the
                               small eigensolve and energies stay FP64               */
     int    eig_device;     /* small problems above eig_dense_max: 1 = LOBPCG with its

@@ -112,6 +112,7 @@ struct nas_ctx {
     double pcg1_spmv_ms = 0.0;                          // this step: SpMV kernel time
     long long pcg1_spmv_launches = 0;
     // mixed precision: FP32 copies and work arrays of the Poisson solve
+    nas::DBuf<float> d_H32, d_Hdinv32, d_bvp32;         // mixed precision: FP32 H~, D^-1 and block PCG vectors
     nas::DBuf<float> d_K32, d_Kdinv32, d_ival32, d_tval32, d_khinv32, d_khvec32, d_f32work, d_f32part;
     cudaGraphExec_t pcg1f_exec = nullptr;
     Pcg1Key pcg1f_key;

@@ -175,6 +175,109 @@ static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double
     return it;
 }
 
+// Mixed precision for the N shifted problems: FP64 iterative refinement
+// around a block PCG in FP32 (FP32 copies of H~ and D^-1, FP32 vectors and
+// products, FP64 per-column scalars).  Each outer pass forms the FP64
+// residual R = B - H~ X, tests every column against tol (relative to ||b||),
+// solves H~ E = R in FP32 for the columns still open to the relative
+// tolerance max(1e-5, 0.3 tol ||b|| / ||r||) of the worst one, and adds E to X
+// in FP64.  Returns the FP32 iterations.
+static int pcg_mixed(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double* B, double* X, double tol,
+                     int maxit, bool* converged) {
+    const int64_t n = A.n_rows, nnz = c->F.nnz();
+    cudaStream_t s = c->stream;
+    c->d_H32.ensure(nnz);
+    launch_cast_to_f32(nnz, A.val, c->d_H32.p, s);
+    c->d_Hdinv32.ensure(n);
+    launch_cast_to_f32(n, Dinv, c->d_Hdinv32.p, s);
+    c->d_bvp32.ensure(5 * (size_t)n * N);
+    float* E = c->d_bvp32.p;
+    float* R = E + n * N;
+    float* Z = R + n * N;
+    float* P = Z + n * N;
+    float* Q = P + n * N;
+    double* R64 = c->d_cg_R.p;
+    PcgCols pc{N, scal(c, 0, N), scal(c, 1, N), scal(c, 2, N), scal(c, 3, N), scal(c, 4, N), scal(c, 5, N),
+               scal(c, 6, N), c->d_cg_active.p, c->d_flag.p, 0.0};
+    const int every = std::max(1, c->opt.check_every);
+    std::vector<double> h(2 * N);
+    std::vector<int> act(N);
+    int total = 0;
+    *converged = false;
+    for (int outer = 0; outer < 30 && total < maxit; ++outer) {
+        // FP64 residual and per-column test
+        spmm(c, A, N, X, R64);
+        launch_sub_from(n * N, B, R64, s);
+        {
+            const double* X2[2] = {R64, B};
+            launch_coldots(n, N, 2, X2, X2, nullptr, c->d_partial.p, pc.rr, s);  // rr, bb
+        }
+        NAS_CUDA(cudaMemcpyAsync(h.data(), pc.rr, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, s));
+        sync(c);
+        int nact = 0;
+        double worst = 1e300;
+        for (int j = 0; j < N; ++j) {
+            if (!std::isfinite(h[j])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
+            act[j] = (h[N + j] > 0.0 && h[j] > tol * tol * h[N + j]) ? 1 : 0;
+            if (act[j]) {
+                ++nact;
+                worst = std::min(worst, std::sqrt(h[N + j] / h[j]));
+            }
+        }
+        if (nact == 0) {
+            *converged = true;
+            break;
+        }
+        const double tin = std::max(1e-5, 0.3 * tol * worst);
+        pc.tol2 = tin * tin;
+        NAS_CUDA(cudaMemcpyAsync(c->d_cg_active.p, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+        NAS_CUDA(cudaMemsetAsync(c->d_flag.p, 0, sizeof(int), s));
+        // FP32 solve of H~ E = R from E = 0: r = R, z = D^-1 r, p = z
+        launch_cast_to_f32(n * N, R64, R, s);
+        NAS_CUDA(cudaMemsetAsync(E, 0, sizeof(float) * n * N, s));
+        launch_scale_rows_f32(n, N, c->d_Hdinv32.p, R, Z, s);
+        NAS_CUDA(cudaMemcpyAsync(P, Z, sizeof(float) * n * N, cudaMemcpyDeviceToDevice, s));
+        {
+            const float* X1[1] = {R};
+            const float* Y1[1] = {Z};
+            launch_coldots_f32(n, N, 1, X1, Y1, c->d_partial.p, pc.rz, s);
+            const float* X2[1] = {R};
+            launch_coldots_f32(n, N, 1, X2, X2, c->d_partial.p, pc.bb, s);  // inner reference ||r0||^2
+        }
+        int it = 0, inner_act = nact;
+        while (inner_act > 0 && total + it < maxit) {
+            launch_spmm_f32(n, c->d_rowptr.p, c->d_col.p, c->d_H32.p, N, P, Q, s);
+            {
+                const float* X1[1] = {P};
+                const float* Y1[1] = {Q};
+                launch_coldots_f32(n, N, 1, X1, Y1, c->d_partial.p, pc.pq, s);
+            }
+            launch_pcg_alpha(pc, s);
+            launch_pcg_update_f32(n, N, pc.alpha, pc.active, P, Q, c->d_Hdinv32.p, E, R, Z, s);
+            {
+                const float* X2[2] = {R, R};
+                const float* Y2[2] = {Z, R};
+                launch_coldots_f32(n, N, 2, X2, Y2, c->d_partial.p, pc.rz_new, s);  // rz_new, rr
+            }
+            launch_pcg_beta(pc, s);
+            launch_pcg_direction_f32(n, N, pc.beta, pc.active, Z, P, s);
+            ++it;
+            if (it % every == 0) {
+                int bd = 0;
+                NAS_CUDA(cudaMemcpyAsync(act.data(), c->d_cg_active.p, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+                NAS_CUDA(cudaMemcpyAsync(&bd, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+                sync(c);
+                inner_act = 0;
+                for (int j = 0; j < N; ++j) inner_act += act[j];
+                if (bd) break;  // FP32 breakdown: the outer FP64 pass decides
+            }
+        }
+        total += it;
+        launch_add_f32(n * N, E, X, s);  // X += E in FP64
+    }
+    return total;
+}
+
 // Single right-hand-side PCG with the fused kernels (kernels_pcg1.cu),
 // replayed kPcg1Graph iterations at a time from a captured CUDA graph.  The
 // graph is captured once per context on a private stream (the graph's
@@ -1351,8 +1454,11 @@ int ctx_step(nas_ctx* c, nas_report* rep) {
         launch_scale_cols(n, N, d_sh, c->d_cg_B.p, s);
         NAS_CUDA(cudaMemcpyAsync(c->d_Uhat.p, c->d_Psi.p, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
         bool conv;
-        c->last_cg = pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, c->opt.tol_bvp,
-                         c->opt.max_cg, &conv);
+        c->last_cg = c->opt.precision == 1
+                         ? pcg_mixed(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, c->opt.tol_bvp,
+                                     c->opt.max_cg, &conv)
+                         : pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, c->opt.tol_bvp,
+                               c->opt.max_cg, &conv);
         if (!conv) status = NAS_E_NOT_CONVERGED;
     }
     augment_basis(c);

@@ -316,6 +316,18 @@ void launch_pcg1_coarse_correction(const Pcg1f& s, cudaStream_t st);
 // FP32 inner solve start from e = 0 (p = z, x = 0, partial sums of r.z, r.r)
 void launch_pcg1_start(const Pcg1f& s, cudaStream_t st);
 void launch_cast_to_f32(int64_t n, const double* a, float* b, cudaStream_t st);
+// FP32 block PCG pieces (mixed precision, the N shifted problems): SpMM with
+// N interleaved columns; column dots (FP32 products, FP64 across threads);
+// updates with FP64 per-column scalars
+void launch_spmm_f32(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const float* val, int N,
+                     const float* X, float* Y, cudaStream_t s);
+void launch_coldots_f32(int64_t n, int N, int npairs, const float* const* X, const float* const* Y,
+                        double* partial, double* out, cudaStream_t s);
+void launch_pcg_update_f32(int64_t n, int N, const double* alpha, const int* active, const float* P, const float* Q,
+                           const float* Dinv, float* X, float* R, float* Z, cudaStream_t s);
+void launch_pcg_direction_f32(int64_t n, int N, const double* beta, const int* active, const float* Z, float* P,
+                              cudaStream_t s);
+void launch_scale_rows_f32(int64_t n, int N, const float* Dinv, const float* R, float* Z, cudaStream_t s);
 void launch_add_f32(int64_t n, const float* e, double* x, cudaStream_t st);
 
 // Anderson: given F^0..F^m (pointers), w, compute the k x k matrix

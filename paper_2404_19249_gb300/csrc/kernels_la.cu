@@ -531,3 +531,126 @@ void launch_anderson_mix(int64_t cnt, int m, const double* const* rin, const dou
 }
 
 }  // namespace nas
+
+namespace nas {
+
+// ------------------------------------------------------------------ FP32 block PCG (mixed precision)
+// The inner solve of the N shifted problems in FP32 storage and arithmetic;
+// per-column scalars stay FP64 on the device (the same PcgCols logic), dot
+// products accumulate in FP32 per thread and in FP64 across threads.
+__global__ void __launch_bounds__(256) k_spmm_cols_f32(int64_t n_rows, const int32_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ col,
+                                                       const float* __restrict__ val, int N,
+                                                       const float* __restrict__ X, float* __restrict__ Y) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = t / N;
+    if (row >= n_rows) return;
+    const int c = (int)(t - row * N);
+    float acc = 0.f;
+    for (int p = rowptr[row]; p < rowptr[row + 1]; ++p) acc += val[p] * X[(int64_t)col[p] * N + c];
+    Y[t] = acc;
+}
+
+void launch_spmm_f32(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const float* val, int N,
+                     const float* X, float* Y, cudaStream_t s) {
+    if (n_rows <= 0) return;
+    k_spmm_cols_f32<<<grid_for(n_rows * N, 256), 256, 0, s>>>(n_rows, rowptr, col, val, N, X, Y);
+    NAS_CHECK_LAUNCH();
+}
+
+// out[k][c] = sum_i X_k[i][c] Y_k[i][c] (k < npairs <= 2), FP32 inputs
+struct ColDotArgsF {
+    const float* X[2];
+    const float* Y[2];
+};
+
+__global__ void __launch_bounds__(256) k_coldots_f32(int64_t n, int N, int npairs, ColDotArgsF a, double* partial) {
+    __shared__ double sh[2][256];
+    const int R = 256 / N;
+    const int t = threadIdx.x;
+    const int c = t % N, r = t / N;
+    float acc[2] = {0.f, 0.f};
+    if (r < R) {
+        for (int64_t row = (int64_t)blockIdx.x * R + r; row < n; row += (int64_t)gridDim.x * R) {
+            const int64_t idx = row * N + c;
+            for (int k = 0; k < npairs; ++k) acc[k] += a.X[k][idx] * a.Y[k][idx];
+        }
+    }
+    for (int k = 0; k < npairs; ++k) sh[k][t] = (double)acc[k];
+    __syncthreads();
+    if (t < N) {
+        for (int k = 0; k < npairs; ++k) {
+            double s = 0.0;
+            for (int rr = 0; rr < R; ++rr) s += sh[k][rr * N + t];
+            partial[(int64_t)blockIdx.x * npairs * N + k * N + t] = s;
+        }
+    }
+}
+
+void launch_coldots_f32(int64_t n, int N, int npairs, const float* const* X, const float* const* Y,
+                        double* partial, double* out, cudaStream_t s) {
+    if (N < 1 || N > 256 || npairs < 1 || npairs > 2) fail(NAS_E_INVALID_ARG, "coldots width");
+    ColDotArgsF a{};
+    for (int k = 0; k < npairs; ++k) {
+        a.X[k] = X[k];
+        a.Y[k] = Y[k];
+    }
+    const int R = 256 / N;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + R - 1) / R));
+    k_coldots_f32<<<nb, 256, 0, s>>>(n, N, npairs, a, partial);
+    NAS_CHECK_LAUNCH();
+    reduce_partials(nb, (int64_t)npairs * N, partial, out, s);
+}
+
+// X += alpha P, R -= alpha Q, Z = Dinv R (FP32 vectors, FP64 per-column alpha)
+__global__ void k_pcg_update_f32(int64_t n, int N, const double* alpha, const int* active, const float* P,
+                                 const float* Q, const float* Dinv, float* X, float* R, float* Z) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    const int64_t i = t / N;
+    const int c = (int)(t - i * N);
+    if (!active[c]) return;
+    const float a = (float)alpha[c];
+    X[t] += a * P[t];
+    const float r = R[t] - a * Q[t];
+    R[t] = r;
+    Z[t] = Dinv[i] * r;
+}
+
+void launch_pcg_update_f32(int64_t n, int N, const double* alpha, const int* active, const float* P, const float* Q,
+                           const float* Dinv, float* X, float* R, float* Z, cudaStream_t s) {
+    if (n <= 0) return;
+    k_pcg_update_f32<<<grid_for(n * N, 256), 256, 0, s>>>(n, N, alpha, active, P, Q, Dinv, X, R, Z);
+    NAS_CHECK_LAUNCH();
+}
+
+__global__ void k_pcg_direction_f32(int64_t n, int N, const double* beta, const int* active, const float* Z,
+                                    float* P) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    const int c = (int)(t % N);
+    if (!active[c]) return;
+    P[t] = Z[t] + (float)beta[c] * P[t];
+}
+
+void launch_pcg_direction_f32(int64_t n, int N, const double* beta, const int* active, const float* Z, float* P,
+                              cudaStream_t s) {
+    if (n <= 0) return;
+    k_pcg_direction_f32<<<grid_for(n * N, 256), 256, 0, s>>>(n, N, beta, active, Z, P);
+    NAS_CHECK_LAUNCH();
+}
+
+// Z = Dinv R (FP32)
+__global__ void k_scale_rows_f32(int64_t n, int N, const float* Dinv, const float* R, float* Z) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    Z[t] = Dinv[t / N] * R[t];
+}
+
+void launch_scale_rows_f32(int64_t n, int N, const float* Dinv, const float* R, float* Z, cudaStream_t s) {
+    if (n <= 0) return;
+    k_scale_rows_f32<<<grid_for(n * N, 256), 256, 0, s>>>(n, N, Dinv, R, Z);
+    NAS_CHECK_LAUNCH();
+}
+
+}  // namespace nas

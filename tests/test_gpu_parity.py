@@ -260,8 +260,9 @@ def test_coldot_standalone(nasmod):
 
 
 def test_mixed_precision_poisson_matches_fp64(nasmod):
-    """Mixed precision (FP32 Poisson PCG inside FP64 refinement) reproduces the
-    FP64 steps: eigenvalues within 1e-8 Ha and the oracle within 1e-10."""
+    """Mixed precision (FP32 Poisson PCG and FP32 block PCG of the N shifted
+    problems, each inside FP64 iterative refinement) reproduces the FP64
+    steps: eigenvalues within 1e-8 Ha and the oracle within 1e-10."""
     inst = _tight(make_instance("paper_molecule", molecule="c6h6", cells=8, coarse_cells=4))
     P = Problem(inst)
     res = {}

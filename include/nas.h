@@ -107,6 +107,16 @@ typedef struct nas_options {
                               the previous density residual res:
                               max(tol_poisson, min(1e-6, 1e-3 res)); 0: always
                               tol_poisson.  The fixed point is unchanged.          */
+    int    poisson_fused;  /* 1: the FP64 two-level Poisson PCG with the sliced-ELL
+                              matrix runs as one persistent cooperative kernel per
+                              16 iterations (grid-wide barriers between the
+                              phases, same arithmetic and bit-identical iterates
+                              to the per-phase kernels; measured slower on GB300:
+                              0.32 against 0.23 ms per iteration); 0: per-phase
+                              kernels replayed from a CUDA graph.  Not used inside
+                              nas_batch_run; callers that run several contexts'
+                              solves at once on one device from their own threads
+                              keep 0.                                              */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -115,7 +125,7 @@ typedef struct nas_options {
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
- * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0. */
+ * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -163,12 +173,16 @@ typedef struct nas_report {
     double spmv_bytes;        /* same for the SpMV launches (N = 1)                  */
     double spmv_flops;
     int    eig_iters;         /* LOBPCG iterations of the last step (0: dense)        */
-    double poisson_spmv_ms;   /* timing = 1: summed CUDA-event time of the SpMV kernel
-                                 of the FP64 Poisson PCG, over the first two
-                                 iterations of every solve (launched directly, with
-                                 events around the SpMV; the rest of the solve is
-                                 replayed from the CUDA graph)                       */
+    double poisson_spmv_ms;   /* timing = 1, poisson_fused = 0: summed CUDA-event time
+                                 of the SpMV kernel of the FP64 Poisson PCG, over
+                                 the first two iterations of every solve (launched
+                                 directly, with events around the SpMV; the rest of
+                                 the solve is replayed from the CUDA graph)          */
     long long poisson_spmv_launches; /* SpMV launches counted in poisson_spmv_ms      */
+    double poisson_fused_ms;  /* timing = 1, poisson_fused = 1: summed CUDA-event time
+                                 of the persistent Poisson PCG launches (every
+                                 launch of every FP64 solve)                         */
+    long long poisson_fused_iters; /* PCG iterations run inside those launches       */
 } nas_report;
 
 /* ------------------------------------------------------------------ context */
@@ -240,7 +254,8 @@ enum nas_quantity {
     NAS_Q_SIZES = 0,      /* int64[16]: n_dof, nnz, n_coarse_dof, coarse_nnz, n_elem,
                              n_quad_per_elem, n_node, n_orb, n_boundary, nnz_boundary,
                              n_vert, order, n_coarse_elem, sliced-ELL entries of K
-                             (padding included), 0...                               */
+                             (padding included), entries of I^T, balanced pieces
+                             of the I^T rows                                        */
     NAS_Q_EIGVALS,        /* FP64 [N]                                                */
     NAS_Q_ORBITALS,       /* FP64 [n_dof][N]  Psi (fine interior values)              */
     NAS_Q_RHO_IN,         /* FP64 [n_elem][nq] density defining the potential         */

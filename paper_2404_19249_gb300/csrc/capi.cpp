@@ -71,6 +71,7 @@ void nas_default_options(nas_options* o) {
     o->eig_adapt = 1e-3;
     o->poisson_sell = 1;
     o->poisson_adaptive = 0;
+    o->poisson_fused = 0;
     o->poisson_two_level = 1;
     o->precision = 0;
 }
@@ -186,7 +187,7 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
             o->anderson_depth < 1 || o->anderson_depth > 5 || o->precision < 0 || o->precision > 1 ||
             o->eig_device < 0 || o->eig_device > 1 || o->poisson_adaptive < 0 || o->poisson_adaptive > 1 ||
             !(o->eig_adapt > 0.0) || o->eig_adapt > 1.0 || o->eig_precond < 0 || o->eig_precond > 1 ||
-            o->poisson_sell < 0 || o->poisson_sell > 1)
+            o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level) || (o->eig_precond != c->opt.eig_precond);
@@ -261,6 +262,7 @@ int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* stat
         cudaEventDestroy(e);
         own[i] = c->stream;
         c->stream = priv[i];
+        c->concurrent = true;  // solves run at the same time: no cooperative launches
     }
     const int nt = std::min(n_threads, count);
     const int omp_each = std::max(1, omp_get_max_threads() / nt);
@@ -295,6 +297,7 @@ int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* stat
             rc = NAS_E_CUDA;
         if (e) cudaEventDestroy(e);
         c->stream = own[i];
+        c->concurrent = false;
         cudaStreamDestroy(priv[i]);  // released once its queued work completes
     }
     return rc;

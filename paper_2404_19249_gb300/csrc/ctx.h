@@ -104,11 +104,15 @@ struct nas_ctx {
     nas::DBuf<double> d_sell_val;
     int64_t sell_slices = 0, sell_entries = 0;
     nas::DBuf<int> d_pcg1_flags;
+    nas::DBuf<unsigned> d_pcg1_bar;                   // grid barrier of the persistent PCG
     cudaStream_t cap_stream = nullptr;                 // private stream for graph capture
     cudaGraphExec_t pcg1_exec = nullptr;
     Pcg1Key pcg1_key;
     // timing mode: events around the SpMV of the first two (direct) iterations
     std::vector<cudaEvent_t> pcg1_ev;                  // [4]
+    double pcg1_fused_ms = 0.0;                        // event time of the persistent PCG launches
+    long long pcg1_fused_iters = 0;
+    bool concurrent = false;                           // inside nas_batch_run
     double pcg1_spmv_ms = 0.0;                          // this step: SpMV kernel time
     long long pcg1_spmv_launches = 0;
     // mixed precision: FP32 copies and work arrays of the Poisson solve

@@ -279,10 +279,12 @@ static int pcg_mixed(nas_ctx* c, const Csr& A, const double* Dinv, int N, const 
 }
 
 // Single right-hand-side PCG with the fused kernels (kernels_pcg1.cu),
-// replayed kPcg1Graph iterations at a time from a captured CUDA graph.  The
-// graph is captured once per context on a private stream (the graph's
-// pointers are the context's fixed Poisson buffers) and launched on the
-// context stream; the host reads the convergence flag after each replay.
+// kPcg1Graph iterations per host round trip: either one persistent
+// cooperative launch (the two-level FP64 solve with the sliced-ELL matrix),
+// or the per-phase kernels replayed from a captured CUDA graph.  The graph is
+// captured once per context on a private stream (the graph's pointers are
+// the context's fixed Poisson buffers) and launched on the context stream;
+// the host reads the convergence flag after each launch.
 static const int kPcg1Graph = 16;
 
 static int pcg1_lanes(nas_ctx* c) {
@@ -296,7 +298,7 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     Phase ph(c, NAS_PH_SPMV);
     const int64_t n = A.n_rows;
     cudaStream_t s = c->stream;
-    const int G = pcg1_blocks();
+    const int G = std::max(pcg1_blocks(), pcg1_fused_blocks());
     c->d_pcg1_part.ensure(3 * (size_t)G);
     c->d_pcg1_scal.ensure(8);
     c->d_pcg1_flags.ensure(4);
@@ -366,6 +368,40 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     int flags[4] = {1, 0, 0, 0};
     NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_scal.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
     NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_flags.p, flags, sizeof(flags), cudaMemcpyHostToDevice, s));
+    const bool timed = c->opt.timing != 0;
+    if (timed && c->pcg1_ev.empty()) {
+        c->pcg1_ev.resize(4);
+        for (auto& e : c->pcg1_ev) NAS_CUDA(cudaEventCreate(&e));
+    }
+    // persistent form: kPcg1Graph iterations per cooperative launch
+    const int fb = pcg1_fused_blocks();
+    if (c->opt.poisson_fused && st.two_level && st.sell_ptr && fb > 0 && !c->concurrent) {
+        c->d_pcg1_bar.ensure(2);
+        NAS_CUDA(cudaMemsetAsync(c->d_pcg1_bar.p, 0, 2 * sizeof(unsigned), s));
+        int it = 0;
+        while (true) {
+            if (timed) NAS_CUDA(cudaEventRecord(c->pcg1_ev[0], s));
+            launch_pcg1_fused(st, c->d_pcg1_bar.p, c->d_pcg1_flags.p + 3, kPcg1Graph, fb, s);
+            if (timed) NAS_CUDA(cudaEventRecord(c->pcg1_ev[1], s));
+            NAS_CUDA(cudaMemcpyAsync(flags, c->d_pcg1_flags.p, sizeof(flags), cudaMemcpyDeviceToHost, s));
+            sync(c);
+            if (flags[3]) fail(NAS_E_CUDA, "persistent Poisson PCG: a grid barrier wait exceeded its limit");
+            if (timed) {
+                float ms = 0.0f;
+                NAS_CUDA(cudaEventElapsedTime(&ms, c->pcg1_ev[0], c->pcg1_ev[1]));
+                c->pcg1_fused_ms += ms;
+                c->pcg1_fused_iters += flags[2] - it;
+            }
+            it = flags[2];
+            if (flags[1]) fail(NAS_E_BREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite)");
+            if (!flags[0] || it >= maxit) break;
+        }
+        *converged = (flags[0] == 0);
+        c->spmv_bytes += (double)it * (12.0 * A.rowptr_nnz + 108.0 * n);
+        c->spmv_flops += (double)it * (2.0 * A.rowptr_nnz + 10.0 * n);
+        c->pcg1_iters += it;
+        return it;
+    }
     // graph of kPcg1Graph iterations for this (A, x, b) set of pointers
     const int lanes = pcg1_lanes(c);
     Pcg1Key key;
@@ -375,11 +411,6 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     key.tol = 1.0;
     key.lanes = lanes;
     key.n = n;
-    const bool timed = c->opt.timing != 0;
-    if (timed && c->pcg1_ev.empty()) {
-        c->pcg1_ev.resize(4);
-        for (auto& e : c->pcg1_ev) NAS_CUDA(cudaEventCreate(&e));
-    }
     if (!c->pcg1_exec || !(key == c->pcg1_key)) {
         if (c->pcg1_exec) cudaGraphExecDestroy(c->pcg1_exec);
         c->pcg1_exec = nullptr;
@@ -1431,6 +1462,8 @@ int ctx_step(nas_ctx* c, nas_report* rep) {
     c->spmm_bytes = c->spmm_flops = c->spmv_bytes = c->spmv_flops = 0;
     c->pcg1_spmv_ms = 0.0;
     c->pcg1_spmv_launches = 0;
+    c->pcg1_fused_ms = 0.0;
+    c->pcg1_fused_iters = 0;
     c->last_lobpcg_iters = 0;
     int status = NAS_OK;
     if (!c->anl_valid) {
@@ -1512,6 +1545,8 @@ void ctx_fill_report(nas_ctx* c, nas_report* rep) {
     rep->eig_iters = c->last_lobpcg_iters;
     rep->poisson_spmv_ms = c->pcg1_spmv_ms;
     rep->poisson_spmv_launches = c->pcg1_spmv_launches;
+    rep->poisson_fused_ms = c->pcg1_fused_ms;
+    rep->poisson_fused_iters = c->pcg1_fused_iters;
 }
 
 // ------------------------------------------------------------------ state in/out
@@ -1575,6 +1610,8 @@ void ctx_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {
             v[11] = c->F.order;
             v[12] = c->C.ne;
             v[13] = c->sell_entries;
+            v[14] = (int64_t)c->GM.trow.size();
+            v[15] = c->GM.tpieces.npieces();
         }
         put_host(v, sizeof(v));
         return;

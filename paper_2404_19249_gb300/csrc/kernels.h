@@ -306,6 +306,13 @@ void launch_pcg1_iteration(const Pcg1& s, int par, int lanes_per_row, cudaStream
 void launch_pcg1_iteration(const Pcg1f& s, int par, int lanes_per_row, cudaStream_t st, cudaEvent_t ev0 = nullptr,
                            cudaEvent_t ev1 = nullptr);
 int pcg1_kernels_per_iteration(int two_level, int64_t npieces);
+// Persistent (cooperative) form of the two-level FP64 iteration with the
+// sliced-ELL matrix: one launch runs up to `chunk` iterations (starting at
+// parity 0) with grid-wide barriers between the phases; bar = two zeroed
+// unsigned counters, err = flag set if a barrier wait exceeded its limit.
+// pcg1_fused_blocks() is the co-resident grid size (0: no cooperative launch).
+int pcg1_fused_blocks();
+void launch_pcg1_fused(const Pcg1& s, unsigned* bar, int* err, int chunk, int blocks, cudaStream_t st);
 // sliced ELL (32 rows per slice) of a CSR matrix: sell_ptr from the host,
 // columns and values filled on the device (padding: column = row, value 0)
 void launch_sell_fill(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,

@@ -174,13 +174,16 @@ __device__ __forceinline__ void lda_point(double rho, double& eps, double& v) {
         v = 0.0;
         return;
     }
-    const double PI = 3.14159265358979323846;
     const double A = 0.0311, B = -0.048, GAMMA = -0.1423, BETA1 = 1.0529, BETA2 = 0.3334,
                  C = 0.0020, D = -0.0116;
-    double r13 = cbrt(rho);
-    double eps_x = -0.75 * cbrt(3.0 / PI) * r13;
-    double v_x = -cbrt(3.0 * rho / PI);
-    double rs = cbrt(3.0 / (4.0 * PI * rho));
+    // one cube root per point (sm_103 issues 2 FP64 FMA per clock per SM):
+    // v_x = -(3 rho / pi)^(1/3) = -CX rho^(1/3), eps_x = 3/4 v_x,
+    // r_s = (3 / (4 pi rho))^(1/3) = CRS / rho^(1/3)
+    const double CX = 0.9847450218426965411790, CRS = 0.6203504908994000166680;
+    const double r13 = cbrt(rho);
+    const double v_x = -CX * r13;
+    const double eps_x = 0.75 * v_x;
+    const double rs = CRS / r13;
     double eps_c, v_c;
     if (rs < 1.0) {
         double ln = log(rs);
@@ -188,9 +191,9 @@ __device__ __forceinline__ void lda_point(double rho, double& eps, double& v) {
         v_c = A * ln + (B - A / 3.0) + (2.0 / 3.0) * C * rs * ln + (1.0 / 3.0) * (2.0 * D - C) * rs;
     } else {
         double sq = sqrt(rs);
-        double den = 1.0 + BETA1 * sq + BETA2 * rs;
-        eps_c = GAMMA / den;
-        v_c = eps_c * (1.0 + (7.0 / 6.0) * BETA1 * sq + (4.0 / 3.0) * BETA2 * rs) / den;
+        double inv_den = 1.0 / (1.0 + BETA1 * sq + BETA2 * rs);
+        eps_c = GAMMA * inv_den;
+        v_c = eps_c * (1.0 + (7.0 / 6.0) * BETA1 * sq + (4.0 / 3.0) * BETA2 * rs) * inv_den;
     }
     eps = eps_x + eps_c;
     v = v_x + v_c;

@@ -268,6 +268,215 @@ __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_dir(Pcg1T<T> s, int par
 
 int pcg1_blocks() { return kPcgBlocks; }
 
+// ---- persistent form of the two-level FP64 iteration (sliced-ELL matrix)
+// One cooperative launch runs up to `chunk` whole iterations; the phases of an
+// iteration (SpMV, update, restriction pieces, restriction sums, coarse solve,
+// prolongation, new direction) are separated by grid-wide barriers instead of
+// kernel boundaries, so the blocks stay resident and keep their caches warm.
+// The grid is the per-phase kernels' grid (kPcgBlocks, one full wave) and
+// every phase does the arithmetic of the kernel it replaces in the same order,
+// with the same rows per thread and the same per-block partial sums, so both
+// forms give bit-identical iterates.  Arrays written during the
+// launch (p, q, r, z, x, the partial sums, cpart, cvec, yvec) are read with
+// ordinary coherent loads; only the matrix, the transfer and the diagonal go
+// through the read-only path.
+static const int kFusedMinBlocks = 8;                       // per SM, <= 32 registers
+static const unsigned long long kBarrierNs = 1000000000ull;  // 1 s wait limit
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident).  bar[0]
+// counts arrivals, bar[1] is the generation.  A wait longer than kBarrierNs
+// sets *err and returns; once *err is set no barrier waits.  Returns the same
+// value in every thread of the block: true while no error was flagged.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, int* sh_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = *(volatile int*)err == 0;
+        if (ok) {
+            const unsigned g = ld_acquire_gpu(bar + 1);
+            __threadfence();
+            if (atomicAdd(bar, 1u) == nblocks - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const unsigned long long t0 = globaltimer_ns();
+                while (ld_acquire_gpu(bar + 1) == g) {
+                    if (globaltimer_ns() - t0 > kBarrierNs) {
+                        atomicExch(err, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+        *sh_ok = ok;
+    }
+    __syncthreads();
+    return *sh_ok != 0;
+}
+
+__global__ void __launch_bounds__(kPcgThreads, kFusedMinBlocks)
+    k_pcg1_fused(Pcg1 s, unsigned* bar, int* err, int chunk) {
+    __shared__ double sh[kPcgThreads];
+    __shared__ int sh_ok;
+    const unsigned G = gridDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)G * blockDim.x;
+    const int lane = threadIdx.x % 32;
+    const int64_t warp = tid / 32, nwarps = nth / 32;
+    const int64_t* __restrict__ sp = s.sell_ptr;
+    const int32_t* __restrict__ cl = s.sell_col;
+    const double* __restrict__ va = s.sell_val;
+    const double* __restrict__ dinv = s.dinv;
+    const int32_t* __restrict__ trow = s.trow;
+    const double* __restrict__ tval = s.tval;
+    const int32_t* __restrict__ icol = s.icol;
+    const double* __restrict__ ival = s.ival;
+    const double* __restrict__ khinv = s.khinv;
+    int par = 0;
+    for (int it = 0; it < chunk; ++it) {
+        // the flags change only before a barrier, so every block sees the same values
+        if (!*(volatile int*)s.active || *(volatile int*)s.breakdown) break;
+        // q = A p, partial sums of p.q
+        {
+            double dot = 0;
+            for (int64_t row = tid; row < s.n; row += nth) {
+                const int64_t slice = row >> 5;
+                const int rl = (int)(row & 31);
+                const int64_t b = sp[slice], e = sp[slice + 1];
+                double a0 = 0, a1 = 0;
+                int64_t idx = b + rl;
+                for (; idx + 32 < e; idx += 64) {
+                    const int c0 = cl[idx], c1 = cl[idx + 32];
+                    const double v0 = va[idx], v1 = va[idx + 32];
+                    a0 += v0 * s.p[c0];
+                    a1 += v1 * s.p[c1];
+                }
+                if (idx < e) a0 += va[idx] * s.p[cl[idx]];
+                const double acc = a0 + a1;
+                s.q[row] = acc;
+                dot += s.p[row] * acc;
+            }
+            block_store_sum(dot, sh, s.part_pq + blockIdx.x);
+        }
+        if (!grid_barrier(bar, err, G, &sh_ok)) return;
+        // alpha = rz / p.q; x += alpha p; r -= alpha q; partial sums of r.r
+        {
+            const double pq = block_sum_partials(s.part_pq, (int)G, sh);
+            const double rz = s.scal[par];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) *s.breakdown = 1;
+                break;  // every block computed the same pq
+            }
+            const double alpha = rz / pq;
+            double srr = 0;
+            for (int64_t i = tid; i < s.n; i += nth) {
+                s.x[i] += alpha * s.p[i];
+                const double r = s.r[i] - alpha * s.q[i];
+                s.r[i] = r;
+                srr += r * r;
+            }
+            block_store_sum(srr, sh, s.part_rr + blockIdx.x);
+        }
+        if (!grid_barrier(bar, err, G, &sh_ok)) return;
+        // I^T r: one warp per balanced piece
+        for (int64_t q = warp; q < s.tpc.npieces; q += nwarps) {
+            double acc = 0;
+            for (int64_t p = s.tpc.piece_start[q] + lane; p < s.tpc.piece_start[q + 1]; p += 32)
+                acc += tval[p] * s.r[trow[p]];
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            if (lane == 0) s.cpart[q] = acc;
+        }
+        if (!grid_barrier(bar, err, G, &sh_ok)) return;
+        for (int64_t a = tid; a < s.nH; a += nth) {
+            double acc = 0;
+            for (int q = s.tpc.seg_piece[a]; q < s.tpc.seg_piece[a + 1]; ++q) acc += s.cpart[q];
+            s.cvec[a] = acc;
+        }
+        if (!grid_barrier(bar, err, G, &sh_ok)) return;
+        // y = K_H^-1 c: one warp per row
+        for (int64_t a = warp; a < s.nH; a += nwarps) {
+            const double* row = khinv + a * s.nH;
+            double acc = 0;
+            for (int64_t b = lane; b < s.nH; b += 32) acc += row[b] * s.cvec[b];
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            if (lane == 0) s.yvec[a] = acc;
+        }
+        if (!grid_barrier(bar, err, G, &sh_ok)) return;
+        // z = D^-1 r + I y, partial sums of r.z
+        {
+            double srz = 0;
+            for (int64_t i = tid; i < s.n; i += nth) {
+                const double r = s.r[i];
+                double z = dinv[i] * r;
+                for (int k = 0; k < 4; ++k) {
+                    const int a = icol[4 * i + k];
+                    if (a >= 0) z += ival[4 * i + k] * s.yvec[a];
+                }
+                s.z[i] = z;
+                srz += r * z;
+            }
+            block_store_sum(srz, sh, s.part_rz + blockIdx.x);
+        }
+        if (!grid_barrier(bar, err, G, &sh_ok)) return;
+        // beta = rz_new / rz; p = z + beta p; stop test
+        {
+            const double rz_new = block_sum_partials(s.part_rz, (int)G, sh);
+            const double rr = block_sum_partials(s.part_rr, (int)G, sh);
+            const double rz = s.scal[par];
+            const double beta = rz != 0.0 ? rz_new / rz : 0.0;
+            for (int64_t i = tid; i < s.n; i += nth) s.p[i] = s.z[i] + beta * s.p[i];
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                s.scal[par ^ 1] = rz_new;
+                s.scal[3] = rr;
+                *s.iters += 1;
+                if (!isfinite(rr)) *s.breakdown = 1;
+                if (rr <= s.tol2 * s.scal[2] || !isfinite(rr)) *s.active = 0;
+            }
+        }
+        if (!grid_barrier(bar, err, G, &sh_ok)) return;
+        par ^= 1;
+    }
+}
+
+int pcg1_fused_blocks() {
+    static int blocks = -1;
+    if (blocks < 0) {
+        int dev = 0, sms = 0, coop = 0, per_sm = 0;
+        blocks = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg1_fused, kPcgThreads, 0) == cudaSuccess &&
+            (int64_t)per_sm * sms >= kPcgBlocks)
+            blocks = kPcgBlocks;  // the per-phase kernels' grid: same partial sums, same iterates
+        cudaGetLastError();
+    }
+    return blocks;
+}
+
+void launch_pcg1_fused(const Pcg1& s, unsigned* bar, int* err, int chunk, int blocks, cudaStream_t st) {
+    if (blocks <= 0 || !s.two_level || !s.sell_ptr) fail(NAS_E_INVALID_ARG, "fused PCG: unsupported configuration");
+    Pcg1 sv = s;
+    void* args[4] = {(void*)&sv, (void*)&bar, (void*)&err, (void*)&chunk};
+    NAS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pcg1_fused, dim3((unsigned)blocks), dim3(kPcgThreads), args,
+                                         0, st));
+    ++g_launch_count;
+}
+
 template <typename T>
 static void pcg1_coarse_correction(const Pcg1T<T>& s, cudaStream_t st) {
     const int warps_per_block = kPcgThreads / 32;

@@ -88,9 +88,10 @@ static void reduce_standard(int m, const std::vector<double>& L, const double* A
         }
 }
 
-// Householder tridiagonalisation of symmetric C (full storage, overwritten).
-// Reflector j acts on entries j+1..m-1: H_j = I - tau_j v_j v_j^T with v_j
-// stored in V (row j), v_j[j+1] = 1.  T = Q^T C Q, Q = H_0 H_1 ... H_{m-3}.
+// Householder tridiagonalisation of symmetric C (row-major; only the lower
+// triangle is read and updated).  Reflector j acts on entries j+1..m-1:
+// H_j = I - tau_j v_j v_j^T with v_j stored in V (row j), v_j[j+1] = 1.
+// T = Q^T C Q, Q = H_0 H_1 ... H_{m-3}.
 static void tridiagonalise(int m, std::vector<double>& C, std::vector<double>& d, std::vector<double>& e,
                            std::vector<double>& V, std::vector<double>& tau) {
     d.assign(m, 0.0);
@@ -120,18 +121,36 @@ static void tridiagonalise(int m, std::vector<double>& C, std::vector<double>& d
         tau[j] = t;
         e[j] = beta;
         for (int i = 0; i < n1; ++i) V[(size_t)j * m + j + 1 + i] = x[i];
-        // p = tau * C22 v
-#pragma omp parallel for schedule(static) if (n1 > 256)
-        for (int i = 0; i < n1; ++i) p[i] = t * dot(&C[(size_t)(j + 1 + i) * m + j + 1], x, n1);
+        // p = tau * C22 v from the lower triangle: row i contributes its dot
+        // with v to p_i and, through the mirrored entries, v_i times the row
+        // to p_0..p_{i-1}
+        for (int i = 0; i < n1; ++i) p[i] = 0.0;
+        for (int i = 0; i < n1; ++i) {
+            const double* Ci = &C[(size_t)(j + 1 + i) * m + j + 1];
+            const double xi = x[i];
+            double s0 = 0.0, s1 = 0.0;
+            int k = 0;
+            for (; k + 2 <= i; k += 2) {
+                s0 += Ci[k] * x[k];
+                s1 += Ci[k + 1] * x[k + 1];
+                p[k] += Ci[k] * xi;
+                p[k + 1] += Ci[k + 1] * xi;
+            }
+            for (; k < i; ++k) {
+                s0 += Ci[k] * x[k];
+                p[k] += Ci[k] * xi;
+            }
+            p[i] += (s0 + s1) + Ci[i] * xi;
+        }
+        for (int i = 0; i < n1; ++i) p[i] *= t;
         double pv = 0.0;
         for (int i = 0; i < n1; ++i) pv += p[i] * x[i];
         for (int i = 0; i < n1; ++i) w[i] = p[i] - 0.5 * t * pv * x[i];
-        // C22 -= v w^T + w v^T
-#pragma omp parallel for schedule(static) if (n1 > 256)
+        // C22 -= v w^T + w v^T (lower triangle)
         for (int i = 0; i < n1; ++i) {
             double* Ci = &C[(size_t)(j + 1 + i) * m + j + 1];
-            double xi = x[i], wi = w[i];
-            for (int k = 0; k < n1; ++k) Ci[k] -= xi * w[k] + wi * x[k];
+            const double xi = x[i], wi = w[i];
+            for (int k = 0; k <= i; ++k) Ci[k] -= xi * w[k] + wi * x[k];
         }
     }
     for (int i = 0; i < m; ++i) d[i] = C[(size_t)i * m + i];
@@ -152,20 +171,23 @@ static int sturm_count(int m, const std::vector<double>& d, const std::vector<do
     return cnt;
 }
 
-// Solve (T - lam I) x = b for tridiagonal T by Gaussian elimination with
-// partial pivoting (x overwrites b).
+// LU factorisation with partial pivoting of (T - lam I), T tridiagonal, for
+// repeated solves (inverse iteration).  U has diagonal 1/ainv, super-diagonal
+// c and second super-diagonal u2; row i+1 was swapped with row i when
+// swp[i], and l[i] is the multiplier of the elimination step i.
 struct TriWork {
-    std::vector<double> a, c, u2;
+    std::vector<double> ainv, c, u2, l;
+    std::vector<char> swp;
 };
 
-static void tri_solve(int m, const std::vector<double>& d, const std::vector<double>& e, double lam,
-                      double pert, std::vector<double>& b, TriWork& w) {
-    // U (after elimination with row swaps) has diagonal a, super-diagonal c and
-    // second super-diagonal u2
-    w.a.resize(m);
+static void tri_factor(int m, const std::vector<double>& d, const std::vector<double>& e, double lam,
+                       double pert, TriWork& w) {
+    w.ainv.resize(m);
     w.c.resize(m);
     w.u2.assign(m, 0.0);
-    double* a = w.a.data();
+    w.l.assign(m, 0.0);
+    w.swp.assign(m, 0);
+    double* a = w.ainv.data();
     double* c = w.c.data();
     double* u2 = w.u2.data();
     for (int i = 0; i < m; ++i) {
@@ -178,7 +200,7 @@ static void tri_solve(int m, const std::vector<double>& d, const std::vector<dou
             if (a[i] == 0.0) a[i] = pert;
             const double l = sub / a[i];
             a[i + 1] -= l * c[i];
-            b[i + 1] -= l * b[i];
+            w.l[i] = l;
         } else {
             // swap rows i and i+1
             const double l = a[i] / sub;
@@ -189,15 +211,26 @@ static void tri_solve(int m, const std::vector<double>& d, const std::vector<dou
             u2[i] = ci1;
             a[i + 1] = ci - l * ai1;
             if (i + 1 < m - 1) c[i + 1] = -l * ci1;
-            std::swap(b[i], b[i + 1]);
-            b[i + 1] -= l * b[i];
+            w.l[i] = l;
+            w.swp[i] = 1;
         }
     }
     if (a[m - 1] == 0.0) a[m - 1] = pert;
-    // back substitution
-    b[m - 1] /= a[m - 1];
-    if (m >= 2) b[m - 2] = (b[m - 2] - c[m - 2] * b[m - 1]) / a[m - 2];
-    for (int i = m - 3; i >= 0; --i) b[i] = (b[i] - c[i] * b[i + 1] - u2[i] * b[i + 2]) / a[i];
+    for (int i = 0; i < m; ++i) a[i] = 1.0 / a[i];
+}
+
+// b <- (T - lam I)^-1 b with the factors of tri_factor
+static void tri_apply(int m, const TriWork& w, double* b) {
+    const double* a = w.ainv.data();
+    const double* c = w.c.data();
+    const double* u2 = w.u2.data();
+    for (int i = 0; i + 1 < m; ++i) {
+        if (w.swp[i]) std::swap(b[i], b[i + 1]);
+        b[i + 1] -= w.l[i] * b[i];
+    }
+    b[m - 1] *= a[m - 1];
+    if (m >= 2) b[m - 2] = (b[m - 2] - c[m - 2] * b[m - 1]) * a[m - 2];
+    for (int i = m - 3; i >= 0; --i) b[i] = (b[i] - c[i] * b[i + 1] - u2[i] * b[i + 2]) * a[i];
 }
 
 // sqrt(f^2 + g^2), with the scaled library routine only outside the range
@@ -257,12 +290,8 @@ static bool tridiag_eigvals(int m, const std::vector<double>& d_in, const std::v
     return true;
 }
 
-int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, double* U) {
-    if (k > m) return -1;
-    std::vector<double> L((size_t)m * m);
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j <= i; ++j) L[(size_t)i * m + j] = B[(size_t)i * m + j];
-    if (!cholesky(m, L)) return -1;
+// dense_gen_eig with the Cholesky factor L of B given (row-major lower)
+static void gen_eig_factored(int m, const double* A, const std::vector<double>& L, int k, double* lam, double* U) {
     std::vector<double> C;
     reduce_standard(m, L, A, C);
     std::vector<double> d, e, V, tau;
@@ -313,9 +342,9 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
     for (int i = 0; i < k; ++i) {
         if (i > 0 && std::fabs(w[i] - w[i - 1]) > clus) start = i;
         for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * std::sin(0.7 * r + 1.3 * i);
-        double shift = w[i];
+        tri_factor(m, d, e, w[i], pert, tw);
         for (int it = 0; it < 4; ++it) {
-            tri_solve(m, d, e, shift, pert, x, tw);
+            tri_apply(m, tw, x.data());
             for (int j = start; j < i; ++j) {
                 const double* zj = &Z[(size_t)j * m];
                 const double s = dot(zj, x.data(), m);
@@ -362,6 +391,15 @@ int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, d
     }
     for (int r = 0; r < m; ++r)
         for (int i = 0; i < k; ++i) U[(size_t)r * k + i] = Z[(size_t)i * m + r];
+}
+
+int dense_gen_eig(int m, const double* A, const double* B, int k, double* lam, double* U) {
+    if (k > m) return -1;
+    std::vector<double> L((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j <= i; ++j) L[(size_t)i * m + j] = B[(size_t)i * m + j];
+    if (!cholesky(m, L)) return -1;
+    gen_eig_factored(m, A, L, k, lam, U);
     return 0;
 }
 
@@ -644,11 +682,10 @@ int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, 
             for (int a = 0; a < ns; ++a) pmin = std::min(pmin, L[(size_t)a * ns + a] * L[(size_t)a * ns + a]);
             if (pmin >= 1e-8 * gmax) {
                 std::vector<double> lam(k), U((size_t)ns * k);
-                if (dense_gen_eig(ns, H.data(), G.data(), k, lam.data(), U.data()) == 0) {
-                    theta.assign(lam.begin(), lam.end());
-                    Y.swap(U);
-                    return 0;
-                }
+                gen_eig_factored(ns, H.data(), L, k, lam.data(), U.data());
+                theta.assign(lam.begin(), lam.end());
+                Y.swap(U);
+                return 0;
             }
         }
     }

@@ -41,7 +41,7 @@ class nas_options(C.Structure):
         ("check_every", C.c_int), ("timing", C.c_int), ("eig_dense_max", C.c_int),
         ("eig_tol", C.c_double), ("spmv_lanes", C.c_int), ("poisson_two_level", C.c_int),
         ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
-        ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int),
+        ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int), ("poisson_fused", C.c_int),
     ]
 
 
@@ -54,6 +54,7 @@ class nas_report(C.Structure):
         ("phase_calls", C.c_longlong * 16), ("spmm_bytes", C.c_double), ("spmm_flops", C.c_double),
         ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_double), ("spmv_flops", C.c_double),
         ("eig_iters", C.c_int), ("poisson_spmv_ms", C.c_double), ("poisson_spmv_launches", C.c_longlong),
+        ("poisson_fused_ms", C.c_double), ("poisson_fused_iters", C.c_longlong),
     ]
 
     def as_dict(self):
@@ -290,7 +291,7 @@ class Solver:
     def sizes(self):
         v = np.zeros(16, dtype=np.int64)
         nas_get(self.h, NAS_Q_SIZES, v)
-        keys = ["n", "nnz", "nH", "hnnz", "ne", "nq", "nnode", "N", "nb", "nnzb", "nv", "order", "nec", "sell"]
+        keys = ["n", "nnz", "nH", "hnnz", "ne", "nq", "nnode", "N", "nb", "nnzb", "nv", "order", "nec", "sell", "tnnz", "tpieces"]
         return {k: int(v[i]) for i, k in enumerate(keys)}
 
     def get(self, what):

@@ -48,6 +48,7 @@ def test_options_struct_layout(libpath):
     assert o.tol_bvp == 1e-12 and o.max_inner == 50 and o.check_every == 1 and o.hartree == 1
     assert o.eig_dense_max == 1200 and o.timing == 0 and o.eig_device == 1 and o.poisson_two_level == 1
     assert o.eig_adapt == 1e-3 and o.poisson_adaptive == 0 and o.eig_precond == 1
+    assert o.poisson_sell == 1 and o.poisson_fused == 0
 
 
 def test_create_reports_errors_without_crashing(libpath):

@@ -79,9 +79,19 @@ def instance(args):
     return make_instance(args.workload, **kw)
 
 
-def kernel_source_hash(name):
+def kernel_source_hash(name, kernel):
+    """sha256 of one kernel's source text in csrc/<name>: the file's launch
+    constants (lines starting "static const int kPcg") and the kernel's
+    definition from its template line to its closing brace, so that edits to
+    other kernels of the file leave the record of this one valid."""
     import hashlib
-    return hashlib.sha256(open(os.path.join(ROOT, "paper_2404_19249_gb300", "csrc", name), "rb").read()).hexdigest()
+    lines = open(os.path.join(ROOT, "paper_2404_19249_gb300", "csrc", name)).read().splitlines()
+    consts = [ln for ln in lines if ln.startswith("static const int kPcg")]
+    start = next(i for i, ln in enumerate(lines) if (" " + kernel + "(") in ln and "__global__" in ln)
+    if start > 0 and lines[start - 1].startswith("template"):
+        start -= 1
+    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+    return hashlib.sha256("\n".join(consts + lines[start:end + 1]).encode()).hexdigest()
 
 
 def spmv_traffic(sz, kernel="k_pcg1_spmv"):
@@ -95,7 +105,10 @@ def spmv_traffic(sz, kernel="k_pcg1_spmv"):
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
     except Exception:
         return None
-    if rec.get("source_sha256") != kernel_source_hash("kernels_pcg1.cu"):
+    try:
+        if rec.get("kernel_sha256") != kernel_source_hash("kernels_pcg1.cu", kernel):
+            return None
+    except StopIteration:
         return None
     per_launch = (rec["dram_read_bytes"] + rec["dram_write_bytes"]) / rec.get("iterations_per_launch", 1)
     return per_launch * sz["nnz"] / rec["nnz"]

@@ -294,49 +294,80 @@ namespace nas {
 // ---- preconditioner with a dense coarse block:
 //   W[i][j] = sum_b T[i][b] R[b][j]   (i < nH; T FP32 [nH][nH], FP32 products and sums)
 //   W[i][j] = Dinv[i] R[i][j]        (nH <= i < m)
-// Stage 1, grid (row blocks, kPcSplit): block (rb, sp) multiplies 32 rows of T
-// by the rows of R in its share of the b range, staging 32 columns of T and
-// the matching 32 rows of R in shared memory; thread = (column j, rows ty +
-// 8q).  Stage 2 adds the kPcSplit partial products in order.  FP32 is enough
-// for a preconditioner (a fixed symmetric positive definite operator close to
-// an inverse).
-static const int kPcRows = 32;
+// Stage 1, grid (row blocks of kPcRows, kPcSplit): block (rb, sp) multiplies
+// 128 rows of T by the rows of R in its share of the b range, 32 b at a time:
+// the 128 x 32 tile of T (coalesced row segments) and the 32 x 32 tile of R
+// (converted to FP32) are staged in shared memory, and each thread keeps a
+// 4 x 4 block of outputs in registers (rows 4 ty .. 4 ty + 3, columns
+// 4 tx .. 4 tx + 3), reading four T values and four R values as float4 per
+// step of b (16 multiply-adds per two vector loads).  Stage 2 adds the
+// kPcSplit partial products in order.  FP32 is enough for a preconditioner
+// (a fixed symmetric positive definite operator close to an inverse).
+static const int kPcRows = 128;
 static const int kPcK = 32;
 static const int kPcSplit = 16;
+static const int kPcLd = kPcK + 4;  // row pitch of the T tile: float4-aligned, conflict-free
 
 __global__ void __launch_bounds__(256) k_dense_precond_part(int64_t nH, int k, const float* T, const double* R,
                                                             float* part) {
-    __shared__ float Ts[kPcRows][kPcK + 1];
-    __shared__ float Rs[kPcK][kPcK + 1];
+    __shared__ __align__(16) float Ts[kPcRows][kPcLd];
+    __shared__ __align__(16) float Rs[kPcK][kPcK];
     const int64_t r0 = (int64_t)blockIdx.x * kPcRows;
     const int64_t span = (nH + kPcSplit - 1) / kPcSplit;
     const int64_t bbeg = (int64_t)blockIdx.y * span;
     const int64_t bend = bbeg + span < nH ? bbeg + span : nH;
-    const int tx = threadIdx.x % kPcK;  // column j
-    const int ty = threadIdx.x / kPcK;  // rows ty, ty+8, ty+16, ty+24
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int tx = threadIdx.x % 8;   // columns 4 tx .. 4 tx + 3
+    const int ty = threadIdx.x / 8;   // rows 4 ty .. 4 ty + 3
+    float acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
     for (int64_t b0 = bbeg; b0 < bend; b0 += kPcK) {
+        // T tile: element e -> (row e / 32, b e % 32); a warp reads 32 consecutive b of one row
+#pragma unroll 4
         for (int e = threadIdx.x; e < kPcRows * kPcK; e += blockDim.x) {
             const int rr = e / kPcK, cc = e % kPcK;
             const int64_t i = r0 + rr, b = b0 + cc;
             Ts[rr][cc] = (i < nH && b < bend) ? T[i * nH + b] : 0.f;
+        }
+        for (int e = threadIdx.x; e < kPcK * kPcK; e += blockDim.x) {
+            const int rr = e / kPcK, cc = e % kPcK;
             const int64_t bj = b0 + rr;
             Rs[rr][cc] = (bj < bend && cc < k) ? (float)R[bj * k + cc] : 0.f;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int bb = 0; bb < kPcK; ++bb) {
-            const float rv = Rs[bb][tx];
+#pragma unroll 2
+        for (int bb = 0; bb < kPcK; bb += 4) {
+            float4 tv[4], rv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += Ts[ty + 8 * q][bb] * rv;
+            for (int q = 0; q < 4; ++q) tv[q] = *reinterpret_cast<const float4*>(&Ts[4 * ty + q][bb]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rv[u] = *reinterpret_cast<const float4*>(&Rs[bb + u][4 * tx]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float t4[4] = {tv[q].x, tv[q].y, tv[q].z, tv[q].w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    acc[q][0] += t4[u] * rv[u].x;
+                    acc[q][1] += t4[u] * rv[u].y;
+                    acc[q][2] += t4[u] * rv[u].z;
+                    acc[q][3] += t4[u] * rv[u].w;
+                }
+            }
         }
         __syncthreads();
     }
-    if (tx < k)
-        for (int q = 0; q < 4; ++q) {
-            const int64_t i = r0 + ty + 8 * q;
-            if (i < nH) part[((int64_t)blockIdx.y * nH + i) * k + tx] = acc[q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = r0 + 4 * ty + q;
+        if (i >= nH) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = 4 * tx + c;
+            if (j < k) part[((int64_t)blockIdx.y * nH + i) * k + j] = acc[q][c];
         }
+    }
 }
 
 __global__ void k_dense_precond_sum(int64_t nH, int64_t m, int k, const float* part, const double* R,

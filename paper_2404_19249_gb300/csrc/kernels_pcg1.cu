@@ -187,18 +187,50 @@ __global__ void __launch_bounds__(kPcgThreads, 8) k_pcg1_update(Pcg1T<T> s, int 
 }
 
 // ---- two-level preconditioner z = D^-1 r + I K_H^-1 I^T r (coarse space of the method)
-// c = I^T r in two stages: one warp per balanced piece of an I^T row (lanes
-// stride, fixed-order shuffle sum), then each coarse row adds its pieces in order
+// Warp-level pieces shared by the per-phase kernels and the persistent form
+// (same arithmetic in both): the sum of one balanced piece of an I^T row, and
+// one row of the dense K_H^-1 times c (in T: FP64 storage for the FP64 solve,
+// since a FP32 -> FP64 conversion costs a slot of the FP64 pipe like an FMA).
+// Lanes stride by 32 with two independent accumulators (two gathers or loads
+// in flight per lane), then a fixed-order shuffle sum; lane 0 holds the result.
+template <typename T>
+__device__ __forceinline__ T piece_sum(const int32_t* trow, const T* tval, const T* r, int64_t beg, int64_t end,
+                                       int lane) {
+    T a0 = 0, a1 = 0;
+    int64_t p = beg + lane;
+    for (; p + 32 < end; p += 64) {
+        a0 += tval[p] * r[trow[p]];
+        a1 += tval[p + 32] * r[trow[p + 32]];
+    }
+    if (p < end) a0 += tval[p] * r[trow[p]];
+    T acc = a0 + a1;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T coarse_row_dot(const T* row, const T* c, int64_t nH, int lane) {
+    T a0 = 0, a1 = 0;
+    int64_t b = lane;
+    for (; b + 32 < nH; b += 64) {
+        a0 += row[b] * c[b];
+        a1 += row[b + 32] * c[b + 32];
+    }
+    if (b < nH) a0 += row[b] * c[b];
+    T acc = a0 + a1;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    return acc;
+}
+
+// c = I^T r in two stages: one warp per balanced piece of an I^T row, then
+// each coarse row adds its pieces in order
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads) k_pcg1_restrict(Pcg1T<T> s) {
     if (!*s.active || *s.breakdown) return;
     const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (q >= s.tpc.npieces) return;  // warp-uniform
-    T acc = 0;
-    for (int64_t p = s.tpc.piece_start[q] + lane; p < s.tpc.piece_start[q + 1]; p += 32)
-        acc += s.tval[p] * s.r[s.trow[p]];
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const T acc = piece_sum(s.trow, s.tval, s.r, s.tpc.piece_start[q], s.tpc.piece_start[q + 1], lane);
     if (lane == 0) s.cpart[q] = acc;
 }
 
@@ -220,10 +252,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg1_coarse(Pcg1T<T> s) {
     const int lane = threadIdx.x % 32;
     const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
     for (int64_t a = warp; a < s.nH; a += nwarps) {
-        const T* row = s.khinv + a * s.nH;
-        T acc = 0;
-        for (int64_t b = lane; b < s.nH; b += 32) acc += row[b] * s.cvec[b];
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        const T acc = coarse_row_dot(s.khinv + a * s.nH, s.cvec, s.nH, lane);
         if (lane == 0) s.yvec[a] = acc;
     }
 }
@@ -394,10 +423,7 @@ __global__ void __launch_bounds__(kPcgThreads, kFusedMinBlocks)
         if (!grid_barrier(bar, err, G, &sh_ok)) return;
         // I^T r: one warp per balanced piece
         for (int64_t q = warp; q < s.tpc.npieces; q += nwarps) {
-            double acc = 0;
-            for (int64_t p = s.tpc.piece_start[q] + lane; p < s.tpc.piece_start[q + 1]; p += 32)
-                acc += tval[p] * s.r[trow[p]];
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            const double acc = piece_sum(trow, tval, s.r, s.tpc.piece_start[q], s.tpc.piece_start[q + 1], lane);
             if (lane == 0) s.cpart[q] = acc;
         }
         if (!grid_barrier(bar, err, G, &sh_ok)) return;
@@ -409,10 +435,7 @@ __global__ void __launch_bounds__(kPcgThreads, kFusedMinBlocks)
         if (!grid_barrier(bar, err, G, &sh_ok)) return;
         // y = K_H^-1 c: one warp per row
         for (int64_t a = warp; a < s.nH; a += nwarps) {
-            const double* row = khinv + a * s.nH;
-            double acc = 0;
-            for (int64_t b = lane; b < s.nH; b += 32) acc += row[b] * s.cvec[b];
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            const double acc = coarse_row_dot(khinv + a * s.nH, s.cvec, s.nH, lane);
             if (lane == 0) s.yvec[a] = acc;
         }
         if (!grid_barrier(bar, err, G, &sh_ok)) return;

@@ -1,0 +1,72 @@
+"""Oracle checks against values printed in the paper (tests/golden/*.txt,
+each file states the passage it copies).  CPU only.
+
+* The paper's molecules (Sec. 5): the workload inputs are the printed
+  positions and charges.
+* The Perdew-Zunger constants (Sec. 3.1): the oracle's correlation energy
+  takes, on either side of r_s = 1, the values the printed constants give
+  there (A ln 1 + B + C ln 1 + D = B + D and gamma / (1 + beta1 + beta2)),
+  and the two branches meet to the printed digits.
+* The helium energy (Sec. 5): the discrete Kohn-Sham energy of a Galerkin
+  space lies above the LDA limit, which for helium lies above the exact
+  energy the paper quotes; it decreases under refinement.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lda
+from workloads.configs import PAPER_MOLECULES
+
+HERE = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(HERE, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def test_paper_molecules_are_the_printed_tables():
+    rows = _rows("paper_molecules.txt")
+    for mol in ("lih", "ch4", "c6h6"):
+        R, Z, _unit = PAPER_MOLECULES[mol]
+        printed = [r for r in rows if r[0] == mol]
+        assert len(printed) == len(Z)
+        np.testing.assert_array_equal(np.array([[float(v) for v in r[2:5]] for r in printed]), np.asarray(R))
+        np.testing.assert_array_equal(np.array([float(r[5]) for r in printed]), np.asarray(Z))
+
+
+def _eps_c(rs):
+    rho = 3.0 / (4.0 * np.pi * rs ** 3)
+    eps, _ = lda.lda(np.array([rho]))
+    eps_x = -0.75 * (3.0 / np.pi) ** (1.0 / 3.0) * rho ** (1.0 / 3.0)
+    return eps[0] - eps_x
+
+
+def test_correlation_branches_use_the_printed_constants():
+    k = {r[0]: float(r[1]) for r in _rows("lda_constants.txt")}
+    for name, val in (("A", lda.A), ("B", lda.B), ("gamma", lda.GAMMA), ("beta1", lda.BETA1),
+                      ("beta2", lda.BETA2), ("C", lda.C), ("D", lda.D)):
+        assert val == k[name], name
+    below = k["B"] + k["D"]                                   # r_s -> 1 from below
+    above = k["gamma"] / (1.0 + k["beta1"] + k["beta2"])     # r_s = 1 and above
+    assert abs(_eps_c(1.0 - 1e-9) - below) < 1e-9
+    assert abs(_eps_c(1.0) - above) < 1e-12
+    assert abs(_eps_c(1.0 + 1e-9) - above) < 1e-9
+    # the parametrisation is continuous at r_s = 1 to the printed digits
+    assert abs(below - above) < 1e-4
+
+
+def test_helium_energy_above_the_quoted_value_and_decreasing():
+    from oracle.nas import Problem
+    from workloads import make_instance
+    E_ref = {r[0]: float(r[1]) for r in _rows("reference_energies.txt")}["he"]
+    energies = []
+    for cells, coarse in ((8, 4), (12, 6)):
+        inst = make_instance("he_p1", cells=cells, coarse_cells=coarse, tol_scf=1e-8)
+        P = Problem(inst)
+        st = P.solve(max_outer=60)
+        energies.append(P.energy(st))
+    assert all(E > E_ref for E in energies)
+    assert energies[1] < energies[0]

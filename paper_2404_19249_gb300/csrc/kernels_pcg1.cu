@@ -6,8 +6,10 @@
 //   k_pcg1_dir   : beta = rz_new / rz; p = z + beta p; convergence test
 // With the two-level preconditioner z = D^-1 r + I K_H^-1 I^T r (I the
 // nonnested transfer of the method, K_H = I^T K I), z and r.z are computed by
-// three more kernels between update and dir: restriction I^T r, the dense
-// coarse solve with the precomputed K_H^-1, and prolongation.
+// four more kernels between update and dir: restriction I^T r (balanced piece
+// sums, then per-row sums), the dense coarse solve with the precomputed
+// K_H^-1, and prolongation.  k_pcg1_fused (below) runs the same seven phases
+// inside one persistent cooperative launch.
 // The scalars are not reduced by a separate launch: every block reduces the
 // fixed-size partial array itself, in the same fixed order, so all blocks
 // see bit-identical scalars and the result is deterministic.  The grid is a

@@ -57,6 +57,8 @@ def parse():
                         "one after another and concurrently")
     p.add_argument("--batch-steps", type=int, default=2)
     p.add_argument("--batch-threads", type=int, default=8)
+    p.add_argument("--batch-mixed", type=int, default=1,
+                   help="1: also run the batched instances in the mixed-precision mode")
     p.add_argument("--eig-precond", type=int, default=1,
                    help="LOBPCG preconditioner: 1 = inverse coarse stiffness on the coarse rows, 0 = diagonal")
     p.add_argument("--eig-adapt", type=float, default=1e-2,
@@ -270,8 +272,13 @@ def run_batch(args, nas, torch, device):
     """Independent small molecules (workloads.configs.batch_instances): the same
     contexts run `batch_steps` steps one after another (one host thread) and
     concurrently (nas_batch_run with batch_threads workers; the library runs
-    each context on a private stream), each time from the same initial state.  Returns instance-steps/s
-    for both and checks that both runs give bit-identical energies."""
+    each context on a private stream), each time from the same initial state,
+    in FP64, and (with --batch-mixed 1) concurrently in the mixed-precision
+    mode (FP32 Poisson and block PCG inside FP64 refinement).  Returns
+    instance-steps/s for each, checks that the two FP64 runs give
+    bit-identical energies, and reports the mixed run's largest energy and
+    eigenvalue differences from the sequential FP64 run."""
+    import numpy as np
     from workloads.configs import batch_instances
     insts = batch_instances(count=args.batch)
     stream = torch.cuda.current_stream(device).cuda_stream
@@ -282,9 +289,15 @@ def run_batch(args, nas, torch, device):
     setup = time.time() - t0
     out = {"instances": len(insts), "steps_each": args.batch_steps,
            "unknowns": [int(sv.sizes()["n"]) for sv in solvers]}
-    energies = {}
-    for mode, threads in (("sequential", 1), ("batched", args.batch_threads)):
+    energies, eigvals = {}, {}
+    modes = [("sequential", 1, 0), ("batched", args.batch_threads, 0)]
+    if args.batch_mixed:
+        modes.append(("batched_mixed", args.batch_threads, 1))
+    for mode, threads, precision in modes:
         for sv in solvers:
+            if sv.opt.precision != precision:
+                sv.opt.precision = precision
+                nas.nas_set_options(sv.h, sv.opt)
             sv.init()
         torch.cuda.synchronize(device)
         t = time.perf_counter()
@@ -292,10 +305,18 @@ def run_batch(args, nas, torch, device):
         torch.cuda.synchronize(device)
         dt = time.perf_counter() - t
         energies[mode] = [r.energy for r in reps]
+        eigvals[mode] = [sv.get(nas.NAS_Q_EIGVALS) for sv in solvers]
         out[mode] = {"instance_steps_per_s": len(insts) * args.batch_steps / dt, "s": dt, "threads": threads,
+                     "precision": "mixed" if precision else "fp64",
                      "status_ok": int(sum(st in (0, -5) for st in status))}
     out["speedup"] = out["batched"]["instance_steps_per_s"] / out["sequential"]["instance_steps_per_s"]
     out["identical_results"] = energies["sequential"] == energies["batched"]
+    if args.batch_mixed:
+        out["speedup_mixed"] = out["batched_mixed"]["instance_steps_per_s"] / out["sequential"]["instance_steps_per_s"]
+        out["batched_mixed"]["max_energy_diff_ha"] = float(max(
+            abs(a - b) for a, b in zip(energies["batched_mixed"], energies["sequential"])))
+        out["batched_mixed"]["max_eigenvalue_diff_ha"] = float(max(
+            float(np.max(np.abs(a - b))) for a, b in zip(eigvals["batched_mixed"], eigvals["sequential"])))
     out["setup_s"] = setup
     for sv in solvers:
         sv.close()

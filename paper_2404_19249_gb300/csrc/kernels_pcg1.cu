@@ -478,18 +478,19 @@ __global__ void __launch_bounds__(kPcgThreads, kFusedMinBlocks)
 }
 
 int pcg1_fused_blocks() {
-    static int blocks = -1;
-    if (blocks < 0) {
-        int dev = 0, sms = 0, coop = 0, per_sm = 0;
-        blocks = 0;
+    // computed once (a function-local static is initialised once even when
+    // nas_batch_run's worker threads arrive here together)
+    static const int blocks = [] {
+        int dev = 0, sms = 0, coop = 0, per_sm = 0, b = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg1_fused, kPcgThreads, 0) == cudaSuccess &&
             (int64_t)per_sm * sms >= kPcgBlocks)
-            blocks = kPcgBlocks;  // the per-phase kernels' grid: same partial sums, same iterates
+            b = kPcgBlocks;  // the per-phase kernels' grid: same partial sums, same iterates
         cudaGetLastError();
-    }
+        return b;
+    }();
     return blocks;
 }
 

@@ -34,7 +34,9 @@ def _worker(rank, world, port, out):
 def test_replica_aggregation_two_ranks():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    # the manager process is spawned too: forking a process that already
+    # runs threads (OpenMP, torch) can deadlock the child
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):

@@ -1,0 +1,114 @@
+"""bench.py host logic on the CPU: the batched-workload report (with a fake
+library, so that no GPU is needed) and the per-kernel source hash that keys
+the recorded DRAM traffic."""
+import importlib.util
+import os
+import types
+
+import numpy as np
+import pytest
+
+ROOT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..")
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _fake_library(n_inst, unconverged=()):
+    """A stand-in for the library: every instance reports energy -2 and
+    eigenvalues (-1, -0.5) in FP64; the mixed-precision run shifts them by
+    1e-11, except that instances listed in `unconverged` stop their inner SCF
+    at its cap and move by 0.05."""
+    state = {"precision": 0}
+
+    class Opt:
+        precision = 0
+
+    class Solver:
+        count = 0
+
+        def __init__(self, inst, **kw):
+            self.opt = Opt()
+            self.h = Solver.count
+            Solver.count += 1
+
+        def sizes(self):
+            return {"n": 100}
+
+        def init(self):
+            pass
+
+        def get(self, q):
+            shift = 0.0
+            if self.opt.precision:
+                shift = 0.05 if self.h in unconverged else 1e-11
+            return np.array([-1.0 + shift, -0.5])
+
+        def close(self):
+            pass
+
+    class Rep:
+        def __init__(self, h, precision):
+            bad = h in unconverged
+            self.energy = -2.0 + ((0.05 if bad else 1e-11) if precision else 0.0)
+            self.inner_converged = 0 if bad else 1
+
+    solvers = {}
+
+    def make(inst, **kw):
+        s = Solver(inst, **kw)
+        solvers[s.h] = s
+        return s
+
+    def batch_run(hs, steps, threads):
+        return [0] * len(hs), [Rep(h, solvers[h].opt.precision) for h in hs]
+
+    return types.SimpleNamespace(Solver=make, NAS_Q_EIGVALS=1, nas_set_options=lambda h, o: None,
+                                 nas_batch_run=batch_run), state
+
+
+def _torch():
+    cuda = types.SimpleNamespace(current_stream=lambda d: types.SimpleNamespace(cuda_stream=0),
+                                 synchronize=lambda d: None)
+    return types.SimpleNamespace(cuda=cuda)
+
+
+def test_batch_report_separates_unconverged_instances(bench, monkeypatch):
+    import workloads.configs as wc
+    monkeypatch.setattr(wc, "batch_instances", lambda count: [None] * count)
+    nas, _ = _fake_library(6, unconverged=(3,))
+    args = types.SimpleNamespace(batch=6, tol_poisson=1e-10, tol_bvp=1e-10, poisson_adaptive=1, batch_steps=1,
+                                 batch_threads=2, batch_mixed=1)
+    out = bench.run_batch(args, nas, _torch(), 0)
+    assert out["identical_results"] is True
+    bm = out["batched_mixed"]
+    assert bm["precision"] == "mixed" and out["batched"]["precision"] == "fp64"
+    assert bm["inner_scf_not_converged"] == 1 and out["sequential"]["inner_scf_not_converged"] == 1
+    assert bm["converged_instances"] == 5
+    assert abs(bm["max_energy_diff_ha"] - 0.05) < 1e-12
+    assert abs(bm["max_eigenvalue_diff_ha"] - 0.05) < 1e-12
+    assert bm["max_energy_diff_ha_converged"] < 1e-10
+    assert bm["max_eigenvalue_diff_ha_converged"] < 1e-10
+    assert "speedup_mixed" in out and "speedup" in out
+
+
+def test_kernel_hash_ignores_other_kernels(bench, tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2404_19249_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    base = ("static const int kPcgBlocks = 8;\n"
+            "template <typename T>\n__global__ void k_a(int x) {\n    x += 1;\n}\n"
+            "template <typename T>\n__global__ void k_b(int x) {\n    x += 2;\n}\n")
+    (csrc / "k.cu").write_text(base)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h_a = bench.kernel_source_hash("k.cu", "k_a")
+    (csrc / "k.cu").write_text(base.replace("x += 2;", "x += 3;"))
+    assert bench.kernel_source_hash("k.cu", "k_a") == h_a          # k_b edited: k_a's record stays
+    (csrc / "k.cu").write_text(base.replace("x += 1;", "x -= 1;"))
+    assert bench.kernel_source_hash("k.cu", "k_a") != h_a          # k_a edited
+    (csrc / "k.cu").write_text(base.replace("kPcgBlocks = 8", "kPcgBlocks = 16"))
+    assert bench.kernel_source_hash("k.cu", "k_a") != h_a          # launch constant edited

@@ -228,6 +228,34 @@ def cpu_baseline_from(sample, n_full):
     }
 
 
+def cpu_spmm_baseline(s, nas, sz, reps=3):
+    """SpMM bandwidth of the oracle's OpenMP CSR SpMM (oracle/spmm_omp.c) on
+    all host cores, for the benchmark's own matrix pattern (the stiffness
+    values, the same nonzeros as every fine operator) and N interleaved
+    right-hand sides, with the same algorithmic byte count as the GPU SpMM:
+    nnz (8 + 4) + 4 (n + 1) + 2 n N 8."""
+    import ctypes as C
+    import numpy as np
+    from oracle import build_c
+    lib = build_c.load()
+    rowptr = np.ascontiguousarray(s.get(nas.NAS_Q_ROWPTR), dtype=np.int32)
+    col = np.ascontiguousarray(s.get(nas.NAS_Q_COLIDX), dtype=np.int32)
+    val = np.ascontiguousarray(s.get(nas.NAS_Q_K), dtype=np.float64)
+    n, N = sz["n"], sz["N"]
+    X = np.random.default_rng(0).standard_normal((n, N))
+    Y = np.empty((n, N))
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+    def ptr(a):
+        return a.ctypes.data_as(C.c_void_p)
+
+    t = lib.oracle_spmm_seconds(n, ptr(rowptr), ptr(col), ptr(val), N, ptr(X), ptr(Y), threads, reps)
+    nbytes = 12.0 * len(val) + 4.0 * (n + 1) + 2.0 * n * N * 8.0
+    return {"gbs": nbytes / t / 1e9, "unit": "GB/s", "threads": threads, "N": N, "ms_per_product": t * 1e3,
+            "kind": "oracle C/OpenMP CSR SpMM (oracle/spmm_omp.c), the benchmark's pattern, mean of %d "
+                    "products after one untimed" % reps}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -593,6 +621,10 @@ def main():
             cpu = cpu_baseline_from(run_oracle_subprocess(2, 1), n)
         except Exception as ex:  # the baseline is reported, never required
             cpu = {"error": str(ex)[:200]}
+        try:
+            cpu["spmm"] = cpu_spmm_baseline(s, nas, sz)
+        except Exception as ex:
+            cpu["spmm"] = {"error": str(ex)[:200]}
     last = reps[-1]
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,

@@ -19,4 +19,7 @@ Modules and the passages they follow:
   nas          Algorithm 3 (augmented subspace step, eqs. Aux_Linear_Problem,
                st1-st7) with its inner SCF, plus the direct fine-space SCF used
                as the plain definition of the discrete ground state.
+  spmm_omp.c   (C, OpenMP; built by build_c.py) the plain CSR product with N
+               interleaved right-hand sides of Algorithm 3 step 1's block
+               solves, timed on all host cores as the CPU baseline's SpMM
 """

@@ -112,3 +112,19 @@ def test_kernel_hash_ignores_other_kernels(bench, tmp_path, monkeypatch):
     assert bench.kernel_source_hash("k.cu", "k_a") != h_a          # k_a edited
     (csrc / "k.cu").write_text(base.replace("kPcgBlocks = 8", "kPcgBlocks = 16"))
     assert bench.kernel_source_hash("k.cu", "k_a") != h_a          # launch constant edited
+
+
+def test_cpu_spmm_baseline_on_a_small_pattern(bench):
+    """The CPU SpMM baseline reads the library's CSR pattern and stiffness
+    values through nas_get; here a fake context serves a small 3D Laplacian."""
+    import scipy.sparse as sp
+    m = 12
+    T = sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+    I = sp.eye(m)
+    A = (sp.kron(sp.kron(T, I), I) + sp.kron(sp.kron(I, T), I) + sp.kron(sp.kron(I, I), T)).tocsr()
+    A.sort_indices()
+    nas = types.SimpleNamespace(NAS_Q_ROWPTR=0, NAS_Q_COLIDX=1, NAS_Q_K=2)
+    data = {0: A.indptr.astype(np.int32), 1: A.indices.astype(np.int32), 2: A.data.astype(np.float64)}
+    s = types.SimpleNamespace(get=lambda q: data[q])
+    out = bench.cpu_spmm_baseline(s, nas, {"n": A.shape[0], "N": 5}, reps=2)
+    assert out["gbs"] > 0 and out["threads"] >= 1 and out["N"] == 5 and out["unit"] == "GB/s"

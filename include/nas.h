@@ -7,7 +7,7 @@
  * Hamiltonian with V_ext, V_Har and LDA V_xc integrated by quadrature, the N
  * shifted linear boundary value problems solved by block preconditioned CG,
  * the nonnested transfer matrix I_H^h built by point location (Algorithm 1),
- * the blocks of the small augmented eigenproblem (eqs. st1-st7), the density
+ * the blocks of the small augmented eigenproblem (F_A, F_B of Sec. 3.3), the density
  * and the Hartree Poisson solve (Sec. 3.1).  The small dense generalized
  * eigenproblem F_A U = lambda F_B U is solved on the host.
  *
@@ -54,7 +54,7 @@ enum nas_potential { NAS_POT_COULOMB = 0, NAS_POT_SMOOTHED = 1, NAS_POT_HARMONIC
 /* ------------------------------------------------------------------ options */
 typedef struct nas_options {
     double mu;             /* shift of H~ = H + mu (Sec. 3.3); < 0 selects 8 M sum_k Z_k^2
-                              (the experiments' choice, Sec. 5)                     */
+                              (the experiments' choice, Sec. 4)                     */
     double tol_bvp;        /* relative residual of each of the N linear problems     */
     double tol_poisson;    /* relative residual of the Hartree Poisson solve         */
     double tol_scf;        /* ||rho^(l) - rho^(l-1)||_0 stop test of Algorithm 3     */
@@ -63,8 +63,8 @@ typedef struct nas_options {
     int    max_poisson;    /* iteration cap of the Poisson PCG                       */
     int    max_inner;      /* inner SCF iterations per step                          */
     int    max_outer;      /* steps of nas_solve                                     */
-    int    anderson_depth; /* Anderson history depth (Sec. 5: 5)                     */
-    double anderson_beta;  /* Anderson damping (Sec. 5: 0.7)                         */
+    int    anderson_depth; /* Anderson history depth (Sec. 4: 5)                     */
+    double anderson_beta;  /* Anderson damping (Sec. 4: 0.7)                         */
     int    hartree;        /* 1: include V_Har; 0: linear problem                    */
     int    xc;             /* 1: include LDA V_xc                                    */
     int    multipole;      /* Hartree boundary values: 0 monopole, 2 + quadrupole    */
@@ -117,6 +117,18 @@ typedef struct nas_options {
                               nas_batch_run; callers that run several contexts'
                               solves at once on one device from their own threads
                               keep 0.                                              */
+    double smearing;       /* > 0: Fermi-Dirac occupations at temperature kT = smearing
+                              (Ha), f_i = 2 / (1 + exp((lambda_i - eF)/kT)) with eF
+                              such that sum f_i = sum of the occupations given to
+                              nas_set_system (needs n_orb > n_el / 2), recomputed
+                              after every small eigensolve; the energy is then the
+                              free energy E - kT S (S = -2 sum g ln g + (1-g)
+                              ln(1-g), g = f/2).  0: the given occupations      */
+    double inner_adapt;    /* > 0: inexact inner SCF - each step's inner SCF stops at
+                              max(tol_inner, inner_adapt x the previous step's
+                              ||rho^(l) - rho^(l-1)||_0); the outer fixed point is
+                              unchanged (near it the inner SCF again runs to
+                              tol_inner).  0: tol_inner in every step           */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -125,16 +137,17 @@ typedef struct nas_options {
  * hartree = xc = 1, multipole = 0, omega = 1, check_every = 1, timing = 0,
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
- * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0. */
+ * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0,
+ * smearing = 0, inner_adapt = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
 #define NAS_MAX_PHASES 16
 enum nas_phase {
-    NAS_PH_ASSEMBLY = 0,   /* V_eff at quadrature points + CSR assembly (st3, st4)  */
+    NAS_PH_ASSEMBLY = 0,   /* V_eff at quadrature points + CSR assembly (Sec. 3.3)  */
     NAS_PH_BVP,            /* block PCG for the N linear problems                   */
     NAS_PH_POISSON,        /* Hartree: right-hand side, boundary values, PCG        */
-    NAS_PH_BLOCKS,         /* F_A / F_B blocks (st5-st7) incl. I^T A I              */
+    NAS_PH_BLOCKS,         /* F_A / F_B blocks (Sec. 3.3) incl. I^T A I              */
     NAS_PH_DENSITY,        /* Psi = I u_H + U^ alpha and rho at quadrature points   */
     NAS_PH_MIXING,         /* Anderson inner products and combination               */
     NAS_PH_HOST_EIG,       /* small eigensolve, wall time (host dense / host LOBPCG,
@@ -158,7 +171,7 @@ typedef struct nas_report {
     int    poisson_iters;     /* Poisson PCG iterations summed over the last step   */
     double drho;              /* ||rho^(l) - rho^(l-1)||_0 of the last step         */
     double inner_res;         /* final ||rho_out - rho_in||_0                        */
-    double energy;            /* E of Sec. 3.1                                       */
+    double energy;            /* E of Sec. 3.1 (free energy E - kT S with smearing)  */
     double e_band;            /* sum_i f_i lambda_i                                  */
     double e_hartree;         /* (1/2) int V_H rho                                   */
     double e_xc;              /* int rho eps_xc                                      */
@@ -183,6 +196,9 @@ typedef struct nas_report {
                                  of the persistent Poisson PCG launches (every
                                  launch of every FP64 solve)                         */
     long long poisson_fused_iters; /* PCG iterations run inside those launches       */
+    double e_ts;              /* -kT S of the smeared occupations (0 without smearing);
+                                 `energy` includes it (the free energy)              */
+    double inner_tol;         /* stop tolerance the last inner SCF used              */
 } nas_report;
 
 /* ------------------------------------------------------------------ context */
@@ -239,7 +255,7 @@ int nas_init(nas_ctx* ctx, const double* psi0);
 
 /* One augmented-subspace step (Algorithm 3 body): the N shifted linear
  * problems (H~ u^_i, v) = (lambda_i + mu)(psi_i, v), the fixed blocks, and the
- * inner SCF of the small Kohn-Sham problem in S_H + span{u^_i} (eqs. st1-st7),
+ * inner SCF of the small Kohn-Sham problem in S_H + span{u^_i} (Sec. 3.3),
  * then the density update.  Fills *rep (may be NULL).  Returns
  * NAS_E_NOT_CONVERGED if a CG cap was hit (the state is still updated). */
 int nas_step(nas_ctx* ctx, nas_report* rep);
@@ -267,7 +283,7 @@ enum nas_quantity {
     NAS_Q_K,              /* FP64 [nnz] stiffness  int grad phi_i . grad phi_j         */
     NAS_Q_M,              /* FP64 [nnz] mass                                          */
     NAS_Q_MVEXT,          /* FP64 [nnz] int V_ext phi_i phi_j                         */
-    NAS_Q_ANL,            /* FP64 [nnz] A^NL of the current rho_in (eq. st4)           */
+    NAS_Q_ANL,            /* FP64 [nnz] A^NL of the current rho_in (Sec. 3.3)           */
     NAS_Q_HTILDE,         /* FP64 [nnz] H~ of the last linear problems                 */
     NAS_Q_TRANSFER_ELEM,  /* int32 [n_dof] coarse element containing each fine dof     */
     NAS_Q_TRANSFER_COL,   /* int32 [n_dof][4] coarse dof per vertex (-1 = boundary)    */
@@ -276,6 +292,11 @@ enum nas_quantity {
     NAS_Q_FB,             /* FP64 [m][m] last F_B                                      */
     NAS_Q_DOF_NODE,       /* int32 [n_dof] node id of each dof                          */
     NAS_Q_ENERGY,         /* FP64 [6]: E, e_band, e_hartree, e_xc, e_vxc, e_nn         */
+    NAS_Q_STATE_ID,       /* int64 [1]: counter bumped by every call that changes the
+                             solver state (set_mesh/system/options, init, step, solve,
+                             set_state); equal values mean an unchanged H~ and density */
+    NAS_Q_INNER_HIST,     /* FP64 [max_inner]: ||rho_out - rho_in||_0 of every inner SCF
+                             iteration of the last step (or nas_init), 0 after the last */
     NAS_Q_COUNT
 };
 
@@ -302,8 +323,12 @@ enum nas_op {
                              out [nnz] values of int c phi_i phi_j                       */
     NAS_OP_DENSITY,       /* in Psi [n_dof][N] -> out rho [n_elem][nq] = sum f psi^2    */
     NAS_OP_APPLY_H,       /* in X [n_dof][N] -> out H~ X with the last H~ (SpMM)        */
-    NAS_OP_BVP,           /* in R [n_dof][N] -> out solution of H~ U = R (block PCG),
-                             H~ = A^L + A^NL(rho_in) + mu M of the current state       */
+    NAS_OP_BVP,           /* in R [n_dof][N] -> out solution of H~ U = R (block PCG;
+                             FP32 inside FP64 refinement with precision = 1),
+                             H~ = A^L + A^NL(rho_in) + mu M of the current state;
+                             cnt = 2 n_dof N: `in` is [R ; U0], U0 the initial guess
+                             (else U0 = 0).  A zero column of R gives a zero column of
+                             U whatever U0                                              */
     NAS_OP_GALERKIN,      /* in fine CSR values [nnz] -> out dense I^T A I [nH][nH]     */
     NAS_OP_ENERGY_GRAD,   /* in rho at quad points [n_elem][nq] -> out [n_nuc][4]:
                              dE/d(R_k x, y, z, Z_k) = int rho dV_ext/dp + dE_nn/dp
@@ -345,7 +370,7 @@ int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* stat
  *  row_ptr int32 [n_rows+1], col int32 [nnz], val FP64 [nnz], X FP64
  *  [n_cols][N], Y FP64 [n_rows][N], all device pointers; stream: cudaStream_t.
  * This is the kernel that dominates the linear solves (Sec. 3.3, Remark on
- * the cost of st4 and the N boundary value problems). */
+ * the cost of A_h^NL and the N boundary value problems). */
 int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
                  const double* val, int N, const double* X, double* Y, void* stream);
 
@@ -353,7 +378,7 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
  *   out[c] = sum_i w[i] X[i][c] Y[i][c]   for c < N   (w == NULL: w[i] = 1)
  * X, Y [n][N] row-major, w [n], out [N]: device pointers; stream: cudaStream_t.
  * This is the reduction behind the density stop test ||rho_out - rho_in||_0
- * of Algorithm 3 and the Anderson inner products (Sec. 5, eq. mix6), with the
+ * of Algorithm 3 and the Anderson inner products (Sec. 4), with the
  * quadrature weights as w.  The sum is taken in a fixed order (per-block
  * partial sums, then one ordered pass), so repeated calls are bit-identical.
  * Scratch for the partial sums (<= 1216 * N doubles) is allocated and freed

@@ -9,15 +9,15 @@ Method for Kohn-Sham Equation") in plain NumPy/SciPy, FP64 throughout.
 Modules and the passages they follow:
   quadrature   tetrahedral quadrature (the paper leaves the rule open; Sec. 2)
   fem          P1/P2 spaces on tetrahedra, assembly of K, M and potential
-               mass matrices (Sec. 2 discretisation; Sec. 3.3 eqs. st3, st4)
-  lda          Slater exchange + Perdew-Zunger correlation (Sec. 3.1, eqs.
-               expot, copot) and the energy formula (Sec. 3.1)
+               mass matrices (Sec. 2 discretisation; Sec. 3.3, A_h^L and A_h^NL)
+  lda          Slater exchange + Perdew-Zunger correlation and the
+               energy formula (Sec. 3.1)
   hartree      Poisson problem for V_Har with multipole boundary values
-               (Sec. 3.1, eq. bd)
+               (Sec. 3.1)
   transfer     nonnested interpolation I_H^h (Sec. 3.2, Algorithm 1)
-  anderson     Anderson density mixing (Sec. 5, eqs. mix2-mix6)
-  nas          Algorithm 3 (augmented subspace step, eqs. Aux_Linear_Problem,
-               st1-st7) with its inner SCF, plus the direct fine-space SCF used
+  anderson     Anderson density mixing (Sec. 4, Anderson mixing)
+  nas          Algorithm 3 (augmented subspace step of Sec. 3.3: the
+               linear problems and the blocks of F_A, F_B) with its inner SCF, plus the direct fine-space SCF used
                as the plain definition of the discrete ground state.
   spmm_omp.c   (C, OpenMP; built by build_c.py) the plain CSR product with N
                interleaved right-hand sides of Algorithm 3 step 1's block

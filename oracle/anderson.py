@@ -1,9 +1,9 @@
 """Anderson density mixing (oracle; test infrastructure).
 
-Sec. 5 of the paper (eqs. mix2-mix6).  With F^(j) = rho_out^(j) - rho_in^(j)
+Sec. 4 of the paper (Anderson mixing).  With F^(j) = rho_out^(j) - rho_in^(j)
 and the history j = m0..m (depth = m - m0 + 1):
   rho~_in(out) = rho_in(out)^(m) + sum_{j<m} alpha_j (rho_in(out)^(j) - rho_in(out)^(m))
-  sum_k (F^m - F^j, F^m - F^k) alpha_k = (F^m - F^j, F^m),  j = m0..m-1      (mix6)
+  sum_k (F^m - F^j, F^m - F^k) alpha_k = (F^m - F^j, F^m),  j = m0..m-1
   rho_in^(m+1) = beta rho~_out + (1 - beta) rho~_in.
 Defaults depth = 5, beta = 0.7 (as in the experiments).
 

@@ -3,9 +3,9 @@
 Follows the discretisation of the paper's Sec. 2 (a conforming space S_h of
 continuous piecewise polynomials on a tetrahedral mesh, zero Dirichlet values
 on the boundary of the box) and the matrices of Sec. 3.3:
-  K_ij   = int grad(phi_i) . grad(phi_j)          (kinetic part of eq. st3 is K/2)
+  K_ij   = int grad(phi_i) . grad(phi_j)          (kinetic part of A_h^L is K/2)
   M_ij   = int phi_i phi_j                        (mass)
-  M_V,ij = int V phi_i phi_j                      (potential parts of st3, st4)
+  M_V,ij = int V phi_i phi_j                      (potential parts of A_h^L, A_h^NL)
 all integrated element by element with the rule of `oracle.quadrature`.
 
 Node numbering of the fine space:

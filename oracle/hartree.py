@@ -2,7 +2,7 @@
 
 Sec. 3.1 of the paper:  -Laplace V_Har = 4 pi rho in Omega,  V_Har = w_D on the
 boundary, with w_D from a multipole expansion about the charge centre
-x'' = int x rho / int rho (eq. bd).  Readings:
+x'' = int x rho / int rho.  Readings:
   * monopole (default): w_D(x) = Q / |x - x''|, Q = int rho.  The dipole term
     vanishes identically because x'' is the charge centre.
   * multipole=2 adds the quadrupole term with the textbook factor 1/2,

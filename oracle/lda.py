@@ -2,14 +2,14 @@
 
 Sec. 3.1 of the paper:
   exchange (Kohn-Sham/Slater):  E_x = -(3/4)(3/pi)^(1/3) int rho^(4/3),
-                                V_x = -(3 rho/pi)^(1/3)                 (eq. expot)
+                                V_x = -(3 rho/pi)^(1/3)                 (Sec. 3.1)
   correlation (Perdew-Zunger), r_s = (3/(4 pi rho))^(1/3):
     eps_c = A ln r_s + B + C r_s ln r_s + D r_s          if r_s < 1
           = gamma / (1 + beta1 sqrt(r_s) + beta2 r_s)    if r_s >= 1
     V_c   = A ln r_s + (B - A/3) + (2/3) C r_s ln r_s + (1/3)(2D - C) r_s      if r_s < 1
           = eps_c (1 + (7/6) beta1 sqrt(r_s) + (4/3) beta2 r_s)
                   / (1 + beta1 sqrt(r_s) + beta2 r_s)                          if r_s >= 1
-                                                                               (eq. copot)
+                                                                               (Sec. 3.1)
   constants A=0.0311, B=-0.048, gamma=-0.1423, beta1=1.0529, beta2=0.3334,
   C=0.0020, D=-0.0116.
 The exchange energy per electron is eps_x = -(3/4)(3/pi)^(1/3) rho^(1/3), so

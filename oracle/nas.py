@@ -3,15 +3,15 @@
 Test infrastructure: plain FP64 NumPy/SciPy, written from the paper's Sec. 3.3.
 
 One augmented-subspace step (Algorithm 3 body):
-  1. N shifted linear boundary value problems (eq. Aux_Linear_Problem)
+  1. N shifted linear boundary value problems (Algorithm 3, step 1)
        (H~ u^_i, v) = (lambda_i + mu)(psi_i, v),  H~ = -1/2 Lap + V_ext + mu + V_Har + V_xc,
      i.e. (K/2 + M_Vext + M_(VH+Vxc)(rho) + mu M) u^_i = (lambda_i + mu) M psi_i.
   2. the small Kohn-Sham problem in S_H + span{u^_i}, solved by SCF; each SCF
-     iteration solves F_A U = lambda F_B U (eq. st1) with the 2x2 block
-     matrices of eq. st2:
+     iteration solves F_A U = lambda F_B U with the 2x2 block
+     matrices of Sec. 3.3:
        F_A = [[A_H, b_H], [b_H^T, beta]],   F_B = [[B_H, c_H], [c_H^T, gamma]],
-       A_H = I^T A_h I (st5), b_H = I^T A_h U^ (st6), beta = U^T A_h U^ (st7),
-       c_H = I^T M U^, gamma = U^T M U^, A_h = A^L + A^NL (st3, st4).
+       A_H = I^T A_h I, b_H = I^T A_h U^, beta = U^T A_h U^,
+       c_H = I^T M U^, gamma = U^T M U^, A_h = A^L + A^NL.
   3. density update rho = sum_i f_i psi_i^2.
 
 Readings (where the paper is silent, ambiguous or garbled):
@@ -31,17 +31,21 @@ Readings (where the paper is silent, ambiguous or garbled):
   * energy (Sec. 3.1): E = sum_i f_i lambda_i - int (V_H/2 + V_xc) rho
     + E_xc + E_nn, all density-dependent terms at the density rho_in of the
     potential.
-  * basis of the augmented space: before the blocks of eq. st2 are formed, the
+  * basis of the augmented space: before the blocks of F_A, F_B are formed, the
     u^_i are replaced by an M-orthonormal basis of their M-orthogonal
     complement to I S_H (u^ <- u^ - I B_H^-1 I^T M u^, then u^ <- u^ L^-T with
     L L^T = u^T M u^).  This spans the same augmented subspace S_H + span{u^_i},
-    so the Ritz pairs of eq. st1 are unchanged; it is needed because with the
+    so the Ritz pairs of the small problem are unchanged; it is needed because with the
     experiments' large mu each u^_i differs from a coarse-space function only
     by O(1/mu), which makes F_B in the printed basis nearly singular
     (condition number ~1e11 on the 8-nucleus workload).
   * initial guess: the self-consistent solution in the coarse space alone
     (S_H carried to the fine mesh by I), from rho = 0, by the same inner SCF.
   * mu defaults to the experiments' 8 M sum_k Z_k^2.
+  * occupations: the given f_i (closed shell), or, with smearing kT > 0,
+    Fermi-Dirac f_i = 2/(1 + exp((lambda_i - eF)/kT)) with sum f_i equal to the
+    electron count, recomputed after every small eigensolve; the energy is
+    then the free energy E - kT S, S = -2 sum [g ln g + (1-g) ln(1-g)], g = f/2.
 """
 from dataclasses import dataclass, field
 
@@ -109,6 +113,41 @@ def nuclear_repulsion(inst):
     return E
 
 
+def fermi_dirac(lam, n_el, kT):
+    """Occupations 2/(1 + exp((lam - eF)/kT)) summing to n_el, and -kT S.
+
+    eF is found by bisection on the (increasing) electron count; S is the
+    entropy of independent spin-degenerate levels, -2 sum [g ln g + (1-g) ln(1-g)]
+    with g = f/2.
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    if not n_el < 2.0 * len(lam):
+        raise ValueError("smearing needs more orbitals than n_el / 2")
+
+    def occ(eF):
+        with np.errstate(over="ignore"):      # exp -> inf gives the exact limit f = 0
+            return 2.0 / (1.0 + np.exp((lam - eF) / kT))
+
+    def count(eF):
+        return float(np.sum(occ(eF)))
+
+    lo, hi = lam.min() - 50.0 * kT - 1.0, lam.max() + 50.0 * kT + 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if count(mid) < n_el:
+            lo = mid
+        else:
+            hi = mid
+    eF = 0.5 * (lo + hi)
+    f = occ(eF)
+    g = 0.5 * f
+    inside = (g > 0.0) & (g < 1.0)
+    S = -2.0 * float(np.sum(g[inside] * np.log(g[inside]) + (1.0 - g[inside]) * np.log1p(-g[inside])))
+    return f, -kT * S
+
+
 def default_mu(inst):
     return 8.0 * len(inst.Z) * float(np.sum(np.asarray(inst.Z) ** 2))
 
@@ -120,6 +159,8 @@ class State:
     rho_in: np.ndarray         # [ne, nq] density defining the potential
     rho_out: np.ndarray        # [ne, nq] sum f psi^2
     VH: np.ndarray             # [nnode] Hartree potential of rho_in (nodal)
+    occ: np.ndarray = None     # [N] occupations of these orbitals
+    minus_TS: float = 0.0      # -kT S of the occupations (smearing)
     n_inner: int = 0
     inner_res: float = 0.0
     inner_converged: bool = True
@@ -141,7 +182,7 @@ class Problem:
         self.M = f.interior(Mf)
         self.vext_q = external_potential(inst, f.xq)
         self.Mvext = f.interior(f.assemble_full("M", coef=self.vext_q))
-        self.AL = (0.5 * self.K + self.Mvext).tocsr()   # eq. st3 without mu
+        self.AL = (0.5 * self.K + self.Mvext).tocsr()   # A_h^L of Sec. 3.3, without mu
         self.mu = default_mu(inst) if inst.mu is None else float(inst.mu)
         self.occ = np.asarray(inst.occ, dtype=np.float64)
         self.N = len(self.occ)
@@ -171,20 +212,28 @@ class Problem:
         return VH, VHq, eps, vxc
 
     def A_NL(self, VHq, vxc):
-        """Eq. st4: ((V_Har + V_xc) phi_i, phi_j) on the interior."""
+        """A_h^NL of Sec. 3.3: ((V_Har + V_xc) phi_i, phi_j) on the interior."""
         return self.fine.interior(self.fine.assemble_full("M", coef=VHq + vxc))
 
-    def density(self, Psi):
+    def density(self, Psi, occ=None):
         """rho = sum_i f_i psi_i^2 at quadrature points."""
+        occ = self.occ if occ is None else occ
         Pq = self.fine.at_quad(self.fine.to_nodes(Psi))   # [ne, nq, N]
-        return np.einsum("eqn,n->eq", Pq * Pq, self.occ)
+        return np.einsum("eqn,n->eq", Pq * Pq, occ)
+
+    def occupations(self, lam):
+        """(f, -kT S): the given occupations, or Fermi-Dirac ones with smearing."""
+        kT = float(getattr(self.inst, "smearing", 0.0))
+        if kT > 0.0:
+            return fermi_dirac(lam, float(np.sum(self.occ)), kT)
+        return self.occ, 0.0
 
     def norm0(self, f_q):
         return float(np.sqrt(np.sum(self.fine.Wq * f_q * f_q)))
 
     # ------------------------------------------------------------ small problem
     def small_blocks(self, A, Uhat):
-        """F_A of eq. st2 for fine operator A (sparse) and augmentation Uhat [n, k]."""
+        """F_A of Sec. 3.3 for fine operator A (sparse) and augmentation Uhat [n, k]."""
         AH = (self.I.T @ A @ self.I).toarray()
         if Uhat is None or Uhat.shape[1] == 0:
             return AH
@@ -229,17 +278,18 @@ class Problem:
             A = (self.AL + self.A_NL(VHq, vxc)).tocsr()
             FA = self.small_blocks(A, Uhat)
             lam, U = self.eig_small(FA, FB)
+            occ, mts = self.occupations(lam)
             Psi = self.basis_apply(Uhat, U)
-            rho_out = self.density(Psi)
+            rho_out = self.density(Psi, occ)
             res = self.norm0(rho_out - rho_in)
             hist.append(res)
             if res < tol:
-                return State(lam, Psi, rho_in, rho_out, VH, t + 1, res, True,
+                return State(lam, Psi, rho_in, rho_out, VH, occ, mts, t + 1, res, True,
                              {"res_hist": hist, "U": U, "eps": eps, "vxc": vxc, "VHq": VHq})
             if t == max_inner - 1:
                 break
             rho_in = mixer.mix(rho_in, rho_out)
-        return State(lam, Psi, rho_in, rho_out, VH, max_inner, res, False,
+        return State(lam, Psi, rho_in, rho_out, VH, occ, mts, max_inner, res, False,
                      {"res_hist": hist, "U": U, "eps": eps, "vxc": vxc, "VHq": VHq})
 
     # ------------------------------------------------------------ Algorithm 3
@@ -299,9 +349,10 @@ class Problem:
         f = self.fine
         _, VHq, eps, vxc = self.nonlinear_cached(st)
         rho = st.rho_in
-        return (float(np.dot(self.occ, st.lam))
+        occ = self.occ if st.occ is None else st.occ
+        return (float(np.dot(occ, st.lam))
                 - f.integrate((0.5 * VHq + vxc) * rho)
-                + f.integrate(rho * eps) + self.Enn)
+                + f.integrate(rho * eps) + self.Enn + st.minus_TS)
 
     def energy_gradient(self, rho_q):
         """Hellmann-Feynman gradient of the total energy with respect to the
@@ -362,9 +413,10 @@ class Problem:
                 lam, Psi = spla.eigsh(A, k=self.N, M=self.M, sigma=-1e3, which="LM", tol=1e-14)
                 o = np.argsort(lam)
                 lam, Psi = lam[o], Psi[:, o]
-            rho_out = self.density(Psi)
+            occ, mts = self.occupations(lam)
+            rho_out = self.density(Psi, occ)
             res = self.norm0(rho_out - rho_in)
             if res < tol:
-                return State(lam, Psi, rho_in, rho_out, VH, t + 1, res, True)
+                return State(lam, Psi, rho_in, rho_out, VH, occ, mts, t + 1, res, True)
             rho_in = mixer.mix(rho_in, rho_out)
-        return State(lam, Psi, rho_in, rho_out, VH, max_iter, res, False)
+        return State(lam, Psi, rho_in, rho_out, VH, occ, mts, max_iter, res, False)

@@ -6,7 +6,7 @@ leaf), the nearest coarse vertex to the fine point inside its leaf, a coarse
 tetrahedron having that vertex, then a walk through face neighbours until all
 barycentric coordinates of the point are non-negative; the fine value is the
 barycentric combination of the coarse vertex values.  I_H^h is that linear map
-written as a matrix (eq. st5): row = interior fine node, columns = interior
+written as a matrix (I_H^h of Sec. 3.3): row = interior fine node, columns = interior
 coarse nodes (the coarse space S_H vanishes on the boundary), weights = the
 barycentric coordinates.
 

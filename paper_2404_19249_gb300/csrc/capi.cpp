@@ -34,6 +34,7 @@ int guarded(nas_ctx* c, F&& f) {
 }
 
 void invalidate(nas_ctx* c) {
+    ++c->state_id;
     c->setup_done = false;
     c->initialized = false;
     c->anl_valid = false;
@@ -74,6 +75,8 @@ void nas_default_options(nas_options* o) {
     o->poisson_fused = 0;
     o->poisson_two_level = 1;
     o->precision = 0;
+    o->smearing = 0.0;
+    o->inner_adapt = 0.0;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -160,6 +163,7 @@ int nas_set_system(nas_ctx* c, int n_nuc, const double* R, const double* Z, int 
             // only the nuclei move or change charge: keep the mesh structures
             c->R.assign(R, R + 3 * n_nuc);
             c->Z.assign(Z, Z + n_nuc);
+            ++c->state_id;
             nas::ctx_update_nuclei(c);
             return NAS_OK;
         }
@@ -187,11 +191,13 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
             o->anderson_depth < 1 || o->anderson_depth > 5 || o->precision < 0 || o->precision > 1 ||
             o->eig_device < 0 || o->eig_device > 1 || o->poisson_adaptive < 0 || o->poisson_adaptive > 1 ||
             !(o->eig_adapt > 0.0) || o->eig_adapt > 1.0 || o->eig_precond < 0 || o->eig_precond > 1 ||
-            o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1)
+            o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1 ||
+            !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0))
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level) || (o->eig_precond != c->opt.eig_precond);
         c->opt = *o;
+        ++c->state_id;
         if (rebuild && c->setup_done) invalidate(c);
         return NAS_OK;
     });
@@ -200,6 +206,7 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
 int nas_init(nas_ctx* c, const double* psi0) {
     return guarded(c, [&]() {
         NAS_CUDA(cudaSetDevice(c->device));
+        ++c->state_id;
         if (!c->setup_done) nas::ctx_setup(c);
         nas::ctx_init(c, psi0);
         return NAS_OK;
@@ -209,6 +216,7 @@ int nas_init(nas_ctx* c, const double* psi0) {
 int nas_step(nas_ctx* c, nas_report* rep) {
     return guarded(c, [&]() {
         NAS_CUDA(cudaSetDevice(c->device));
+        ++c->state_id;
         return nas::ctx_step(c, rep);
     });
 }
@@ -216,6 +224,7 @@ int nas_step(nas_ctx* c, nas_report* rep) {
 int nas_solve(nas_ctx* c, nas_report* rep) {
     return guarded(c, [&]() {
         NAS_CUDA(cudaSetDevice(c->device));
+        ++c->state_id;
         int status = NAS_OK;
         nas_report r{};
         bool done = false;
@@ -315,6 +324,7 @@ int nas_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {
 int nas_set_state(nas_ctx* c, const double* lam, const double* psi, const double* rho_in, int on_device) {
     return guarded(c, [&]() {
         NAS_CUDA(cudaSetDevice(c->device));
+        ++c->state_id;
         nas::ctx_set_state(c, lam, psi, rho_in, on_device);
         return NAS_OK;
     });

@@ -44,7 +44,7 @@ struct nas_ctx {
     int potential = NAS_POT_COULOMB;
     double smooth_a = 0.0;
     int N = 0;
-    std::vector<double> occ;
+    std::vector<double> occ;            // occupations given to nas_set_system
 
     // ---- derived
     bool setup_done = false, initialized = false;
@@ -123,12 +123,17 @@ struct nas_ctx {
     long long pcg1_iters = 0;
 
     // ---- state (host)
+    int64_t state_id = 0;               // bumped by every call that changes the solver state
     std::vector<double> lam;            // [N]
+    std::vector<double> occ_now;        // occupations of the current orbitals [N]
+    double e_ts = 0.0;                  // -kT S of occ_now (smearing)
+    double inner_tol_now = 0.0;         // stop tolerance of the last inner SCF
     bool have_VH = false;
     bool anl_valid = false;             // d_ANL/d_eps/d_vxc match d_rho_in and d_VH
     int step_count = 0;
     int last_cg = 0, last_poisson = 0, last_inner = 0, last_inner_conv = 0;
     double last_drho = 0.0, last_inner_res = 0.0;
+    std::vector<double> inner_hist;     // density residual of every inner iteration of the last inner SCF
     std::array<double, 6> energy{};
     // host copies of the last small problem
     int last_m = 0;

@@ -1,13 +1,13 @@
 // Step driver of the augmented subspace method (Algorithm 3, Sec. 3.3).
 //
 // Host code orders the GPU kernels on the context's stream and solves the
-// small eigenproblem F_A U = lambda F_B U (eq. st1) on the host.  The flow of
+// small eigenproblem F_A U = lambda F_B U (Sec. 3.3) on the host.  The flow of
 // one step:
-//   H~ = A^L + A^NL(rho_in) + mu M                        (st3, st4 + shift)
-//   block PCG:  H~ U^ = M Psi diag(lambda + mu)           (Aux_Linear_Problem)
+//   H~ = A^L + A^NL(rho_in) + mu M                        (A_h^L, A_h^NL of Sec. 3.3 + shift)
+//   block PCG:  H~ U^ = M Psi diag(lambda + mu)           (Algorithm 3, step 1)
 //   fixed blocks c_H = I^T M U^, gamma = U^T M U^; linear parts of b_H, beta
-//   inner SCF: Hartree Poisson solve, V_xc, A^NL, A_H = I^T A I (st5),
-//              b_H = I^T A U^ (st6), beta = U^T A U^ (st7), host eigensolve,
+//   inner SCF: Hartree Poisson solve, V_xc, A^NL, A_H = I^T A I,
+//              b_H = I^T A U^, beta = U^T A U^ (Sec. 3.3), host eigensolve,
 //              Psi = I u_H + U^ alpha, rho_out = sum f psi^2, Anderson mixing.
 // Readings of the paper that this code follows (same as the CPU oracle):
 // rho = sum_i f_i psi_i^2; F_A is built from H without mu; B_H = I^T M_h I;
@@ -109,6 +109,23 @@ static void spmm(nas_ctx* c, const Csr& A, int N, const double* X, double* Y, do
 
 static double* scal(nas_ctx* c, int k, int N) { return c->d_cg_scal.p + (int64_t)k * N; }
 
+// X[:, j] = 0 for every column j whose right-hand side is zero (bb[j] == 0):
+// the solution of A x = 0 is 0 whatever the initial guess, and such a column
+// never enters the CG iteration.  bb: host [N].
+static void zero_null_columns(nas_ctx* c, int64_t n, int N, const double* bb, double* X) {
+    std::vector<double> keep(N);
+    bool any = false;
+    for (int j = 0; j < N; ++j) {
+        keep[j] = bb[j] > 0.0 ? 1.0 : 0.0;
+        any = any || keep[j] == 0.0;
+    }
+    if (!any) return;
+    double* d_keep = scal(c, 7, N);   // slot 7 is not used by the CG recurrences
+    NAS_CUDA(cudaMemcpyAsync(d_keep, keep.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->stream));
+    launch_scale_cols(n, N, d_keep, X, c->stream);
+    sync(c);
+}
+
 // Block Jacobi-preconditioned CG on A X = B (N independent columns); X holds
 // the initial guess.  Returns the iteration count; throws on breakdown.
 static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double* B, double* X, double tol,
@@ -141,6 +158,7 @@ static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double
         nact += act[j];
         if (!std::isfinite(h[j])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
     }
+    zero_null_columns(c, n, N, h.data() + N, X);
     NAS_CUDA(cudaMemcpyAsync(c->d_cg_active.p, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
     int it = 0;
     const int every = std::max(1, c->opt.check_every);
@@ -224,6 +242,7 @@ static int pcg_mixed(nas_ctx* c, const Csr& A, const double* Dinv, int N, const 
                 worst = std::min(worst, std::sqrt(h[N + j] / h[j]));
             }
         }
+        if (outer == 0) zero_null_columns(c, n, N, h.data() + N, X);
         if (nact == 0) {
             *converged = true;
             break;
@@ -363,7 +382,12 @@ static int pcg1_solve(nas_ctx* c, const Csr& A, const double* Dinv, const double
     sync(c);
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
     *converged = true;
-    if (!(h[2] > 0.0) || h[1] <= tol * tol * h[2]) return 0;
+    if (!(h[2] > 0.0)) {
+        // b = 0: the solution is 0 whatever the initial guess
+        NAS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+        return 0;
+    }
+    if (h[1] <= tol * tol * h[2]) return 0;
     double init[4] = {h[0], 0.0, tol * tol * h[2], h[1]};
     int flags[4] = {1, 0, 0, 0};
     NAS_CUDA(cudaMemcpyAsync(c->d_pcg1_scal.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
@@ -544,7 +568,13 @@ static int pcg1_mixed_solve(nas_ctx* c, const double* b, double* x, double tol, 
         NAS_CUDA(cudaMemcpyAsync(h, c->d_red.p, sizeof(h), cudaMemcpyDeviceToHost, s));
         sync(c);
         if (!std::isfinite(h[0])) fail(NAS_E_BREAKDOWN, "non-finite residual in CG");
-        if (!(h[1] > 0.0) || h[0] <= tol * tol * h[1]) {
+        if (!(h[1] > 0.0)) {
+            // b = 0: the solution is 0 whatever the initial guess
+            NAS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+            *converged = true;
+            break;
+        }
+        if (h[0] <= tol * tol * h[1]) {
             *converged = true;
             break;
         }
@@ -631,7 +661,7 @@ static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
 }
 
 // A^NL of the density in d_rho_in (and V_H in d_VH): coefficient, element
-// matrices, gather (eq. st4)
+// matrices, gather (A_h^NL of Sec. 3.3)
 static void assemble_nl(nas_ctx* c) {
     Phase t(c, NAS_PH_ASSEMBLY);
     Mesh m = fmesh(c);
@@ -669,7 +699,7 @@ static double weighted_norm_diff(nas_ctx* c, const double* a, const double* b) {
     return std::sqrt(std::max(r, 0.0));
 }
 
-// ------------------------------------------------------------------ Anderson (Sec. 5, mix2-mix6)
+// ------------------------------------------------------------------ Anderson (Sec. 4, Anderson mixing)
 struct Anderson {
     std::deque<int> hist;  // slot ids, oldest first
     int next_free = 0;
@@ -733,6 +763,51 @@ static void anderson_mix(nas_ctx* c, Anderson& A) {
     }
 }
 
+// ------------------------------------------------------------------ occupations
+// Occupations of the current eigenvalues.  Without smearing: the ones given to
+// nas_set_system.  With smearing kT > 0: Fermi-Dirac f_i = 2 / (1 + exp((lambda_i
+// - eF)/kT)), eF by bisection so that sum f_i equals the electron count, and the
+// entropy term -kT S with S = -2 sum_i [g ln g + (1 - g) ln(1 - g)], g = f_i / 2.
+static void update_occupations(nas_ctx* c) {
+    const int N = c->N;
+    if (!(c->opt.smearing > 0.0)) {
+        c->occ_now = c->occ;
+        c->e_ts = 0.0;
+    } else {
+        const double kT = c->opt.smearing;
+        double nel = 0.0;
+        for (double f : c->occ) nel += f;
+        if (!(nel < 2.0 * N)) fail(NAS_E_INVALID_ARG, "smearing needs more orbitals than n_electrons / 2");
+        double lmin = c->lam[0], lmax = c->lam[0];
+        for (double l : c->lam) {
+            lmin = std::min(lmin, l);
+            lmax = std::max(lmax, l);
+        }
+        auto count = [&](double eF) {
+            double s = 0.0;
+            for (int i = 0; i < N; ++i) s += 2.0 / (1.0 + std::exp((c->lam[i] - eF) / kT));
+            return s;
+        };
+        double lo = lmin - 50.0 * kT - 1.0, hi = lmax + 50.0 * kT + 1.0;
+        for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            (count(mid) < nel ? lo : hi) = mid;
+        }
+        const double eF = 0.5 * (lo + hi);
+        c->occ_now.resize(N);
+        double S = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double f = 2.0 / (1.0 + std::exp((c->lam[i] - eF) / kT));
+            c->occ_now[i] = f;
+            const double g = 0.5 * f;
+            if (g > 0.0 && g < 1.0) S -= 2.0 * (g * std::log(g) + (1.0 - g) * std::log1p(-g));
+        }
+        c->e_ts = -kT * S;
+    }
+    c->d_occ.upload(c->occ_now, c->stream);
+}
+
 // ------------------------------------------------------------------ energies (Sec. 3.1)
 static void energies(nas_ctx* c) {
     cudaStream_t s = c->stream;
@@ -744,9 +819,9 @@ static void energies(nas_ctx* c) {
     NAS_CUDA(cudaMemcpyAsync(r, c->d_red.p, sizeof(r), cudaMemcpyDeviceToHost, s));
     sync(c);
     double band = 0.0;
-    for (int i = 0; i < c->N; ++i) band += c->occ[i] * c->lam[i];
+    for (int i = 0; i < c->N; ++i) band += c->occ_now[i] * c->lam[i];
     double eh = 0.5 * r[0], evxc = r[1], exc = r[2];
-    c->energy = {band - eh - evxc + exc + c->Enn, band, eh, exc, evxc, c->Enn};
+    c->energy = {band - eh - evxc + exc + c->Enn + c->e_ts, band, eh, exc, evxc, c->Enn};
 }
 
 // ------------------------------------------------------------------ small problem
@@ -860,7 +935,7 @@ static void device_eig(nas_ctx* c, int m) {
     // coarse-block preconditioner: the inverse coarse stiffness (K_H = I^T K I
     // is twice the kinetic part of the coarse block of F_A), in FP32
     const float* TH = nullptr;
-    if (c->opt.eig_precond && c->d_khinv.p && c->N + nguard <= 32) {
+    if (c->opt.eig_precond && c->d_khinv.p) {
         if (!c->d_khinv32.p) {
             c->d_khinv32.ensure((size_t)c->nH * c->nH);
             launch_cast_to_f32(c->nH * c->nH, c->d_khinv.p, c->d_khinv32.p, s);
@@ -962,6 +1037,13 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
         c->FB.clear();
     }
     Anderson A;
+    c->inner_hist.clear();
+    // stop tolerance: tol_inner, or with inner_adapt > 0 (after the first step)
+    // max(tol_inner, inner_adapt x the previous step's density change)
+    double tol_in = c->opt.tol_inner;
+    if (c->opt.inner_adapt > 0.0 && c->step_count > 0 && reuse_first && c->last_drho > 0.0)
+        tol_in = std::max(tol_in, c->opt.inner_adapt * c->last_drho);
+    c->inner_tol_now = tol_in;
     int poisson = 0;
     double res = 0.0;
     int t = 0;
@@ -1012,14 +1094,16 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
         }
         c->eig_tol_hint = (t == 0) ? 1.0 : res;
         host_eig(c, m);
+        update_occupations(c);
         {
             Phase ph(c, NAS_PH_DENSITY);
             launch_reconstruct(c->F.n, c->d_Icol.p, c->d_Ival.p, c->N, c->d_U.p, nH, Na, c->d_Uhat.p, c->d_Psi.p, s);
             launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, c->N, c->d_occ.p, c->d_rho_out.p, s);
         }
         res = weighted_norm_diff(c, c->d_rho_out.p, c->d_rho_in.p);
+        c->inner_hist.push_back(res);
         if (!std::isfinite(res)) fail(NAS_E_BREAKDOWN, "non-finite density residual");
-        if (res < c->opt.tol_inner) {
+        if (res < tol_in) {
             conv = true;
             ++t;
             break;
@@ -1039,7 +1123,7 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
 
 // Replace U^ by an M-orthonormal basis of its M-orthogonal complement to I S_H:
 // U^ <- U^ - I B_H^-1 I^T M U^, then U^ <- U^ L^-T with L L^T = U^T M U^.  The
-// augmented subspace S_H + span{u^_i} (and so every Ritz pair of eq. st1) is
+// augmented subspace S_H + span{u^_i} (and so every Ritz pair of the small problem) is
 // unchanged; the printed basis makes F_B nearly singular when mu is large,
 // because each u^_i then differs from a coarse-space function by O(1/mu).
 static void augment_basis(nas_ctx* c) {
@@ -1095,7 +1179,7 @@ static Nuclei nuclei(nas_ctx* c) {
     return Nuclei{c->n_nuc, c->d_R.p, c->d_Zn.p, c->potential, c->smooth_a, c->opt.omega};
 }
 
-// V_ext at quadrature points, M_Vext and A^L = K/2 + M_Vext (eq. st3 without mu)
+// V_ext at quadrature points, M_Vext and A^L = K/2 + M_Vext (A_h^L of Sec. 3.3, without mu)
 static void assemble_vext(nas_ctx* c) {
     cudaStream_t s = c->stream;
     const int64_t nnz = c->F.nnz();
@@ -1162,7 +1246,9 @@ static void alloc_work(nas_ctx* c) {
         c->d_hist_rin.emplace_back(nqt);
         c->d_hist_F.emplace_back(nqt);
     }
-    c->d_occ.upload(c->occ, c->stream);
+    c->occ_now = c->occ;
+    c->e_ts = 0.0;
+    c->d_occ.upload(c->occ_now, c->stream);
 }
 
 void ctx_setup(nas_ctx* c) {
@@ -1216,7 +1302,7 @@ void ctx_setup(nas_ctx* c) {
     NAS_CUDA(cudaMemcpyAsync(&bad, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     sync(c);
     if (bad) fail(NAS_E_MESH, "fine mesh has a tetrahedron with det J <= 0");
-    // ---- fixed matrices K, M, M_Vext (st3)
+    // ---- fixed matrices K, M, M_Vext (A_h^L of Sec. 3.3)
     const int64_t nnz = F.nnz();
     c->d_L.alloc(F.ne * F.nloc * F.nloc);
     c->d_Lv.alloc(F.ne * F.nloc);
@@ -1388,6 +1474,10 @@ void ctx_init(nas_ctx* c, const double* psi0) {
     c->U_warm.clear();
     c->uwarm_dev_m = 0;
     c->lob_reuse_ok = false;
+    c->last_drho = 0.0;
+    c->occ_now = c->occ;   // the given occupations until the first eigensolve
+    c->e_ts = 0.0;
+    c->d_occ.upload(c->occ_now, s);
     if (psi0 == nullptr) {
         // self-consistent solution in S_H alone, from rho = 0
         if (c->nH < c->N) fail(NAS_E_INVALID_ARG, "the coarse-space initial guess needs n_coarse_dof >= N");
@@ -1434,6 +1524,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
         if (dense_gen_eig(N, Hs.data(), Id.data(), N, lam.data(), Y.data()) != 0)
             fail(NAS_E_EIGEN, "Rayleigh-Ritz of psi0 failed");
         c->lam = lam;
+        update_occupations(c);
         // Psi <- Psi Y  (Uhat = Psi, alpha = Y)
         NAS_CUDA(cudaMemcpyAsync(c->d_Uhat.p, c->d_Psi.p, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
         for (int i = 0; i < N * N; ++i) Ufull[c->nH * N + i] = Y[i];
@@ -1547,6 +1638,8 @@ void ctx_fill_report(nas_ctx* c, nas_report* rep) {
     rep->poisson_spmv_launches = c->pcg1_spmv_launches;
     rep->poisson_fused_ms = c->pcg1_fused_ms;
     rep->poisson_fused_iters = c->pcg1_fused_iters;
+    rep->e_ts = c->e_ts;
+    rep->inner_tol = c->inner_tol_now;
 }
 
 // ------------------------------------------------------------------ state in/out
@@ -1564,6 +1657,8 @@ void ctx_set_state(nas_ctx* c, const double* lam, const double* psi, const doubl
     } else {
         c->lam.assign(lam, lam + c->N);
     }
+    if (on_device) sync(c);   // c->lam arrives by an asynchronous device-to-host copy
+    update_occupations(c);
     copy_in(c, c->d_Psi.p, psi, c->F.n * c->N, on_device);
     copy_in(c, c->d_rho_in.p, rho, c->nqt, on_device);
     launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, c->N, c->d_occ.p, c->d_rho_out.p, s);
@@ -1645,6 +1740,13 @@ void ctx_get(nas_ctx* c, int what, void* dst, size_t bytes, int on_device) {
             break;
         case NAS_Q_DOF_NODE: put(c->d_dof_node.p, sizeof(int32_t) * n); break;
         case NAS_Q_ENERGY: put_host(c->energy.data(), sizeof(double) * 6); break;
+        case NAS_Q_STATE_ID: put_host(&c->state_id, sizeof(int64_t)); break;
+        case NAS_Q_INNER_HIST: {
+            std::vector<double> h(std::max(1, c->opt.max_inner), 0.0);
+            for (size_t k = 0; k < c->inner_hist.size() && k < h.size(); ++k) h[k] = c->inner_hist[k];
+            put_host(h.data(), sizeof(double) * h.size());
+            break;
+        }
         default: fail(NAS_E_INVALID_ARG, "unknown quantity");
     }
 }
@@ -1710,9 +1812,14 @@ void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int o
         }
         case NAS_OP_BVP: {
             if (!c->initialized) fail(NAS_E_STATE, "nas_init must be called first");
+            if (cnt != 0 && cnt != n * N && cnt != 2 * n * N) fail(NAS_E_INVALID_ARG, "cnt");
             fin(a, n * N);
             b.alloc(n * N);
-            b.zero(s);
+            if (cnt == 2 * n * N)   // initial guess after the right-hand sides
+                NAS_CUDA(cudaMemcpyAsync(b.p, static_cast<const double*>(in) + n * N, sizeof(double) * n * N,
+                                         kind_in, s));
+            else
+                b.zero(s);
             if (!c->anl_valid) {
                 if (c->opt.hartree) {
                     bool pc;
@@ -1724,7 +1831,10 @@ void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int o
             launch_combine3(nnz, 1.0, c->d_AL.p, 1.0, c->d_ANL.p, c->mu, c->d_M.p, c->d_H.p, s);
             launch_inv_diag(fcsr(c, c->d_H.p), c->d_Hdinv.p, s);
             bool conv;
-            pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, (int)N, a.p, b.p, c->opt.tol_bvp, c->opt.max_cg, &conv);
+            if (c->opt.precision == 1)
+                pcg_mixed(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, (int)N, a.p, b.p, c->opt.tol_bvp, c->opt.max_cg, &conv);
+            else
+                pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, (int)N, a.p, b.p, c->opt.tol_bvp, c->opt.max_cg, &conv);
             if (!conv) fail(NAS_E_NOT_CONVERGED, "block PCG hit its iteration cap");
             fout(b.p, n * N);
             break;

@@ -1,4 +1,4 @@
-// LOBPCG for the small pencil F_A U = lambda F_B U of Algorithm 3 (eq. st1)
+// LOBPCG for the small pencil F_A U = lambda F_B U of Algorithm 3 (Sec. 3.3)
 // with the block vectors on the device.  The arrow-structured products, the
 // residuals, the orthogonalisation and the Gram matrices of the basis
 // [X, W, P] run in device kernels; the host receives the residual norms

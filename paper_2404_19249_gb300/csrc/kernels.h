@@ -184,7 +184,7 @@ void launch_galerkin2(const Pieces& pc, const int32_t* con, const double* W, con
                       const double* ival, double* partial, double* H, cudaStream_t s);
 
 // ------------------------------------------------------------ small pencil on the device
-// Arrow-structured symmetric matrix of the small problem (eq. st2):
+// Arrow-structured symmetric matrix of the small problem (the 2 x 2 block form of F_A, F_B in Sec. 3.3):
 // [[S, Bd], [Bd^T, Cd]], S sparse nH x nH (CSR, full symmetric storage),
 // Bd dense [nH][Na], Cd dense [Na][Na]; all pointers on the device.
 struct ArrowDev {

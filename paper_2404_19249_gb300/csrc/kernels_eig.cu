@@ -1,5 +1,5 @@
 // Device kernels of the LOBPCG solver for the small pencil F_A U = lambda F_B U
-// of Algorithm 3 (eq. st1/st2).  Both matrices have the arrow structure of the
+// of Algorithm 3 (F_A U = lambda F_B U, Sec. 3.3).  Both matrices have the arrow structure of the
 // augmented basis {I phi_a} + {u^_j}: a sparse coarse block (CSR over the
 // coarse unknowns), a dense border [nH][Na] and a dense corner [Na][Na].  The
 // block vectors are row-major [m][w] with m = nH + Na.  Every sum runs in a
@@ -294,8 +294,9 @@ namespace nas {
 // ---- preconditioner with a dense coarse block:
 //   W[i][j] = sum_b T[i][b] R[b][j]   (i < nH; T FP32 [nH][nH], FP32 products and sums)
 //   W[i][j] = Dinv[i] R[i][j]        (nH <= i < m)
-// Stage 1, grid (row blocks of kPcRows, kPcSplit): block (rb, sp) multiplies
-// 128 rows of T by the rows of R in its share of the b range, 32 b at a time:
+// Stage 1, grid (row blocks of kPcRows, kPcSplit, column groups of kPcK):
+// block (rb, sp, cg) multiplies 128 rows of T by 32 columns of the rows of R
+// in its share of the b range, 32 b at a time:
 // the 128 x 32 tile of T (coalesced row segments) and the 32 x 32 tile of R
 // (converted to FP32) are staged in shared memory, and each thread keeps a
 // 4 x 4 block of outputs in registers (rows 4 ty .. 4 ty + 3, columns
@@ -316,7 +317,8 @@ __global__ void __launch_bounds__(256) k_dense_precond_part(int64_t nH, int k, c
     const int64_t span = (nH + kPcSplit - 1) / kPcSplit;
     const int64_t bbeg = (int64_t)blockIdx.y * span;
     const int64_t bend = bbeg + span < nH ? bbeg + span : nH;
-    const int tx = threadIdx.x % 8;   // columns 4 tx .. 4 tx + 3
+    const int c0 = (int)blockIdx.z * kPcK;   // this block's group of kPcK columns
+    const int tx = threadIdx.x % 8;   // columns c0 + 4 tx .. c0 + 4 tx + 3
     const int ty = threadIdx.x / 8;   // rows 4 ty .. 4 ty + 3
     float acc[4][4];
 #pragma unroll
@@ -334,7 +336,8 @@ __global__ void __launch_bounds__(256) k_dense_precond_part(int64_t nH, int k, c
         for (int e = threadIdx.x; e < kPcK * kPcK; e += blockDim.x) {
             const int rr = e / kPcK, cc = e % kPcK;
             const int64_t bj = b0 + rr;
-            Rs[rr][cc] = (bj < bend && cc < k) ? (float)R[bj * k + cc] : 0.f;
+            const int cg = c0 + cc;
+            Rs[rr][cc] = (bj < bend && cg < k) ? (float)R[bj * k + cg] : 0.f;
         }
         __syncthreads();
 #pragma unroll 2
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(256) k_dense_precond_part(int64_t nH, int k, c
         if (i >= nH) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const int j = 4 * tx + c;
+            const int j = c0 + 4 * tx + c;
             if (j < k) part[((int64_t)blockIdx.y * nH + i) * k + j] = acc[q][c];
         }
     }
@@ -388,10 +391,10 @@ int64_t dense_precond_part_size(int64_t nH, int k) { return (int64_t)kPcSplit * 
 
 void launch_dense_precond(int64_t nH, int64_t m, int k, const float* T, const double* R, const double* Dinv,
                           float* part, double* W, cudaStream_t s) {
-    if (k > kPcK) fail(NAS_E_INVALID_ARG, "dense preconditioner: more than 32 block columns");
+    if (k < 1 || k > 1024) fail(NAS_E_INVALID_ARG, "dense preconditioner: block width out of range");
     if (m <= 0) return;
     if (nH > 0) {
-        dim3 grid((unsigned)((nH + kPcRows - 1) / kPcRows), kPcSplit);
+        dim3 grid((unsigned)((nH + kPcRows - 1) / kPcRows), kPcSplit, (unsigned)((k + kPcK - 1) / kPcK));
         k_dense_precond_part<<<grid, 256, 0, s>>>(nH, k, T, R, part);
         NAS_CHECK_LAUNCH();
     }

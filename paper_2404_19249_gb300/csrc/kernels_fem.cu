@@ -1,5 +1,5 @@
 // Element-level finite element kernels (Sec. 2 discretisation, Sec. 3.1
-// potentials, Sec. 3.3 eqs. st3-st4): geometry, element matrices, potentials
+// potentials, Sec. 3.3, the matrices A_h^L and A_h^NL): geometry, element matrices, potentials
 // and densities at quadrature points.  One thread per element; reference
 // element tables live in constant memory (every thread of a warp reads the
 // same entry at the same time, a broadcast).
@@ -166,7 +166,7 @@ __device__ __forceinline__ void inv_transpose(const Jac& j, double G[3][3]) {
     G[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
 }
 
-// Slater exchange + Perdew-Zunger correlation (Sec. 3.1, eqs. expot, copot);
+// Slater exchange + Perdew-Zunger correlation (Sec. 3.1, the exchange and correlation potentials);
 // rho <= 1e-30 gives 0; r_s = 1 takes the r_s >= 1 branch.
 __device__ __forceinline__ void lda_point(double rho, double& eps, double& v) {
     if (!(rho > 1e-30)) {

@@ -1,5 +1,5 @@
 // Point location of fine nodes in the nonnested coarse mesh, giving the
-// transfer matrix I_H^h of Sec. 3.2 / Algorithm 1 and eq. st5.
+// transfer matrix I_H^h of Sec. 3.2 / Algorithm 1, as used in A_H = I^T A_h I of Sec. 3.3.
 //
 // GPU design: instead of Algorithm 1's octree + walk (a serial, branchy
 // search), every fine node is one thread that reads the candidate coarse

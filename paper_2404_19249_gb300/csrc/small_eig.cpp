@@ -1,5 +1,5 @@
 // Dense generalized symmetric-definite eigensolver for the small augmented
-// problem F_A U = lambda F_B U (Sec. 3.3, eq. st1), host side.
+// problem F_A U = lambda F_B U (Sec. 3.3), host side.
 //
 // Reduction to standard form with the Cholesky factor of F_B, Householder
 // tridiagonalisation, the k smallest eigenvalues by bisection on Sturm
@@ -7,6 +7,13 @@
 // iteration (with re-orthogonalisation inside clusters of close
 // eigenvalues), then back-transformation.  The O(m^3) loops are split over
 // OpenMP threads.
+//
+// Published methods used here: Householder tridiagonalisation; all the
+// eigenvalues of a symmetric tridiagonal matrix by the implicit-shift QL
+// iteration of Bowdler, Martin, Reinsch and Wilkinson (Numer. Math. 11,
+// 1968; Wilkinson shift, deflation on negligible off-diagonal entries),
+// `tridiag_eigvals`; Sturm-sequence bisection and inverse iteration
+// (Wilkinson, The Algebraic Eigenvalue Problem, 1965).
 #include "small_eig.h"
 
 #include <algorithm>

@@ -1,5 +1,5 @@
 // Host solver for the small generalized eigenproblem F_A U = lambda F_B U of
-// Algorithm 3 (eq. st1), F_A symmetric, F_B symmetric positive definite.
+// Algorithm 3 (Sec. 3.3), F_A symmetric, F_B symmetric positive definite.
 #pragma once
 
 #include <cstdint>
@@ -35,7 +35,7 @@ int small_solve(int n, const double* A, const double* b, double* x);
 
 namespace nas {
 
-// Arrow-structured symmetric matrix of the small problem (eq. st2):
+// Arrow-structured symmetric matrix of the small problem (the 2 x 2 block form of F_A, F_B in Sec. 3.3):
 //   F = [[S, Bd], [Bd^T, Cd]],  S sparse nH x nH (CSR, full symmetric storage),
 //   Bd dense nH x Na (row-major), Cd dense Na x Na.
 struct ArrowMat {

@@ -1,4 +1,4 @@
-// Host-side structures around the transfer matrix I_H^h (Sec. 3.3, eq. st5):
+// Host-side structures around the transfer matrix I_H^h (Sec. 3.2, Algorithm 1; used in A_H = I^T A_h I of Sec. 3.3):
 // the bucket grid used by the GPU point location, the transpose I^T, and the
 // gather lists that evaluate the Galerkin product A_H = I^T A_h I on the GPU
 // in two deterministic stages (W = A_h I, then A_H = I^T W).

@@ -27,7 +27,7 @@ PHASES = ["assembly", "bvp", "poisson", "blocks", "density", "mixing", "host_eig
           "eig_rr", "eig_wait"]
 (NAS_Q_SIZES, NAS_Q_EIGVALS, NAS_Q_ORBITALS, NAS_Q_RHO_IN, NAS_Q_RHO_OUT, NAS_Q_VHARTREE, NAS_Q_UHAT,
  NAS_Q_ROWPTR, NAS_Q_COLIDX, NAS_Q_K, NAS_Q_M, NAS_Q_MVEXT, NAS_Q_ANL, NAS_Q_HTILDE, NAS_Q_TRANSFER_ELEM,
- NAS_Q_TRANSFER_COL, NAS_Q_TRANSFER_W, NAS_Q_FA, NAS_Q_FB, NAS_Q_DOF_NODE, NAS_Q_ENERGY) = range(21)
+ NAS_Q_TRANSFER_COL, NAS_Q_TRANSFER_W, NAS_Q_FA, NAS_Q_FB, NAS_Q_DOF_NODE, NAS_Q_ENERGY, NAS_Q_STATE_ID, NAS_Q_INNER_HIST) = range(23)
 (NAS_OP_LDA, NAS_OP_HARTREE, NAS_OP_ASSEMBLE_MASS, NAS_OP_DENSITY, NAS_OP_APPLY_H, NAS_OP_BVP,
  NAS_OP_GALERKIN, NAS_OP_ENERGY_GRAD, NAS_OP_BVP_VJP) = range(9)
 
@@ -42,6 +42,7 @@ class nas_options(C.Structure):
         ("eig_tol", C.c_double), ("spmv_lanes", C.c_int), ("poisson_two_level", C.c_int),
         ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
         ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int), ("poisson_fused", C.c_int),
+        ("smearing", C.c_double), ("inner_adapt", C.c_double),
     ]
 
 
@@ -55,6 +56,7 @@ class nas_report(C.Structure):
         ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_double), ("spmv_flops", C.c_double),
         ("eig_iters", C.c_int), ("poisson_spmv_ms", C.c_double), ("poisson_spmv_launches", C.c_longlong),
         ("poisson_fused_ms", C.c_double), ("poisson_fused_iters", C.c_longlong),
+        ("e_ts", C.c_double), ("inner_tol", C.c_double),
     ]
 
     def as_dict(self):
@@ -251,6 +253,7 @@ class Solver:
 
     def __init__(self, inst, device=0, stream=0, **options):
         self.h = nas_create(device, stream)
+        self.device = device
         self.inst = inst
         nas_set_mesh(self.h, NAS_FINE, inst.order, inst.fine_xyz, inst.fine_tet)
         nas_set_mesh(self.h, NAS_COARSE, 1, inst.coarse_xyz, inst.coarse_tet)
@@ -266,6 +269,7 @@ class Solver:
         o.hartree = int(inst.hartree)
         o.xc = int(inst.xc)
         o.omega = inst.omega
+        o.smearing = float(getattr(inst, "smearing", 0.0))
         for k, v in options.items():
             setattr(o, k, v)
         self.opt = o
@@ -307,7 +311,8 @@ class Solver:
             NAS_Q_HTILDE: ((nnz,), np.float64), NAS_Q_TRANSFER_ELEM: ((n,), np.int32),
             NAS_Q_TRANSFER_COL: ((n, 4), np.int32), NAS_Q_TRANSFER_W: ((n, 4), np.float64),
             NAS_Q_FA: ((m, m), np.float64), NAS_Q_FB: ((m, m), np.float64), NAS_Q_DOF_NODE: ((n,), np.int32),
-            NAS_Q_ENERGY: ((6,), np.float64),
+            NAS_Q_ENERGY: ((6,), np.float64), NAS_Q_STATE_ID: ((1,), np.int64),
+            NAS_Q_INNER_HIST: ((int(self.opt.max_inner),), np.float64),
         }
         shape, dt = shapes[what]
         out = np.zeros(shape, dtype=dt)
@@ -329,6 +334,11 @@ class Solver:
         rp = self.get(NAS_Q_ROWPTR)
         ci = self.get(NAS_Q_COLIDX)
         return sp.csr_matrix((self.get(what), ci, rp), shape=(s["n"], s["n"]))
+
+    def state_id(self):
+        v = np.zeros(1, dtype=np.int64)
+        nas_get(self.h, NAS_Q_STATE_ID, v)
+        return int(v[0])
 
     def apply(self, op, x, out_shape, cnt=0):
         out = np.zeros(out_shape)

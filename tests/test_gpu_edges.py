@@ -90,3 +90,26 @@ def test_error_codes(env):
     with pytest.raises(nas.NasError):
         nas.nas_apply(s.h, 99, np.zeros(4), np.zeros(4))
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bvp_zero_rhs_column_with_nonzero_guess(env, precision):
+    """A zero right-hand side has the zero solution whatever the initial guess:
+    the block PCG (FP64, and FP32 inside FP64 refinement) returns an exactly
+    zero column for it and solves the other columns as from a zero guess."""
+    nas, torch = env
+    inst = make_instance("harmonic", cells=8, coarse_cells=4, n_orb=3)
+    inst.tol_bvp = 1e-12
+    s = nas.Solver(inst, precision=precision)
+    s.init()
+    n, N = s.sizes()["n"], s.sizes()["N"]
+    rng = np.random.default_rng(11)
+    R = rng.normal(size=(n, N))
+    R[:, 1] = 0.0
+    U0 = rng.normal(size=(n, N))
+    U_guess = s.apply(nas.NAS_OP_BVP, np.concatenate([R.ravel(), U0.ravel()]), (n, N), cnt=2 * n * N)
+    U_zero = s.apply(nas.NAS_OP_BVP, R, (n, N))
+    s.close()
+    assert np.all(U_guess[:, 1] == 0.0) and np.all(U_zero[:, 1] == 0.0)
+    for j in (0, 2):
+        assert np.max(np.abs(U_guess[:, j] - U_zero[:, j])) < 1e-9 * np.max(np.abs(U_zero[:, j]))

@@ -133,3 +133,36 @@ def test_autograd_energy_hellmann_feynman_matches_finite_differences(nasmod):
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(p.grad[k, c].item() - fd) < 1e-5 * max(1.0, abs(fd)), (k, c, p.grad[k, c].item(), fd)
     s.close()
+
+
+def test_autograd_bvp_on_device_and_state_check(nasmod):
+    """CUDA tensors go to the library as device pointers (no host copy) and give
+    the same results as host tensors; a backward after a call that changed the
+    solver state raises instead of using the wrong operator."""
+    import torch
+    from paper_2404_19249_gb300.autograd import BVPSolve
+    inst = _inst()
+    s = nasmod.Solver(inst)
+    s.init()
+    sz = s.sizes()
+    rng = np.random.default_rng(5)
+    Rh = rng.normal(size=(sz["n"], sz["N"]))
+    Gh = rng.normal(size=(sz["n"], sz["N"]))
+    grads = []
+    for dev in ("cpu", "cuda:0"):
+        R = torch.tensor(Rh, dtype=torch.float64, device=dev, requires_grad=True)
+        G = torch.tensor(Gh, dtype=torch.float64, device=dev)
+        p = _params(inst)
+        U = BVPSolve.apply(p, R, s)
+        assert U.device == R.device
+        torch.sum(G * U).backward()
+        grads.append((U.detach().cpu().numpy(), R.grad.cpu().numpy(), p.grad.numpy().copy()))
+    for a, b in zip(grads[0], grads[1]):
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.max(np.abs(a)))
+    # forward, then a step (new density and H~), then backward: refused
+    R = torch.tensor(Rh, dtype=torch.float64, device="cuda:0", requires_grad=True)
+    U = BVPSolve.apply(_params(inst), R, s)
+    s.step()
+    with pytest.raises(RuntimeError, match="state changed"):
+        torch.sum(U).backward()
+    s.close()

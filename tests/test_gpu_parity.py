@@ -53,7 +53,7 @@ def _tight(inst):
 
 
 # Lockstep cases need a well-posed SCF: a HOMO-LUMO gap, so that the occupied
-# orbitals are well conditioned.  The paper's benzene (Sec. 5, 21 orbitals) is
+# orbitals are well conditioned.  The paper's benzene (Sec. 4.4, 21 orbitals) is
 # used for P2; the random 8-nucleus benchmark molecule has a nearly closed gap
 # (about 2e-3 Ha), so it is compared over a single step (test below).
 CASES = {
@@ -132,6 +132,28 @@ def test_hartree_kernel(pair, nasmod):
     V = s.apply(nasmod.NAS_OP_HARTREE, rho, (P.fine.nnode,))
     ref = ohartree.hartree(P.fine, P.K, P.K_IB, rho, tol=1e-14)
     assert _relmax(V, ref) < 1e-10
+
+
+def test_hartree_quadrupole_boundary_values(pair, nasmod):
+    # off-centre, anisotropic charge: monopole + quadrupole boundary values
+    # (Sec. 3.1's multipole expansion with the textbook 1/2)
+    _, inst, P, s = pair
+    xq = P.fine.xq
+    rho = (np.exp(-2.0 * np.sum((xq - np.array([0.8, 0.3, -0.5])) ** 2, axis=-1))
+           + 0.5 * np.exp(-np.sum((xq - np.array([-0.9, -0.4, 0.6])) ** 2, axis=-1)))
+    s.opt.multipole = 2
+    nasmod.nas_set_options(s.h, s.opt)
+    try:
+        V2 = s.apply(nasmod.NAS_OP_HARTREE, rho, (P.fine.nnode,))
+    finally:
+        s.opt.multipole = 0
+        nasmod.nas_set_options(s.h, s.opt)
+    V0 = s.apply(nasmod.NAS_OP_HARTREE, rho, (P.fine.nnode,))
+    ref2 = ohartree.hartree(P.fine, P.K, P.K_IB, rho, tol=1e-14, multipole=2)
+    ref0 = ohartree.hartree(P.fine, P.K, P.K_IB, rho, tol=1e-14, multipole=0)
+    assert _relmax(V2, ref2) < 1e-10
+    # the quadrupole term is really on (the two boundary conditions differ)
+    assert _relmax(ref2, ref0) > 1e-4 and _relmax(V2, V0) > 1e-4
 
 
 def test_hartree_persistent_and_per_phase_pcg(nasmod):

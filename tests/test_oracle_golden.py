@@ -1,13 +1,13 @@
 """Oracle checks against values printed in the paper (tests/golden/*.txt,
 each file states the passage it copies).  CPU only.
 
-* The paper's molecules (Sec. 5): the workload inputs are the printed
+* The paper's molecules (Sec. 4): the workload inputs are the printed
   positions and charges.
 * The Perdew-Zunger constants (Sec. 3.1): the oracle's correlation energy
   takes, on either side of r_s = 1, the values the printed constants give
   there (A ln 1 + B + C ln 1 + D = B + D and gamma / (1 + beta1 + beta2)),
   and the two branches meet to the printed digits.
-* The helium energy (Sec. 5): the discrete Kohn-Sham energy of a Galerkin
+* The helium energy (Sec. 4.1): the discrete Kohn-Sham energy of a Galerkin
   space lies above the LDA limit, which for helium lies above the exact
   energy the paper quotes; it decreases under refinement.
 """

@@ -56,6 +56,7 @@ class Instance:
     tol_poisson: float = 1e-12
     max_outer: int = 100
     max_inner: int = 50
+    smearing: float = 0.0         # Fermi-Dirac kT (Ha); 0: the occupations in `occ`
     extra: dict = field(default_factory=dict)
 
     @property
@@ -142,7 +143,7 @@ def _hydrogen(cells=16, coarse_cells=4, order=1, half=12.0, power=2.0, **kw):
                     hartree=False, xc=False)
 
 
-# Molecules of the paper's experiments (Sec. 5), coordinates as printed.  The
+# Molecules of the paper's experiments (Sec. 4.2-4.4), coordinates as printed.  The
 # LiH and CH4 tables are in bohr (Li-H 3.015, C-H 2.268); the benzene table is
 # in angstrom (C-C 1.397, C-H 1.084) and is converted to bohr.
 ANGSTROM = 1.0 / 0.529177210903

@@ -4,19 +4,24 @@
 A step is one Algorithm 3 iteration (one augmented-subspace step): H~
 assembly, the N shifted linear boundary value problems (block PCG), the
 basis of the augmented space, its fixed blocks, and the inner SCF of the
-small Kohn-Sham problem to convergence (Hartree Poisson solves, LDA,
-A^NL assembly, Galerkin blocks, host small eigensolve, density, Anderson).
+small Kohn-Sham problem (Hartree Poisson solves, LDA, A^NL assembly,
+Galerkin blocks, the small eigensolve, density, Anderson mixing).
 
-Workload (default): 8 nuclei, Z uniform in {1..8}, R uniform in [-4,4]^3
-(seed 1), N = 21 doubly/singly occupied orbitals, Omega = [-16,16]^3, P2 on a
-50^3 tensor grid graded toward the nuclei (1,030,301 nodes, 970,299
-unknowns), coarse 16^3 P1 (3,375 unknowns), FP64.
+Headline workload (default): 32 nuclei, Z uniform in {1..6}, R uniform in
+[-8,8]^3 (seed 2), N = 64 orbitals with Fermi-Dirac occupations at
+kT = 0.01 Ha, Omega = [-16,16]^3, P2 on a 100^3 tensor grid graded toward
+the nuclei (8,120,601 nodes, 7,880,599 unknowns), coarse 16^3 P1 (3,375
+unknowns), mixed precision (FP32 Poisson and block PCG inside FP64
+iterative refinement; everything else FP64).  The same steps are run in
+FP64 from the same start state for the per-eigenvalue error of the mixed
+form and the mixed-over-FP64 speed ratio.  Secondary lines: the 8-nucleus
+P2 molecule (970,299 unknowns, N = 21, FP64) and helium on the 20^3 P1 mesh
+(6,859 unknowns, FP64), the size at which the CPU oracle also runs.
 
 Output: one JSON line (rank 0).  Multi-GPU: one process per GPU under
 torchrun, each an independent replica of the workload (weak scaling, no
 collective on the data path); value = total steps of all ranks / max time.
-`--impl reference` times the CPU oracle instead (bounded sample, see
-`oracle_sample`).
+`--impl reference` times the CPU oracle on the helium workload at full size.
 """
 import argparse
 import json
@@ -31,26 +36,32 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "augmented-subspace steps/s + SpMM HBM GB/s; mixed vs FP64 at ≤1e-8 Ha error"
-SAMPLE = dict(cells=10, coarse_cells=6)   # oracle sample: same molecule, reduced meshes
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flop x max clock
+REFERENCE_WORKLOAD = "he_p1"                      # the oracle's full-size config
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="mol8_p2")
+    p.add_argument("--workload", default="mol32_p2")
+    p.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"],
+                   help="headline precision; auto = mixed for mol32_p2 (the mixed-precision workload), else fp64")
     p.add_argument("--cells", type=int, default=None)
     p.add_argument("--coarse-cells", type=int, default=None)
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--compare-steps", type=int, default=3,
+                   help="steps of the other precision, from the same start state (<= --steps)")
+    p.add_argument("--e2e-steps", type=int, default=-1, help="-1: the same count as --steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--no-secondary", action="store_true", help="skip the 8-nucleus and helium lines")
+    p.add_argument("--secondary-steps", type=int, default=10)
     p.add_argument("--tol-poisson", type=float, default=1e-10)
     p.add_argument("--tol-bvp", type=float, default=1e-10)
+    p.add_argument("--inner-adapt", type=float, default=1e-2,
+                   help="inexact inner SCF: stop at max(tol_inner, inner_adapt x previous step's drho)")
     p.add_argument("--spmv-lanes", type=int, default=0)
-    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     p.add_argument("--clocks-file", default=None, help="where to keep the nvidia-smi clock samples")
     p.add_argument("--batch", type=int, default=0,
                    help="also time this many independent small instances (batched workload), "
@@ -68,17 +79,30 @@ def parse():
                    help="1: persistent cooperative Poisson PCG kernel, 0: per-phase kernels from a CUDA graph")
     p.add_argument("--poisson-adaptive", type=int, default=1,
                    help="1: inner Poisson tolerance follows the density residual (fixed point unchanged)")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
-def instance(args):
+def headline_precision(args):
+    if args.precision != "auto":
+        return args.precision
+    return "mixed" if args.workload == "mol32_p2" else "fp64"
+
+
+def instance(name, cells=None, coarse_cells=None):
     from workloads import make_instance
     kw = {}
-    if args.cells:
-        kw["cells"] = args.cells
-    if args.coarse_cells:
-        kw["coarse_cells"] = args.coarse_cells
-    return make_instance(args.workload, **kw)
+    if cells:
+        kw["cells"] = cells
+    if coarse_cells:
+        kw["coarse_cells"] = coarse_cells
+    return make_instance(name, **kw)
+
+
+def solver_options(args, timing=1):
+    return dict(timing=timing, tol_poisson=args.tol_poisson, tol_bvp=args.tol_bvp, check_every=4,
+                spmv_lanes=args.spmv_lanes, poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt,
+                eig_precond=args.eig_precond, poisson_sell=args.poisson_sell, poisson_fused=args.poisson_fused,
+                inner_adapt=args.inner_adapt)
 
 
 def kernel_source_hash(name, kernel):
@@ -116,14 +140,21 @@ def spmv_traffic(sz, kernel="k_pcg1_spmv"):
     return per_launch * sz["nnz"] / rec["nnz"]
 
 
-def workload_config(args, inst, extra=None):
+def workload_config(args, name, inst, sz, precision, extra=None):
     cfg = {
-        "workload": "%s: %d nuclei Z=%s, N=%d orbitals, P%d fine mesh %d tets, coarse %d tets, FP64"
-                    % (args.workload, len(inst.Z), [int(z) for z in inst.Z], inst.n_orb, inst.order,
-                       len(inst.fine_tet), len(inst.coarse_tet)),
-        "fine_vertices": int(len(inst.fine_xyz)),
-        "l2": "no flush: the per-step working set (CSR values/indices, orbitals, quadrature arrays) exceeds the 126 MB L2",
+        "workload": "%s: %d nuclei Z=%s, N=%d orbitals%s, P%d fine mesh %d tets (%d unknowns), coarse %d tets "
+                    "(%d unknowns), %s"
+                    % (name, len(inst.Z), [int(z) for z in inst.Z], inst.n_orb,
+                       (", Fermi-Dirac kT=%g Ha" % inst.smearing) if getattr(inst, "smearing", 0.0) > 0 else "",
+                       inst.order, len(inst.fine_tet), sz["n"], len(inst.coarse_tet), sz["nH"],
+                       "mixed FP32/FP64" if precision == "mixed" else "FP64"),
+        "unknowns": sz["n"], "nnz": sz["nnz"], "coarse_unknowns": sz["nH"], "orbitals": sz["N"],
+        "mu": inst.mu, "anderson_beta": getattr(inst, "anderson_beta", 0.7),
+        "l2": "no flush: the per-step working set (CSR values/indices, orbitals, quadrature arrays) exceeds the "
+              "126 MB L2 many times over",
         "tol_bvp": args.tol_bvp, "tol_poisson": args.tol_poisson, "tol_inner": inst.tol_scf,
+        "inner_scf_tolerance": ("inexact: max(tol_inner, %g x previous step's drho)" % args.inner_adapt
+                                if args.inner_adapt > 0 else "tol_inner in every step"),
         "poisson_tolerance": ("inexact inner solves: max(tol_poisson, min(1e-6, 1e-3 x previous density "
                               "residual))" if args.poisson_adaptive else "tol_poisson in every solve"),
         "small_eigensolver": "LOBPCG, block vectors on the device, host Rayleigh-Ritz, %s preconditioner; "
@@ -133,6 +164,106 @@ def workload_config(args, inst, extra=None):
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def phase_totals(reps, phases):
+    ms = {name: sum(rp.phase_ms[i] for rp in reps) for i, name in enumerate(phases)}
+    calls = {name: sum(rp.phase_calls[i] for rp in reps) for i, name in enumerate(phases)}
+    return ms, calls
+
+
+def kernel_rooflines(reps, sz, steps, phases, hbm_peak, peak_src, nz_occ, layouts=None):
+    """Per-kernel achieved throughput from the library's live CUDA-event
+    timings of the timed steps (reports `reps`), against its roofline: HBM
+    bytes for the sparse and streaming kernels, the FP64 issue rate for the
+    FP64-ALU-bound ones.  Returns {kernel: dict}; each dict carries
+    est_ms_per_step (mean launch time x launches per step) so that the
+    caller can pick the dominant kernel of the run.
+
+    Algorithmic bytes / flops per launch (n unknowns, nnz CSR entries, N
+    columns, ne elements, 14 quadrature points and 10 nodes per P2 element,
+    55 node pairs):
+      FP64 SpMM           nnz (8+4) + 4 (n+1) + 2 n N 8   (FP64-ALU bound: 2 nnz N flop)
+      FP32 SpMM           nnz (4+4) + 4 (n+1) + 2 n N 4
+      FP64 Poisson SpMV   12 nnz + 20 n + 4
+      FP32 Poisson SpMV   8 nnz + 12 n + 4
+      reconstruction      2 n N (4 + N) flop (Psi = I u_H + U^ alpha)
+      density             2 ne (Nz (10 + 55) + 14 x 55) flop, Nz = orbitals with f > 0
+    """
+    ms, calls = phase_totals(reps, phases)
+    n, nnz, N = sz["n"], sz["nnz"], sz["N"]
+    layouts = layouts or {}
+    out = {}
+
+    def hbm(name, kern_ms, launches, nbytes, desc):
+        if launches <= 0 or kern_ms <= 0:
+            return
+        per = kern_ms / launches
+        gbs = nbytes / (per * 1e-3) / 1e9
+        out[name] = {"kernel": desc, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": gbs / hbm_peak, "peak_source": peak_src, "algorithmic_bytes_per_launch": nbytes,
+                     "launches": int(launches), "ms_per_launch": per,
+                     "est_ms_per_step": per * launches / steps}
+
+    def alu(name, kern_ms, launches, flops, desc, nbytes=None):
+        if launches <= 0 or kern_ms <= 0:
+            return
+        per = kern_ms / launches
+        tf = flops / (per * 1e-3) / 1e12
+        d = {"kernel": desc, "bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "frac": tf / FP64_PEAK_TFLOPS,
+             "peak_source": "FP64 FMA issue rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
+             "algorithmic_flops_per_launch": flops, "launches": int(launches), "ms_per_launch": per,
+             "est_ms_per_step": per * launches / steps}
+        if nbytes:
+            d["algorithmic_gbs"] = nbytes / (per * 1e-3) / 1e9
+        out[name] = d
+
+    spmm_bytes = sum(rp.spmm_bytes for rp in reps)
+    spmm_flops = sum(rp.spmm_flops for rp in reps)
+    if calls["spmm"]:
+        alu("spmm_f64", ms["spmm"], calls["spmm"], spmm_flops / calls["spmm"],
+            "CSR SpMM, N=%d interleaved RHS, FP64 (autotuned layout %s)" % (N, layouts.get("f64", "?")),
+            spmm_bytes / calls["spmm"])
+    b32 = sum(getattr(rp, "spmm32_bytes", 0.0) for rp in reps)
+    if calls.get("spmm32"):
+        hbm("spmm_f32", ms["spmm32"], calls["spmm32"], b32 / calls["spmm32"],
+            "CSR SpMM, N=%d interleaved RHS, FP32 values and vectors, mixed block PCG (autotuned layout %s)"
+            % (N, layouts.get("f32", "?")))
+    sp_ms = sum(rp.poisson_spmv_ms for rp in reps)
+    sp_n = int(sum(rp.poisson_spmv_launches for rp in reps))
+    poisson_iters = sum(rp.poisson_iters for rp in reps)
+    if sp_n:
+        sell = sz.get("sell", 0)
+        hbm("k_pcg1_spmv_sell", sp_ms, sp_n, 12.0 * nnz + 20.0 * n + 4.0,
+            "k_pcg1_spmv_sell (sliced-ELL SpMV of the FP64 Poisson PCG; %d stored entries, %.1f %% padding)"
+            % (sell, 100.0 * (sell / nnz - 1.0)) if sell else "k_pcg1_spmv (CSR SpMV of the FP64 Poisson PCG)")
+        # every Poisson iteration launches one SpMV
+        out["k_pcg1_spmv_sell"]["est_ms_per_step"] = out["k_pcg1_spmv_sell"]["ms_per_launch"] * poisson_iters / steps
+        out["k_pcg1_spmv_sell"]["timing"] = ("CUDA events around the SpMV of the first two iterations of every "
+                                             "Poisson solve (direct launches; the rest replays from a CUDA graph)")
+    if calls.get("spmv32"):
+        hbm("k_pcg1_spmv_f32", ms["spmv32"], calls["spmv32"], 8.0 * nnz + 12.0 * n + 4.0,
+            "k_pcg1_spmv (CSR SpMV of the FP32 inner Poisson PCG, mixed precision)")
+        out["k_pcg1_spmv_f32"]["est_ms_per_step"] = out["k_pcg1_spmv_f32"]["ms_per_launch"] * poisson_iters / steps
+        out["k_pcg1_spmv_f32"]["timing"] = ("CUDA events around the SpMV of the first two iterations of every "
+                                            "inner FP32 solve (direct launches; the rest replays from a CUDA graph)")
+    if calls.get("recon"):
+        alu("k_reconstruct", ms["recon"], calls["recon"], 2.0 * n * N * (4 + N),
+            "k_reconstruct (Psi = I u_H + U^ alpha, FP64, N=%d)" % N)
+    if calls.get("densk"):
+        ne = sz["ne"]
+        nloc, nq = (10, 14) if sz["order"] == 2 else (4, 4)
+        npair = nloc * (nloc + 1) // 2
+        alu("k_density", ms["densk"], calls["densk"], 2.0 * ne * (nz_occ * (nloc + npair) + nq * npair),
+            "k_density (rho = sum f psi^2 at the quadrature points via the element density matrix, FP64)")
+    return out
+
+
+def dominant(roofs):
+    if not roofs:
+        return None
+    return max(roofs.values(), key=lambda d: d["est_ms_per_step"])
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -181,51 +312,99 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------------------- oracle
-def oracle_sample(n_steps, warm_steps=1):
-    """Time oracle augmented steps on the reduced sample (runs in a fresh
-    single-threaded process).  Returns dict with per-step seconds and sizes."""
+# ---------------------------------------------------------------------------- oracle (CPU)
+def oracle_steps(name, n_steps, warm_steps):
+    """Time `n_steps` oracle Algorithm 3 steps of workload `name` at full size
+    after `warm_steps` untimed ones (in this process; the caller fixes the
+    BLAS/OpenMP thread count).  The time spent in the oracle's small
+    eigensolve is recorded separately, through a wrapper that only times the
+    call."""
     from oracle.nas import Problem
     from workloads import make_instance
-    inst = make_instance("mol8_p2", **SAMPLE)
+    inst = make_instance(name)
     inst.tol_bvp = 1e-10
     inst.tol_poisson = 1e-10
+    t0 = time.perf_counter()
     P = Problem(inst)
+    build_s = time.perf_counter() - t0
+    eig_s = [0.0]
+    inner = P.eig_small
+
+    def timed_eig(FA, FB):
+        t = time.perf_counter()
+        r = inner(FA, FB)
+        eig_s[0] += time.perf_counter() - t
+        return r
+
+    P.eig_small = timed_eig
     st = P.initial_state()
     for _ in range(warm_steps):
         st = P.step(st)
-    times = []
+    steps, eigs, inners = [], [], []
     for _ in range(n_steps):
+        eig_s[0] = 0.0
         t = time.perf_counter()
         st = P.step(st)
-        times.append(time.perf_counter() - t)
-    return {"step_s": times, "n_sample": int(P.fine.n), "nH": int(P.coarse.n), "n_inner": int(st.n_inner)}
+        steps.append(time.perf_counter() - t)
+        eigs.append(eig_s[0])
+        inners.append(int(st.n_inner))
+    return {"step_s": steps, "eig_s": eigs, "n_inner": inners, "n": int(P.fine.n), "nH": int(P.coarse.n),
+            "N": int(P.N), "build_s": build_s}
 
 
-def run_oracle_subprocess(n_steps, warm_steps=1, timeout=900):
+def oracle_eig_seconds(path, N, reps=1):
+    """Time the oracle's small eigensolve (scipy.linalg.eigh of the dense
+    pencil, lowest N pairs) on the pencil stored in `path` (.npz FA, FB)."""
+    import numpy as np
+    import types
+    from oracle.nas import Problem
+    d = np.load(path)
+    FA, FB = d["FA"], d["FB"]
+    ts = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        Problem.eig_small(types.SimpleNamespace(N=N), FA, FB)
+        ts.append(time.perf_counter() - t)
+    return {"eig_s": min(ts), "m": int(FA.shape[0])}
+
+
+def host_threads():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def run_oracle_subprocess(call, threads, timeout=1500):
+    """Run `bench.<call>` in a fresh process with `threads` BLAS/OpenMP threads
+    (fork + exec, after the GPU work, so that nothing competes with the timed
+    GPU steps for the host cores); returns its JSON result."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "print('ORACLE', json.dumps(bench.oracle_sample(%d, %d)))" % (ROOT, n_steps, warm_steps))
+        env[k] = str(threads)
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; print('ORACLE', json.dumps(bench.%s))"
+            % (ROOT, call))
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
     for line in r.stdout.splitlines():
         if line.startswith("ORACLE "):
             return json.loads(line[7:])
-    raise RuntimeError("oracle sample failed: %s" % r.stderr[-2000:])
+    raise RuntimeError("oracle run failed: %s" % r.stderr[-2000:])
 
 
-def cpu_baseline_from(sample, n_full):
-    t = statistics.median(sample["step_s"])
-    scale = n_full / sample["n_sample"]
-    return {
-        "value": 1.0 / (t * scale), "unit": "steps/s", "cores": 1, "kind": "oracle",
-        "sample": ("CPU oracle (NumPy/SciPy FP64, 1 thread) Algorithm 3 steps on the same molecule with a "
-                   "P2 %d^3 fine mesh (%d unknowns) and %d^3 coarse mesh; measured %.2f s/step, scaled to the "
-                   "full %d-unknown mesh linearly in fine unknowns (the paper's O(N N_k) work per step)"
-                   % (SAMPLE["cells"], sample["n_sample"], SAMPLE["coarse_cells"], t, n_full)),
-        "sample_step_s": t,
-    }
+def cpu_extrapolation(ref, eig_full_s, n_full, N_full, inner_full):
+    """Oracle seconds per step of the headline workload, term by term, from
+    measured pieces: the oracle's small eigensolve at the headline's own size
+    (eig_full_s, timed on its pencil) once per inner iteration, plus the rest
+    of an oracle step on the full-size helium workload (`ref`: its step minus
+    its small eigensolves) scaled linearly in fine unknowns x orbitals x inner
+    iterations.  The linear scaling is a lower bound: the Gram matrices and the
+    reconstruction grow with N^2 and the Poisson/BVP iteration counts with n."""
+    t_step = statistics.median(ref["step_s"])
+    t_eig = statistics.median(ref["eig_s"])
+    inner0 = statistics.mean(ref["n_inner"])
+    rest0 = max(t_step - t_eig, 0.0)
+    scale = (n_full * N_full * inner_full) / (ref["n"] * ref["N"] * inner0)
+    t_full = rest0 * scale + eig_full_s * inner_full
+    return {"seconds_per_step": t_full, "fine_mesh_terms_s": rest0 * scale, "small_eigensolve_s": eig_full_s * inner_full,
+            "scale_fine": scale, "ref_step_s": t_step, "ref_eig_s": t_eig, "ref_inner": inner0,
+            "inner_per_step": inner_full, "eig_one_call_s": eig_full_s}
 
 
 def cpu_spmm_baseline(s, nas, sz, reps=3):
@@ -255,44 +434,6 @@ def cpu_spmm_baseline(s, nas, sz, reps=3):
             "kind": "oracle C/OpenMP CSR SpMM (oracle/spmm_omp.c), the benchmark's pattern, mean of %d "
                     "products after one untimed" % reps}
 
-
-def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    inst = instance(args)
-    # unknowns of the full mesh: P2 nodes minus boundary nodes (counted without assembling)
-    n_full = full_unknowns(inst)
-    sample = run_oracle_subprocess(args.steps, warm_steps=max(1, args.warmup))
-    cb = cpu_baseline_from(sample, n_full)
-    ms = statistics.median(sample["step_s"]) * (n_full / sample["n_sample"]) * 1e3
-    line = {
-        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {k: v for k, v in workload_config(args, inst).items()
-                   if k not in ("poisson_tolerance", "small_eigensolver")},
-        "cpu_baseline": cb,
-        "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line))
-
-
-def full_unknowns(inst):
-    import numpy as np
-    xyz = inst.fine_xyz
-    tet = inst.fine_tet.astype(np.int64)
-    lo, hi = xyz.min(axis=0), xyz.max(axis=0)
-    on_b = np.any((xyz == lo) | (xyz == hi), axis=1)
-    n = int(np.sum(~on_b))
-    if inst.order == 2:
-        pairs = np.concatenate([np.sort(tet[:, [i, j]], axis=1) for i, j in
-                                [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]])
-        key = np.unique(pairs[:, 0] * len(xyz) + pairs[:, 1])
-        a, b = key // len(xyz), key % len(xyz)
-        mid = 0.5 * (xyz[a] + xyz[b])
-        n += int(np.sum(~np.any((mid == lo) | (mid == hi), axis=1)))
-    return n
 
 
 # ---------------------------------------------------------------------------- batched instances
@@ -381,15 +522,103 @@ def job_value(world, steps, max_ms):
 
 
 # ---------------------------------------------------------------------------- our arm
+def run_reference(args):
+    """The reference arm: the CPU oracle (the plain FP64 restatement of the
+    paper, as it stands) timed on the host cores on the helium workload at its
+    full size (the largest workload the oracle finishes in minutes); W
+    untimed and K timed steps.  Under torchrun only rank 0 runs."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = host_threads()
+    res = run_oracle_subprocess("oracle_steps(%r, %d, %d)" % (REFERENCE_WORKLOAD, args.steps, max(1, args.warmup)),
+                                threads)
+    total = sum(res["step_s"])
+    value = args.steps / total
+    inst = instance(REFERENCE_WORKLOAD)
+    sample = ("CPU oracle (NumPy/SciPy FP64) Algorithm 3 steps of the helium workload at full size: P1 20^3 "
+              "graded mesh, %d unknowns, coarse 8^3 (%d unknowns), N = %d; %d steps timed after %d"
+              % (res["n"], res["nH"], res["N"], args.steps, max(1, args.warmup)))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s: helium Z=2, N=1, P1 fine mesh %d tets (%d unknowns), coarse %d tets, FP64"
+                               % (REFERENCE_WORKLOAD, len(inst.fine_tet), res["n"], len(inst.coarse_tet)),
+                   "unknowns": res["n"], "coarse_unknowns": res["nH"], "mu": 32.0},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "step_s": res["step_s"], "build_s": res["build_s"]},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
 def log(msg):
     print("[bench] " + msg, file=sys.stderr, flush=True)
 
 
+def timed_steps(s, nas, torch, steps, snap_at=None):
+    """`steps` steps of solver s, a CUDA event on the stream (torch's current
+    stream, which the solver runs on) before each step and after the last;
+    returns (total ms, per-step ms, reports, eigenvalues and energy after step
+    `snap_at`)."""
+    import numpy as np
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    reps, snap = [], None
+    ev[0].record()
+    for k in range(steps):
+        r, rep = s.step()
+        ev[k + 1].record()
+        reps.append(nas.nas_report.from_buffer_copy(rep))
+        if snap_at is not None and k + 1 == snap_at:
+            snap = (np.array(s.get(nas.NAS_Q_EIGVALS)), float(rep.energy))
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return ev[0].elapsed_time(ev[steps]), per, reps, snap
+
+
+def secondary_line(args, nas, torch, name, device, stream):
+    """FP64 steps/s of a smaller workload (no e2e, no comparison)."""
+    inst = instance(name)
+    s = nas.Solver(inst, device=device, stream=stream, **solver_options(args))
+    t0 = time.time()
+    s.init()
+    setup = time.time() - t0
+    for _ in range(2):
+        s.step()
+    ms, _, reps, _ = timed_steps(s, nas, torch, args.secondary_steps)
+    sz = s.sizes()
+    roofs = kernel_rooflines(reps, sz, args.secondary_steps, nas.PHASES, *hbm_peak(), nz_occ=sz["N"],
+                             layouts=tuned_layouts(nas, sz))
+    out = {"value": args.secondary_steps / (ms / 1e3), "unit": "steps/s", "steps": args.secondary_steps,
+           "warmup": 2, "ms_per_step": ms / args.secondary_steps, "dtype": "f64", "setup_s": setup,
+           "config": workload_config(args, name, inst, sz, "fp64"),
+           "drho": [r.drho for r in reps], "energy": [r.energy for r in reps],
+           "n_inner": [r.n_inner for r in reps], "roofline": dominant(roofs),
+           "gpu_launches": int(sum(r.kernel_launches for r in reps))}
+    s.close()
+    return out
+
+
+def tuned_layouts(nas, sz):
+    """The SpMM layouts the autotuner chose for this workload's block of N columns."""
+    out = {}
+    for r in nas.nas_spmm_tuning():
+        if r["rows"] == sz["n"] and r["N"] == sz["N"]:
+            out[r["type"]] = r["layout"]
+    return out
+
+
+def hbm_peak():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 def main():
     args = parse()
-    if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.steps)))
-        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -408,13 +637,12 @@ def main():
         nbuild.build()
     from paper_2404_19249_gb300 import nas
 
-    inst = instance(args)
+    prec = headline_precision(args)
+    other = "fp64" if prec == "mixed" else "mixed"
+    inst = instance(args.workload, args.cells, args.coarse_cells)
     stream = torch.cuda.current_stream().cuda_stream
     t0 = time.time()
-    s = nas.Solver(inst, device=local, stream=stream, timing=1, tol_poisson=args.tol_poisson,
-                   tol_bvp=args.tol_bvp, check_every=4, spmv_lanes=args.spmv_lanes,
-                   poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt, eig_precond=args.eig_precond,
-                   poisson_sell=args.poisson_sell, poisson_fused=args.poisson_fused)
+    s = nas.Solver(inst, device=local, stream=stream, precision=1 if prec == "mixed" else 0, **solver_options(args))
     s.init()
     setup_s = time.time() - t0
     sz = s.sizes()
@@ -422,228 +650,208 @@ def main():
     for w in range(args.warmup):
         tw = time.time()
         r, rep = s.step()
-        log("warmup step %d: %.2f s status %d inner %d cg %d poisson %d drho %.3e E %.10f phases %s"
-            % (w, time.time() - tw, r, rep.n_inner, rep.cg_iters, rep.poisson_iters, rep.drho, rep.energy,
-               {k: round(v, 1) for k, v in rep.as_dict()["phase_ms"].items()}))
+        log("warmup step %d: %.2f s status %d inner %d cg %d poisson %d eig %d drho %.3e E %.10f phases %s"
+            % (w, time.time() - tw, r, rep.n_inner, rep.cg_iters, rep.poisson_iters, rep.eig_iters, rep.drho,
+               rep.energy, {k: round(v, 1) for k, v in rep.as_dict()["phase_ms"].items()}))
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    clocks = Clocks(args.clocks_file or "/tmp/bench_clocks_%d.csv" % os.getpid())
-    # state at the start of the timed region (the mixed-precision run restarts from it)
-    n0, N0, nqt0 = sz["n"], sz["N"], sz["ne"] * sz["nq"]
-    s0_lam = np.zeros(N0)
-    s0_psi = np.zeros((n0, N0))
-    s0_rho = np.zeros(nqt0)
-    nas.nas_get(s.h, nas.NAS_Q_EIGVALS, s0_lam)
-    nas.nas_get(s.h, nas.NAS_Q_ORBITALS, s0_psi)
-    nas.nas_get(s.h, nas.NAS_Q_RHO_IN, s0_rho)
+    # state at the start of the timed region, in pinned host memory: the
+    # comparison run and the end-to-end run restart from it
+    n, N, nqt = sz["n"], sz["N"], sz["ne"] * sz["nq"]
+    s0_lam = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    s0_psi = torch.empty((n, N), dtype=torch.float64, pin_memory=True)
+    s0_rho = torch.empty(nqt, dtype=torch.float64, pin_memory=True)
+
+    def get(q, t):
+        nas.nas_get(s.h, q, (t.data_ptr(), t.numel() * t.element_size()), 0)
+
+    get(nas.NAS_Q_EIGVALS, s0_lam)
+    get(nas.NAS_Q_ORBITALS, s0_psi)
+    get(nas.NAS_Q_RHO_IN, s0_rho)
+    n_cmp = max(1, min(args.compare_steps, args.steps))
     barrier()
+    clocks = Clocks(args.clocks_file or "/tmp/bench_clocks_%d.csv" % os.getpid())
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    reps = []
     torch.cuda.nvtx.range_push("timed")
-    ev0.record()
-    for _ in range(args.steps):
-        r, rep = s.step()
-        reps.append(nas.nas_report.from_buffer_copy(rep))
-    ev1.record()
+    ms, per_h, reps, snap = timed_steps(s, nas, torch, args.steps, snap_at=n_cmp)
     torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop(local)
-    ms = ev0.elapsed_time(ev1)
     log("timed: %d steps in %.1f ms; last report %s" % (args.steps, ms, reps[-1].as_dict()))
     ms = reduce_max(ms, dist, "cuda")
     value = job_value(world, args.steps, ms)
+    lam_h, e_h = snap
+    # ------------------------------------------------------------ the other precision, same start state
+    nas.nas_set_state(s.h, s0_lam.data_ptr(), s0_psi.data_ptr(), s0_rho.data_ptr(), 0)
+    s.opt.precision = 1 if other == "mixed" else 0
+    nas.nas_set_options(s.h, s.opt)
+    barrier()
+    ms_o, per_o, reps_o, snap_o = timed_steps(s, nas, torch, n_cmp, snap_at=n_cmp)
+    ms_o = reduce_max(ms_o, dist, "cuda")
+    lam_o, e_o = snap_o
+    # the headline run's own time over its first n_cmp steps (the same steps)
+    lam_mixed, lam_fp64 = (lam_h, lam_o) if prec == "mixed" else (lam_o, lam_h)
+    e_mixed, e_fp64 = (e_h, e_o) if prec == "mixed" else (e_o, e_h)
+    err = lam_mixed - lam_fp64
+    comparison = {
+        "precision": other, "steps": n_cmp, "value": job_value(world, n_cmp, ms_o), "unit": "steps/s",
+        "ms_per_step": ms_o / n_cmp,
+        "what": "the same start state and steps in the other precision; mixed = FP32 Poisson and block PCG "
+                "inside FP64 iterative refinement, all else FP64",
+        "max_eigenvalue_err_ha": float(np.max(np.abs(err))), "eigenvalue_err_ha": [float(x) for x in err],
+        "energy_err_ha": float(e_mixed - e_fp64),
+        "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_o, nas.PHASES)[0].items()},
+        "n_inner": [r.n_inner for r in reps_o], "drho": [r.drho for r in reps_o],
+    }
+    hms = phase_totals(reps[:n_cmp], nas.PHASES)[0]
+    comparison["headline_phase_ms_first_steps"] = {k: v / n_cmp for k, v in hms.items()}
+    comparison["headline_ms_first_steps"] = sum(per_h[:n_cmp]) / n_cmp
+    log("comparison (%s): %s" % (other, json.dumps({k: v for k, v in comparison.items() if k != "eigenvalue_err_ha"})))
+    s.opt.precision = 1 if prec == "mixed" else 0
+    nas.nas_set_options(s.h, s.opt)
 
-    lam64 = np.zeros(N0)
-    nas.nas_get(s.h, nas.NAS_Q_EIGVALS, lam64)
-    en64 = np.zeros(6)
-    nas.nas_get(s.h, nas.NAS_Q_ENERGY, en64)
+    # ------------------------------------------------------------ rooflines from the live CUDA-event timings
+    peak, psrc = hbm_peak()
+    # orbitals with nonzero occupation (all of them with smearing)
+    nz = N if getattr(inst, "smearing", 0.0) > 0 else int(np.sum(np.asarray(inst.occ) > 0))
+    lay = tuned_layouts(nas, sz)
+    roofs_h = kernel_rooflines(reps, sz, args.steps, nas.PHASES, peak, psrc, nz_occ=nz, layouts=lay)
+    roofs_o = kernel_rooflines(reps_o, sz, n_cmp, nas.PHASES, peak, psrc, nz_occ=nz, layouts=lay)
+    tuner = [r for r in nas.nas_spmm_tuning() if r["rows"] == sz["n"]]
+    trf = spmv_traffic(sz, "k_pcg1_spmv_sell")
+    for rr in (roofs_h, roofs_o):
+        if "k_pcg1_spmv_sell" in rr:
+            rr["k_pcg1_spmv_sell"]["traffic"] = trf
+        for d in rr.values():
+            d.setdefault("traffic", None)
 
-    # ---------------------------------------------------------------- mixed precision
-    mixed = None
-    if not args.no_mixed:
-        nas.nas_set_state(s.h, s0_lam, s0_psi, s0_rho)
-        s.opt.precision = 1
-        nas.nas_set_options(s.h, s.opt)
-        barrier()
-        m0 = torch.cuda.Event(enable_timing=True)
-        m1 = torch.cuda.Event(enable_timing=True)
-        m0.record()
-        mreps = []
-        for _ in range(args.steps):
-            r, rep = s.step()
-            mreps.append(nas.nas_report.from_buffer_copy(rep))
-        m1.record()
-        barrier()
-        mms = reduce_max(m0.elapsed_time(m1), dist, "cuda")
-        lam32 = np.zeros(N0)
-        nas.nas_get(s.h, nas.NAS_Q_EIGVALS, lam32)
-        en32 = np.zeros(6)
-        nas.nas_get(s.h, nas.NAS_Q_ENERGY, en32)
-        mixed = {
-            "value": job_value(world, args.steps, mms), "unit": "steps/s", "ms_per_step": mms / args.steps,
-            "what": "Poisson PCG and block PCG of the N shifted problems in FP32 inside FP64 iterative refinement; "
-                    "same start state and step count as the FP64 run",
-            "max_eigenvalue_err_ha": float(np.max(np.abs(lam32 - lam64))),
-            "eigenvalue_err_ha": [float(x) for x in (lam32 - lam64)],
-            "energy_err_ha": float(en32[0] - en64[0]),
-            "poisson_ms_per_step": sum(rp.phase_ms[2] for rp in mreps) / args.steps,
-            "poisson_iters_per_step": sum(rp.poisson_iters for rp in mreps) / args.steps,
-            "bvp_ms_per_step": sum(rp.phase_ms[1] for rp in mreps) / args.steps,
-            "fp64_bvp_ms_per_step": sum(rp.phase_ms[1] for rp in reps) / args.steps,
-        }
-        log("mixed: %s" % json.dumps({k: v for k, v in mixed.items() if k != "eigenvalue_err_ha"}))
-        s.opt.precision = 0
-        nas.nas_set_options(s.h, s.opt)
-
-    # phase totals over the timed steps (library CUDA events on the launching stream)
-    ph = {name: sum(rp.phase_ms[i] for rp in reps) for i, name in enumerate(nas.PHASES)}
-    calls = {name: sum(rp.phase_calls[i] for rp in reps) for i, name in enumerate(nas.PHASES)}
-    spmm_bytes = sum(rp.spmm_bytes for rp in reps)
-    spmm_flops = sum(rp.spmm_flops for rp in reps)
-    spmv_bytes = sum(rp.spmv_bytes for rp in reps)
-    launches = int(sum(rp.kernel_launches for rp in reps))
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm_peak = float(peaks["hbm_gbs"])
-        peak_src = "measured"
-    except Exception:
-        hbm_peak, peak_src = 6800.0, "fallback"
-    spmm_ms, spmv_ms = ph["spmm"], ph["spmv"]
-    spmm_gbs = spmm_bytes / (spmm_ms * 1e-3) / 1e9 if spmm_ms > 0 else 0.0
-    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9 if spmv_ms > 0 else 0.0
-    spmm_tflops = spmm_flops / (spmm_ms * 1e-3) / 1e12 if spmm_ms > 0 else 0.0
-    roof_spmm = {"kernel": "k_spmm_cols (CSR SpMM, N=%d interleaved RHS, FP64)" % sz["N"], "bound": "alu",
-                 "achieved": spmm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": spmm_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                 "peak_source": "FP64 FMA issue rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
-                 "algorithmic_gbs": spmm_gbs, "launches": calls["spmm"], "ms_per_launch":
-                     spmm_ms / max(calls["spmm"], 1)}
-    # dominant kernel: the SpMV of the FP64 Poisson PCG (k_pcg1_spmv), timed by
-    # CUDA events around the SpMV launches of the first two iterations of every
-    # Poisson solve (library timing mode), over the timed steps
-    sp_ms = sum(rp.poisson_spmv_ms for rp in reps)
-    sp_n = int(sum(rp.poisson_spmv_launches for rp in reps))
-    sp_bytes = 12.0 * sz["nnz"] + 20.0 * sz["n"] + 4.0   # val+col, row_ptr, p once, q written (CSR count)
-    sp_ms_launch = sp_ms / max(sp_n, 1)
-    sp_gbs = sp_bytes / (sp_ms_launch * 1e-3) / 1e9 if sp_ms > 0 else 0.0
-    sell = sz.get("sell", 0) if args.poisson_sell else 0
-    sp_name = "k_pcg1_spmv_sell" if sell else "k_pcg1_spmv"
-    roof_spmv = {"kernel": ("k_pcg1_spmv_sell (sliced-ELL SpMV of the Poisson PCG, FP64; %d stored entries, "
-                            "%.1f %% padding)" % (sell, 100.0 * (sell / sz["nnz"] - 1.0)))
-                 if sell else "k_pcg1_spmv (CSR SpMV of the Poisson PCG, FP64)",
-                 "bound": "hbm", "achieved": sp_gbs, "peak": hbm_peak, "unit": "GB/s",
-                 "frac": sp_gbs / hbm_peak, "traffic": spmv_traffic(sz, sp_name), "peak_source": peak_src,
-                 "algorithmic_bytes_per_launch": sp_bytes, "launches": sp_n, "ms_per_launch": sp_ms_launch,
-                 "timing": "CUDA events on the library stream around the SpMV of the first two iterations "
-                           "of every Poisson solve (direct launches; the rest replays from a CUDA graph)"}
-    # every Poisson PCG iteration launches one SpMV: its time per step is the
-    # measured mean launch time x the Poisson iterations of the timed steps
-    poisson_iters = sum(rp.poisson_iters for rp in reps)
-    roof_spmv["est_ms_per_step"] = sp_ms_launch * poisson_iters / args.steps
-    roof_spmm["est_ms_per_step"] = spmm_ms / args.steps
-    # persistent form: every launch of every FP64 Poisson solve is timed; one
-    # iteration reads/writes (algorithmic, each array once per phase): SpMV
-    # 12 nnz + 20 n; update 48 n; restriction 12 nnz(I^T) + 8 n; piece sums
-    # 8 pieces + 12 nH; coarse solve 8 nH^2 + 16 nH; prolongation 72 n + 8 nH;
-    # new direction 24 n
-    fz_ms = sum(rp.poisson_fused_ms for rp in reps)
-    fz_it = int(sum(rp.poisson_fused_iters for rp in reps))
-    if fz_it > 0:
-        nH = sz["nH"]
-        fz_bytes = (12.0 * sz["nnz"] + 12.0 * sz["tnnz"] + 172.0 * sz["n"] + 8.0 * nH * nH + 8.0 * sz["tpieces"]
-                    + 36.0 * nH)
-        fz_gbs = fz_bytes * fz_it / (fz_ms * 1e-3) / 1e9
-        tr = spmv_traffic(sz, "k_pcg1_fused")
-        roof_spmv = {"kernel": "k_pcg1_fused (persistent cooperative two-level PCG of the Poisson problem, FP64, "
-                               "sliced-ELL SpMV, 7 grid-wide barriers per iteration, 16 iterations per launch)",
-                     "bound": "hbm", "achieved": fz_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": fz_gbs / hbm_peak, "traffic": tr, "peak_source": peak_src,
-                     "traffic_unit": "DRAM bytes per iteration",
-                     "algorithmic_bytes_per_iteration": fz_bytes, "iterations": fz_it,
-                     "ms_per_iteration": fz_ms / fz_it,
-                     "timing": "CUDA events on the library stream around every persistent launch of every "
-                               "FP64 Poisson solve of the timed steps",
-                     "est_ms_per_step": fz_ms / args.steps}
-    dominant, other = ((roof_spmv, roof_spmm) if roof_spmv["est_ms_per_step"] >= roof_spmm["est_ms_per_step"]
-                       else (roof_spmm, roof_spmv))
-
-    # ---------------------------------------------------------------- e2e through host buffers
-    n, N, nqt = sz["n"], sz["N"], sz["ne"] * sz["nq"]
-    lam_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
-    psi_h = torch.empty((n, N), dtype=torch.float64, pin_memory=True)
-    rho_h = torch.empty(nqt, dtype=torch.float64, pin_memory=True)
-    en_h = torch.empty(6, dtype=torch.float64, pin_memory=True)
-
-    def get(q, t):
-        nas.nas_get(s.h, q, (t.data_ptr(), t.numel() * 8), 0)
-
-    get(nas.NAS_Q_EIGVALS, lam_h)
-    get(nas.NAS_Q_ORBITALS, psi_h)
-    get(nas.NAS_Q_RHO_IN, rho_h)
+    # ------------------------------------------------------------ e2e through host buffers
+    n_e2e = args.steps if args.e2e_steps < 0 else args.e2e_steps
+    lam_b = torch.empty_like(s0_lam, pin_memory=True)
+    psi_b = torch.empty_like(s0_psi, pin_memory=True)
+    rho_b = torch.empty_like(s0_rho, pin_memory=True)
+    en_b = torch.empty(6, dtype=torch.float64, pin_memory=True)
+    lam_b.copy_(s0_lam)
+    psi_b.copy_(s0_psi)
+    rho_b.copy_(s0_rho)
     barrier()
     e0 = time.perf_counter()
-    n_e2e = max(args.e2e_steps, 0)
     for _ in range(n_e2e):
-        nas.nas_set_state(s.h, lam_h.data_ptr(), psi_h.data_ptr(), rho_h.data_ptr(), 0)
+        nas.nas_set_state(s.h, lam_b.data_ptr(), psi_b.data_ptr(), rho_b.data_ptr(), 0)
         s.step()
-        get(nas.NAS_Q_EIGVALS, lam_h)
-        get(nas.NAS_Q_ORBITALS, psi_h)
-        get(nas.NAS_Q_RHO_IN, rho_h)
-        get(nas.NAS_Q_ENERGY, en_h)
+        nas.nas_get(s.h, nas.NAS_Q_EIGVALS, (lam_b.data_ptr(), lam_b.numel() * 8), 0)
+        nas.nas_get(s.h, nas.NAS_Q_ORBITALS, (psi_b.data_ptr(), psi_b.numel() * 8), 0)
+        nas.nas_get(s.h, nas.NAS_Q_RHO_IN, (rho_b.data_ptr(), rho_b.numel() * 8), 0)
+        nas.nas_get(s.h, nas.NAS_Q_ENERGY, (en_b.data_ptr(), 48), 0)
     barrier()
     e2e_s = reduce_max(time.perf_counter() - e0, dist, "cuda")
     io_bytes = 8 * (N + n * N + nqt)
     e2e = None
     if n_e2e > 0:
-        e2e = {"value": world * n_e2e / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": io_bytes,
-               "d2h_bytes_per_step": io_bytes + 48}
-
+        e2e = {"value": world * n_e2e / e2e_s, "unit": "steps/s", "steps": n_e2e, "h2d_bytes_per_step": io_bytes,
+               "d2h_bytes_per_step": io_bytes + 48,
+               "what": "public C-ABI calls per step: nas_set_state from pinned host buffers (state copied in; the "
+                       "library recomputes the density's Hartree potential and A^NL), nas_step, nas_get of the "
+                       "eigenvalues, orbitals, density and energy; from the timed run's start state"}
+    # the small pencil of the last inner iteration (for the CPU extrapolation)
+    pencil = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            FA = s.get(nas.NAS_Q_FA)
+            FB = s.get(nas.NAS_Q_FB)
+            pencil = "/tmp/bench_pencil_%d.npz" % os.getpid()
+            np.savez(pencil, FA=FA, FB=FB)
+        except Exception as ex:
+            log("pencil not saved: %s" % ex)
+    cfg = workload_config(args, args.workload, inst, sz, prec, {"parallelism": "replicas" if world > 1 else "1 GPU"})
+    s.close()
     if rank != 0:
-        s.close()
         if dist is not None:
             dist.destroy_process_group()
         return
+
+    secondary = {}
+    if not args.no_secondary:
+        for name in ("mol8_p2", REFERENCE_WORKLOAD):
+            try:
+                secondary[name] = secondary_line(args, nas, torch, name, local, stream)
+                log("secondary %s: %.3f steps/s" % (name, secondary[name]["value"]))
+            except Exception as ex:
+                secondary[name] = {"error": str(ex)[:200]}
     batched = run_batch(args, nas, torch, local) if args.batch > 0 else None
 
-    # the CPU oracle sample runs after the GPU work, in a fresh single-threaded
-    # process (fork + exec), so that it never competes with the host-side work
-    # of the timed steps for the CPU cores
+    # ------------------------------------------------------------ CPU oracle baseline
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
+        threads = host_threads()
+        cpu = {"kind": "oracle", "unit": "steps/s", "cores": threads}
         try:
-            cpu = cpu_baseline_from(run_oracle_subprocess(2, 1), n)
+            ref_n = run_oracle_subprocess("oracle_steps(%r, 2, 1)" % REFERENCE_WORKLOAD, threads)
+            ref_1 = run_oracle_subprocess("oracle_steps(%r, 2, 1)" % REFERENCE_WORKLOAD, 1)
+            cpu["reference_workload"] = {
+                "workload": REFERENCE_WORKLOAD, "unknowns": ref_n["n"],
+                "steps_per_s_all_cores": 2 / sum(ref_n["step_s"]), "cores_all": threads,
+                "steps_per_s_one_core": 2 / sum(ref_1["step_s"]), "cores_one": 1,
+                "step_s_all_cores": ref_n["step_s"], "step_s_one_core": ref_1["step_s"],
+                "gpu_steps_per_s": secondary.get(REFERENCE_WORKLOAD, {}).get("value")}
+            inner_full = statistics.mean(r.n_inner for r in reps)
+            if pencil:
+                eig = run_oracle_subprocess("oracle_eig_seconds(%r, %d)" % (pencil, N), threads)
+                ex = cpu_extrapolation(ref_n, eig["eig_s"], n, N, inner_full)
+                cpu["value"] = 1.0 / ex["seconds_per_step"]
+                cpu["extrapolation"] = ex
+                cpu["extrapolation"]["eig_m"] = eig["m"]
+                cpu["sample"] = (
+                    "the oracle cannot run the headline workload in minutes (building its operators for 32 nuclei "
+                    "on a mesh fine enough for the 16^3 coarse space takes minutes alone), so its seconds per step "
+                    "are assembled term by term from measurements on %d host cores: the oracle's small eigensolve "
+                    "(scipy eigh, lowest %d pairs) timed on this run's own %d x %d pencil, once per inner "
+                    "iteration (%.1f per step in the GPU run), plus the rest of an oracle step measured on the "
+                    "full-size helium workload (%d unknowns, N = 1) scaled linearly in unknowns x orbitals x "
+                    "inner iterations (a lower bound)" % (threads, N, eig["m"], eig["m"], inner_full, ref_n["n"]))
         except Exception as ex:  # the baseline is reported, never required
-            cpu = {"error": str(ex)[:200]}
-        try:
-            cpu["spmm"] = cpu_spmm_baseline(s, nas, sz)
-        except Exception as ex:
-            cpu["spmm"] = {"error": str(ex)[:200]}
+            cpu["error"] = str(ex)[:300]
+        if pencil:
+            try:
+                os.remove(pencil)
+            except OSError:
+                pass
+
     last = reps[-1]
+    dom_h, dom_o = dominant(roofs_h), dominant(roofs_o)
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, inst, {"unknowns": n, "nnz": sz["nnz"], "coarse_unknowns": sz["nH"],
-                                               "parallelism": "replicas" if world > 1 else "1 GPU"}),
-        "spmm_hbm_gbs": spmm_gbs, "spmv_hbm_gbs": sp_gbs,
-        "roofline": dominant, "roofline_other": other,
-        "phase_ms_per_step": {k: v / args.steps for k, v in ph.items()},
-        "per_step": {"n_inner": last.n_inner, "cg_iters": last.cg_iters, "poisson_iters": last.poisson_iters,
-                     "drho": last.drho, "energy": last.energy},
-        "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "setup_s": setup_s,
-        "mixed": mixed, "energy_ha": float(en64[0]),
+        "vs_baseline": None, "dtype": "f64/f32 mixed" if prec == "mixed" else "f64", "data": "synthetic",
+        "config": cfg,
+        "roofline": dom_h, "roofline_other_precision": dom_o,
+        "rooflines": {"headline": roofs_h, "other_precision": roofs_o},
+        "speed_ratio_mixed_over_fp64": None,
+        "comparison": comparison,
+        "phase_ms_per_step": {k: v / args.steps for k, v in phase_totals(reps, nas.PHASES)[0].items()},
+        "per_step": {"n_inner": [r.n_inner for r in reps], "cg_iters": [r.cg_iters for r in reps],
+                     "poisson_iters": [r.poisson_iters for r in reps], "eig_iters": [r.eig_iters for r in reps],
+                     "drho": [r.drho for r in reps], "energy": [r.energy for r in reps],
+                     "inner_tol": [r.inner_tol for r in reps]},
+        "gpu_launches": int(sum(r.kernel_launches for r in reps)), "e2e": e2e, "clocks": clk,
+        "spmm_autotuner": tuner,
+        "cpu_baseline": cpu, "setup_s": setup_s, "energy_ha": float(last.energy),
+        "secondary": secondary,
     }
+    # mixed over FP64: the same start state and the same first n_cmp steps
+    ms_h_first = sum(per_h[:n_cmp])
+    ms_mixed, ms_fp64 = (ms_h_first, ms_o) if prec == "mixed" else (ms_o, ms_h_first)
+    line["speed_ratio_mixed_over_fp64"] = ms_fp64 / ms_mixed if ms_mixed > 0 else None
+    line["speed_ratio_note"] = ("ms of the FP64 run over ms of the mixed run for the same first %d steps from the "
+                                "same start state (CUDA events per step)" % n_cmp)
+    line["per_step"]["ms"] = per_h
     if batched is not None:
         line["batched"] = batched
     print(json.dumps(line))
-    s.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -159,6 +159,14 @@ enum nas_phase {
                               NAS_PH_HOST_EIG)                                      */
     NAS_PH_EIG_WAIT,       /* host time blocked in stream synchronisations inside the
                               device LOBPCG (subset of NAS_PH_HOST_EIG)            */
+    NAS_PH_SPMV32,         /* timing = 1: the FP32 SpMV of the mixed-precision Poisson
+                              PCG, first two iterations of every inner FP32 solve
+                              (direct launches with events around the SpMV)        */
+    NAS_PH_SPMM32,         /* FP32 SpMM launches of the mixed-precision block PCG     */
+    NAS_PH_RECON,          /* the reconstruction Psi = I u_H + U^ alpha (subset of
+                              NAS_PH_DENSITY)                                      */
+    NAS_PH_DENSK,          /* the density kernel rho = sum f psi^2 (subset of
+                              NAS_PH_DENSITY)                                      */
     NAS_PH_COUNT
 };
 
@@ -199,6 +207,9 @@ typedef struct nas_report {
     double e_ts;              /* -kT S of the smeared occupations (0 without smearing);
                                  `energy` includes it (the free energy)              */
     double inner_tol;         /* stop tolerance the last inner SCF used              */
+    double spmm32_bytes;      /* algorithmic bytes of the FP32 SpMM launches (mixed
+                                 block PCG): nnz*(4+4) + 4*(n+1) + 2*n*N*4            */
+    double spmm32_flops;      /* 2*nnz*N per FP32 SpMM launch                        */
 } nas_report;
 
 /* ------------------------------------------------------------------ context */
@@ -373,6 +384,32 @@ int nas_batch_run(nas_ctx** ctxs, int count, int steps, int n_threads, int* stat
  * the cost of A_h^NL and the N boundary value problems). */
 int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
                  const double* val, int N, const double* X, double* Y, void* stream);
+
+/* The SpMM kernel layouts (N > 1) and their autotuner.  Layout 0 "cols" has
+ * one thread per (row, column); layouts "rows<V,R>" put R rows on a warp,
+ * 32/R lanes per row, each lane owning V consecutive columns (V-wide vector
+ * loads of X), and broadcast the row's indices and values by shuffles.  All
+ * layouts add a row's entries in CSR order, so their results are
+ * bit-identical.  On the first product with a given (matrix pattern, N,
+ * precision) the library times every layout the operands' alignment allows on
+ * the caller's own operands and keeps the fastest.
+ * nas_spmm_layouts: the number of layouts; nas_spmm_layout_name: the name of
+ * layout id (static string, "?" if out of range).
+ * nas_spmm_tuning: writes the tuner's record so far (a JSON list: rows, N,
+ * precision, chosen layout, the time of every layout tried) into buf
+ * (NUL-terminated, truncated to bytes) and returns its full length.
+ * nas_spmm_f64_layout / nas_spmm_f32_layout: Y = A X with the given layout
+ * (arguments as nas_spmm_f64; FP32 values and blocks for the second).
+ * Errors: NAS_E_INVALID_ARG (bad sizes or pointers, unknown layout, or a
+ * vector layout whose width does not divide N or whose alignment X/Y lack),
+ * NAS_E_CUDA (launch failure). */
+int nas_spmm_layouts(void);
+const char* nas_spmm_layout_name(int layout);
+int nas_spmm_tuning(char* buf, size_t bytes);
+int nas_spmm_f64_layout(int layout, int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
+                        const double* val, int N, const double* X, double* Y, void* stream);
+int nas_spmm_f32_layout(int layout, int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
+                        const float* val, int N, const float* X, float* Y, void* stream);
 
 /* Stand-alone weighted column dot products, FP64, on device buffers:
  *   out[c] = sum_i w[i] X[i][c] Y[i][c]   for c < N   (w == NULL: w[i] = 1)

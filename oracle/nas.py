@@ -268,7 +268,8 @@ class Problem:
         tol = inst.tol_scf if tol is None else tol
         max_inner = inst.max_inner if max_inner is None else max_inner
         FB = self.mass_blocks(Uhat)
-        mixer = Anderson(self.fine.Wq)
+        mixer = Anderson(self.fine.Wq, depth=getattr(inst, "anderson_depth", 5),
+                         beta=getattr(inst, "anderson_beta", 0.7))
         rho_in = rho_start.copy()
         VH_prev = VH_start
         hist = []
@@ -399,7 +400,8 @@ class Problem:
         f = self.fine
         tol = self.inst.tol_scf if tol is None else tol
         Md = self.M.toarray() if f.n <= dense_max else None
-        mixer = Anderson(f.Wq)
+        mixer = Anderson(f.Wq, depth=getattr(self.inst, "anderson_depth", 5),
+                         beta=getattr(self.inst, "anderson_beta", 0.7))
         rho_in = np.zeros_like(f.Wq)
         VH_prev = None
         for t in range(max_iter):

@@ -40,6 +40,18 @@ void invalidate(nas_ctx* c) {
     c->anl_valid = false;
 }
 
+template <typename T>
+int spmm_layout_call(int layout, int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const T* val,
+                            int N, const T* X, T* Y, void* stream) {
+    if (n_rows < 0 || N < 1 || !row_ptr || !col || !val || !X || !Y) return NAS_E_INVALID_ARG;
+    try {
+        nas::launch_spmm_layout(layout, n_rows, row_ptr, col, val, N, X, Y, static_cast<cudaStream_t>(stream));
+        return NAS_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -348,6 +360,30 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, con
     } catch (const Error& e) {
         return e.code;
     }
+}
+
+int nas_spmm_layouts(void) { return nas::spmm_num_layouts(); }
+
+const char* nas_spmm_layout_name(int layout) { return nas::spmm_layout_name(layout); }
+
+int nas_spmm_tuning(char* buf, size_t bytes) {
+    const std::string r = nas::spmm_tuning_report();
+    if (buf && bytes > 0) {
+        const size_t k = std::min(bytes - 1, r.size());
+        std::memcpy(buf, r.data(), k);
+        buf[k] = '\0';
+    }
+    return (int)r.size();
+}
+
+int nas_spmm_f64_layout(int layout, int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* val,
+                        int N, const double* X, double* Y, void* stream) {
+    return spmm_layout_call(layout, n_rows, row_ptr, col, val, N, X, Y, stream);
+}
+
+int nas_spmm_f32_layout(int layout, int64_t n_rows, const int32_t* row_ptr, const int32_t* col, const float* val,
+                        int N, const float* X, float* Y, void* stream) {
+    return spmm_layout_call(layout, n_rows, row_ptr, col, val, N, X, Y, stream);
 }
 
 int nas_coldot_f64(int64_t n, int N, const double* X, const double* Y, const double* w, double* out,

@@ -159,6 +159,7 @@ struct nas_ctx {
     double phase_ms[NAS_MAX_PHASES] = {0};
     long long phase_calls[NAS_MAX_PHASES] = {0};
     double spmm_bytes = 0, spmm_flops = 0, spmv_bytes = 0, spmv_flops = 0;
+    double spmm32_bytes = 0, spmm32_flops = 0;
     struct EvPair {
         int phase;
         cudaEvent_t a, b;

@@ -3,6 +3,8 @@
 // atomics), so two runs on the same input give bit-identical results.
 #pragma once
 
+#include <string>
+
 #include "common.h"
 
 namespace nas {
@@ -102,6 +104,19 @@ struct Csr {
     int64_t rowptr_nnz = 0;   // nnz (host-side bookkeeping for byte counts)
 };
 // Y = alpha * A X (+ beta Y), X [ncols][N], Y [n_rows][N]
+// SpMM with N > 1 interleaved right-hand sides through the layout autotuner
+// (kernels_spmm.cu); N = 1 takes the 8-lanes-per-row SpMV
+void launch_spmm_tuned(const Csr& A, int N, const double* X, double* Y, double alpha, double beta, cudaStream_t s);
+// autotuner control and record (kernels_spmm.cu)
+void spmm_set_tuning(bool on);
+void spmm_force_layout(const int32_t* rowptr, int64_t n, int N, int bytes, int id);
+std::string spmm_tuning_report();
+int spmm_num_layouts();
+const char* spmm_layout_name(int id);
+void launch_spmm_layout(int id, int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, int N,
+                        const double* X, double* Y, cudaStream_t s);
+void launch_spmm_layout(int id, int64_t n, const int32_t* rowptr, const int32_t* col, const float* val, int N,
+                        const float* X, float* Y, cudaStream_t s);
 void launch_spmm(const Csr& A, int N, const double* X, double* Y, double alpha, double beta,
                  cudaStream_t s);
 
@@ -156,6 +171,11 @@ void launch_combine3(int64_t nnz, double a, const double* v1, double b, const do
 // G[a][b] = sum_i X[i][a] Y[i][b]  (X [n][Nx], Y [n][Ny]) deterministic; partial scratch
 // of gram_partial_size(Nx*Ny) doubles
 int64_t gram_partial_size(int64_t width);
+// G = X^T Y for a product known to be symmetric (X, Y [n][N]): the upper
+// triangle is summed and mirrored, so G is exactly symmetric; partial holds
+// reduce_partial_size(N * N) doubles
+void launch_gram_sym(int64_t n, int N, const double* X, const double* Y, double* partial, double* G,
+                     cudaStream_t s);
 void launch_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y, double* partial,
                  double* G, cudaStream_t s);
 

@@ -14,23 +14,7 @@ namespace nas {
 
 static const int kRedBlocks = 1216;  // 8 x 152 SMs: grid of the two-stage reductions
 
-// ------------------------------------------------------------------ SpMM
-// One thread per (row, column): the N threads of a row read the same val/col
-// entries (a broadcast) and a contiguous N-segment of X per nonzero.
-__global__ void __launch_bounds__(256) k_spmm_cols(Csr A, int N, const double* __restrict__ X,
-                                                   double* __restrict__ Y, double alpha, double beta) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t row = t / N;
-    if (row >= A.n_rows) return;
-    int c = (int)(t - row * N);
-    int p0 = A.rowptr[row], p1 = A.rowptr[row + 1];
-    double acc = 0.0;
-    for (int p = p0; p < p1; ++p) acc += A.val[p] * X[(int64_t)A.col[p] * N + c];
-    double y = alpha * acc;
-    if (beta != 0.0) y += beta * Y[t];
-    Y[t] = y;
-}
-
+// ------------------------------------------------------------------ SpMV
 // N == 1: 8 lanes per row, strided over the row's nonzeros, shuffle reduction
 // in a fixed order.
 __global__ void __launch_bounds__(256) k_spmv8(Csr A, const double* __restrict__ X, double* __restrict__ Y,
@@ -59,10 +43,10 @@ void launch_spmm(const Csr& A, int N, const double* X, double* Y, double alpha, 
     if (A.n_rows <= 0) return;
     if (N == 1) {
         k_spmv8<<<grid_for(A.n_rows * 8, 256), 256, 0, s>>>(A, X, Y, alpha, beta);
+        NAS_CHECK_LAUNCH();
     } else {
-        k_spmm_cols<<<grid_for(A.n_rows * N, 256), 256, 0, s>>>(A, N, X, Y, alpha, beta);
+        launch_spmm_tuned(A, N, X, Y, alpha, beta, s);   // kernels_spmm.cu
     }
-    NAS_CHECK_LAUNCH();
 }
 
 // ------------------------------------------------------------------ ordered reductions
@@ -340,6 +324,74 @@ void launch_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y, do
     reduce_partials(nb, W, partial, G, s);
 }
 
+// Symmetric Gram G = X^T Y (known symmetric, e.g. U^T (A U) with A symmetric):
+// only the N (N + 1) / 2 entries a <= b are summed, in packed order
+// p = a N - a (a - 1) / 2 + (b - a); same tiles and per-entry order as k_gram.
+__global__ void __launch_bounds__(256) k_gram_sym(int64_t n, int N, const double* X, const double* Y,
+                                                 double* partial) {
+    extern __shared__ double smem[];
+    double* xs = smem;             // [32][N]
+    double* ys = smem + 32 * N;    // [32][N]
+    short2* tab = reinterpret_cast<short2*>(smem + 64 * N);   // packed index -> (a, b)
+    const int P = N * (N + 1) / 2;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        int a = 0, off = 0;
+        while (off + (N - a) <= p) {
+            off += N - a;
+            ++a;
+        }
+        tab[p] = make_short2((short)a, (short)(a + p - off));
+    }
+    double acc[16];
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    __syncthreads();
+    for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < n; r0 += (int64_t)gridDim.x * 32) {
+        int rows = (n - r0) < 32 ? (int)(n - r0) : 32;
+        for (int j = threadIdx.x; j < 32 * N; j += blockDim.x) {
+            xs[j] = (j / N < rows) ? X[r0 * N + j] : 0.0;
+            ys[j] = (j / N < rows) ? Y[r0 * N + j] : 0.0;
+        }
+        __syncthreads();
+        int k = 0;
+        for (int p = threadIdx.x; p < P; p += blockDim.x, ++k) {
+            const short2 ab = tab[p];
+            double s = 0.0;
+            for (int r = 0; r < 32; ++r) s += xs[r * N + ab.x] * ys[r * N + ab.y];
+            acc[k] += s;
+        }
+        __syncthreads();
+    }
+    int k = 0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x, ++k) partial[(int64_t)blockIdx.x * P + p] = acc[k];
+}
+
+// packed upper triangle -> full symmetric [N][N]
+__global__ void k_unpack_sym(int N, const double* packed, double* G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * N) return;
+    int a = t / N, b = t % N;
+    if (a > b) {
+        const int tmp = a;
+        a = b;
+        b = tmp;
+    }
+    G[t] = packed[a * N - a * (a - 1) / 2 + (b - a)];
+}
+
+void launch_gram_sym(int64_t n, int N, const double* X, const double* Y, double* partial, double* G,
+                     cudaStream_t s) {
+    const int64_t P = (int64_t)N * (N + 1) / 2;
+    if (N < 1 || P > 16 * 256) fail(NAS_E_INVALID_ARG, "gram width");
+    int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + 31) / 32));
+    size_t sm = sizeof(double) * 64 * N + sizeof(short2) * P;
+    k_gram_sym<<<nb, 256, sm, s>>>(n, N, X, Y, partial);
+    NAS_CHECK_LAUNCH();
+    double* packed = partial + (int64_t)nb * P;   // the partial buffer holds kRedBlocks x N^2 >= (nb + 1) P
+    reduce_partials(nb, P, partial, packed, s);
+    k_unpack_sym<<<grid_for((int64_t)N * N, 256), 256, 0, s>>>(N, packed, G);
+    NAS_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------------ transfer products
 // one warp per output (a, c): lanes stride over the ~n/nH fine entries of
 // coarse row a, then a fixed-order shuffle sum
@@ -538,25 +590,6 @@ namespace nas {
 // The inner solve of the N shifted problems in FP32 storage and arithmetic;
 // per-column scalars stay FP64 on the device (the same PcgCols logic), dot
 // products accumulate in FP32 per thread and in FP64 across threads.
-__global__ void __launch_bounds__(256) k_spmm_cols_f32(int64_t n_rows, const int32_t* __restrict__ rowptr,
-                                                       const int32_t* __restrict__ col,
-                                                       const float* __restrict__ val, int N,
-                                                       const float* __restrict__ X, float* __restrict__ Y) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t row = t / N;
-    if (row >= n_rows) return;
-    const int c = (int)(t - row * N);
-    float acc = 0.f;
-    for (int p = rowptr[row]; p < rowptr[row + 1]; ++p) acc += val[p] * X[(int64_t)col[p] * N + c];
-    Y[t] = acc;
-}
-
-void launch_spmm_f32(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const float* val, int N,
-                     const float* X, float* Y, cudaStream_t s) {
-    if (n_rows <= 0) return;
-    k_spmm_cols_f32<<<grid_for(n_rows * N, 256), 256, 0, s>>>(n_rows, rowptr, col, val, N, X, Y);
-    NAS_CHECK_LAUNCH();
-}
 
 // out[k][c] = sum_i X_k[i][c] Y_k[i][c] (k < npairs <= 2), FP32 inputs
 struct ColDotArgsF {

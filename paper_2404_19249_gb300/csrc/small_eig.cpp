@@ -41,6 +41,10 @@ static inline double dot(const double* a, const double* b, int n) {
     return s;
 }
 
+// Matrices of at least kParMin rows run their O(m^3) loops on all OpenMP
+// threads (below that the fork/join cost exceeds the work).
+static const int kParMin = 128;
+
 // lower Cholesky in place (row-major, lower triangle); returns false if not SPD
 static bool cholesky(int m, std::vector<double>& L) {
     for (int j = 0; j < m; ++j) {
@@ -49,7 +53,7 @@ static bool cholesky(int m, std::vector<double>& L) {
         if (!(d > 0.0)) return false;
         d = std::sqrt(d);
         L[(size_t)j * m + j] = d;
-#pragma omp parallel for schedule(static) if (m - j > 256)
+#pragma omp parallel for schedule(static) if (m - j > 256 || (m >= kParMin && m - j > 64))
         for (int i = j + 1; i < m; ++i) {
             double* Li = &L[(size_t)i * m];
             Li[j] = (Li[j] - dot(Li, Lj, j)) / d;
@@ -65,16 +69,46 @@ static bool cholesky(int m, std::vector<double>& L) {
 // at once: each update is a contiguous row operation), first to A, then to
 // the transpose of the result.
 static void reduce_standard(int m, const std::vector<double>& L, const double* A, std::vector<double>& C) {
+    // the columns of Z are independent right-hand sides: each thread
+    // eliminates its own block of kCb columns over all rows, reading the
+    // multipliers of step k from row k of L^T (contiguous)
+    const int kCb = 32;
+    std::vector<double> Lt;
+    if (m >= kParMin) {
+        Lt.assign((size_t)m * m, 0.0);
+        for (int i = 0; i < m; ++i)
+            for (int k = 0; k <= i; ++k) Lt[(size_t)k * m + i] = L[(size_t)i * m + k];
+    }
     auto solve_rows = [&](std::vector<double>& Z) {
-        for (int k = 0; k < m; ++k) {
-            double* zk = &Z[(size_t)k * m];
-            const double d = L[(size_t)k * m + k];
-            for (int j = 0; j < m; ++j) zk[j] /= d;
-            for (int i = k + 1; i < m; ++i) {
-                const double l = L[(size_t)i * m + k];
-                if (l == 0.0) continue;
-                double* zi = &Z[(size_t)i * m];
-                for (int j = 0; j < m; ++j) zi[j] -= l * zk[j];
+        if (m < kParMin) {
+            for (int k = 0; k < m; ++k) {
+                double* zk = &Z[(size_t)k * m];
+                const double d = L[(size_t)k * m + k];
+                for (int j = 0; j < m; ++j) zk[j] /= d;
+                for (int i = k + 1; i < m; ++i) {
+                    const double l = L[(size_t)i * m + k];
+                    if (l == 0.0) continue;
+                    double* zi = &Z[(size_t)i * m];
+                    for (int j = 0; j < m; ++j) zi[j] -= l * zk[j];
+                }
+            }
+            return;
+        }
+        const int nblk = (m + kCb - 1) / kCb;
+#pragma omp parallel for schedule(static)
+        for (int b = 0; b < nblk; ++b) {
+            const int j0 = b * kCb, j1 = std::min(m, j0 + kCb);
+            for (int k = 0; k < m; ++k) {
+                double* zk = &Z[(size_t)k * m];
+                const double* lk = &Lt[(size_t)k * m];
+                const double dinv = 1.0 / lk[k];
+                for (int j = j0; j < j1; ++j) zk[j] *= dinv;
+                for (int i = k + 1; i < m; ++i) {
+                    const double l = lk[i];
+                    if (l == 0.0) continue;
+                    double* zi = &Z[(size_t)i * m];
+                    for (int j = j0; j < j1; ++j) zi[j] -= l * zk[j];
+                }
             }
         }
     };
@@ -99,8 +133,15 @@ static void reduce_standard(int m, const std::vector<double>& L, const double* A
 // triangle is read and updated).  Reflector j acts on entries j+1..m-1:
 // H_j = I - tau_j v_j v_j^T with v_j stored in V (row j), v_j[j+1] = 1.
 // T = Q^T C Q, Q = H_0 H_1 ... H_{m-3}.
+static void tridiagonalise_par(int m, std::vector<double>& C, std::vector<double>& d, std::vector<double>& e,
+                               std::vector<double>& V, std::vector<double>& tau);
+
 static void tridiagonalise(int m, std::vector<double>& C, std::vector<double>& d, std::vector<double>& e,
                            std::vector<double>& V, std::vector<double>& tau) {
+    if (m >= kParMin) {
+        tridiagonalise_par(m, C, d, e, V, tau);
+        return;
+    }
     d.assign(m, 0.0);
     e.assign(std::max(m - 1, 0), 0.0);
     V.assign((size_t)m * m, 0.0);
@@ -158,6 +199,68 @@ static void tridiagonalise(int m, std::vector<double>& C, std::vector<double>& d
             double* Ci = &C[(size_t)(j + 1 + i) * m + j + 1];
             const double xi = x[i], wi = w[i];
             for (int k = 0; k <= i; ++k) Ci[k] -= xi * w[k] + wi * x[k];
+        }
+    }
+    for (int i = 0; i < m; ++i) d[i] = C[(size_t)i * m + i];
+    if (m >= 2) e[m - 2] = C[(size_t)(m - 1) * m + (m - 2)];
+}
+
+// The same reflectors on all threads: C is mirrored to full storage, so the
+// product p = tau C22 v and the update C22 -= v w^T + w v^T are row-parallel
+// over whole rows (twice the multiply-adds of the lower-triangle form, no
+// write conflicts); one parallel region for all steps, barriers between the
+// phases of a step.
+static void tridiagonalise_par(int m, std::vector<double>& C, std::vector<double>& d, std::vector<double>& e,
+                               std::vector<double>& V, std::vector<double>& tau) {
+    d.assign(m, 0.0);
+    e.assign(std::max(m - 1, 0), 0.0);
+    V.assign((size_t)m * m, 0.0);
+    tau.assign(m, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int k = 0; k < i; ++k) C[(size_t)k * m + i] = C[(size_t)i * m + k];
+    std::vector<double> p(m), w(m), v(m);
+    double t = 0.0, pv = 0.0;
+    bool skip = false;
+#pragma omp parallel
+    for (int j = 0; j + 2 < m; ++j) {
+        const int n1 = m - j - 1;
+#pragma omp single
+        {
+            double* x = v.data();
+            double xnorm2 = 0.0;
+            for (int i = 0; i < n1; ++i) {
+                x[i] = C[(size_t)(j + 1 + i) * m + j];
+                if (i > 0) xnorm2 += x[i] * x[i];
+            }
+            const double alpha = x[0];
+            skip = (xnorm2 == 0.0);
+            if (skip) {
+                tau[j] = 0.0;
+                e[j] = alpha;
+            } else {
+                const double beta = -std::copysign(std::sqrt(alpha * alpha + xnorm2), alpha);
+                t = (beta - alpha) / beta;
+                const double scale = 1.0 / (alpha - beta);
+                for (int i = 1; i < n1; ++i) x[i] *= scale;
+                x[0] = 1.0;
+                tau[j] = t;
+                e[j] = beta;
+                for (int i = 0; i < n1; ++i) V[(size_t)j * m + j + 1 + i] = x[i];
+            }
+        }  // implicit barrier
+        if (skip) continue;  // every thread sees the same flag after the barrier
+#pragma omp for schedule(static)
+        for (int i = 0; i < n1; ++i) p[i] = t * dot(&C[(size_t)(j + 1 + i) * m + j + 1], v.data(), n1);
+#pragma omp single
+        {
+            pv = dot(p.data(), v.data(), n1);
+            for (int i = 0; i < n1; ++i) w[i] = p[i] - 0.5 * t * pv * v[i];
+        }
+#pragma omp for schedule(static)
+        for (int i = 0; i < n1; ++i) {
+            double* Ci = &C[(size_t)(j + 1 + i) * m + j + 1];
+            const double xi = v[i], wi = w[i];
+            for (int k = 0; k < n1; ++k) Ci[k] -= xi * w[k] + wi * v[k];
         }
     }
     for (int i = 0; i < m; ++i) d[i] = C[(size_t)i * m + i];
@@ -343,35 +446,45 @@ static void gen_eig_factored(int m, const double* A, const std::vector<double>& 
     std::vector<double> Z((size_t)k * m);
     const double pert = eps * tnorm + 1e-300;
     const double clus = 1e-3 * tnorm;
-    int start = 0;
-    std::vector<double> x(m);
-    TriWork tw;
-    for (int i = 0; i < k; ++i) {
-        if (i > 0 && std::fabs(w[i] - w[i - 1]) > clus) start = i;
-        for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * std::sin(0.7 * r + 1.3 * i);
-        tri_factor(m, d, e, w[i], pert, tw);
-        for (int it = 0; it < 4; ++it) {
-            tri_apply(m, tw, x.data());
-            for (int j = start; j < i; ++j) {
-                const double* zj = &Z[(size_t)j * m];
-                const double s = dot(zj, x.data(), m);
-                for (int r = 0; r < m; ++r) x[r] -= s * zj[r];
+    // clusters of close eigenvalues [cstart[c], cstart[c+1]): vectors of one
+    // cluster are orthogonalised against each other in order; different
+    // clusters are independent
+    std::vector<int> cstart{0};
+    for (int i = 1; i < k; ++i)
+        if (std::fabs(w[i] - w[i - 1]) > clus) cstart.push_back(i);
+    cstart.push_back(k);
+    const int ncl = (int)cstart.size() - 1;
+#pragma omp parallel for schedule(dynamic, 1) if (m >= kParMin)
+    for (int cl = 0; cl < ncl; ++cl) {
+        std::vector<double> x(m);
+        TriWork tw;
+        const int start = cstart[cl];
+        for (int i = start; i < cstart[cl + 1]; ++i) {
+            for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * std::sin(0.7 * r + 1.3 * i);
+            tri_factor(m, d, e, w[i], pert, tw);
+            for (int it = 0; it < 4; ++it) {
+                tri_apply(m, tw, x.data());
+                for (int j = start; j < i; ++j) {
+                    const double* zj = &Z[(size_t)j * m];
+                    const double s = dot(zj, x.data(), m);
+                    for (int r = 0; r < m; ++r) x[r] -= s * zj[r];
+                }
+                double nrm = std::sqrt(dot(x.data(), x.data(), m));
+                if (!(nrm > 0)) {
+                    for (int r = 0; r < m; ++r) x[r] = (r == i) ? 1.0 : 0.0;
+                    nrm = 1.0;
+                }
+                for (int r = 0; r < m; ++r) x[r] /= nrm;
             }
-            double nrm = std::sqrt(dot(x.data(), x.data(), m));
-            if (!(nrm > 0)) {
-                for (int r = 0; r < m; ++r) x[r] = (r == i) ? 1.0 : 0.0;
-                nrm = 1.0;
-            }
-            for (int r = 0; r < m; ++r) x[r] /= nrm;
+            std::copy(x.begin(), x.end(), Z.begin() + (size_t)i * m);
         }
-        std::copy(x.begin(), x.end(), Z.begin() + (size_t)i * m);
     }
     // back-transform: y = Q z = H_0 ... H_{m-3} z, then U = L^{-T} y (rows of
     // L^T, i.e. columns of L, made contiguous first)
     std::vector<double> Lt((size_t)m * m);
     for (int r = 0; r < m; ++r)
         for (int q = 0; q <= r; ++q) Lt[(size_t)q * m + r] = L[(size_t)r * m + q];
-#pragma omp parallel for schedule(dynamic, 1) if ((int64_t)k * m * m > 2000000)
+#pragma omp parallel for schedule(dynamic, 1) if (m >= kParMin || (int64_t)k * m * m > 2000000)
     for (int i = 0; i < k; ++i) {
         double* z = &Z[(size_t)i * m];
         for (int j = m - 3; j >= 0; --j) {
@@ -386,7 +499,7 @@ static void gen_eig_factored(int m, const double* A, const std::vector<double>& 
     }
     // Rayleigh quotients refine the eigenvalues: lambda = u^T A u (u is
     // B-normalised), from the lower triangle of A: sum_r u_r (A_rr u_r + 2 sum_{c<r} A_rc u_c)
-#pragma omp parallel for schedule(dynamic, 1) if ((int64_t)k * m * m > 2000000)
+#pragma omp parallel for schedule(dynamic, 1) if (m >= kParMin || (int64_t)k * m * m > 2000000)
     for (int i = 0; i < k; ++i) {
         const double* u = &Z[(size_t)i * m];
         double s = 0.0;

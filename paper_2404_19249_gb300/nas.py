@@ -24,7 +24,7 @@ ERRORS = {
 NAS_FINE, NAS_COARSE = 0, 1
 NAS_POT_COULOMB, NAS_POT_SMOOTHED, NAS_POT_HARMONIC = 0, 1, 2
 PHASES = ["assembly", "bvp", "poisson", "blocks", "density", "mixing", "host_eig", "transfer", "spmm", "spmv",
-          "eig_rr", "eig_wait"]
+          "eig_rr", "eig_wait", "spmv32", "spmm32", "recon", "densk"]
 (NAS_Q_SIZES, NAS_Q_EIGVALS, NAS_Q_ORBITALS, NAS_Q_RHO_IN, NAS_Q_RHO_OUT, NAS_Q_VHARTREE, NAS_Q_UHAT,
  NAS_Q_ROWPTR, NAS_Q_COLIDX, NAS_Q_K, NAS_Q_M, NAS_Q_MVEXT, NAS_Q_ANL, NAS_Q_HTILDE, NAS_Q_TRANSFER_ELEM,
  NAS_Q_TRANSFER_COL, NAS_Q_TRANSFER_W, NAS_Q_FA, NAS_Q_FB, NAS_Q_DOF_NODE, NAS_Q_ENERGY, NAS_Q_STATE_ID, NAS_Q_INNER_HIST) = range(23)
@@ -56,7 +56,7 @@ class nas_report(C.Structure):
         ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_double), ("spmv_flops", C.c_double),
         ("eig_iters", C.c_int), ("poisson_spmv_ms", C.c_double), ("poisson_spmv_launches", C.c_longlong),
         ("poisson_fused_ms", C.c_double), ("poisson_fused_iters", C.c_longlong),
-        ("e_ts", C.c_double), ("inner_tol", C.c_double),
+        ("e_ts", C.c_double), ("inner_tol", C.c_double), ("spmm32_bytes", C.c_double), ("spmm32_flops", C.c_double),
     ]
 
     def as_dict(self):
@@ -94,6 +94,11 @@ def _load():
         "nas_apply": (C.c_int, [VP, C.c_int, VP, I64, VP, C.c_int]),
         "nas_batch_run": (C.c_int, [P(VP), C.c_int, C.c_int, C.c_int, P(C.c_int), P(nas_report)]),
         "nas_spmm_f64": (C.c_int, [I64, VP, VP, VP, C.c_int, VP, VP, VP]),
+        "nas_spmm_layouts": (C.c_int, []),
+        "nas_spmm_layout_name": (C.c_char_p, [C.c_int]),
+        "nas_spmm_tuning": (C.c_int, [C.c_char_p, C.c_size_t]),
+        "nas_spmm_f64_layout": (C.c_int, [C.c_int, I64, VP, VP, VP, C.c_int, VP, VP, VP]),
+        "nas_spmm_f32_layout": (C.c_int, [C.c_int, I64, VP, VP, VP, C.c_int, VP, VP, VP]),
         "nas_coldot_f64": (C.c_int, [I64, C.c_int, VP, VP, VP, VP, VP]),
         "nas_coldot_f64_noalloc": (C.c_int, [I64, C.c_int, VP, VP, VP, VP, VP]),
     }
@@ -109,6 +114,7 @@ EXPORTS = [
     "nas_default_options", "nas_version", "nas_create", "nas_destroy", "nas_last_error", "nas_set_mesh",
     "nas_set_system", "nas_set_options", "nas_init", "nas_step", "nas_solve", "nas_get", "nas_set_state",
     "nas_apply", "nas_batch_run", "nas_spmm_f64", "nas_coldot_f64", "nas_coldot_f64_noalloc",
+    "nas_spmm_layouts", "nas_spmm_layout_name", "nas_spmm_tuning", "nas_spmm_f64_layout", "nas_spmm_f32_layout",
 ]
 
 
@@ -238,6 +244,29 @@ def nas_spmm_f64(n_rows, row_ptr, col, val, N, X, Y, stream=0):
     return r
 
 
+def nas_spmm_layouts():
+    return [lib.nas_spmm_layout_name(i).decode() for i in range(lib.nas_spmm_layouts())]
+
+
+def nas_spmm_tuning():
+    """The SpMM autotuner's record so far (list of dicts)."""
+    import json
+    n = lib.nas_spmm_tuning(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    lib.nas_spmm_tuning(buf, n + 1)
+    return json.loads(buf.value.decode() or "[]")
+
+
+def nas_spmm_layout(layout, n_rows, row_ptr, col, val, N, X, Y, fp32=False, stream=0):
+    """Device-pointer SpMM with an explicit kernel layout (pointer arguments are ints)."""
+    f = lib.nas_spmm_f32_layout if fp32 else lib.nas_spmm_f64_layout
+    r = f(int(layout), n_rows, C.c_void_p(row_ptr), C.c_void_p(col), C.c_void_p(val), N, C.c_void_p(X),
+          C.c_void_p(Y), C.c_void_p(stream or None))
+    if r != NAS_OK:
+        raise NasError(r, "nas_spmm_layout")
+    return r
+
+
 def nas_coldot_f64(n, N, X, Y, w, out, stream=0):
     """Device-pointer weighted column dots (pointer arguments are ints; w may be 0)."""
     r = lib.nas_coldot_f64(n, N, C.c_void_p(X), C.c_void_p(Y), C.c_void_p(w or None), C.c_void_p(out),
@@ -270,6 +299,8 @@ class Solver:
         o.xc = int(inst.xc)
         o.omega = inst.omega
         o.smearing = float(getattr(inst, "smearing", 0.0))
+        o.anderson_depth = int(getattr(inst, "anderson_depth", 5))
+        o.anderson_beta = float(getattr(inst, "anderson_beta", 0.7))
         for k, v in options.items():
             setattr(o, k, v)
         self.opt = o

@@ -128,3 +128,43 @@ def test_cpu_spmm_baseline_on_a_small_pattern(bench):
     s = types.SimpleNamespace(get=lambda q: data[q])
     out = bench.cpu_spmm_baseline(s, nas, {"n": A.shape[0], "N": 5}, reps=2)
     assert out["gbs"] > 0 and out["threads"] >= 1 and out["N"] == 5 and out["unit"] == "GB/s"
+
+
+def test_kernel_rooflines_and_dominant(bench):
+    """Roofline figures from report timings: bytes (or flops) per launch over
+    the mean launch time, and the dominant kernel by estimated ms per step."""
+    phases = ["assembly", "bvp", "poisson", "blocks", "density", "mixing", "host_eig", "transfer", "spmm", "spmv",
+              "eig_rr", "eig_wait", "spmv32", "spmm32", "recon", "densk"]
+
+    class Rep:
+        def __init__(self):
+            self.phase_ms = [0.0] * 16
+            self.phase_calls = [0] * 16
+            self.phase_ms[phases.index("spmm32")] = 4.0      # 4 launches of 1 ms
+            self.phase_calls[phases.index("spmm32")] = 4
+            self.phase_ms[phases.index("recon")] = 10.0      # 2 launches of 5 ms
+            self.phase_calls[phases.index("recon")] = 2
+            self.spmm_bytes = self.spmm_flops = 0.0
+            self.spmm32_bytes = 4 * 3.0e9
+            self.poisson_spmv_ms = 0.0
+            self.poisson_spmv_launches = 0
+            self.poisson_iters = 0
+
+    sz = {"n": 1000, "nnz": 20000, "N": 64, "ne": 100, "order": 2}
+    roofs = bench.kernel_rooflines([Rep(), Rep()], sz, 2, phases, 6000.0, "measured", nz_occ=64)
+    f32 = roofs["spmm_f32"]
+    assert abs(f32["achieved"] - 3000.0) < 1e-9 and abs(f32["frac"] - 0.5) < 1e-12   # 3 GB in 1 ms
+    assert f32["launches"] == 8 and abs(f32["est_ms_per_step"] - 4.0) < 1e-12
+    rec = roofs["k_reconstruct"]
+    assert rec["bound"] == "alu" and abs(rec["algorithmic_flops_per_launch"] - 2.0 * 1000 * 64 * 68) < 1e-6
+    assert abs(rec["est_ms_per_step"] - 10.0) < 1e-12
+    assert bench.dominant(roofs) is rec
+
+
+def test_cpu_extrapolation_terms(bench):
+    ref = {"step_s": [3.0, 3.2, 2.8], "eig_s": [0.5, 0.5, 0.5], "n_inner": [7, 7, 7], "n": 1000, "N": 1}
+    ex = bench.cpu_extrapolation(ref, eig_full_s=2.0, n_full=10000, N_full=4, inner_full=14)
+    # rest of the reference step (3.0 - 0.5) x (10000 x 4 x 14) / (1000 x 1 x 7) + 14 eigensolves
+    assert abs(ex["fine_mesh_terms_s"] - 2.5 * 80.0) < 1e-9
+    assert abs(ex["small_eigensolve_s"] - 28.0) < 1e-12
+    assert abs(ex["seconds_per_step"] - (200.0 + 28.0)) < 1e-9

@@ -248,8 +248,13 @@ def test_spmm_standalone(nasmod):
 
 
 def test_benchmark_molecule_first_step(nasmod):
-    """One augmented step of the 8-nucleus benchmark molecule on a reduced mesh."""
-    inst = _tight(make_instance("mol8_p2", cells=6, coarse_cells=4))
+    """One augmented step of the 8-nucleus benchmark molecule on a reduced mesh,
+    with the paper's mu = 8 M sum Z^2.  (The workload's own mu = max Z^2 makes
+    the shifted operator ~250x worse conditioned on this 6^3 mesh; one step
+    from the coarse-space start, far from self-consistency, then depends to
+    first order on the FP64 CG solves, whose attainable accuracy is ~eps
+    cond(H~): GPU and the oracle's exact solves differ by 1.8e-9.)"""
+    inst = _tight(make_instance("mol8_p2", cells=6, coarse_cells=4, mu=None))
     P = Problem(inst)
     s = nasmod.Solver(inst)
     s.init()
@@ -325,3 +330,32 @@ def test_mixed_precision_poisson_matches_fp64(nasmod):
     for _ in range(2):
         st = P.step(st)
     assert _relmax(res[1][0], st.lam) < TOL_EIG
+
+
+def test_smeared_occupations_lockstep(nasmod):
+    """Fermi-Dirac occupations (option smearing): a Be-like atom whose 2s and
+    2p levels share two electrons; initial SCF and three steps against the
+    oracle, eigenvalues, occupations and free energies at 1e-10."""
+    inst = _tight(make_instance("he_p1", cells=6, coarse_cells=3, mu=6.0))
+    inst.Z = np.array([4.0])
+    inst.occ = np.array([2.0, 2.0, 0.0, 0.0])
+    inst.smearing = 0.05
+    P = Problem(inst)
+    st = P.initial_state()
+    s = nasmod.Solver(inst)
+    s.init()
+    try:
+        assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG
+        for step in range(3):
+            r, rep = s.step()
+            assert r == 0
+            st = P.step(st)
+            assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG
+            E = P.energy(st)
+            assert abs(rep.energy - E) < TOL_EIG * abs(E)
+            assert abs(rep.e_ts - st.minus_TS) < TOL_EIG * abs(E)
+            assert rep.e_ts < 0.0 and 0.0 < st.occ[2] < 2.0
+            rho = s.get(nasmod.NAS_Q_RHO_OUT)
+            assert _relmax(rho, st.rho_out) < 1e-8
+    finally:
+        s.close()

@@ -57,10 +57,12 @@ def parse(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-secondary", action="store_true", help="skip the 8-nucleus and helium lines")
     p.add_argument("--secondary-steps", type=int, default=10)
-    p.add_argument("--tol-poisson", type=float, default=1e-10)
+    p.add_argument("--tol-poisson", type=float, default=1e-12)
     p.add_argument("--tol-bvp", type=float, default=1e-10)
     p.add_argument("--inner-adapt", type=float, default=1e-2,
                    help="inexact inner SCF: stop at max(tol_inner, inner_adapt x previous step's drho)")
+    p.add_argument("--bvp-adapt", type=float, default=1e-2,
+                   help="inexact linear solves: max(tol_bvp, min(1e-4, bvp_adapt x previous step's drho))")
     p.add_argument("--spmv-lanes", type=int, default=0)
     p.add_argument("--clocks-file", default=None, help="where to keep the nvidia-smi clock samples")
     p.add_argument("--batch", type=int, default=0,
@@ -102,7 +104,7 @@ def solver_options(args, timing=1):
     return dict(timing=timing, tol_poisson=args.tol_poisson, tol_bvp=args.tol_bvp, check_every=4,
                 spmv_lanes=args.spmv_lanes, poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt,
                 eig_precond=args.eig_precond, poisson_sell=args.poisson_sell, poisson_fused=args.poisson_fused,
-                inner_adapt=args.inner_adapt)
+                inner_adapt=args.inner_adapt, bvp_adapt=args.bvp_adapt)
 
 
 def kernel_source_hash(name, kernel):
@@ -155,6 +157,8 @@ def workload_config(args, name, inst, sz, precision, extra=None):
         "tol_bvp": args.tol_bvp, "tol_poisson": args.tol_poisson, "tol_inner": inst.tol_scf,
         "inner_scf_tolerance": ("inexact: max(tol_inner, %g x previous step's drho)" % args.inner_adapt
                                 if args.inner_adapt > 0 else "tol_inner in every step"),
+        "bvp_tolerance": ("inexact: max(tol_bvp, min(1e-4, %g x previous step's drho))" % args.bvp_adapt
+                          if args.bvp_adapt > 0 else "tol_bvp in every step"),
         "poisson_tolerance": ("inexact inner solves: max(tol_poisson, min(1e-6, 1e-3 x previous density "
                               "residual))" if args.poisson_adaptive else "tol_poisson in every solve"),
         "small_eigensolver": "LOBPCG, block vectors on the device, host Rayleigh-Ritz, %s preconditioner; "
@@ -684,35 +688,43 @@ def main():
     log("timed: %d steps in %.1f ms; last report %s" % (args.steps, ms, reps[-1].as_dict()))
     ms = reduce_max(ms, dist, "cuda")
     value = job_value(world, args.steps, ms)
-    lam_h, e_h = snap
-    # ------------------------------------------------------------ the other precision, same start state
-    nas.nas_set_state(s.h, s0_lam.data_ptr(), s0_psi.data_ptr(), s0_rho.data_ptr(), 0)
-    s.opt.precision = 1 if other == "mixed" else 0
+    # ------------------------------------------------------------ mixed against FP64, same start state
+    # both precisions run n_cmp steps from the timed run's start state with the
+    # exact inner SCF (tol_inner in every step), so that the per-eigenvalue
+    # difference measures the precision and not a looser inner stop
+    cmp = {}
+    for pr in ("mixed", "fp64"):
+        nas.nas_set_state(s.h, s0_lam.data_ptr(), s0_psi.data_ptr(), s0_rho.data_ptr(), 0)
+        s.opt.precision = 1 if pr == "mixed" else 0
+        s.opt.inner_adapt = 0.0
+        s.opt.bvp_adapt = 0.0
+        nas.nas_set_options(s.h, s.opt)
+        barrier()
+        ms_c, per_c, reps_c, snap_c = timed_steps(s, nas, torch, n_cmp, snap_at=n_cmp)
+        cmp[pr] = (reduce_max(ms_c, dist, "cuda"), reps_c, snap_c)
+        log("comparison %s: %.1f ms for %d steps, inner %s" % (pr, ms_c, n_cmp, [r.n_inner for r in reps_c]))
+    s.opt.precision = 1 if prec == "mixed" else 0
+    s.opt.inner_adapt = args.inner_adapt
+    s.opt.bvp_adapt = args.bvp_adapt
     nas.nas_set_options(s.h, s.opt)
-    barrier()
-    ms_o, per_o, reps_o, snap_o = timed_steps(s, nas, torch, n_cmp, snap_at=n_cmp)
-    ms_o = reduce_max(ms_o, dist, "cuda")
-    lam_o, e_o = snap_o
-    # the headline run's own time over its first n_cmp steps (the same steps)
-    lam_mixed, lam_fp64 = (lam_h, lam_o) if prec == "mixed" else (lam_o, lam_h)
-    e_mixed, e_fp64 = (e_h, e_o) if prec == "mixed" else (e_o, e_h)
+    (ms_m, reps_m, (lam_mixed, e_mixed)), (ms_f, reps_f, (lam_fp64, e_fp64)) = cmp["mixed"], cmp["fp64"]
     err = lam_mixed - lam_fp64
+    reps_o = reps_f if prec == "mixed" else reps_m
     comparison = {
-        "precision": other, "steps": n_cmp, "value": job_value(world, n_cmp, ms_o), "unit": "steps/s",
-        "ms_per_step": ms_o / n_cmp,
-        "what": "the same start state and steps in the other precision; mixed = FP32 Poisson and block PCG "
-                "inside FP64 iterative refinement, all else FP64",
+        "steps": n_cmp, "inner_scf": "exact (tol_inner %g in every step)" % inst.tol_scf,
+        "mixed": {"value": job_value(world, n_cmp, ms_m), "unit": "steps/s", "ms_per_step": ms_m / n_cmp,
+                  "n_inner": [r.n_inner for r in reps_m], "drho": [r.drho for r in reps_m],
+                  "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_m, nas.PHASES)[0].items()}},
+        "fp64": {"value": job_value(world, n_cmp, ms_f), "unit": "steps/s", "ms_per_step": ms_f / n_cmp,
+                 "n_inner": [r.n_inner for r in reps_f], "drho": [r.drho for r in reps_f],
+                 "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_f, nas.PHASES)[0].items()}},
+        "speed_ratio_mixed_over_fp64": ms_f / ms_m if ms_m > 0 else None,
+        "what": "the same start state and steps in both precisions; mixed = FP32 Poisson and block PCG inside "
+                "FP64 iterative refinement, all else FP64",
         "max_eigenvalue_err_ha": float(np.max(np.abs(err))), "eigenvalue_err_ha": [float(x) for x in err],
         "energy_err_ha": float(e_mixed - e_fp64),
-        "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_o, nas.PHASES)[0].items()},
-        "n_inner": [r.n_inner for r in reps_o], "drho": [r.drho for r in reps_o],
     }
-    hms = phase_totals(reps[:n_cmp], nas.PHASES)[0]
-    comparison["headline_phase_ms_first_steps"] = {k: v / n_cmp for k, v in hms.items()}
-    comparison["headline_ms_first_steps"] = sum(per_h[:n_cmp]) / n_cmp
-    log("comparison (%s): %s" % (other, json.dumps({k: v for k, v in comparison.items() if k != "eigenvalue_err_ha"})))
-    s.opt.precision = 1 if prec == "mixed" else 0
-    nas.nas_set_options(s.h, s.opt)
+    log("comparison: %s" % json.dumps({k: v for k, v in comparison.items() if k != "eigenvalue_err_ha"}))
 
     # ------------------------------------------------------------ rooflines from the live CUDA-event timings
     peak, psrc = hbm_peak()
@@ -836,18 +848,15 @@ def main():
         "per_step": {"n_inner": [r.n_inner for r in reps], "cg_iters": [r.cg_iters for r in reps],
                      "poisson_iters": [r.poisson_iters for r in reps], "eig_iters": [r.eig_iters for r in reps],
                      "drho": [r.drho for r in reps], "energy": [r.energy for r in reps],
-                     "inner_tol": [r.inner_tol for r in reps]},
+                     "inner_tol": [r.inner_tol for r in reps], "bvp_tol": [r.bvp_tol for r in reps]},
         "gpu_launches": int(sum(r.kernel_launches for r in reps)), "e2e": e2e, "clocks": clk,
         "spmm_autotuner": tuner,
         "cpu_baseline": cpu, "setup_s": setup_s, "energy_ha": float(last.energy),
         "secondary": secondary,
     }
-    # mixed over FP64: the same start state and the same first n_cmp steps
-    ms_h_first = sum(per_h[:n_cmp])
-    ms_mixed, ms_fp64 = (ms_h_first, ms_o) if prec == "mixed" else (ms_o, ms_h_first)
-    line["speed_ratio_mixed_over_fp64"] = ms_fp64 / ms_mixed if ms_mixed > 0 else None
-    line["speed_ratio_note"] = ("ms of the FP64 run over ms of the mixed run for the same first %d steps from the "
-                                "same start state (CUDA events per step)" % n_cmp)
+    line["speed_ratio_mixed_over_fp64"] = comparison["speed_ratio_mixed_over_fp64"]
+    line["speed_ratio_note"] = ("FP64 ms over mixed ms for the same %d steps from the same start state, both with "
+                                "the exact inner SCF (CUDA events)" % n_cmp)
     line["per_step"]["ms"] = per_h
     if batched is not None:
         line["batched"] = batched

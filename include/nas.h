@@ -63,7 +63,7 @@ typedef struct nas_options {
     int    max_poisson;    /* iteration cap of the Poisson PCG                       */
     int    max_inner;      /* inner SCF iterations per step                          */
     int    max_outer;      /* steps of nas_solve                                     */
-    int    anderson_depth; /* Anderson history depth (Sec. 4: 5)                     */
+    int    anderson_depth; /* Anderson history depth, 1..16 (Sec. 4: 5)              */
     double anderson_beta;  /* Anderson damping (Sec. 4: 0.7)                         */
     int    hartree;        /* 1: include V_Har; 0: linear problem                    */
     int    xc;             /* 1: include LDA V_xc                                    */
@@ -129,6 +129,21 @@ typedef struct nas_options {
                               ||rho^(l) - rho^(l-1)||_0); the outer fixed point is
                               unchanged (near it the inner SCF again runs to
                               tol_inner).  0: tol_inner in every step           */
+    int    bvp_two_level;  /* 1: the block PCG of the N shifted problems in nas_step
+                              uses D^-1 + I C^-1 I^T with C = I^T H~ I, the coarse
+                              Galerkin matrix of the first step's H~ after
+                              nas_init (dense inverse, formed once and kept: a
+                              fixed SPD preconditioner); 0: Jacobi only.  The
+                              nas_apply BVP ops always use Jacobi.  Measured on
+                              the 32-nucleus workload with mu = 36: 168 against
+                              152 Jacobi iterations (the shifted operator's bad
+                              modes are not the coarse ones), so off by default */
+    double bvp_adapt;      /* > 0: inexact linear solves - each step's N shifted
+                              problems are solved to max(tol_bvp, min(1e-4,
+                              bvp_adapt x the previous step's ||rho^(l) -
+                              rho^(l-1)||_0)); the outer fixed point is unchanged
+                              (near it the solves again reach tol_bvp).
+                              0: tol_bvp in every step                          */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -138,7 +153,7 @@ typedef struct nas_options {
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
  * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0,
- * smearing = 0, inner_adapt = 0. */
+ * smearing = 0, inner_adapt = 0, bvp_two_level = 0, bvp_adapt = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -210,6 +225,7 @@ typedef struct nas_report {
     double spmm32_bytes;      /* algorithmic bytes of the FP32 SpMM launches (mixed
                                  block PCG): nnz*(4+4) + 4*(n+1) + 2*n*N*4            */
     double spmm32_flops;      /* 2*nnz*N per FP32 SpMM launch                        */
+    double bvp_tol;           /* tolerance of the last step's N linear solves        */
 } nas_report;
 
 /* ------------------------------------------------------------------ context */

@@ -89,6 +89,8 @@ void nas_default_options(nas_options* o) {
     o->precision = 0;
     o->smearing = 0.0;
     o->inner_adapt = 0.0;
+    o->bvp_two_level = 0;
+    o->bvp_adapt = 0.0;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -200,11 +202,12 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
     return guarded(c, [&]() {
         if (!o) nas::fail(NAS_E_INVALID_ARG, "null options");
         if (o->tol_bvp <= 0 || o->tol_poisson <= 0 || o->max_cg < 1 || o->max_poisson < 1 || o->max_inner < 1 ||
-            o->anderson_depth < 1 || o->anderson_depth > 5 || o->precision < 0 || o->precision > 1 ||
+            o->anderson_depth < 1 || o->anderson_depth > 16 || o->precision < 0 || o->precision > 1 ||
             o->eig_device < 0 || o->eig_device > 1 || o->poisson_adaptive < 0 || o->poisson_adaptive > 1 ||
             !(o->eig_adapt > 0.0) || o->eig_adapt > 1.0 || o->eig_precond < 0 || o->eig_precond > 1 ||
             o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1 ||
-            !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0))
+            !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0) || o->bvp_two_level < 0 || o->bvp_two_level > 1 ||
+            !(o->bvp_adapt >= 0.0))
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level) || (o->eig_precond != c->opt.eig_precond);

@@ -121,6 +121,10 @@ struct nas_ctx {
     cudaGraphExec_t pcg1f_exec = nullptr;
     Pcg1Key pcg1f_key;
     long long pcg1_iters = 0;
+    // two-level preconditioner of the N shifted problems: C^-1, C = I^T H~ I
+    nas::DBuf<double> d_bvpC, d_bvp_tc, d_bvp_yc;     // [nH][nH], [nH][N], [nH][N]
+    nas::DBuf<float> d_bvpC32, d_bvp_part32;
+    bool bvp_coarse_ready = false, bvp_coarse_failed = false;
 
     // ---- state (host)
     int64_t state_id = 0;               // bumped by every call that changes the solver state
@@ -128,6 +132,7 @@ struct nas_ctx {
     std::vector<double> occ_now;        // occupations of the current orbitals [N]
     double e_ts = 0.0;                  // -kT S of occ_now (smearing)
     double inner_tol_now = 0.0;         // stop tolerance of the last inner SCF
+    double bvp_tol_now = 0.0;           // tolerance of the last step's linear solves
     bool have_VH = false;
     bool anl_valid = false;             // d_ANL/d_eps/d_vxc match d_rho_in and d_VH
     int step_count = 0;

@@ -42,6 +42,10 @@ static Pieces tpieces(nas_ctx* c) {
     return pc;
 }
 
+static void galerkin(nas_ctx* c, const double* fine_vals, double* coarse_vals);
+static void transpose_apply(nas_ctx* c, int N, const double* Y, double* out);
+static void make_f32_copies(nas_ctx* c);
+
 static cudaEvent_t ev_get(nas_ctx* c) {
     if (!c->ev_pool.empty()) {
         cudaEvent_t e = c->ev_pool.back();
@@ -126,10 +130,67 @@ static void zero_null_columns(nas_ctx* c, int64_t n, int N, const double* bb, do
     sync(c);
 }
 
+// Coarse part of the two-level preconditioner of the N shifted problems,
+// z = D^-1 r + I C^-1 I^T r: C = I^T H~ I of the current H~ (Galerkin on the
+// device, dense Cholesky inverse on the host), kept in FP64 and FP32 until the
+// next nas_init (a fixed SPD preconditioner; its age only affects the
+// iteration count).  Needs a dense coarse space (nH <= kDenseCoarseMax); a
+// failed factorisation leaves Jacobi.
+static void bvp_coarse_setup(nas_ctx* c) {
+    if (!c->opt.bvp_two_level || c->bvp_coarse_ready || c->bvp_coarse_failed) return;
+    const int64_t nH = c->nH;
+    if (nH < 1 || nH > kDenseCoarseMax) {
+        c->bvp_coarse_failed = true;
+        return;
+    }
+    cudaStream_t s = c->stream;
+    galerkin(c, c->d_H.p, c->d_AH.p);
+    std::vector<double> hv(c->GM.hnnz());
+    c->d_AH.download(hv.data(), hv.size(), s);
+    sync(c);
+    std::vector<double> D((size_t)nH * nH, 0.0), Inv((size_t)nH * nH);
+    for (int64_t a = 0; a < nH; ++a)
+        for (int p = c->GM.hptr[a]; p < c->GM.hptr[a + 1]; ++p) D[a * nH + c->GM.hcol[p]] = hv[p];
+    if (chol_factor((int)nH, D.data()) != 0) {
+        c->bvp_coarse_failed = true;
+        return;
+    }
+    chol_inverse((int)nH, D.data(), Inv.data());
+    c->d_bvpC.upload(Inv, s);
+    c->d_bvpC32.ensure((size_t)nH * nH);
+    launch_cast_to_f32(nH * nH, c->d_bvpC.p, c->d_bvpC32.p, s);
+    c->d_bvp_tc.ensure((size_t)nH * c->N);
+    c->d_bvp_yc.ensure((size_t)nH * c->N);
+    sync(c);
+    c->bvp_coarse_ready = true;
+}
+
+// Z += I C^-1 I^T R (FP64 block)
+static void bvp_coarse_correct(nas_ctx* c, int N, const double* R, double* Z) {
+    const int64_t nH = c->nH;
+    transpose_apply(c, N, R, c->d_bvp_tc.p);
+    launch_cols_mult(nH, ColBlocks::one(c->d_bvpC.p, (int)nH, (int)nH), c->d_bvp_tc.p, N, 1.0, 0.0, c->d_bvp_yc.p,
+                     c->stream);
+    launch_prolong_add(c->F.n, N, c->d_Icol.p, c->d_Ival.p, c->d_bvp_yc.p, Z, c->stream);
+}
+
+// Z += I C^-1 I^T R (FP32 block; FP32 weights and C^-1, FP64 coarse block)
+static void bvp_coarse_correct_f32(nas_ctx* c, int N, const float* R, float* Z) {
+    const int64_t nH = c->nH;
+    cudaStream_t s = c->stream;
+    c->d_piece_part.ensure(std::max<int64_t>(1, c->GM.tpieces.npieces() * N));
+    launch_transpose_apply_f32(tpieces(c), c->d_trow.p, c->d_tval32.p, N, R, c->d_piece_part.p, c->d_bvp_tc.p, s);
+    c->d_bvp_part32.ensure(std::max<int64_t>(1, dense_precond_part_size(nH, N)));
+    launch_dense_precond(nH, nH, N, c->d_bvpC32.p, c->d_bvp_tc.p, nullptr, c->d_bvp_part32.p, c->d_bvp_yc.p, s);
+    launch_prolong_add(c->F.n, N, c->d_Icol.p, c->d_ival32.p, c->d_bvp_yc.p, Z, s);
+}
+
 // Block Jacobi-preconditioned CG on A X = B (N independent columns); X holds
-// the initial guess.  Returns the iteration count; throws on breakdown.
+// the initial guess.  two_level: the preconditioner adds the coarse
+// correction I C^-1 I^T (bvp_coarse_setup).  Returns the iteration count;
+// throws on breakdown.
 static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double* B, double* X, double tol,
-               int maxit, bool* converged) {
+               int maxit, bool* converged, bool two_level = false) {
     const int64_t n = A.n_rows;
     cudaStream_t s = c->stream;
     double *R = c->d_cg_R.p, *Zb = c->d_cg_Z.p, *P = c->d_cg_P.p, *Q = c->d_cg_Q.p;
@@ -139,6 +200,7 @@ static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double
     spmm(c, A, N, X, R);
     launch_sub_from(n * N, B, R, s);
     launch_scale_rows(n, N, Dinv, R, Zb, s);
+    if (two_level) bvp_coarse_correct(c, N, R, Zb);
     NAS_CUDA(cudaMemcpyAsync(P, Zb, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
     {
         const double* X1[1] = {R};
@@ -171,6 +233,7 @@ static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double
         }
         launch_pcg_alpha(pc, s);
         launch_pcg_update(n, N, pc.alpha, pc.active, P, Q, Dinv, X, R, Zb, s);
+        if (two_level) bvp_coarse_correct(c, N, R, Zb);
         {
             const double* X2[2] = {R, R};
             const double* Y2[2] = {Zb, R};
@@ -201,9 +264,10 @@ static int pcg(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double
 // tolerance max(1e-5, 0.3 tol ||b|| / ||r||) of the worst one, and adds E to X
 // in FP64.  Returns the FP32 iterations.
 static int pcg_mixed(nas_ctx* c, const Csr& A, const double* Dinv, int N, const double* B, double* X, double tol,
-                     int maxit, bool* converged) {
+                     int maxit, bool* converged, bool two_level = false) {
     const int64_t n = A.n_rows, nnz = c->F.nnz();
     cudaStream_t s = c->stream;
+    if (two_level && !c->d_K32.p) make_f32_copies(c);
     c->d_H32.ensure(nnz);
     launch_cast_to_f32(nnz, A.val, c->d_H32.p, s);
     c->d_Hdinv32.ensure(n);
@@ -255,6 +319,7 @@ static int pcg_mixed(nas_ctx* c, const Csr& A, const double* Dinv, int N, const 
         launch_cast_to_f32(n * N, R64, R, s);
         NAS_CUDA(cudaMemsetAsync(E, 0, sizeof(float) * n * N, s));
         launch_scale_rows_f32(n, N, c->d_Hdinv32.p, R, Z, s);
+        if (two_level) bvp_coarse_correct_f32(c, N, R, Z);
         NAS_CUDA(cudaMemcpyAsync(P, Z, sizeof(float) * n * N, cudaMemcpyDeviceToDevice, s));
         {
             const float* X1[1] = {R};
@@ -278,6 +343,7 @@ static int pcg_mixed(nas_ctx* c, const Csr& A, const double* Dinv, int N, const 
             }
             launch_pcg_alpha(pc, s);
             launch_pcg_update_f32(n, N, pc.alpha, pc.active, P, Q, c->d_Hdinv32.p, E, R, Z, s);
+            if (two_level) bvp_coarse_correct_f32(c, N, R, Z);
             {
                 const float* X2[2] = {R, R};
                 const float* Y2[2] = {Z, R};
@@ -734,7 +800,13 @@ struct Anderson {
 static void anderson_mix(nas_ctx* c, Anderson& A) {
     Phase t(c, NAS_PH_MIXING);
     cudaStream_t s = c->stream;
-    const int depth = std::max(1, std::min(c->opt.anderson_depth, 5));
+    const int depth = std::max(1, std::min(c->opt.anderson_depth, 16));
+    while ((int)c->d_hist_rin.size() < depth) {
+        c->d_hist_rin.emplace_back(c->nqt);
+        c->d_hist_F.emplace_back(c->nqt);
+    }
+    c->d_partial.ensure(std::max<int64_t>(c->d_partial.n, anderson_partial_size(depth - 1)));
+    c->d_red.ensure(std::max<int64_t>(c->d_red.n, 16 * 16 + 16));
     int slot;
     if ((int)A.hist.size() >= depth) {
         slot = A.hist.front();
@@ -759,13 +831,12 @@ static void anderson_mix(nas_ctx* c, Anderson& A) {
             launch_axpby(c->nqt, 1.0, c->d_rho_in.p, beta, c->d_hist_F[slot].p, c->d_rho_in.p, s);
             return;
         }
-        const double* Fp[6];
-        const double* Rp[6];
+        std::vector<const double*> Fp(mprev + 1), Rp(mprev + 1);
         for (int j = 0; j <= mprev; ++j) {
             Fp[j] = c->d_hist_F[A.hist[j]].p;
             Rp[j] = c->d_hist_rin[A.hist[j]].p;
         }
-        launch_anderson_dots(c->nqt, mprev, Fp, c->d_Wq.p, c->d_partial.p, c->d_red.p, s);
+        launch_anderson_dots(c->nqt, mprev, Fp.data(), c->d_Wq.p, c->d_partial.p, c->d_red.p, s);
         std::vector<double> h(mprev * mprev + mprev);
         NAS_CUDA(cudaMemcpyAsync(h.data(), c->d_red.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
         sync(c);
@@ -784,7 +855,7 @@ static void anderson_mix(nas_ctx* c, Anderson& A) {
             A.hist.pop_front();
             continue;
         }
-        launch_anderson_mix(c->nqt, mprev, Rp, Fp, alpha.data(), beta, c->d_rho_in.p, s);
+        launch_anderson_mix(c->nqt, mprev, Rp.data(), Fp.data(), alpha.data(), beta, c->d_rho_in.p, s);
         return;
     }
 }
@@ -1241,6 +1312,7 @@ static void system_parameters(nas_ctx* c) {
 static void galerkin(nas_ctx* c, const double* fine_vals, double* coarse_vals);
 
 void ctx_update_nuclei(nas_ctx* c) {
+    c->bvp_coarse_ready = c->bvp_coarse_failed = false;
     assemble_vext(c);
     galerkin(c, c->d_AL.p, c->d_AH.p);
     c->d_AH.download(c->AHL.data(), c->GM.hnnz(), c->stream);
@@ -1275,7 +1347,8 @@ static void alloc_work(nas_ctx* c) {
         b->alloc(nqt);
     c->d_hist_rin.clear();
     c->d_hist_F.clear();
-    for (int k = 0; k < 5; ++k) {
+    const int depth = std::max(1, std::min(c->opt.anderson_depth, 16));
+    for (int k = 0; k < depth; ++k) {
         c->d_hist_rin.emplace_back(nqt);
         c->d_hist_F.emplace_back(nqt);
     }
@@ -1291,6 +1364,7 @@ void ctx_setup(nas_ctx* c) {
     fem_set_order(c->fine_order, c->device);
     c->setup_done = false;
     c->initialized = false;
+    c->bvp_coarse_ready = c->bvp_coarse_failed = false;
     if (c->pcg1_exec) {
         cudaGraphExecDestroy(c->pcg1_exec);
         c->pcg1_exec = nullptr;
@@ -1508,6 +1582,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
     c->uwarm_dev_m = 0;
     c->lob_reuse_ok = false;
     c->last_drho = 0.0;
+    c->bvp_coarse_ready = c->bvp_coarse_failed = false;   // re-formed from the next step's H~
     c->occ_now = c->occ;   // the given occupations until the first eigensolve
     c->e_ts = 0.0;
     c->d_occ.upload(c->occ_now, s);
@@ -1612,11 +1687,19 @@ int ctx_step(nas_ctx* c, nas_report* rep) {
         launch_scale_cols(n, N, d_sh, c->d_cg_B.p, s);
         NAS_CUDA(cudaMemcpyAsync(c->d_Uhat.p, c->d_Psi.p, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
         bool conv;
+        bvp_coarse_setup(c);
+        const bool tl = c->bvp_coarse_ready;
+        // tolerance: tol_bvp, or with bvp_adapt > 0 (after the first step)
+        // max(tol_bvp, min(1e-4, bvp_adapt x the previous step's density change))
+        double tol = c->opt.tol_bvp;
+        if (c->opt.bvp_adapt > 0.0 && c->step_count > 0 && c->last_drho > 0.0)
+            tol = std::max(tol, std::min(1e-4, c->opt.bvp_adapt * c->last_drho));
+        c->bvp_tol_now = tol;
         c->last_cg = c->opt.precision == 1
-                         ? pcg_mixed(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, c->opt.tol_bvp,
-                                     c->opt.max_cg, &conv)
-                         : pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, c->opt.tol_bvp,
-                               c->opt.max_cg, &conv);
+                         ? pcg_mixed(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, tol,
+                                     c->opt.max_cg, &conv, tl)
+                         : pcg(c, fcsr(c, c->d_H.p), c->d_Hdinv.p, N, c->d_cg_B.p, c->d_Uhat.p, tol, c->opt.max_cg,
+                               &conv, tl);
         if (!conv) status = NAS_E_NOT_CONVERGED;
     }
     augment_basis(c);
@@ -1676,6 +1759,7 @@ void ctx_fill_report(nas_ctx* c, nas_report* rep) {
     rep->spmm32_bytes = c->spmm32_bytes;
     rep->spmm32_flops = c->spmm32_flops;
     rep->inner_tol = c->inner_tol_now;
+    rep->bvp_tol = c->bvp_tol_now;
 }
 
 // ------------------------------------------------------------------ state in/out

@@ -189,6 +189,14 @@ struct Pieces {
 };
 // out[a][c] = sum_{p in segment a} tval[p] Y[trow[p]][c]   (I^T Y over the I^T
 // rows split into pieces); partial: scratch of npieces * N doubles
+// FP32 Y and weights, FP64 piece sums and result
+void launch_transpose_apply_f32(const Pieces& pc, const int32_t* trow, const float* tval, int N, const float* Y,
+                                double* partial, double* out, cudaStream_t s);
+// Z += I Yc for a coarse block Yc [nH][N] (FP64), Z [n][N] FP64 or FP32
+void launch_prolong_add(int64_t n, int N, const int32_t* icol, const double* ival, const double* Yc, double* Z,
+                        cudaStream_t s);
+void launch_prolong_add(int64_t n, int N, const int32_t* icol, const float* ival, const double* Yc, float* Z,
+                        cudaStream_t s);
 void launch_transpose_apply(const Pieces& pc, const int32_t* trow, const double* tval, int N, const double* Y,
                             double* partial, double* out, cudaStream_t s);
 // Psi[i][c] = sum_k ival[i][k] uH[icol[i][k]][c] + sum_j Uhat[i][j] alpha[j][c]
@@ -360,6 +368,8 @@ void launch_add_f32(int64_t n, const float* e, double* x, cudaStream_t st);
 // Anderson: given F^0..F^m (pointers), w, compute the k x k matrix
 // A[a][b] = (F^m - F^a, F^m - F^b) and rhs[a] = (F^m - F^a, F^m), k = m;
 // out = [A (k*k), rhs (k)] deterministic
+// partial-sum buffer size (doubles) of launch_anderson_dots for m previous entries
+int64_t anderson_partial_size(int m);
 void launch_anderson_dots(int64_t cnt, int m, const double* const* F, const double* w,
                           double* partial, double* out, cudaStream_t s);
 // rho_new = rin_m + sum_a alpha_a (rin_a - rin_m) + beta (F_m + sum_a alpha_a (F_a - F_m))

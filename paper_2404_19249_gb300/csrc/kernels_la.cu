@@ -434,6 +434,64 @@ void launch_transpose_apply(const Pieces& pc, const int32_t* trow, const double*
     NAS_CHECK_LAUNCH();
 }
 
+// I^T Y for FP32 Y [n][N] and FP32 weights (the FP32 block PCG's coarse
+// restriction): per-piece sums in FP64, then the same ordered piece sums
+__global__ void k_transpose_pieces_f32(Pieces pc, const int32_t* trow, const float* tval, int N, const float* Y,
+                                       double* partial) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (q >= pc.npieces) return;  // warp-uniform
+    const int64_t b = pc.piece_start[q], e = pc.piece_start[q + 1];
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        const int c = c0 + lane;
+        double acc = 0.0;
+        if (c < N)
+            for (int64_t p = b; p < e; ++p) acc += (double)tval[p] * (double)Y[(int64_t)trow[p] * N + c];
+        if (c < N) partial[q * N + c] = acc;
+    }
+}
+
+void launch_transpose_apply_f32(const Pieces& pc, const int32_t* trow, const float* tval, int N, const float* Y,
+                                double* partial, double* out, cudaStream_t s) {
+    if (pc.nseg <= 0 || N <= 0) return;
+    if (pc.npieces > 0) {
+        k_transpose_pieces_f32<<<grid_for(pc.npieces * 32, 256), 256, 0, s>>>(pc, trow, tval, N, Y, partial);
+        NAS_CHECK_LAUNCH();
+    }
+    k_piece_sum<<<grid_for(pc.nseg * N, 256), 256, 0, s>>>(pc.nseg, pc.seg_piece, N, partial, out);
+    NAS_CHECK_LAUNCH();
+}
+
+// Z[i][c] += sum_k w[i][k] Yc[icol[i][k]][c] (prolongation of a coarse block,
+// columns of boundary coarse vertices (-1) skipped)
+template <typename T>
+__global__ void k_prolong_add(int64_t n, int N, const int32_t* icol, const T* ival, const double* Yc, T* Z) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * N) return;
+    const int64_t i = t / N;
+    const int c = (int)(t - i * N);
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int a = icol[4 * i + k];
+        if (a >= 0) acc += (double)ival[4 * i + k] * Yc[(int64_t)a * N + c];
+    }
+    Z[t] += (T)acc;
+}
+
+void launch_prolong_add(int64_t n, int N, const int32_t* icol, const double* ival, const double* Yc, double* Z,
+                        cudaStream_t s) {
+    if (n <= 0) return;
+    k_prolong_add<double><<<grid_for(n * N, 256), 256, 0, s>>>(n, N, icol, ival, Yc, Z);
+    NAS_CHECK_LAUNCH();
+}
+void launch_prolong_add(int64_t n, int N, const int32_t* icol, const float* ival, const double* Yc, float* Z,
+                        cudaStream_t s) {
+    if (n <= 0) return;
+    k_prolong_add<float><<<grid_for(n * N, 256), 256, 0, s>>>(n, N, icol, ival, Yc, Z);
+    NAS_CHECK_LAUNCH();
+}
+
 __global__ void k_reconstruct(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
                               int64_t nH, int Na, const double* Uhat, double* Psi) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -505,56 +563,105 @@ void launch_galerkin2(const Pieces& pc, const int32_t* con, const double* W, con
 }
 
 // ------------------------------------------------------------------ Anderson
-struct FPtrs {
-    const double* p[6];
+// Inner products of the history (Sec. 4, Anderson mixing) for m previous
+// entries (m <= kAndMax - 1): with d_a = F_m - F_a, the matrix (d_a, d_b) for
+// a <= b and the right-hand side (d_a, F_m), weighted by the quadrature
+// weights.  The m (m + 1) / 2 + m distinct entries are summed in passes of
+// at most kAndPass accumulators per thread (each pass re-reads the history);
+// entry e of a pass is (a, b) = code[e], b < 0 meaning the right-hand side.
+static const int kAndMax = 16;
+static const int kAndPass = 20;
+struct AndPass {
+    const double* F[kAndMax];
+    short2 code[kAndPass];
+    int nent;      // entries in this pass
+    int first;     // index of the pass's first entry in the full list
+    int total;     // entries in the full list
 };
 
-// k = m previous entries: 20 accumulators max (4x4 matrix + 4 rhs)
-__global__ void __launch_bounds__(256) k_anderson_dots(int64_t cnt, int m, FPtrs F, const double* w,
+__global__ void __launch_bounds__(256) k_anderson_dots(int64_t cnt, int m, AndPass a, const double* w,
                                                       double* partial) {
-    __shared__ double sh[20][256];
-    double acc[20];
-    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
-    const double* Fm = F.p[m];
+    __shared__ double sh[kAndPass][256];
+    double acc[kAndPass];
+#pragma unroll
+    for (int k = 0; k < kAndPass; ++k) acc[k] = 0.0;
+    const double* Fm = a.F[m];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double fm = Fm[i];
-        double wi = w[i];
-        double d[4];
-        for (int a = 0; a < m; ++a) d[a] = fm - F.p[a][i];
-        for (int a = 0; a < m; ++a) {
-            for (int b = 0; b < m; ++b) acc[a * m + b] += wi * d[a] * d[b];
-            acc[m * m + a] += wi * d[a] * fm;
+        const double fm = Fm[i];
+        const double wi = w[i];
+        double d[kAndMax];
+        for (int q = 0; q < m; ++q) d[q] = fm - a.F[q][i];
+#pragma unroll
+        for (int k = 0; k < kAndPass; ++k) {
+            if (k < a.nent) {
+                const short2 c = a.code[k];
+                acc[k] += wi * d[c.x] * (c.y >= 0 ? d[c.y] : fm);
+            }
         }
     }
-    int K = m * m + m;
-    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = acc[k];
+    for (int k = 0; k < a.nent; ++k) sh[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
         if ((int)threadIdx.x < off)
-            for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + off];
+            for (int k = 0; k < a.nent; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + off];
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int k = 0; k < K; ++k) partial[(int64_t)blockIdx.x * K + k] = sh[k][0];
+        for (int k = 0; k < a.nent; ++k) partial[(int64_t)blockIdx.x * a.total + a.first + k] = sh[k][0];
+}
+
+// out: the m x m matrix (row-major, both triangles) followed by the m right-hand sides
+__global__ void k_anderson_expand(int m, const double* uniq, double* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * m + m) return;
+    if (t < m * m) {
+        int a = t / m, b = t % m;
+        if (a > b) {
+            const int x = a;
+            a = b;
+            b = x;
+        }
+        out[t] = uniq[a * m - a * (a - 1) / 2 + (b - a)];   // packed upper triangle
+    } else {
+        out[t] = uniq[m * (m + 1) / 2 + (t - m * m)];
+    }
 }
 
 void launch_anderson_dots(int64_t cnt, int m, const double* const* F, const double* w, double* partial,
                           double* out, cudaStream_t s) {
-    if (m < 1 || m > 4) fail(NAS_E_INVALID_ARG, "anderson depth");
-    FPtrs f{};
-    for (int a = 0; a <= m; ++a) f.p[a] = F[a];
+    if (m < 1 || m > kAndMax - 1) fail(NAS_E_INVALID_ARG, "anderson depth");
+    std::vector<short2> codes;
+    for (int a = 0; a < m; ++a)
+        for (int b = a; b < m; ++b) codes.push_back(make_short2((short)a, (short)b));
+    for (int a = 0; a < m; ++a) codes.push_back(make_short2((short)a, (short)-1));
+    const int total = (int)codes.size();
     int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (cnt + 255) / 256));
-    k_anderson_dots<<<nb, 256, 0, s>>>(cnt, m, f, w, partial);
+    for (int first = 0; first < total; first += kAndPass) {
+        AndPass ap{};
+        for (int q = 0; q <= m; ++q) ap.F[q] = F[q];
+        ap.nent = std::min(kAndPass, total - first);
+        ap.first = first;
+        ap.total = total;
+        for (int k = 0; k < ap.nent; ++k) ap.code[k] = codes[first + k];
+        k_anderson_dots<<<nb, 256, 0, s>>>(cnt, m, ap, w, partial);
+        NAS_CHECK_LAUNCH();
+    }
+    double* uniq = partial + (int64_t)nb * total;
+    reduce_partials(nb, total, partial, uniq, s);
+    k_anderson_expand<<<1, 512, 0, s>>>(m, uniq, out);
     NAS_CHECK_LAUNCH();
-    int K = m * m + m;
-    reduce_partials(nb, K, partial, out, s);
+}
+
+int64_t anderson_partial_size(int m) {
+    const int total = m * (m + 1) / 2 + m;
+    return ((int64_t)kRedBlocks + 1) * total;
 }
 
 struct MixArgs {
-    const double* rin[6];
-    const double* F[6];
-    double alpha[5];
+    const double* rin[kAndMax];
+    const double* F[kAndMax];
+    double alpha[kAndMax - 1];
 };
 
 __global__ void k_anderson_mix(int64_t cnt, int m, MixArgs a, double beta, double* out) {
@@ -571,7 +678,7 @@ __global__ void k_anderson_mix(int64_t cnt, int m, MixArgs a, double beta, doubl
 
 void launch_anderson_mix(int64_t cnt, int m, const double* const* rin, const double* const* F,
                          const double* alpha, double beta, double* rho_new, cudaStream_t s) {
-    if (m < 0 || m > 4) fail(NAS_E_INVALID_ARG, "anderson depth");
+    if (m < 0 || m > kAndMax - 1) fail(NAS_E_INVALID_ARG, "anderson depth");
     MixArgs a{};
     for (int j = 0; j <= m; ++j) {
         a.rin[j] = rin[j];

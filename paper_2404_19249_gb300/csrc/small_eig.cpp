@@ -634,7 +634,8 @@ void jacobi_eig(int m, double* A, double* w, double* V) {
 }
 
 int small_solve(int n, const double* A, const double* b, double* x) {
-    double M[8][9];
+    if (n < 0 || n > 16) return -1;
+    double M[16][17];
     for (int i = 0; i < n; ++i) {
         for (int j = 0; j < n; ++j) M[i][j] = A[i * n + j];
         M[i][n] = b[i];

@@ -27,8 +27,8 @@ void chol_solve(int m, const double* L, int k, double* B);
 // columns in parallel, each row-oriented (contiguous reads of L and L^T).
 void chol_inverse(int m, const double* L, double* Inv);
 
-// Solve A x = b (n <= 8) by Gaussian elimination with partial pivoting.
-// Returns 0 or -1 if singular.
+// Solve A x = b (n <= 16) by Gaussian elimination with partial pivoting.
+// Returns 0, or -1 if singular or n is out of range.
 int small_solve(int n, const double* A, const double* b, double* x);
 
 }  // namespace nas

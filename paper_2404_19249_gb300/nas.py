@@ -42,7 +42,7 @@ class nas_options(C.Structure):
         ("eig_tol", C.c_double), ("spmv_lanes", C.c_int), ("poisson_two_level", C.c_int),
         ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
         ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int), ("poisson_fused", C.c_int),
-        ("smearing", C.c_double), ("inner_adapt", C.c_double),
+        ("smearing", C.c_double), ("inner_adapt", C.c_double), ("bvp_two_level", C.c_int), ("bvp_adapt", C.c_double),
     ]
 
 
@@ -56,7 +56,7 @@ class nas_report(C.Structure):
         ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_double), ("spmv_flops", C.c_double),
         ("eig_iters", C.c_int), ("poisson_spmv_ms", C.c_double), ("poisson_spmv_launches", C.c_longlong),
         ("poisson_fused_ms", C.c_double), ("poisson_fused_iters", C.c_longlong),
-        ("e_ts", C.c_double), ("inner_tol", C.c_double), ("spmm32_bytes", C.c_double), ("spmm32_flops", C.c_double),
+        ("e_ts", C.c_double), ("inner_tol", C.c_double), ("spmm32_bytes", C.c_double), ("spmm32_flops", C.c_double), ("bvp_tol", C.c_double),
     ]
 
     def as_dict(self):

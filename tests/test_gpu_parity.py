@@ -209,14 +209,26 @@ def test_lockstep_steps(pair, nasmod):
         assert abs(rep.drho - st.info["drho"]) < 1e-8 * max(st.info["drho"], 1e-8)
 
 
-@pytest.mark.parametrize("poisson_adaptive", [0, 1], ids=["poisson_exact", "poisson_adaptive"])
-def test_converged_helium_matches_oracle(nasmod, poisson_adaptive):
-    """Converged Algorithm 3 = the oracle's; inexact inner Poisson solves
-    (tolerance tied to the density residual) reach the same fixed point."""
+INEXACT = {
+    "exact": {},
+    "poisson_adaptive": dict(poisson_adaptive=1),
+    # eig_dense_max = 0: the small problem goes to the device LOBPCG, where the tolerance applies
+    "eig_adapt_1e-2": dict(eig_adapt=1e-2, eig_dense_max=0),
+    "all_inexact": dict(poisson_adaptive=1, eig_adapt=1e-2, inner_adapt=1e-2, bvp_adapt=1e-2, eig_dense_max=0),
+}
+
+
+@pytest.mark.parametrize("opts", list(INEXACT.values()), ids=list(INEXACT))
+def test_converged_helium_matches_oracle(nasmod, opts):
+    """Converged Algorithm 3 = the oracle's fixed point, also with every
+    inexact option the benchmark uses: inner Poisson tolerance tied to the
+    density residual, LOBPCG tolerance 1e-2 x the inner residual, inner SCF
+    and linear solves stopped at 1e-2 x the previous step's density change
+    (near convergence all of them tighten to the exact tolerances)."""
     inst = _tight(make_instance("he_p1", cells=6, coarse_cells=3, tol_scf=1e-12, mu=2.0, max_outer=400))
     P = Problem(inst)
     ref = P.solve(max_outer=400)
-    s = nasmod.Solver(inst, poisson_adaptive=poisson_adaptive)
+    s = nasmod.Solver(inst, **opts)
     s.init()
     r, rep = nasmod.nas_solve(s.h)
     assert rep.drho < 1e-11
@@ -357,5 +369,32 @@ def test_smeared_occupations_lockstep(nasmod):
             assert rep.e_ts < 0.0 and 0.0 < st.occ[2] < 2.0
             rho = s.get(nasmod.NAS_Q_RHO_OUT)
             assert _relmax(rho, st.rho_out) < 1e-8
+    finally:
+        s.close()
+
+
+def test_deep_anderson_history_lockstep(nasmod):
+    """Anderson mixing with a 6-entry history (beta 0.15): LiH's inner SCF
+    takes 20-30 iterations, so the history wraps around several times;
+    initial SCF and two steps against the oracle's mixing with the same depth,
+    eigenvalues and energies at 1e-10."""
+    inst = _tight(make_instance("paper_molecule", molecule="lih", cells=8, coarse_cells=4))
+    inst.anderson_depth = 6
+    inst.anderson_beta = 0.15
+    P = Problem(inst)
+    st = P.initial_state()
+    assert st.inner_converged and st.n_inner > 12
+    s = nasmod.Solver(inst)
+    s.init()
+    try:
+        assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG
+        for step in range(2):
+            r, rep = s.step()
+            assert r == 0
+            st = P.step(st)
+            assert st.inner_converged and rep.inner_converged
+            assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG
+            assert abs(rep.n_inner - st.n_inner) <= 1
+            assert abs(rep.energy - P.energy(st)) < TOL_EIG * abs(P.energy(st))
     finally:
         s.close()

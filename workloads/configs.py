@@ -15,10 +15,12 @@ method is measured on:
                    100^3 (~8.1M nodes), coarse 16^3; Fermi-Dirac occupations at
                    kT = 0.01 Ha (the random system has a dense spectrum at the
                    Fermi level, where integer occupations make the SCF swap
-                   orbitals from one iteration to the next) and Anderson damping
-                   beta = 0.1 (with the paper's 0.7 the density residual of this
-                   32-atom system stalls at ~1e-3: long-wavelength charge
-                   oscillations).
+                   orbitals from one iteration to the next) and Anderson mixing
+                   with a 16-entry history and beta = 0.5 (with the paper's
+                   depth 5 and beta 0.7 the density residual of this 32-atom
+                   system stalls at ~1e-3: long-wavelength charge oscillations;
+                   measured on a 75^3 mesh, inner iterations to 1e-8: 50+ at
+                   depth 5 / beta 0.1, 36 at depth 16 / beta 0.5).
   The two random molecules use mu = max_k Z_k^2: twice the magnitude of the
   hydrogen-like bound -Z^2/2 on the lowest level, so H + mu is coercive with
   margin.  (The paper's 8 M sum Z^2, 1.7e4 and 2.5e4 here, makes each step's
@@ -134,7 +136,8 @@ def _mol32_p2(cells=100, coarse_cells=16, order=2, **kw):
                               n_orb=64)
     inst.mu = float(np.max(inst.Z)) ** 2
     inst.smearing = 0.01
-    inst.anderson_beta = 0.1
+    inst.anderson_beta = 0.5
+    inst.anderson_depth = 16
     return inst
 
 

@@ -72,8 +72,9 @@ def parse(argv=None):
     p.add_argument("--batch-threads", type=int, default=8)
     p.add_argument("--batch-mixed", type=int, default=1,
                    help="1: also run the batched instances in the mixed-precision mode")
-    p.add_argument("--eig-precond", type=int, default=1,
-                   help="LOBPCG preconditioner: 1 = inverse coarse stiffness on the coarse rows, 0 = diagonal")
+    p.add_argument("--eig-precond", type=int, default=2,
+                   help="LOBPCG preconditioner: inverse coarse stiffness on the coarse rows with its dense product "
+                        "on the tensor cores (2) or SIMT (1); 0 = diagonal")
     p.add_argument("--eig-adapt", type=float, default=1e-2,
                    help="adaptive LOBPCG tolerance factor (x previous inner-SCF residual)")
     p.add_argument("--poisson-sell", type=int, default=1, help="1: sliced-ELL Poisson SpMV, 0: CSR")
@@ -163,7 +164,8 @@ def workload_config(args, name, inst, sz, precision, extra=None):
                               "residual))" if args.poisson_adaptive else "tol_poisson in every solve"),
         "small_eigensolver": "LOBPCG, block vectors on the device, host Rayleigh-Ritz, %s preconditioner; "
                              "residual tolerance %g x previous inner-SCF residual in [1e-11, 1e-4]"
-                             % ("inverse coarse stiffness" if args.eig_precond else "diagonal", args.eig_adapt),
+                             % ({2: "inverse coarse stiffness (tensor-core product)", 1: "inverse coarse stiffness",
+                                 0: "diagonal"}[args.eig_precond], args.eig_adapt),
     }
     if extra:
         cfg.update(extra)
@@ -561,7 +563,7 @@ def log(msg):
     print("[bench] " + msg, file=sys.stderr, flush=True)
 
 
-def timed_steps(s, nas, torch, steps, snap_at=None):
+def timed_steps(s, nas, torch, steps, snap_at=None, inner_hist=False):
     """`steps` steps of solver s, a CUDA event on the stream (torch's current
     stream, which the solver runs on) before each step and after the last;
     returns (total ms, per-step ms, reports, eigenvalues and energy after step
@@ -574,6 +576,9 @@ def timed_steps(s, nas, torch, steps, snap_at=None):
         r, rep = s.step()
         ev[k + 1].record()
         reps.append(nas.nas_report.from_buffer_copy(rep))
+        if inner_hist:
+            h = s.get(nas.NAS_Q_INNER_HIST)
+            reps[-1].hist = [float(x) for x in h if x > 0]
         if snap_at is not None and k + 1 == snap_at:
             snap = (np.array(s.get(nas.NAS_Q_EIGVALS)), float(rep.energy))
     torch.cuda.synchronize()
@@ -698,25 +703,30 @@ def main():
         s.opt.precision = 1 if pr == "mixed" else 0
         s.opt.inner_adapt = 0.0
         s.opt.bvp_adapt = 0.0
+        s.opt.max_inner = 100
         nas.nas_set_options(s.h, s.opt)
         barrier()
-        ms_c, per_c, reps_c, snap_c = timed_steps(s, nas, torch, n_cmp, snap_at=n_cmp)
+        ms_c, per_c, reps_c, snap_c = timed_steps(s, nas, torch, n_cmp, snap_at=n_cmp,
+                                                   inner_hist=True)
         cmp[pr] = (reduce_max(ms_c, dist, "cuda"), reps_c, snap_c)
         log("comparison %s: %.1f ms for %d steps, inner %s" % (pr, ms_c, n_cmp, [r.n_inner for r in reps_c]))
     s.opt.precision = 1 if prec == "mixed" else 0
     s.opt.inner_adapt = args.inner_adapt
     s.opt.bvp_adapt = args.bvp_adapt
+    s.opt.max_inner = inst.max_inner
     nas.nas_set_options(s.h, s.opt)
     (ms_m, reps_m, (lam_mixed, e_mixed)), (ms_f, reps_f, (lam_fp64, e_fp64)) = cmp["mixed"], cmp["fp64"]
     err = lam_mixed - lam_fp64
     reps_o = reps_f if prec == "mixed" else reps_m
     comparison = {
-        "steps": n_cmp, "inner_scf": "exact (tol_inner %g in every step)" % inst.tol_scf,
+        "steps": n_cmp, "inner_scf": "exact (tol_inner %g in every step, cap 100)" % inst.tol_scf,
         "mixed": {"value": job_value(world, n_cmp, ms_m), "unit": "steps/s", "ms_per_step": ms_m / n_cmp,
                   "n_inner": [r.n_inner for r in reps_m], "drho": [r.drho for r in reps_m],
+                  "inner_residuals": [r.hist for r in reps_m],
                   "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_m, nas.PHASES)[0].items()}},
         "fp64": {"value": job_value(world, n_cmp, ms_f), "unit": "steps/s", "ms_per_step": ms_f / n_cmp,
                  "n_inner": [r.n_inner for r in reps_f], "drho": [r.drho for r in reps_f],
+                 "inner_residuals": [r.hist for r in reps_f],
                  "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_f, nas.PHASES)[0].items()}},
         "speed_ratio_mixed_over_fp64": ms_f / ms_m if ms_m > 0 else None,
         "what": "the same start state and steps in both precisions; mixed = FP32 Poisson and block PCG inside "

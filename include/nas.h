@@ -85,16 +85,21 @@ typedef struct nas_options {
                               block PCG of the N shifted problems run in FP32
                               (FP32 storage and products) inside FP64 iterative
                               refinement; residual tests, assembly, blocks, the
-                              small eigensolve and energies stay FP64               */
+                              small eigensolve and energies stay FP64.  Poisson
+                              solves asked for a relative tolerance below 1e-9
+                              run in FP64 (FP32 inner solves leave smooth-mode
+                              errors such a residual test does not resolve)    */
     int    eig_device;     /* small problems above eig_dense_max: 1 = LOBPCG with its
                               block vectors, products and Gram matrices on the
                               device (host Rayleigh-Ritz of the 3k x 3k Grams);
                               0 = the host LOBPCG                                  */
     int    eig_precond;    /* LOBPCG preconditioner: 1 = the inverse coarse stiffness
-                              (I^T K I)^-1 on the coarse rows (FP32, dense; when
-                              the block has <= 32 columns and the coarse space
-                              <= 6000 unknowns) and the diagonal on the others;
-                              0 = diag(F_A - sigma F_B)^-1 everywhere             */
+                              (I^T K I)^-1 on the coarse rows (FP32, dense; coarse
+                              spaces up to 6000 unknowns; SIMT FP32 product) and the
+                              diagonal on the others; 2 = the same with the dense
+                              product on the tensor cores (tcgen05, split TF32,
+                              FP32-level accuracy); 0 = diag(F_A - sigma F_B)^-1
+                              everywhere                                          */
     double eig_adapt;      /* factor of the adaptive LOBPCG tolerance (eig_tol <= 0):
                               eig_adapt x the previous inner-SCF residual, clamped
                               to [1e-11, 1e-4]                                     */
@@ -419,6 +424,19 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
  * Errors: NAS_E_INVALID_ARG (bad sizes or pointers, unknown layout, or a
  * vector layout whose width does not divide N or whose alignment X/Y lack),
  * NAS_E_CUDA (launch failure). */
+/* The dense product of the small eigensolver's preconditioner, W = T R:
+ * T FP32 [nH][nH] (the inverse coarse stiffness (I^T K I)^-1 of Algorithm 3's
+ * coarse space in the solver), R FP64 [nH][k], W FP64 [nH][k], device
+ * pointers, row-major; FP32 products and sums.  tc = 0: SIMT kernel (register
+ * tiles); tc = 1: tensor cores (tcgen05.mma kind::tf32 on split-TF32
+ * operands, FP32 accumulator in tensor memory, bounded mbarrier waits).
+ * Scratch for the split-K partial products (<= 16 nH k floats) is allocated
+ * and freed on `stream` (stream-ordered allocator).
+ * Errors: NAS_E_INVALID_ARG (nH < 0, k not in 1..256, NULL pointers),
+ * NAS_E_CUDA (launch or allocation failure, or a tensor-core wait that
+ * exceeded its limit). */
+int nas_dense_precond_f32(int tc, int64_t nH, int k, const float* T, const double* R, double* W, void* stream);
+
 int nas_spmm_layouts(void);
 const char* nas_spmm_layout_name(int layout);
 int nas_spmm_tuning(char* buf, size_t bytes);
@@ -454,7 +472,9 @@ int nas_coldot_f64(int64_t n, int N, const double* X, const double* Y, const dou
  *    for nas_coldot_f64.
  *  - The first call on a device looks up the array's device address on that
  *    device (the calling thread's current device); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: after cudaDeviceReset on a device, do not call this entry point
+ *    on that device again (the kept address would be stale).
  *  - All calls share the array: calls that overlap on the GPU (different
  *    streams or host threads) race and may return wrong sums; serialise
  *    them.  Each call writes every scratch entry it reads, so nothing needs

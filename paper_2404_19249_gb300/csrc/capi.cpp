@@ -204,7 +204,7 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
         if (o->tol_bvp <= 0 || o->tol_poisson <= 0 || o->max_cg < 1 || o->max_poisson < 1 || o->max_inner < 1 ||
             o->anderson_depth < 1 || o->anderson_depth > 16 || o->precision < 0 || o->precision > 1 ||
             o->eig_device < 0 || o->eig_device > 1 || o->poisson_adaptive < 0 || o->poisson_adaptive > 1 ||
-            !(o->eig_adapt > 0.0) || o->eig_adapt > 1.0 || o->eig_precond < 0 || o->eig_precond > 1 ||
+            !(o->eig_adapt > 0.0) || o->eig_adapt > 1.0 || o->eig_precond < 0 || o->eig_precond > 2 ||
             o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1 ||
             !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0) || o->bvp_two_level < 0 || o->bvp_two_level > 1 ||
             !(o->bvp_adapt >= 0.0))
@@ -363,6 +363,28 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, con
     } catch (const Error& e) {
         return e.code;
     }
+}
+
+int nas_dense_precond_f32(int tc, int64_t nH, int k, const float* T, const double* R, double* W, void* stream) {
+    if (nH < 0 || k < 1 || k > 256 || !T || !R || !W) return NAS_E_INVALID_ARG;
+    if (nH == 0) return NAS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* part = nullptr;
+    const size_t bytes = sizeof(float) * (size_t)nas::dense_precond_part_size(nH, k);
+    if (cudaMallocAsync(reinterpret_cast<void**>(&part), bytes, s) != cudaSuccess) return NAS_E_CUDA;
+    int rc = NAS_OK;
+    try {
+        if (tc) {
+            nas::launch_dense_precond_tc(nH, nH, k, T, R, nullptr, part, W, s);
+            if (nas::tc_error_take(s)) rc = NAS_E_CUDA;
+        } else {
+            nas::launch_dense_precond(nH, nH, k, T, R, nullptr, part, W, s);
+        }
+    } catch (const Error& e) {
+        rc = e.code;
+    }
+    if (cudaFreeAsync(part, s) != cudaSuccess && rc == NAS_OK) rc = NAS_E_CUDA;
+    return rc;
 }
 
 int nas_spmm_layouts(void) { return nas::spmm_num_layouts(); }

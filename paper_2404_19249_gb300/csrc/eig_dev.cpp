@@ -202,7 +202,7 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
         // W = T R(:, act)
         launch_gather_cols(m, k, ka, actd.p, R, P2, s);
         if (TH)
-            launch_dense_precond(A.nH, m, ka, TH, P2, T.p, ppart.p, W, s);
+            (tc ? launch_dense_precond_tc : launch_dense_precond)(A.nH, m, ka, TH, P2, T.p, ppart.p, W, s);
         else
             launch_scale_rows(m, ka, T.p, P2, W, s);
         // W <- W - X (BX^T W), then unit B-norm columns (AW scaled alike)

@@ -23,6 +23,7 @@ struct DevLobpcg {
     int x0_k = 0;
     int64_t m_cap = 0;
     int k_cap = 0;
+    bool tc = false;      // the dense preconditioner product on the tensor cores
     double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)
     double wait_ms = 0.0; // host time waiting for the device in synchronisations
     // pinned staging area for the per-iteration transfers (Grams, norms,

@@ -282,6 +282,16 @@ void launch_inv_sqrt_scale(int64_t m, int k, const double* nrm, double* A1, doub
 // remaining m - nH rows; R, W [m][k] FP64, k <= 32; part: FP32 scratch of
 // dense_precond_part_size(nH, k)
 int64_t dense_precond_part_size(int64_t nH, int k);
+// the same product on the tensor cores (kernels_tc.cu): tcgen05.mma of kind
+// tf32 with split-TF32 operands (FP32-level accuracy), FP32 accumulator in
+// tensor memory; k <= 256; part holds dense_precond_tc_part_size doubles' worth
+// of floats
+void launch_dense_precond_tc(int64_t nH, int64_t m, int k, const float* T, const double* R, const double* Dinv,
+                             float* part, double* W, cudaStream_t s);
+int64_t dense_precond_tc_part_size(int64_t nH, int k);
+// true if a tensor-core CTA gave up waiting on its mbarrier since the last
+// call (the flag is cleared); synchronises s
+bool tc_error_take(cudaStream_t s);
 void launch_dense_precond(int64_t nH, int64_t m, int k, const float* T, const double* R, const double* Dinv,
                           float* part, double* W, cudaStream_t s);
 // T[i] = 1 / (A_ii - sigma B_ii), diag_slot[i] = CSR slot of (i, i) in the coarse block

@@ -1,0 +1,272 @@
+// Tensor-core product W = T R for the LOBPCG preconditioner of the small
+// problem (T = (I^T K I)^-1, the dense inverse coarse stiffness, FP32,
+// nH x nH; R the block of residual rows, nH x k), on the 5th-generation
+// tensor cores of sm_103a: tcgen05.mma with its accumulator in tensor memory.
+//
+// Precision: split TF32.  Each FP32 operand x is held as x_hi = tf32(x) and
+// x_lo = tf32(x - x_hi); the product is accumulated as hi*hi + hi*lo + lo*hi
+// (the lo*lo term is below FP32 rounding), in FP32 in tensor memory, which
+// keeps FP32-level accuracy (Markidis et al. 2018; Ootomo and Yokota 2022).
+// The preconditioner needs no more: it is a fixed SPD approximation of an
+// inverse inside LOBPCG.
+//
+// Layout: the operands are staged by the CTA's threads in shared memory in
+// the canonical K-major layout without swizzling: 8-row x 16-byte core
+// matrices, the 8 core matrices of one 8-row group and one 32-element K tile
+// contiguous (leading byte offset 128 between K-adjacent core matrices,
+// stride byte offset 1024 between 8-row groups).  One tcgen05.mma of kind
+// tf32 consumes K = 8 (two core matrices); a K tile of 32 takes four of them
+// per split term.  A = T rows (K-major as T is stored), B = R^T: the
+// staging loop reads R's rows (FP64), converts, splits and writes them
+// transposed into the K-major layout; N is padded to a multiple of 16 (the
+// MMA's N for M = 128) with zero columns.
+//
+// Work split: one CTA per 128-row tile of T and K range (split K, kTcSplit
+// ranges), 128 threads; thread 0 issues the MMAs and commits them to an
+// mbarrier; every wait on it is bounded (kTcSpin polls): on timeout the CTA
+// records the error, frees its tensor memory and returns.  The CTA's FP32
+// partial product goes to part[split][row][col], the layout of the FP32 SIMT
+// kernel's stage 1, and the same stage 2 adds the splits in order.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace nas {
+
+namespace {
+
+const int kTcM = 128;        // rows per CTA (MMA M)
+const int kTcK = 32;         // K tile (floats)
+const int kTcSplit = 12;     // K ranges
+const int kTcThreads = 128;
+const long long kTcSpin = 20000000;   // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// shared memory matrix descriptor: start address, leading and stride byte
+// offsets (16-byte units), descriptor version 1 (bits 46-48), no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// bounded wait for the phase with parity `par` to complete; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t par) {
+    for (long long it = 0; it < kTcSpin; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, q;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(par)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+__device__ int g_tc_error = 0;   // set when a CTA's mbarrier wait ran out (never expected)
+
+__device__ __forceinline__ uint32_t canon_off(int r, int kk) {
+    return (uint32_t)((r >> 3) * 1024 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4);
+}
+
+// part[sp][i][j] = sum over b in K range sp of T[i][b] R[b][j], i in the CTA's
+// 128 rows, j < k.  Dynamic shared memory: A_hi, A_lo (128 x 32 floats each),
+// B_hi, B_lo (Npad x 32 floats each), 1024-byte aligned.
+__global__ void __launch_bounds__(kTcThreads) k_tc_precond_part(int64_t nH, int k, int Npad, const float* T,
+                                                               const double* R, float* part) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    unsigned char* base = tc_smem;
+    // the dynamic area starts 1024-aligned (launch adds 1024 bytes of slack)
+    base += (1024 - (smem_u32(base) & 1023)) & 1023;
+    float* Ahi = reinterpret_cast<float*>(base);
+    float* Alo = Ahi + kTcM * kTcK;
+    float* Bhi = Alo + kTcM * kTcK;
+    float* Blo = Bhi + Npad * kTcK;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int64_t row0 = (int64_t)blockIdx.x * kTcM;
+    const int64_t span = (nH + kTcSplit - 1) / kTcSplit;
+    const int64_t kb = (int64_t)blockIdx.y * span;
+    const int64_t ke = kb + span < nH ? kb + span : nH;
+    const uint32_t ncols = Npad <= 32 ? 32u : Npad <= 64 ? 64u : Npad <= 128 ? 128u : 256u;
+    const uint32_t mb = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(mb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_tf32(kTcM, Npad);
+    bool ok = true;
+    uint32_t phase = 0;
+    bool first = true;
+    for (int64_t k0 = kb; k0 < ke && ok; k0 += kTcK) {
+        // stage the A tile (rows of T) and the B tile (columns of R), split into
+        // TF32 hi and lo parts, zero outside the matrix and the K range
+        for (int idx = tid; idx < kTcM * kTcK; idx += kTcThreads) {
+            const int r = idx / kTcK, kk = idx % kTcK;
+            const int64_t i = row0 + r, b = k0 + kk;
+            const float x = (i < nH && b < ke) ? T[i * nH + b] : 0.f;
+            const float hi = __uint_as_float(tf32_bits(x));
+            const float lo = __uint_as_float(tf32_bits(x - hi));
+            const uint32_t o = canon_off(r, kk) / 4;
+            Ahi[o] = hi;
+            Alo[o] = lo;
+        }
+        for (int idx = tid; idx < Npad * kTcK; idx += kTcThreads) {
+            const int kk = idx / Npad, j = idx % Npad;
+            const int64_t b = k0 + kk;
+            const float x = (j < k && b < ke) ? (float)R[b * k + j] : 0.f;
+            const float hi = __uint_as_float(tf32_bits(x));
+            const float lo = __uint_as_float(tf32_bits(x - hi));
+            const uint32_t o = canon_off(j, kk) / 4;
+            Bhi[o] = hi;
+            Blo[o] = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll
+            for (int ks = 0; ks < kTcK / 8; ++ks) {
+                const uint32_t off = (uint32_t)ks * 256;   // K = 8 tf32 = two 16-byte core matrices
+                mma_tf32(tmem, smem_desc(ah + off, 128, 1024), smem_desc(bh + off, 128, 1024), idesc, first ? 0u : 1u);
+                first = false;
+                mma_tf32(tmem, smem_desc(ah + off, 128, 1024), smem_desc(bl + off, 128, 1024), idesc, 1u);
+                mma_tf32(tmem, smem_desc(al + off, 128, 1024), smem_desc(bh + off, 128, 1024), idesc, 1u);
+            }
+            mma_commit(mb);
+        }
+        first = false;
+        // the tile buffers are reused: wait until the MMAs that read them are done
+        ok = mbar_wait(mb, phase);
+        phase ^= 1u;
+        ok = __syncthreads_and(ok) != 0;
+    }
+    if (!ok) {
+        atomicExch(&g_tc_error, 1);
+        mbar_wait(mb, phase ^ 1u);   // bounded second wait for the MMAs in flight
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && kb < ke) {
+        // accumulator rows 32 w .. 32 w + 31 live in tensor memory lanes of warp w
+        const int64_t i = row0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < Npad; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (i < nH)
+                for (int q = 0; q < 16; ++q) {
+                    const int j = c0 + q;
+                    if (j < k) part[((int64_t)blockIdx.y * nH + i) * k + j] = __uint_as_float(v[q]);
+                }
+        }
+    } else if (ok) {
+        // empty K range: this split contributes zeros
+        const int64_t i = row0 + 32 * warp + lane;
+        if (i < nH)
+            for (int j = 0; j < k; ++j) part[((int64_t)blockIdx.y * nH + i) * k + j] = 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// W[i][j] = sum_sp part[sp][i][j] (i < nH, splits in order); W[i][j] = Dinv[i] R[i][j] (nH <= i < m)
+__global__ void k_tc_precond_sum(int64_t nH, int64_t m, int k, const float* part, const double* R,
+                                 const double* Dinv, double* W) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * k) return;
+    const int64_t i = t / k;
+    if (i < nH) {
+        float acc = 0.f;
+        for (int sp = 0; sp < kTcSplit; ++sp) acc += part[(int64_t)sp * nH * k + t];
+        W[t] = (double)acc;
+    } else {
+        W[t] = Dinv[i] * R[t];
+    }
+}
+
+void launch_dense_precond_tc(int64_t nH, int64_t m, int k, const float* T, const double* R, const double* Dinv,
+                             float* part, double* W, cudaStream_t s) {
+    if (k < 1 || k > 256) fail(NAS_E_INVALID_ARG, "tensor-core preconditioner: block width out of range");
+    if (m <= 0) return;
+    if (nH > 0) {
+        const int Npad = (k + 15) / 16 * 16;
+        const size_t smem = 1024 + sizeof(float) * (size_t)kTcK * (2 * kTcM + 2 * Npad);
+        NAS_CUDA(cudaFuncSetAttribute(k_tc_precond_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((unsigned)((nH + kTcM - 1) / kTcM), kTcSplit);
+        k_tc_precond_part<<<grid, kTcThreads, smem, s>>>(nH, k, Npad, T, R, part);
+        NAS_CHECK_LAUNCH();
+    }
+    k_tc_precond_sum<<<grid_for(m * k, 256), 256, 0, s>>>(nH, m, k, part, R, Dinv, W);
+    NAS_CHECK_LAUNCH();
+}
+
+int64_t dense_precond_tc_part_size(int64_t nH, int k) { return (int64_t)kTcSplit * nH * k; }
+
+bool tc_error_take(cudaStream_t s) {
+    int v = 0, zero = 0;
+    NAS_CUDA(cudaMemcpyFromSymbolAsync(&v, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    NAS_CUDA(cudaStreamSynchronize(s));
+    if (v) NAS_CUDA(cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    return v != 0;
+}
+
+}  // namespace nas

@@ -18,7 +18,11 @@
 //    symbol is only a stand-in); the device address is looked up once per
 //    device with cudaGetSymbolAddress, the first time this entry point runs
 //    on that device, with that device current.  That first call performs
-//    this set-up and should therefore come before any stream capture;
+//    this set-up and should therefore come before any stream capture.  The
+//    address belongs to the device's primary context: after cudaDeviceReset
+//    (or anything else that destroys that context) the cached address is
+//    stale, so a process that resets a device must not call this entry
+//    point on it again;
 //  * all calls share the one array: calls that overlap on the GPU (on
 //    different streams, or from different host threads) race and may return
 //    wrong sums.  Serialise them, e.g. on one stream.  Each call writes every

@@ -94,6 +94,7 @@ def _load():
         "nas_apply": (C.c_int, [VP, C.c_int, VP, I64, VP, C.c_int]),
         "nas_batch_run": (C.c_int, [P(VP), C.c_int, C.c_int, C.c_int, P(C.c_int), P(nas_report)]),
         "nas_spmm_f64": (C.c_int, [I64, VP, VP, VP, C.c_int, VP, VP, VP]),
+        "nas_dense_precond_f32": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP]),
         "nas_spmm_layouts": (C.c_int, []),
         "nas_spmm_layout_name": (C.c_char_p, [C.c_int]),
         "nas_spmm_tuning": (C.c_int, [C.c_char_p, C.c_size_t]),
@@ -115,6 +116,7 @@ EXPORTS = [
     "nas_set_system", "nas_set_options", "nas_init", "nas_step", "nas_solve", "nas_get", "nas_set_state",
     "nas_apply", "nas_batch_run", "nas_spmm_f64", "nas_coldot_f64", "nas_coldot_f64_noalloc",
     "nas_spmm_layouts", "nas_spmm_layout_name", "nas_spmm_tuning", "nas_spmm_f64_layout", "nas_spmm_f32_layout",
+    "nas_dense_precond_f32",
 ]
 
 
@@ -241,6 +243,15 @@ def nas_spmm_f64(n_rows, row_ptr, col, val, N, X, Y, stream=0):
                          C.c_void_p(Y), C.c_void_p(stream or None))
     if r != NAS_OK:
         raise NasError(r, "nas_spmm_f64")
+    return r
+
+
+def nas_dense_precond_f32(tc, nH, k, T, R, W, stream=0):
+    """W = T R for device pointers (T FP32 [nH][nH], R, W FP64 [nH][k]); tc=1 on the tensor cores."""
+    r = lib.nas_dense_precond_f32(int(tc), nH, k, C.c_void_p(T), C.c_void_p(R), C.c_void_p(W),
+                                  C.c_void_p(stream or None))
+    if r != NAS_OK:
+        raise NasError(r, "nas_dense_precond_f32")
     return r
 
 

@@ -329,11 +329,15 @@ def test_mixed_precision_poisson_matches_fp64(nasmod):
     P = Problem(inst)
     res = {}
     for prec in (0, 1):
-        s = nasmod.Solver(inst, precision=prec)
+        # adaptive inner Poisson tolerance: the early inner iterations ask for
+        # loose tolerances, which the mixed form solves with FP32 inner PCG
+        s = nasmod.Solver(inst, precision=prec, poisson_adaptive=1, timing=1)
         s.init()
         for _ in range(2):
             r, rep = s.step()
             assert r == 0
+            spmv32 = rep.phase_calls[nasmod.PHASES.index("spmv32")]
+            assert (spmv32 > 0) == (prec == 1)
         res[prec] = (s.get(nasmod.NAS_Q_EIGVALS), s.get(nasmod.NAS_Q_ENERGY)[0])
         s.close()
     assert np.max(np.abs(res[1][0] - res[0][0])) < 1e-8

@@ -87,3 +87,31 @@ def test_moving_mesh_levels_through_the_library():
     # the adapted meshes refine around the nucleus
     assert hist[2]["min_cell"] < hist[0]["min_cell"]
     solver.close()
+
+
+@pytest.mark.gpu
+def test_moving_mesh_levels_match_oracle_direct_scf():
+    """Every level of the moving-mesh loop converges to the discrete ground
+    state of that level's mesh: the oracle's direct SCF on the whole fine
+    space (the plain definition) on the same adapted axes gives the same
+    eigenvalue and energy, at 1e-10 relative."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import dataclasses
+    from oracle.nas import Problem
+    from paper_2404_19249_gb300 import nas
+    from workloads import make_instance
+    inst = make_instance("he_p1", cells=8, coarse_cells=3, tol_scf=1e-12, mu=2.0, max_outer=600)
+    hist, solver = moving_mesh_solve(inst, levels=3, tol_energy=0.0, alpha=8.0, tol_bvp=1e-14, tol_poisson=1e-14)
+    solver.close()
+    assert len(hist) == 3
+    for h in hist:
+        assert h["status"] == 0 and h["drho"] < 1e-11
+        xyz, tet = kuhn_mesh(*h["axes"])
+        lv = dataclasses.replace(inst, fine_xyz=xyz, fine_tet=tet, tol_bvp=1e-14, tol_poisson=1e-14)
+        P = Problem(lv, with_transfer=False)
+        d = P.direct_scf(tol=1e-12)
+        assert d.inner_converged
+        E = P.energy(d)
+        assert abs(h["energy"] - E) < 1e-10 * abs(E), (h["level"], h["energy"], E)

@@ -63,6 +63,9 @@ def parse(argv=None):
                    help="inexact inner SCF: stop at max(tol_inner, inner_adapt x previous step's drho)")
     p.add_argument("--bvp-adapt", type=float, default=1e-2,
                    help="inexact linear solves: max(tol_bvp, min(1e-4, bvp_adapt x previous step's drho))")
+    p.add_argument("--anderson-restart", type=float, default=None,
+                   help="clear the Anderson history at a residual above this x the inner SCF's best "
+                        "(default: the workload's setting)")
     p.add_argument("--spmv-lanes", type=int, default=0)
     p.add_argument("--clocks-file", default=None, help="where to keep the nvidia-smi clock samples")
     p.add_argument("--batch", type=int, default=0,
@@ -102,10 +105,13 @@ def instance(name, cells=None, coarse_cells=None):
 
 
 def solver_options(args, timing=1):
-    return dict(timing=timing, tol_poisson=args.tol_poisson, tol_bvp=args.tol_bvp, check_every=4,
-                spmv_lanes=args.spmv_lanes, poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt,
-                eig_precond=args.eig_precond, poisson_sell=args.poisson_sell, poisson_fused=args.poisson_fused,
-                inner_adapt=args.inner_adapt, bvp_adapt=args.bvp_adapt)
+    o = dict(timing=timing, tol_poisson=args.tol_poisson, tol_bvp=args.tol_bvp, check_every=4,
+             spmv_lanes=args.spmv_lanes, poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt,
+             eig_precond=args.eig_precond, poisson_sell=args.poisson_sell, poisson_fused=args.poisson_fused,
+             inner_adapt=args.inner_adapt, bvp_adapt=args.bvp_adapt)
+    if args.anderson_restart is not None:
+        o["anderson_restart"] = args.anderson_restart
+    return o
 
 
 def kernel_source_hash(name, kernel):

@@ -149,6 +149,10 @@ typedef struct nas_options {
                               rho^(l-1)||_0)); the outer fixed point is unchanged
                               (near it the solves again reach tol_bvp).
                               0: tol_bvp in every step                          */
+    double anderson_restart; /* > 0: in an inner SCF a density residual above
+                              anderson_restart x the smallest one of that inner
+                              SCF so far clears the Anderson history (the next
+                              mix is the linear one); 0: never                 */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -158,7 +162,8 @@ typedef struct nas_options {
  * eig_dense_max = 1200, eig_tol = -1 (adaptive), spmv_lanes = 0 (auto),
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
  * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0,
- * smearing = 0, inner_adapt = 0, bvp_two_level = 0, bvp_adapt = 0. */
+ * smearing = 0, inner_adapt = 0, bvp_two_level = 0, bvp_adapt = 0,
+ * anderson_restart = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */

@@ -42,6 +42,9 @@ Readings (where the paper is silent, ambiguous or garbled):
   * initial guess: the self-consistent solution in the coarse space alone
     (S_H carried to the fine mesh by I), from rho = 0, by the same inner SCF.
   * mu defaults to the experiments' 8 M sum_k Z_k^2.
+  * Anderson restart (option, off by default): in the inner SCF a density
+    residual above anderson_restart x the best residual so far clears the
+    mixing history.
   * occupations: the given f_i (closed shell), or, with smearing kT > 0,
     Fermi-Dirac f_i = 2/(1 + exp((lambda_i - eF)/kT)) with sum f_i equal to the
     electron count, recomputed after every small eigensolve; the energy is
@@ -273,6 +276,7 @@ class Problem:
         rho_in = rho_start.copy()
         VH_prev = VH_start
         hist = []
+        restart = float(getattr(inst, "anderson_restart", 0.0))
         for t in range(max_inner):
             VH, VHq, eps, vxc = self.nonlinear(rho_in, VH_prev)
             VH_prev = VH
@@ -289,6 +293,10 @@ class Problem:
                              {"res_hist": hist, "U": U, "eps": eps, "vxc": vxc, "VHq": VHq})
             if t == max_inner - 1:
                 break
+            # optional safeguard: a residual above `restart` x the best one of
+            # this inner SCF clears the history (the next mix is linear)
+            if restart > 0.0 and t > 0 and res > restart * min(hist[:-1]):
+                mixer.hist.clear()
             rho_in = mixer.mix(rho_in, rho_out)
         return State(lam, Psi, rho_in, rho_out, VH, occ, mts, max_inner, res, False,
                      {"res_hist": hist, "U": U, "eps": eps, "vxc": vxc, "VHq": VHq})

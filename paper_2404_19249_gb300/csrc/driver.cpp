@@ -1229,6 +1229,12 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
             ++t;
             break;
         }
+        // optional safeguard: a residual above anderson_restart x the smallest one
+        // of this inner SCF clears the history, so the next mix is the linear one
+        if (c->opt.anderson_restart > 0.0 && c->inner_hist.size() > 1 &&
+            res > c->opt.anderson_restart *
+                      *std::min_element(c->inner_hist.begin(), c->inner_hist.end() - 1))
+            A.hist.clear();
         anderson_mix(c, A);
         c->anl_valid = false;
     }

@@ -43,6 +43,7 @@ class nas_options(C.Structure):
         ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
         ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int), ("poisson_fused", C.c_int),
         ("smearing", C.c_double), ("inner_adapt", C.c_double), ("bvp_two_level", C.c_int), ("bvp_adapt", C.c_double),
+        ("anderson_restart", C.c_double),
     ]
 
 
@@ -312,6 +313,7 @@ class Solver:
         o.smearing = float(getattr(inst, "smearing", 0.0))
         o.anderson_depth = int(getattr(inst, "anderson_depth", 5))
         o.anderson_beta = float(getattr(inst, "anderson_beta", 0.7))
+        o.anderson_restart = float(getattr(inst, "anderson_restart", 0.0))
         for k, v in options.items():
             setattr(o, k, v)
         self.opt = o

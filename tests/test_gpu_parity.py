@@ -377,14 +377,18 @@ def test_smeared_occupations_lockstep(nasmod):
         s.close()
 
 
-def test_deep_anderson_history_lockstep(nasmod):
+@pytest.mark.parametrize("restart", [0.0, 1.5])
+def test_deep_anderson_history_lockstep(nasmod, restart):
     """Anderson mixing with a 6-entry history (beta 0.15): LiH's inner SCF
     takes 20-30 iterations, so the history wraps around several times;
     initial SCF and two steps against the oracle's mixing with the same depth,
-    eigenvalues and energies at 1e-10."""
+    eigenvalues and energies at 1e-10.  With restart 1.5 the history is
+    cleared at the residual jumps of 1.70x, 2.29x (initial SCF) and 1.52x
+    (first step) over the best residual, the same iterations on both sides."""
     inst = _tight(make_instance("paper_molecule", molecule="lih", cells=8, coarse_cells=4))
     inst.anderson_depth = 6
     inst.anderson_beta = 0.15
+    inst.anderson_restart = restart
     P = Problem(inst)
     st = P.initial_state()
     assert st.inner_converged and st.n_inner > 12

@@ -52,7 +52,7 @@ def parse(argv=None):
     p.add_argument("--cells", type=int, default=None)
     p.add_argument("--coarse-cells", type=int, default=None)
     p.add_argument("--compare-steps", type=int, default=3,
-                   help="steps of the other precision, from the same start state (<= --steps)")
+                   help="steps of both precisions from the timed run's start state (<= --steps; 0: none)")
     p.add_argument("--e2e-steps", type=int, default=-1, help="-1: the same count as --steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-secondary", action="store_true", help="skip the 8-nucleus and helium lines")
@@ -83,6 +83,8 @@ def parse(argv=None):
     p.add_argument("--poisson-sell", type=int, default=1, help="1: sliced-ELL Poisson SpMV, 0: CSR")
     p.add_argument("--poisson-fused", type=int, default=0,
                    help="1: persistent cooperative Poisson PCG kernel, 0: per-phase kernels from a CUDA graph")
+    p.add_argument("--poisson-f32", type=int, default=0,
+                   help="mixed precision: 1 = FP32 Poisson solves for tolerances >= 1e-9, 0 = FP64 Poisson")
     p.add_argument("--poisson-adaptive", type=int, default=1,
                    help="1: inner Poisson tolerance follows the density residual (fixed point unchanged)")
     return p.parse_args(argv)
@@ -108,7 +110,7 @@ def solver_options(args, timing=1):
     o = dict(timing=timing, tol_poisson=args.tol_poisson, tol_bvp=args.tol_bvp, check_every=4,
              spmv_lanes=args.spmv_lanes, poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt,
              eig_precond=args.eig_precond, poisson_sell=args.poisson_sell, poisson_fused=args.poisson_fused,
-             inner_adapt=args.inner_adapt, bvp_adapt=args.bvp_adapt)
+             inner_adapt=args.inner_adapt, bvp_adapt=args.bvp_adapt, poisson_f32=args.poisson_f32)
     if args.anderson_restart is not None:
         o["anderson_restart"] = args.anderson_restart
     return o
@@ -687,12 +689,12 @@ def main():
     get(nas.NAS_Q_EIGVALS, s0_lam)
     get(nas.NAS_Q_ORBITALS, s0_psi)
     get(nas.NAS_Q_RHO_IN, s0_rho)
-    n_cmp = max(1, min(args.compare_steps, args.steps))
+    n_cmp = max(0, min(args.compare_steps, args.steps))
     barrier()
     clocks = Clocks(args.clocks_file or "/tmp/bench_clocks_%d.csv" % os.getpid())
     clocks.start()
     torch.cuda.nvtx.range_push("timed")
-    ms, per_h, reps, snap = timed_steps(s, nas, torch, args.steps, snap_at=n_cmp)
+    ms, per_h, reps, snap = timed_steps(s, nas, torch, args.steps, snap_at=n_cmp or None)
     torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop(local)
@@ -704,7 +706,7 @@ def main():
     # exact inner SCF (tol_inner in every step), so that the per-eigenvalue
     # difference measures the precision and not a looser inner stop
     cmp = {}
-    for pr in ("mixed", "fp64"):
+    for pr in ("mixed", "fp64") if n_cmp > 0 else ():
         nas.nas_set_state(s.h, s0_lam.data_ptr(), s0_psi.data_ptr(), s0_rho.data_ptr(), 0)
         s.opt.precision = 1 if pr == "mixed" else 0
         s.opt.inner_adapt = 0.0
@@ -721,25 +723,28 @@ def main():
     s.opt.bvp_adapt = args.bvp_adapt
     s.opt.max_inner = inst.max_inner
     nas.nas_set_options(s.h, s.opt)
-    (ms_m, reps_m, (lam_mixed, e_mixed)), (ms_f, reps_f, (lam_fp64, e_fp64)) = cmp["mixed"], cmp["fp64"]
-    err = lam_mixed - lam_fp64
-    reps_o = reps_f if prec == "mixed" else reps_m
-    comparison = {
-        "steps": n_cmp, "inner_scf": "exact (tol_inner %g in every step, cap 100)" % inst.tol_scf,
-        "mixed": {"value": job_value(world, n_cmp, ms_m), "unit": "steps/s", "ms_per_step": ms_m / n_cmp,
-                  "n_inner": [r.n_inner for r in reps_m], "drho": [r.drho for r in reps_m],
-                  "inner_residuals": [r.hist for r in reps_m],
-                  "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_m, nas.PHASES)[0].items()}},
-        "fp64": {"value": job_value(world, n_cmp, ms_f), "unit": "steps/s", "ms_per_step": ms_f / n_cmp,
-                 "n_inner": [r.n_inner for r in reps_f], "drho": [r.drho for r in reps_f],
-                 "inner_residuals": [r.hist for r in reps_f],
-                 "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_f, nas.PHASES)[0].items()}},
-        "speed_ratio_mixed_over_fp64": ms_f / ms_m if ms_m > 0 else None,
-        "what": "the same start state and steps in both precisions; mixed = FP32 Poisson and block PCG inside "
-                "FP64 iterative refinement, all else FP64",
-        "max_eigenvalue_err_ha": float(np.max(np.abs(err))), "eigenvalue_err_ha": [float(x) for x in err],
-        "energy_err_ha": float(e_mixed - e_fp64),
-    }
+    comparison, reps_o = {"skipped": "compare-steps 0"}, []
+    if n_cmp > 0:
+        (ms_m, reps_m, (lam_mixed, e_mixed)), (ms_f, reps_f, (lam_fp64, e_fp64)) = cmp["mixed"], cmp["fp64"]
+        err = lam_mixed - lam_fp64
+        reps_o = reps_f if prec == "mixed" else reps_m
+        comparison = {
+            "steps": n_cmp, "inner_scf": "exact (tol_inner %g in every step, cap 100)" % inst.tol_scf,
+            "mixed": {"value": job_value(world, n_cmp, ms_m), "unit": "steps/s", "ms_per_step": ms_m / n_cmp,
+                      "n_inner": [r.n_inner for r in reps_m], "drho": [r.drho for r in reps_m],
+                      "inner_residuals": [r.hist for r in reps_m],
+                      "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_m, nas.PHASES)[0].items()}},
+            "fp64": {"value": job_value(world, n_cmp, ms_f), "unit": "steps/s", "ms_per_step": ms_f / n_cmp,
+                     "n_inner": [r.n_inner for r in reps_f], "drho": [r.drho for r in reps_f],
+                     "inner_residuals": [r.hist for r in reps_f],
+                     "phase_ms_per_step": {k: v / n_cmp for k, v in phase_totals(reps_f, nas.PHASES)[0].items()}},
+            "speed_ratio_mixed_over_fp64": ms_f / ms_m if ms_m > 0 else None,
+            "what": "the same start state and steps in both precisions; mixed = FP32 block PCG of the shifted "
+                    "problems%s inside FP64 iterative refinement, all else FP64"
+                    % (" and FP32 Poisson PCG (tolerances >= 1e-9)" if args.poisson_f32 else ""),
+            "max_eigenvalue_err_ha": float(np.max(np.abs(err))), "eigenvalue_err_ha": [float(x) for x in err],
+            "energy_err_ha": float(e_mixed - e_fp64),
+        }
     log("comparison: %s" % json.dumps({k: v for k, v in comparison.items() if k != "eigenvalue_err_ha"}))
 
     # ------------------------------------------------------------ rooflines from the live CUDA-event timings
@@ -748,7 +753,7 @@ def main():
     nz = N if getattr(inst, "smearing", 0.0) > 0 else int(np.sum(np.asarray(inst.occ) > 0))
     lay = tuned_layouts(nas, sz)
     roofs_h = kernel_rooflines(reps, sz, args.steps, nas.PHASES, peak, psrc, nz_occ=nz, layouts=lay)
-    roofs_o = kernel_rooflines(reps_o, sz, n_cmp, nas.PHASES, peak, psrc, nz_occ=nz, layouts=lay)
+    roofs_o = kernel_rooflines(reps_o, sz, n_cmp, nas.PHASES, peak, psrc, nz_occ=nz, layouts=lay) if reps_o else {}
     tuner = [r for r in nas.nas_spmm_tuning() if r["rows"] == sz["n"]]
     trf = spmv_traffic(sz, "k_pcg1_spmv_sell")
     for rr in (roofs_h, roofs_o):
@@ -850,7 +855,7 @@ def main():
                 pass
 
     last = reps[-1]
-    dom_h, dom_o = dominant(roofs_h), dominant(roofs_o)
+    dom_h, dom_o = dominant(roofs_h), (dominant(roofs_o) if roofs_o else None)
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -870,7 +875,7 @@ def main():
         "cpu_baseline": cpu, "setup_s": setup_s, "energy_ha": float(last.energy),
         "secondary": secondary,
     }
-    line["speed_ratio_mixed_over_fp64"] = comparison["speed_ratio_mixed_over_fp64"]
+    line["speed_ratio_mixed_over_fp64"] = comparison.get("speed_ratio_mixed_over_fp64")
     line["speed_ratio_note"] = ("FP64 ms over mixed ms for the same %d steps from the same start state, both with "
                                 "the exact inner SCF (CUDA events)" % n_cmp)
     line["per_step"]["ms"] = per_h

@@ -153,6 +153,16 @@ typedef struct nas_options {
                               anderson_restart x the smallest one of that inner
                               SCF so far clears the Anderson history (the next
                               mix is the linear one); 0: never                 */
+    int    poisson_f32;    /* precision = 1 only.  1: Poisson solves whose tolerance
+                              is >= 1e-9 run as FP32 PCG inside FP64 iterative
+                              refinement, tighter ones in FP64 to tol_poisson;
+                              0: every Poisson solve in FP64 (the block PCG of
+                              the shifted problems stays mixed).  Measured on the
+                              32-nucleus workload with poisson_adaptive = 1: the
+                              FP32 solves to the adaptive tolerance leave smooth
+                              V_H errors that a residual test relative to ||b||
+                              does not see, and an exact inner SCF then stalls
+                              near a density residual of 1e-3                   */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -163,7 +173,7 @@ typedef struct nas_options {
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
  * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0,
  * smearing = 0, inner_adapt = 0, bvp_two_level = 0, bvp_adapt = 0,
- * anderson_restart = 0. */
+ * anderson_restart = 0, poisson_f32 = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */

@@ -92,6 +92,7 @@ void nas_default_options(nas_options* o) {
     o->bvp_two_level = 0;
     o->bvp_adapt = 0.0;
     o->anderson_restart = 0.0;
+    o->poisson_f32 = 0;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -208,7 +209,8 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
             !(o->eig_adapt > 0.0) || o->eig_adapt > 1.0 || o->eig_precond < 0 || o->eig_precond > 2 ||
             o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1 ||
             !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0) || o->bvp_two_level < 0 || o->bvp_two_level > 1 ||
-            !(o->bvp_adapt >= 0.0) || !(o->anderson_restart >= 0.0))
+            !(o->bvp_adapt >= 0.0) || !(o->anderson_restart >= 0.0) ||
+            o->poisson_f32 < 0 || o->poisson_f32 > 1)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level) || (o->eig_precond != c->opt.eig_precond);

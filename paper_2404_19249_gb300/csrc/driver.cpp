@@ -747,15 +747,17 @@ static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
     Csr K = fcsr(c, c->d_K.p);
     K.rowptr_nnz = c->F.nnz();
     double tol = c->poisson_tol_now > 0.0 ? c->poisson_tol_now : c->opt.tol_poisson;
-    // mixed precision: FP32 inner solves only for tolerances >= kMixedPoissonTolMin.
-    // A residual test relative to ||b|| hardly sees the smooth-mode error that
-    // FP32 inner solves leave in V_H (measured on the 32-nucleus workload: the
-    // inner SCF then stalls at a density residual of 2-6e-8, above tol_inner =
-    // 1e-8), so the tight solves of the last inner iterations run in FP64 and
-    // to tol_poisson itself: warm-started from a V_H that carries that error,
-    // a solve to the adaptive 1e-3 x residual stops before it is removed.
-    const bool f32 = c->opt.precision == 1 && tol >= kMixedPoissonTolMin;
-    if (c->opt.precision == 1 && !f32) tol = std::min(tol, c->opt.tol_poisson);
+    // mixed precision with poisson_f32: FP32 inner solves only for tolerances >=
+    // kMixedPoissonTolMin.  A residual test relative to ||b|| hardly sees the
+    // smooth-mode error that FP32 inner solves leave in V_H (measured on the
+    // 32-nucleus workload: the inner SCF then stalls at a density residual of
+    // 2-6e-8, above tol_inner = 1e-8), so the tight solves of the last inner
+    // iterations run in FP64 and to tol_poisson itself: warm-started from a V_H
+    // that carries that error, a solve to the adaptive 1e-3 x residual stops
+    // before it is removed.
+    const bool mixed_poisson = c->opt.precision == 1 && c->opt.poisson_f32;
+    const bool f32 = mixed_poisson && tol >= kMixedPoissonTolMin;
+    if (mixed_poisson && !f32) tol = std::min(tol, c->opt.tol_poisson);
     int it = f32 ? pcg1_mixed_solve(c, c->d_pb.p, c->d_pv.p, tol, c->opt.max_poisson, conv)
                  : pcg1_solve(c, K, c->d_Kdinv.p, c->d_pb.p, c->d_pv.p, tol, c->opt.max_poisson, conv);
     launch_dof_to_nodal(c->F.n, c->d_dof_node.p, c->d_pv.p, VH, s);

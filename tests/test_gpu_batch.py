@@ -54,18 +54,23 @@ def test_batch_run_matches_sequential():
 
 @pytest.mark.gpu
 def test_batch_run_matches_oracle():
-    """Six instances of the batched workload run concurrently through
+    """Eight instances of the batched workload run concurrently through
     nas_batch_run, each compared with the CPU oracle run on its own (initial
     coarse-space SCF and one augmented step): eigenvalues and energies within
-    1e-10 relative wherever both inner SCFs met their tolerance (an instance
-    whose inner SCF stops at its iteration cap - a degenerate, partly occupied
-    highest level - has no well-defined iterate to compare)."""
+    1e-10 relative wherever every inner SCF met its tolerance.  Closed-shell
+    instances only: with an odd electron count the half-filled highest level
+    lies close to the next one on these coarse spaces (a lithium atom on 3^3
+    coarse cells: -0.053 and -0.043 Ha), the coarse-space initial SCF stops at
+    its iteration cap, and an unconverged start is an iterate that rounding
+    decides, with nothing well defined to compare."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from oracle.nas import Problem
     from paper_2404_19249_gb300 import nas
-    insts = [i for i in batch_instances(count=64, dof_hi=3e4)][:6]
+    # the batched workload's recipe at 2-4k unknowns per instance (the oracle
+    # takes 100-330 s per instance at the 1e4-3e4 unknowns of the full recipe)
+    insts = [i for i in batch_instances(count=64, dof_lo=2e3, dof_hi=4e3) if int(i.Z.sum()) % 2 == 0][:8]
     for inst in insts:
         inst.tol_bvp = 1e-15
         inst.tol_poisson = 1e-14
@@ -79,8 +84,9 @@ def test_batch_run_matches_oracle():
     compared = 0
     for inst, s, st_gpu, rep in zip(insts, solvers, status, reps):
         P = Problem(inst)
-        st = P.step(P.initial_state())
-        if not (st.inner_converged and rep.inner_converged):
+        st0 = P.initial_state()
+        st = P.step(st0)
+        if not (st0.inner_converged and st.inner_converged and rep.inner_converged):
             continue
         assert st_gpu == 0
         lam = s.get(nas.NAS_Q_EIGVALS)
@@ -88,6 +94,6 @@ def test_batch_run_matches_oracle():
         E = P.energy(st)
         assert abs(rep.energy - E) < 1e-10 * abs(E)
         compared += 1
-    assert compared >= 4
+    assert compared >= 5     # the oracle's inner SCFs converge for 6 of the 8
     for s in solvers:
         s.close()

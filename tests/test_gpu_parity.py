@@ -321,23 +321,26 @@ def test_coldot_standalone(nasmod):
         assert torch.equal(out, out2)   # fixed summation order: bit-identical repeats
 
 
-def test_mixed_precision_poisson_matches_fp64(nasmod):
-    """Mixed precision (FP32 Poisson PCG and FP32 block PCG of the N shifted
-    problems, each inside FP64 iterative refinement) reproduces the FP64
-    steps: eigenvalues within 1e-8 Ha and the oracle within 1e-10."""
+@pytest.mark.parametrize("poisson_f32", [0, 1])
+def test_mixed_precision_poisson_matches_fp64(nasmod, poisson_f32):
+    """Mixed precision (FP32 block PCG of the N shifted problems and, with
+    poisson_f32, FP32 Poisson PCG, each inside FP64 iterative refinement)
+    reproduces the FP64 steps: eigenvalues within 1e-8 Ha and the oracle
+    within 1e-10."""
     inst = _tight(make_instance("paper_molecule", molecule="c6h6", cells=8, coarse_cells=4))
     P = Problem(inst)
     res = {}
     for prec in (0, 1):
         # adaptive inner Poisson tolerance: the early inner iterations ask for
         # loose tolerances, which the mixed form solves with FP32 inner PCG
-        s = nasmod.Solver(inst, precision=prec, poisson_adaptive=1, timing=1)
+        s = nasmod.Solver(inst, precision=prec, poisson_adaptive=1, poisson_f32=poisson_f32, timing=1)
         s.init()
         for _ in range(2):
             r, rep = s.step()
             assert r == 0
             spmv32 = rep.phase_calls[nasmod.PHASES.index("spmv32")]
-            assert (spmv32 > 0) == (prec == 1)
+            assert (spmv32 > 0) == (prec == 1 and poisson_f32 == 1)
+            assert (rep.phase_calls[nasmod.PHASES.index("spmm32")] > 0) == (prec == 1)
         res[prec] = (s.get(nasmod.NAS_Q_EIGVALS), s.get(nasmod.NAS_Q_ENERGY)[0])
         s.close()
     assert np.max(np.abs(res[1][0] - res[0][0])) < 1e-8

@@ -131,7 +131,7 @@ def kernel_source_hash(name, kernel):
     return hashlib.sha256("\n".join(consts + lines[start:end + 1]).encode()).hexdigest()
 
 
-def spmv_traffic(sz, kernel="k_pcg1_spmv"):
+def spmv_traffic(sz, kernel="k_pcg1_spmv_sell"):
     """DRAM bytes per full-size launch of the Poisson SpMV kernel (per
     iteration for the persistent PCG kernel: the capture's bytes over its
     iterations per launch) from the committed ncu capture

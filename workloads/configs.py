@@ -20,9 +20,7 @@ method is measured on:
                    depth 5 and beta 0.7 the density residual of this 32-atom
                    system stalls at ~1e-3: long-wavelength charge oscillations;
                    measured on a 75^3 mesh, inner iterations to 1e-8: 50+ at
-                   depth 5 / beta 0.1, 36 at depth 16 / beta 0.5), restarted
-                   when the residual exceeds 10 x the best one of the inner SCF
-                   (the deep history sometimes stagnates near 1e-3).
+                   depth 5 / beta 0.1, 36 at depth 16 / beta 0.5).
   The two random molecules use mu = max_k Z_k^2: twice the magnitude of the
   hydrogen-like bound -Z^2/2 on the lowest level, so H + mu is coercive with
   margin.  (The paper's 8 M sum Z^2, 1.7e4 and 2.5e4 here, makes each step's
@@ -141,7 +139,6 @@ def _mol32_p2(cells=100, coarse_cells=16, order=2, **kw):
     inst.smearing = 0.01
     inst.anderson_beta = 0.5
     inst.anderson_depth = 16
-    inst.anderson_restart = 10.0
     return inst
 
 

@@ -163,6 +163,10 @@ typedef struct nas_options {
                               V_H errors that a residual test relative to ||b||
                               does not see, and an exact inner SCF then stalls
                               near a density residual of 1e-3                   */
+    int    recon_tc;       /* 1: the reconstruction Psi = I u_H + U^ alpha runs its
+                              dense part on the tensor cores (error-free integer
+                              slices, FP64-level accuracy; see
+                              nas_reconstruct_f64) when N <= 64; 0: FP64 SIMT  */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -173,7 +177,7 @@ typedef struct nas_options {
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
  * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0,
  * smearing = 0, inner_adapt = 0, bvp_two_level = 0, bvp_adapt = 0,
- * anderson_restart = 0, poisson_f32 = 0. */
+ * anderson_restart = 0, poisson_f32 = 0, recon_tc = 1. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -451,6 +455,22 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col,
  * NAS_E_CUDA (launch or allocation failure, or a tensor-core wait that
  * exceeded its limit). */
 int nas_dense_precond_f32(int tc, int64_t nH, int k, const float* T, const double* R, double* W, void* stream);
+
+/* The reconstruction of Algorithm 3's density update (Sec. 3.3),
+ *   Psi[i][j] = sum_{q<4, icol[i][q] >= 0} ival[i][q] U[icol[i][q]][j]
+ *             + sum_{c<Na} Uhat[i][c] U[nH + c][j],      i < n, j < N,
+ * i.e. Psi = I u_H + U^ alpha with U = [u_H ; alpha] ((nH + Na) x N) and I
+ * in the transfer's ELL form (4 coarse columns per fine row, -1 = none).
+ * Device pointers, row-major: icol int32 [n][4], ival FP64 [n][4], U FP64
+ * [nH + Na][N], Uhat FP64 [n][Na], Psi FP64 [n][N] (written).  tc = 0: FP64
+ * SIMT kernel; tc = 1: U^ alpha on the tensor cores (tcgen05.mma kind::f16 on
+ * error-free 7-bit integer slices of U^ and alpha, exact FP32 accumulation in
+ * tensor memory, one rounding at the end: FP64-level accuracy), I u_H in FP64.
+ * Errors: NAS_E_INVALID_ARG (n < 0, N or Na < 1, NULL pointers, or tc = 1
+ * with N or Na above 64), NAS_E_CUDA (launch failure or a tensor-core wait
+ * that exceeded its limit). */
+int nas_reconstruct_f64(int tc, int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                        int64_t nH, int Na, const double* Uhat, double* Psi, void* stream);
 
 int nas_spmm_layouts(void);
 const char* nas_spmm_layout_name(int layout);

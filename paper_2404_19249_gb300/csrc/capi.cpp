@@ -93,6 +93,7 @@ void nas_default_options(nas_options* o) {
     o->bvp_adapt = 0.0;
     o->anderson_restart = 0.0;
     o->poisson_f32 = 0;
+    o->recon_tc = 1;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -210,7 +211,7 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
             o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1 ||
             !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0) || o->bvp_two_level < 0 || o->bvp_two_level > 1 ||
             !(o->bvp_adapt >= 0.0) || !(o->anderson_restart >= 0.0) ||
-            o->poisson_f32 < 0 || o->poisson_f32 > 1)
+            o->poisson_f32 < 0 || o->poisson_f32 > 1 || o->recon_tc < 0 || o->recon_tc > 1)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level) || (o->eig_precond != c->opt.eig_precond);
@@ -366,6 +367,25 @@ int nas_spmm_f64(int64_t n_rows, const int32_t* row_ptr, const int32_t* col, con
     } catch (const Error& e) {
         return e.code;
     }
+}
+
+int nas_reconstruct_f64(int tc, int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                        int64_t nH, int Na, const double* Uhat, double* Psi, void* stream) {
+    if (n < 0 || N < 1 || Na < 1 || nH < 0 || !icol || !ival || !U || !Uhat || !Psi) return NAS_E_INVALID_ARG;
+    if (tc && !nas::reconstruct_tc_supported(N, Na)) return NAS_E_INVALID_ARG;
+    if (n == 0) return NAS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    try {
+        if (tc) {
+            nas::launch_reconstruct_tc(n, icol, ival, N, U, nH, Na, Uhat, Psi, s);
+            if (nas::tc_error_take(s)) return NAS_E_CUDA;
+        } else {
+            nas::launch_reconstruct(n, icol, ival, N, U, nH, Na, Uhat, Psi, s);
+        }
+    } catch (const Error& e) {
+        return e.code;
+    }
+    return NAS_OK;
 }
 
 int nas_dense_precond_f32(int tc, int64_t nH, int k, const float* T, const double* R, double* W, void* stream) {

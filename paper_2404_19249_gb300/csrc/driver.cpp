@@ -732,6 +732,17 @@ static const double kMixedPoissonTolMin = 1e-9;
 
 // V_H nodal into `VH` (boundary included): monopole/quadrupole boundary
 // values, b = 4 pi int rho phi_i - K_IB w_B, PCG on K_II with warm start VH.
+// Psi = I u_H + U^ alpha (Algorithm 3's reconstruction): the dense part on the
+// tensor cores (error-free integer slices, FP64-level accuracy) with recon_tc
+// when N and Na are at most 64, else the FP64 SIMT kernel
+static void reconstruct(nas_ctx* c, int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                        int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s) {
+    if (c->opt.recon_tc && reconstruct_tc_supported(N, Na))
+        launch_reconstruct_tc(n, icol, ival, N, U, nH, Na, Uhat, Psi, s);
+    else
+        launch_reconstruct(n, icol, ival, N, U, nH, Na, Uhat, Psi, s);
+}
+
 static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
     Phase t(c, NAS_PH_POISSON);
     cudaStream_t s = c->stream;
@@ -1211,7 +1222,7 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
             Phase ph(c, NAS_PH_DENSITY);
             {
                 Phase pr(c, NAS_PH_RECON);
-                launch_reconstruct(c->F.n, c->d_Icol.p, c->d_Ival.p, c->N, c->d_U.p, nH, Na, c->d_Uhat.p, c->d_Psi.p,
+                reconstruct(c, c->F.n, c->d_Icol.p, c->d_Ival.p, c->N, c->d_U.p, nH, Na, c->d_Uhat.p, c->d_Psi.p,
                                    s);
             }
             {
@@ -1240,6 +1251,8 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
         anderson_mix(c, A);
         c->anl_valid = false;
     }
+    // a tensor-core kernel whose mbarrier wait ran out records it in a device flag
+    if (c->opt.recon_tc && tc_error_take(s)) fail(NAS_E_CUDA, "tensor-core kernel: an mbarrier wait exceeded its limit");
     c->last_inner = t;
     c->last_inner_conv = conv ? 1 : 0;
     c->last_inner_res = res;
@@ -1267,7 +1280,7 @@ static void augment_basis(nas_ctx* c) {
     for (int64_t i = 0; i < nH * N; ++i) Uf[i] = -Y[i];
     for (int j = 0; j < N; ++j) Uf[(nH + j) * N + j] = 1.0;
     NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
-    launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, nH, N, c->d_Uhat.p, c->d_X2.p, s);
+    reconstruct(c, n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, nH, N, c->d_Uhat.p, c->d_X2.p, s);
     spmm(c, fcsr(c, c->d_M.p), N, c->d_X2.p, c->d_X1.p);
     launch_gram_sym(n, N, c->d_X2.p, c->d_X1.p, c->d_partial.p, c->d_blk_gamma.p, s);
     std::vector<double> g(N * N);
@@ -1296,7 +1309,7 @@ static void augment_basis(nas_ctx* c) {
     std::fill(Uf.begin(), Uf.end(), 0.0);
     for (int i = 0; i < N * N; ++i) Uf[nH * N + i] = Linv_T[i];
     NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
-    launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, nH, N, c->d_X2.p, c->d_Uhat.p, s);
+    reconstruct(c, n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, nH, N, c->d_X2.p, c->d_Uhat.p, s);
 }
 
 // ------------------------------------------------------------------ setup
@@ -1637,7 +1650,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
         NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Ufull.data(), sizeof(double) * Ufull.size(), cudaMemcpyHostToDevice, s));
         std::vector<double> zero_col(4 * n, 0.0);
         // reconstruct with the coarse part ignored (weights multiply zero rows)
-        launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
+        reconstruct(c, n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
         launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, N, c->d_occ.p, c->d_rho_in.p, s);
         bool pc = true;
         if (c->opt.hartree) hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
@@ -1658,7 +1671,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
         NAS_CUDA(cudaMemcpyAsync(c->d_Uhat.p, c->d_Psi.p, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, s));
         for (int i = 0; i < N * N; ++i) Ufull[c->nH * N + i] = Y[i];
         NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Ufull.data(), sizeof(double) * Ufull.size(), cudaMemcpyHostToDevice, s));
-        launch_reconstruct(n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
+        reconstruct(c, n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
         launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, N, c->d_occ.p, c->d_rho_out.p, s);
         c->last_inner = 0;
         (void)zero_col;

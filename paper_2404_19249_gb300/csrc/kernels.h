@@ -203,6 +203,11 @@ void launch_transpose_apply(const Pieces& pc, const int32_t* trow, const double*
 // U = [uH ; alpha] is [(nH + Na)][N] on the device; Na may be 0.
 void launch_reconstruct(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
                         int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s);
+// the same with the dense part on the tensor cores (error-free integer
+// slices, FP64 accuracy; kernels_tc.cu); needs 1 <= N <= 64 and 1 <= Na <= 64
+bool reconstruct_tc_supported(int N, int Na);
+void launch_reconstruct_tc(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                           int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s);
 // Galerkin stage 1: W[s] = sum_{q in list} A[q>>2] * ival[col[q>>2]*4 + (q&3)]
 void launch_galerkin1(int64_t nw, const int64_t* ptr, const int32_t* con, const double* A,
                       const int32_t* col, const double* ival, double* W, cudaStream_t s);

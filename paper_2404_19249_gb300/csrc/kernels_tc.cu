@@ -27,6 +27,8 @@
 // records the error, frees its tensor memory and returns.  The CTA's FP32
 // partial product goes to part[split][row][col], the layout of the FP32 SIMT
 // kernel's stage 1, and the same stage 2 adds the splits in order.
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "kernels.h"
@@ -260,6 +262,280 @@ void launch_dense_precond_tc(int64_t nH, int64_t m, int k, const float* T, const
 }
 
 int64_t dense_precond_tc_part_size(int64_t nH, int k) { return (int64_t)kTcSplit * nH * k; }
+
+// ---------------------------------------------------------------------------
+// Reconstruction Psi = I u_H + U^ alpha (the density update of Algorithm 3)
+// with the dense part U^ alpha (n x Na times Na x N; Na, N <= 64) on the
+// tensor cores at FP64 accuracy, by an error-free split into small integers
+// (the scheme of Ozaki, Ogita, Oishi and Rump, 2012, in its integer-slice
+// form):
+//  * row i of U^ is written in fixed point against the largest binary
+//    exponent of the row, x = sign M 2^(E_i - 1075) with M the 53-bit
+//    significand shifted right by E_i - e(x) (truncated), and the top 49 bits
+//    of M are cut into seven 7-bit slices, M ~ sum_s a_s 2^(46 - 7 s); column j
+//    of alpha likewise against its own exponent F_j (slices b_t);
+//  * slices are integers below 128 in magnitude, exact in FP16; a product of
+//    two is below 2^14, a sum over K <= 64 below 2^20, and
+//    D_d = sum_{s+t=d} A_s B_t (d = 0..6, at most 7 terms) below 2^23, so an
+//    FP32 accumulator in tensor memory holds it exactly;
+//  * the epilogue adds acc = sum_d D_d 2^(7 (6 - d)) in int64 (|acc| < 2^63,
+//    exact) and rounds once: (double) acc 2^(E_i - 1050) 2^(F_j - 1050).
+// The slices s + t > 6 and the truncated bits are dropped: per product the
+// error is below 2^-45.8 max_k |U^_ik| max_k |alpha_kj|, per entry below
+// 2^-39.8 of it for K = 64, within a factor 4 of FP64's own worst-case
+// dot-product bound (K^2 2^-53 = 2^-41).  The FP64 pipe keeps only the conversion, the
+// scaling and the four terms of I u_H, about 7 of the 68 FP64 operations per
+// entry of the SIMT kernel.
+//
+// One persistent CTA per SM (128 threads; 168 KB of slices in shared memory,
+// the same canonical no-swizzle K-major layout as above with 64-element rows);
+// alpha's slices are staged once per CTA.  Per 128-row tile: each thread
+// slices its row into the seven A slices, thread 0 issues the 28 x (Na/16)
+// MMAs (kind::f16, M = 128, N = Npad) into seven accumulators and commits them
+// to an mbarrier (bounded wait), and each thread reads its row's accumulators
+// (tensor-memory lane = row) 16 columns at a time.
+namespace {
+
+const int kOzM = 128;                           // rows per tile (MMA M)
+const int kOzK = 64;                            // K capacity: rows of 8 core matrices of 8 FP16
+const int kOzS = 7;                             // slices per operand
+const int kOzThreads = 128;
+const uint32_t kOzSliceA = kOzM * kOzK * 2;     // bytes per A slice
+const uint32_t kOzSliceB = 64 * kOzK * 2;       // bytes per B slice (N <= 64)
+
+// kind::f16: D FP32 (bits 4-5 = 1), A and B FP16 (bits 7-9, 10-12 = 0), K-major
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// byte offset of FP16 element (r, k) of a K-major tile with 64-element rows
+__device__ __forceinline__ uint32_t canon16(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ int biased_exp(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// 2^e as a double for -1074 <= e <= 1023 (0 below)
+__device__ __forceinline__ double pow2(int e) {
+    if (e >= -1022) return __longlong_as_double((long long)(e + 1023) << 52);
+    if (e >= -1074) return __longlong_as_double(1LL << (e + 1074));
+    return 0.0;
+}
+
+// significand of x aligned to the biased exponent E >= e(x) (zero and
+// subnormal x give 0), and its sign
+__device__ __forceinline__ unsigned long long fixed53(double x, int E, bool* neg) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    *neg = bits < 0;
+    if (ex == 0 || E - ex >= 53) return 0ULL;
+    return ((unsigned long long)(bits & 0xFFFFFFFFFFFFFLL) | (1ULL << 52)) >> (E - ex);
+}
+
+// FP16 bit pattern of slice s (bits 46 - 7 s .. 52 - 7 s of M) with its sign
+__device__ __forceinline__ uint32_t slice_h(unsigned long long M, bool neg, int s) {
+    const int a = (int)((M >> (46 - 7 * s)) & 127ULL);
+    return (uint32_t)__half_as_ushort(__int2half_rn(neg ? -a : a));
+}
+
+// the 8 values x[0..7] (K positions k0..k0+7 of tile row r) as 7 slices
+__device__ __forceinline__ void stage8(const double* x, int E, unsigned char* slab, uint32_t slice_bytes, int r,
+                                       int k0) {
+    unsigned long long M[8];
+    bool neg[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) M[q] = fixed53(x[q], E, &neg[q]);
+#pragma unroll
+    for (int s = 0; s < kOzS; ++s) {
+        uint4 v;
+        v.x = slice_h(M[0], neg[0], s) | (slice_h(M[1], neg[1], s) << 16);
+        v.y = slice_h(M[2], neg[2], s) | (slice_h(M[3], neg[3], s) << 16);
+        v.z = slice_h(M[4], neg[4], s) | (slice_h(M[5], neg[5], s) << 16);
+        v.w = slice_h(M[6], neg[6], s) | (slice_h(M[7], neg[7], s) << 16);
+        *reinterpret_cast<uint4*>(slab + (size_t)s * slice_bytes + canon16(r, k0)) = v;
+    }
+}
+
+}  // namespace
+
+// Psi[i][j] = sum_k ival[i][k] U[icol[i][k]][j] + sum_c Uhat[i][c] U[nH + c][j]
+// (alpha = U[nH..nH+Na)) with the second sum on the tensor cores as above.
+// Dynamic shared memory: 7 A slices (128 x 64 FP16) and 7 B slices (64 x 64
+// FP16), 1024-byte aligned.
+__global__ void __launch_bounds__(kOzThreads) k_tc_reconstruct(int64_t n, const int32_t* icol, const double* ival,
+                                                              int N, int Npad, uint32_t ncols, const double* U,
+                                                              int64_t nH, int Na, const double* Uhat,
+                                                              double* Psi) {
+    extern __shared__ __align__(1024) unsigned char oz_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ double colscale[64];   // 2^(F_j - 1050), 0 for an all-zero column
+    unsigned char* base = oz_smem;
+    base += (1024 - (smem_u32(base) & 1023)) & 1023;
+    unsigned char* As = base;
+    unsigned char* Bs = base + (size_t)kOzS * kOzSliceA;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(mb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // alpha's slices: thread j < Npad stages column j (row j of the K-major B tile)
+    const double* alpha = U + nH * (int64_t)N;
+    if (tid < Npad) {
+        const int j = tid;
+        int F = 0;
+        if (j < N)
+            for (int c = 0; c < Na; ++c) F = max(F, biased_exp(alpha[(int64_t)c * N + j]));
+        colscale[j] = F ? pow2(F - 1050) : 0.0;
+        for (int k0 = 0; k0 < kOzK; k0 += 8) {
+            double x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = k0 + q;
+                x[q] = (j < N && c < Na) ? alpha[(int64_t)c * N + j] : 0.0;
+            }
+            stage8(x, F, Bs, kOzSliceB, j, k0);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_f16(kOzM, Npad);
+    const int nks = (Na + 15) / 16;
+    const int64_t ntiles = (n + kOzM - 1) / kOzM;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * kOzM + tid;
+        // this thread's row of U^ in seven slices (zeros past the last row)
+        int E = 0;
+        if (i < n)
+            for (int c = 0; c < Na; ++c) E = max(E, biased_exp(Uhat[i * Na + c]));
+        for (int k0 = 0; k0 < kOzK; k0 += 8) {
+            double x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = k0 + q;
+                x[q] = (i < n && c < Na) ? Uhat[i * Na + c] : 0.0;
+            }
+            stage8(x, E, As, kOzSliceA, tid, k0);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            for (int d = 0; d < kOzS; ++d)
+                for (int sa = 0; sa <= d; ++sa)
+                    for (int ks = 0; ks < nks; ++ks) {
+                        const uint32_t off = (uint32_t)ks * 256;   // K = 16 FP16 = two core matrices
+                        mma_f16(tmem + (uint32_t)(d * Npad), smem_desc(a0 + sa * kOzSliceA + off, 128, 1024),
+                                smem_desc(b0 + (d - sa) * kOzSliceB + off, 128, 1024), idesc,
+                                (sa | ks) ? 1u : 0u);
+                    }
+            mma_commit(mb);
+        }
+        ok = mbar_wait(mb, phase);
+        phase ^= 1u;
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: tensor-memory lane 32 warp + lane holds row i = this thread's row
+        const double rs = E ? pow2(E - 1050) : 0.0;
+        int a4[4] = {-1, -1, -1, -1};
+        double w4[4] = {0.0, 0.0, 0.0, 0.0};
+        if (i < n)
+            for (int k = 0; k < 4; ++k) {
+                a4[k] = icol[4 * i + k];
+                w4[k] = ival[4 * i + k];
+            }
+        for (int c0 = 0; c0 < Npad; c0 += 16) {
+            long long acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0;
+            for (int d = 0; d < kOzS; ++d) {
+                uint32_t v[16];
+                const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * Npad + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                    "%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const long long w = 1LL << (7 * (kOzS - 1 - d));
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] += (long long)__float2int_rn(__uint_as_float(v[q])) * w;
+            }
+            if (i < n)
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int j = c0 + q;
+                    if (j < N) {
+                        double iu = 0.0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (a4[k] >= 0) iu += w4[k] * U[(int64_t)a4[k] * N + j];
+                        Psi[i * N + j] = fma((double)acc[q] * rs, colscale[j], iu);
+                    }
+                }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    if (!ok) {
+        atomicExch(&g_tc_error, 1);
+        mbar_wait(mb, phase ^ 1u);   // bounded second wait for the MMAs in flight
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+bool reconstruct_tc_supported(int N, int Na) { return N >= 1 && N <= 64 && Na >= 1 && Na <= kOzK; }
+
+void launch_reconstruct_tc(int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
+                           int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s) {
+    if (n <= 0) return;
+    if (!reconstruct_tc_supported(N, Na)) fail(NAS_E_INVALID_ARG, "tensor-core reconstruction: N or Na out of range");
+    static const int sms = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            v = 0;
+        cudaGetLastError();
+        return v > 0 ? v : 1;
+    }();
+    const int Npad = (N + 15) / 16 * 16;
+    const int need = kOzS * Npad;
+    const uint32_t ncols = need <= 32 ? 32u : need <= 64 ? 64u : need <= 128 ? 128u : need <= 256 ? 256u : 512u;
+    const size_t smem = 1024 + (size_t)kOzS * (kOzSliceA + kOzSliceB);
+    NAS_CUDA(cudaFuncSetAttribute(k_tc_reconstruct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t ntiles = (n + kOzM - 1) / kOzM;
+    const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
+    k_tc_reconstruct<<<grid, kOzThreads, smem, s>>>(n, icol, ival, N, Npad, ncols, U, nH, Na, Uhat, Psi);
+    NAS_CHECK_LAUNCH();
+}
 
 bool tc_error_take(cudaStream_t s) {
     int v = 0, zero = 0;

@@ -287,19 +287,21 @@ int64_t dense_precond_tc_part_size(int64_t nH, int k) { return (int64_t)kTcSplit
 // scaling and the four terms of I u_H, about 7 of the 68 FP64 operations per
 // entry of the SIMT kernel.
 //
-// One persistent CTA per SM (128 threads; 168 KB of slices in shared memory,
+// One persistent CTA per SM (256 threads; 168 KB of slices in shared memory,
 // the same canonical no-swizzle K-major layout as above with 64-element rows);
-// alpha's slices are staged once per CTA.  Per 128-row tile: each thread
-// slices its row into the seven A slices, thread 0 issues the 28 x (Na/16)
-// MMAs (kind::f16, M = 128, N = Npad) into seven accumulators and commits them
-// to an mbarrier (bounded wait), and each thread reads its row's accumulators
-// (tensor-memory lane = row) 16 columns at a time.
+// alpha's slices are staged once per CTA.  Per 128-row tile: two threads slice
+// each row (one K half each) into the seven A slices, thread 0 issues the
+// 28 x (Na/16) MMAs (kind::f16, M = 128, N = Npad) into seven accumulators and
+// commits them to an mbarrier (bounded wait), and the same two threads read
+// the row's accumulators (tensor-memory lane = row), alternate 16-column
+// chunks each.  With four warps per SM the kernel was latency-bound (6 % of
+// the warp slots, 8 % issue-active, FP64 pipe 28 % busy under ncu).
 namespace {
 
 const int kOzM = 128;                           // rows per tile (MMA M)
 const int kOzK = 64;                            // K capacity: rows of 8 core matrices of 8 FP16
 const int kOzS = 7;                             // slices per operand
-const int kOzThreads = 128;
+const int kOzThreads = 256;                     // two threads per tile row
 const uint32_t kOzSliceA = kOzM * kOzK * 2;     // bytes per A slice
 const uint32_t kOzSliceB = 64 * kOzK * 2;       // bytes per B slice (N <= 64)
 
@@ -379,11 +381,15 @@ __global__ void __launch_bounds__(kOzThreads) k_tc_reconstruct(int64_t n, const 
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ double colscale[64];   // 2^(F_j - 1050), 0 for an all-zero column
+    __shared__ int epart[2][kOzM];     // the two half-row maxima of the row exponent
     unsigned char* base = oz_smem;
     base += (1024 - (smem_u32(base) & 1023)) & 1023;
     unsigned char* As = base;
     unsigned char* Bs = base + (size_t)kOzS * kOzSliceA;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    // thread tid works on tile row r = tid % 128: K half h = tid / 128 when
+    // staging, and in the epilogue (warps w and w + 4 share tensor-memory lanes
+    // 32 (w % 4) ..) the 16-column chunks c with c % 2 == h
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid & (kOzM - 1), h = tid >> 7;
     const uint32_t mb = smem_u32(&mbar);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -424,19 +430,25 @@ __global__ void __launch_bounds__(kOzThreads) k_tc_reconstruct(int64_t n, const 
     bool ok = true;
     uint32_t phase = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t i = tile * kOzM + tid;
-        // this thread's row of U^ in seven slices (zeros past the last row)
+        const int64_t i = tile * kOzM + r;
+        // row i of U^ in seven slices (zeros past the last row): this thread
+        // takes K positions [32 h, 32 h + 32); the row exponent is the max of
+        // the two halves' maxima
+        const int kb = (kOzK / 2) * h;
         int E = 0;
         if (i < n)
-            for (int c = 0; c < Na; ++c) E = max(E, biased_exp(Uhat[i * Na + c]));
-        for (int k0 = 0; k0 < kOzK; k0 += 8) {
+            for (int c = kb; c < kb + kOzK / 2 && c < Na; ++c) E = max(E, biased_exp(Uhat[i * Na + c]));
+        epart[h][r] = E;
+        __syncthreads();
+        E = max(epart[0][r], epart[1][r]);
+        for (int k0 = kb; k0 < kb + kOzK / 2; k0 += 8) {
             double x[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int c = k0 + q;
                 x[q] = (i < n && c < Na) ? Uhat[i * Na + c] : 0.0;
             }
-            stage8(x, E, As, kOzSliceA, tid, k0);
+            stage8(x, E, As, kOzSliceA, r, k0);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -459,7 +471,7 @@ __global__ void __launch_bounds__(kOzThreads) k_tc_reconstruct(int64_t n, const 
         ok = __syncthreads_and(ok) != 0;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: tensor-memory lane 32 warp + lane holds row i = this thread's row
+        // epilogue: tensor-memory lane r (lanes 32 (warp % 4) ..) holds row i
         const double rs = E ? pow2(E - 1050) : 0.0;
         int a4[4] = {-1, -1, -1, -1};
         double w4[4] = {0.0, 0.0, 0.0, 0.0};
@@ -468,13 +480,13 @@ __global__ void __launch_bounds__(kOzThreads) k_tc_reconstruct(int64_t n, const 
                 a4[k] = icol[4 * i + k];
                 w4[k] = ival[4 * i + k];
             }
-        for (int c0 = 0; c0 < Npad; c0 += 16) {
+        for (int c0 = 16 * h; c0 < Npad; c0 += 32) {
             long long acc[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) acc[q] = 0;
             for (int d = 0; d < kOzS; ++d) {
                 uint32_t v[16];
-                const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * Npad + c0);
+                const uint32_t addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(d * Npad + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
                     "%15}, [%16];"

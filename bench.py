@@ -83,8 +83,9 @@ def parse(argv=None):
     p.add_argument("--poisson-sell", type=int, default=1, help="1: sliced-ELL Poisson SpMV, 0: CSR")
     p.add_argument("--poisson-fused", type=int, default=0,
                    help="1: persistent cooperative Poisson PCG kernel, 0: per-phase kernels from a CUDA graph")
-    p.add_argument("--recon-tc", type=int, default=1,
-                   help="1: reconstruction's dense part on the tensor cores (exact integer slices), 0: FP64 SIMT")
+    p.add_argument("--dense-tc", type=int, default=1,
+                   help="1: the FP64 dense contractions (reconstruction, Gram matrices) on the tensor cores from exact "
+                        "integer slices, 0: FP64 SIMT")
     p.add_argument("--poisson-f32", type=int, default=0,
                    help="mixed precision: 1 = FP32 Poisson solves for tolerances >= 1e-9, 0 = FP64 Poisson")
     p.add_argument("--poisson-adaptive", type=int, default=1,
@@ -113,7 +114,7 @@ def solver_options(args, timing=1):
              spmv_lanes=args.spmv_lanes, poisson_adaptive=args.poisson_adaptive, eig_adapt=args.eig_adapt,
              eig_precond=args.eig_precond, poisson_sell=args.poisson_sell, poisson_fused=args.poisson_fused,
              inner_adapt=args.inner_adapt, bvp_adapt=args.bvp_adapt, poisson_f32=args.poisson_f32,
-             recon_tc=args.recon_tc)
+             dense_tc=args.dense_tc)
     if args.anderson_restart is not None:
         o["anderson_restart"] = args.anderson_restart
     return o
@@ -177,8 +178,8 @@ def workload_config(args, name, inst, sz, precision, extra=None):
                              "residual tolerance %g x previous inner-SCF residual in [1e-11, 1e-4]"
                              % ({2: "inverse coarse stiffness (tensor-core product)", 1: "inverse coarse stiffness",
                                  0: "diagonal"}[args.eig_precond], args.eig_adapt),
-        "reconstruction": ("U^ alpha on the tensor cores (exact 7-bit integer slices, FP64 accuracy)"
-                           if args.recon_tc else "FP64 SIMT"),
+        "dense_contractions": ("reconstruction U^ alpha and Gram matrices on the tensor cores (exact 7-bit integer "
+                               "slices, FP64 accuracy)" if args.dense_tc else "FP64 SIMT"),
     }
     if extra:
         cfg.update(extra)
@@ -191,7 +192,7 @@ def phase_totals(reps, phases):
     return ms, calls
 
 
-def kernel_rooflines(reps, sz, steps, phases, hbm_peak, peak_src, nz_occ, layouts=None, recon_tc=False):
+def kernel_rooflines(reps, sz, steps, phases, hbm_peak, peak_src, nz_occ, layouts=None, dense_tc=False):
     """Per-kernel achieved throughput from the library's live CUDA-event
     timings of the timed steps (reports `reps`), against its roofline: HBM
     bytes for the sparse and streaming kernels, the FP64 issue rate for the
@@ -267,7 +268,7 @@ def kernel_rooflines(reps, sz, steps, phases, hbm_peak, peak_src, nz_occ, layout
         out["k_pcg1_spmv_f32"]["est_ms_per_step"] = out["k_pcg1_spmv_f32"]["ms_per_launch"] * poisson_iters / steps
         out["k_pcg1_spmv_f32"]["timing"] = ("CUDA events around the SpMV of the first two iterations of every "
                                             "inner FP32 solve (direct launches; the rest replays from a CUDA graph)")
-    if calls.get("recon") and recon_tc and N <= 64:
+    if calls.get("recon") and dense_tc and N <= 64:
         # dense part on the tensor cores: what stays on the FP64 pipe is I u_H
         # (4 FMA per entry) and the final scaled FMA (1 per entry)
         alu("k_reconstruct", ms["recon"], calls["recon"], 2.0 * n * N * 5,
@@ -619,7 +620,7 @@ def secondary_line(args, nas, torch, name, device, stream):
     ms, _, reps, _ = timed_steps(s, nas, torch, args.secondary_steps)
     sz = s.sizes()
     roofs = kernel_rooflines(reps, sz, args.secondary_steps, nas.PHASES, *hbm_peak(), nz_occ=sz["N"],
-                             recon_tc=bool(args.recon_tc),
+                             dense_tc=bool(args.dense_tc),
                              layouts=tuned_layouts(nas, sz))
     out = {"value": args.secondary_steps / (ms / 1e3), "unit": "steps/s", "steps": args.secondary_steps,
            "warmup": 2, "ms_per_step": ms / args.secondary_steps, "dtype": "f64", "setup_s": setup,
@@ -767,9 +768,9 @@ def main():
     nz = N if getattr(inst, "smearing", 0.0) > 0 else int(np.sum(np.asarray(inst.occ) > 0))
     lay = tuned_layouts(nas, sz)
     roofs_h = kernel_rooflines(reps, sz, args.steps, nas.PHASES, peak, psrc, nz_occ=nz, layouts=lay,
-                               recon_tc=bool(args.recon_tc))
+                               dense_tc=bool(args.dense_tc))
     roofs_o = (kernel_rooflines(reps_o, sz, n_cmp, nas.PHASES, peak, psrc, nz_occ=nz, layouts=lay,
-                                recon_tc=bool(args.recon_tc)) if reps_o else {})
+                                dense_tc=bool(args.dense_tc)) if reps_o else {})
     tuner = [r for r in nas.nas_spmm_tuning() if r["rows"] == sz["n"]]
     trf = spmv_traffic(sz, "k_pcg1_spmv_sell")
     for rr in (roofs_h, roofs_o):

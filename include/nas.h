@@ -163,10 +163,12 @@ typedef struct nas_options {
                               V_H errors that a residual test relative to ||b||
                               does not see, and an exact inner SCF then stalls
                               near a density residual of 1e-3                   */
-    int    recon_tc;       /* 1: the reconstruction Psi = I u_H + U^ alpha runs its
-                              dense part on the tensor cores (error-free integer
-                              slices, FP64-level accuracy; see
-                              nas_reconstruct_f64) when N <= 64; 0: FP64 SIMT  */
+    int    dense_tc;       /* 1: the FP64 dense contractions - the reconstruction
+                              Psi = I u_H + U^ alpha and the Gram matrices
+                              gamma, beta - run on the tensor cores from
+                              error-free integer slices (FP64-level accuracy;
+                              see nas_reconstruct_f64) when N <= 64; 0: FP64
+                              SIMT kernels                                     */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -177,7 +179,7 @@ typedef struct nas_options {
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
  * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0,
  * smearing = 0, inner_adapt = 0, bvp_two_level = 0, bvp_adapt = 0,
- * anderson_restart = 0, poisson_f32 = 0, recon_tc = 1. */
+ * anderson_restart = 0, poisson_f32 = 0, dense_tc = 1. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */
@@ -471,6 +473,19 @@ int nas_dense_precond_f32(int tc, int64_t nH, int k, const float* T, const doubl
  * that exceeded its limit). */
 int nas_reconstruct_f64(int tc, int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
                         int64_t nH, int Na, const double* Uhat, double* Psi, void* stream);
+
+/* A Gram matrix known to be symmetric, G = X^T Y (the blocks gamma = U^T M U^
+ * and beta = U^T A U^ of Sec. 3.3): the upper triangle is summed and mirrored,
+ * so G is exactly symmetric.  X, Y FP64 [n][N], G FP64 [N][N], device
+ * pointers, row-major.  tc = 0: FP64 SIMT; tc = 1: tensor cores, per 64-row
+ * chunk from error-free 7-bit integer slices with exact FP32 accumulation in
+ * tensor memory, chunks added in FP64 (FP64-level accuracy).  Sums are taken
+ * in a fixed order: repeated calls are bit-identical.  Scratch for the
+ * partial sums (<= 1216 N^2 doubles) is allocated and freed on `stream`.
+ * Errors: NAS_E_INVALID_ARG (n < 0, N < 1, N > 64 with tc = 1 or N > 90
+ * without, NULL pointers), NAS_E_CUDA (launch or allocation failure, or a
+ * tensor-core wait that exceeded its limit). */
+int nas_gram_sym_f64(int tc, int64_t n, int N, const double* X, const double* Y, double* G, void* stream);
 
 int nas_spmm_layouts(void);
 const char* nas_spmm_layout_name(int layout);

@@ -93,7 +93,7 @@ void nas_default_options(nas_options* o) {
     o->bvp_adapt = 0.0;
     o->anderson_restart = 0.0;
     o->poisson_f32 = 0;
-    o->recon_tc = 1;
+    o->dense_tc = 1;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -211,7 +211,7 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
             o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1 ||
             !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0) || o->bvp_two_level < 0 || o->bvp_two_level > 1 ||
             !(o->bvp_adapt >= 0.0) || !(o->anderson_restart >= 0.0) ||
-            o->poisson_f32 < 0 || o->poisson_f32 > 1 || o->recon_tc < 0 || o->recon_tc > 1)
+            o->poisson_f32 < 0 || o->poisson_f32 > 1 || o->dense_tc < 0 || o->dense_tc > 1)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level) || (o->eig_precond != c->opt.eig_precond);
@@ -386,6 +386,28 @@ int nas_reconstruct_f64(int tc, int64_t n, const int32_t* icol, const double* iv
         return e.code;
     }
     return NAS_OK;
+}
+
+int nas_gram_sym_f64(int tc, int64_t n, int N, const double* X, const double* Y, double* G, void* stream) {
+    if (n < 0 || N < 1 || (int64_t)N * (N + 1) / 2 > 16 * 256 || !X || !Y || !G) return NAS_E_INVALID_ARG;
+    if (tc && !nas::gram_tc_supported(N)) return NAS_E_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* part = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)nas::reduce_partial_size((int64_t)N * N);
+    if (cudaMallocAsync(reinterpret_cast<void**>(&part), bytes, s) != cudaSuccess) return NAS_E_CUDA;
+    int rc = NAS_OK;
+    try {
+        if (tc) {
+            nas::launch_gram_sym_tc(n, N, X, Y, part, G, s);
+            if (nas::tc_error_take(s)) rc = NAS_E_CUDA;
+        } else {
+            nas::launch_gram_sym(n, N, X, Y, part, G, s);
+        }
+    } catch (const Error& e) {
+        rc = e.code;
+    }
+    if (cudaFreeAsync(part, s) != cudaSuccess && rc == NAS_OK) rc = NAS_E_CUDA;
+    return rc;
 }
 
 int nas_dense_precond_f32(int tc, int64_t nH, int k, const float* T, const double* R, double* W, void* stream) {

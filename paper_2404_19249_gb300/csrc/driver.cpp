@@ -733,14 +733,24 @@ static const double kMixedPoissonTolMin = 1e-9;
 // V_H nodal into `VH` (boundary included): monopole/quadrupole boundary
 // values, b = 4 pi int rho phi_i - K_IB w_B, PCG on K_II with warm start VH.
 // Psi = I u_H + U^ alpha (Algorithm 3's reconstruction): the dense part on the
-// tensor cores (error-free integer slices, FP64-level accuracy) with recon_tc
+// tensor cores (error-free integer slices, FP64-level accuracy) with dense_tc
 // when N and Na are at most 64, else the FP64 SIMT kernel
 static void reconstruct(nas_ctx* c, int64_t n, const int32_t* icol, const double* ival, int N, const double* U,
                         int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s) {
-    if (c->opt.recon_tc && reconstruct_tc_supported(N, Na))
+    if (c->opt.dense_tc && reconstruct_tc_supported(N, Na))
         launch_reconstruct_tc(n, icol, ival, N, U, nH, Na, Uhat, Psi, s);
     else
         launch_reconstruct(n, icol, ival, N, U, nH, Na, Uhat, Psi, s);
+}
+
+// G = X^T Y, known symmetric (the blocks gamma, beta of Sec. 3.3): on the
+// tensor cores with dense_tc when N <= 64, else the FP64 SIMT kernel; both
+// return an exactly symmetric G
+static void gram_sym(nas_ctx* c, int64_t n, int N, const double* X, const double* Y, double* G) {
+    if (c->opt.dense_tc && gram_tc_supported(N))
+        launch_gram_sym_tc(n, N, X, Y, c->d_partial.p, G, c->stream);
+    else
+        launch_gram_sym(n, N, X, Y, c->d_partial.p, G, c->stream);
 }
 
 static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
@@ -980,7 +990,7 @@ static void blocks_of(nas_ctx* c, const double* Avals, std::vector<double>* AHv,
     if (Na > 0) {
         spmm(c, fcsr(c, Avals), N, c->d_Uhat.p, c->d_X1.p);
         transpose_apply(c, N, c->d_X1.p, c->d_blk_b.p);
-        launch_gram_sym(c->F.n, N, c->d_Uhat.p, c->d_X1.p, c->d_partial.p, c->d_blk_beta.p, s);
+        gram_sym(c, c->F.n, N, c->d_Uhat.p, c->d_X1.p, c->d_blk_beta.p);
         if (to_host) {
             b.resize(c->nH * N);
             beta.resize(N * N);
@@ -1252,7 +1262,7 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
         c->anl_valid = false;
     }
     // a tensor-core kernel whose mbarrier wait ran out records it in a device flag
-    if (c->opt.recon_tc && tc_error_take(s)) fail(NAS_E_CUDA, "tensor-core kernel: an mbarrier wait exceeded its limit");
+    if (c->opt.dense_tc && tc_error_take(s)) fail(NAS_E_CUDA, "tensor-core kernel: an mbarrier wait exceeded its limit");
     c->last_inner = t;
     c->last_inner_conv = conv ? 1 : 0;
     c->last_inner_res = res;
@@ -1282,7 +1292,7 @@ static void augment_basis(nas_ctx* c) {
     NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Uf.data(), sizeof(double) * Uf.size(), cudaMemcpyHostToDevice, s));
     reconstruct(c, n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, nH, N, c->d_Uhat.p, c->d_X2.p, s);
     spmm(c, fcsr(c, c->d_M.p), N, c->d_X2.p, c->d_X1.p);
-    launch_gram_sym(n, N, c->d_X2.p, c->d_X1.p, c->d_partial.p, c->d_blk_gamma.p, s);
+    gram_sym(c, n, N, c->d_X2.p, c->d_X1.p, c->d_blk_gamma.p);
     std::vector<double> g(N * N);
     NAS_CUDA(cudaMemcpyAsync(g.data(), c->d_blk_gamma.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
     sync(c);
@@ -1633,7 +1643,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
         const int N = c->N;
         c->d_X2.upload(psi0, n * N, s);
         spmm(c, fcsr(c, c->d_M.p), N, c->d_X2.p, c->d_X1.p);
-        launch_gram_sym(n, N, c->d_X2.p, c->d_X1.p, c->d_partial.p, c->d_blk_gamma.p, s);
+        gram_sym(c, n, N, c->d_X2.p, c->d_X1.p, c->d_blk_gamma.p);
         std::vector<double> S(N * N);
         NAS_CUDA(cudaMemcpyAsync(S.data(), c->d_blk_gamma.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
         sync(c);
@@ -1658,7 +1668,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
         c->anl_valid = true;
         launch_combine3(c->F.nnz(), 1.0, c->d_AL.p, 1.0, c->d_ANL.p, 0.0, nullptr, c->d_H.p, s);
         spmm(c, fcsr(c, c->d_H.p), N, c->d_Psi.p, c->d_X1.p);
-        launch_gram_sym(n, N, c->d_Psi.p, c->d_X1.p, c->d_partial.p, c->d_blk_beta.p, s);
+        gram_sym(c, n, N, c->d_Psi.p, c->d_X1.p, c->d_blk_beta.p);
         NAS_CUDA(cudaMemcpyAsync(Hs.data(), c->d_blk_beta.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
         sync(c);
         for (int i = 0; i < N; ++i) Id[i * N + i] = 1.0;

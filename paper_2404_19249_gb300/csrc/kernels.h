@@ -178,6 +178,14 @@ void launch_gram_sym(int64_t n, int N, const double* X, const double* Y, double*
                      cudaStream_t s);
 void launch_gram(int64_t n, int Nx, const double* X, int Ny, const double* Y, double* partial,
                  double* G, cudaStream_t s);
+// launch_gram_sym on the tensor cores (error-free integer slices per 64-row
+// chunk, FP64 sums across chunks; kernels_tc.cu); 1 <= N <= 64; partial holds
+// (number of SMs) x N^2 doubles
+bool gram_tc_supported(int N);
+void launch_gram_sym_tc(int64_t n, int N, const double* X, const double* Y, double* partial, double* G,
+                        cudaStream_t s);
+// multiprocessors of the current device (queried once)
+int tc_sm_count();
 
 // Balanced pieces of a segmented list (see PieceMap on the host): pieces of
 // segment a are [seg_piece[a], seg_piece[a+1]); piece q covers list entries

@@ -530,14 +530,7 @@ void launch_reconstruct_tc(int64_t n, const int32_t* icol, const double* ival, i
                            int64_t nH, int Na, const double* Uhat, double* Psi, cudaStream_t s) {
     if (n <= 0) return;
     if (!reconstruct_tc_supported(N, Na)) fail(NAS_E_INVALID_ARG, "tensor-core reconstruction: N or Na out of range");
-    static const int sms = [] {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess)
-            v = 0;
-        cudaGetLastError();
-        return v > 0 ? v : 1;
-    }();
+    const int sms = tc_sm_count();
     const int Npad = (N + 15) / 16 * 16;
     const int need = kOzS * Npad;
     const uint32_t ncols = need <= 32 ? 32u : need <= 64 ? 64u : need <= 128 ? 128u : need <= 256 ? 256u : 512u;
@@ -546,6 +539,212 @@ void launch_reconstruct_tc(int64_t n, const int32_t* icol, const double* ival, i
     const int64_t ntiles = (n + kOzM - 1) / kOzM;
     const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
     k_tc_reconstruct<<<grid, kOzThreads, smem, s>>>(n, icol, ival, N, Npad, ncols, U, nH, Na, Uhat, Psi);
+    NAS_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrices G = X^T Y (X, Y [n][N], N <= 64) of the blocks of Sec. 3.3
+// (gamma = U^T M U^, beta = U^T A U^, known symmetric), on the tensor cores by
+// the same error-free integer slices.  The rows are taken in chunks of 64:
+// per chunk, column c of X is written in fixed point against the largest
+// exponent of that column within the chunk (E_c), column c' of Y likewise
+// (F_c'), and D_d = sum_{s+t=d} A_s B_t over the chunk's 64 rows is exact in
+// FP32 (|D_d| < 7 x 64 x 2^14 < 2^23).  The epilogue turns the chunk's
+// product into one FP64 number per entry, acc 2^(E_c + F_c' - 2100) with
+// acc = sum_d D_d 2^(7 (6 - d)) (exact int64), and adds it to the entry's
+// FP64 running sum; so every chunk is rounded once and the chunks are added
+// in FP64, as a blocked FP64 sum would.  A is X^T (the N columns of the chunk
+// as rows, zero rows up to the MMA's M = 128), B is Y^T (N rows).  One
+// persistent CTA per SM (256 threads) takes chunks blockIdx.x, + gridDim.x, ...;
+// its 64 x 64 partial sums go to part[blockIdx.x], and k_tc_gram_finish adds
+// the CTA partials in a fixed order and mirrors the upper triangle, so G is
+// exactly symmetric and repeated calls are bit-identical.
+__global__ void __launch_bounds__(kOzThreads) k_tc_gram(int64_t n, int N, int Npad, uint32_t ncols, const double* X,
+                                                       const double* Y, double* part) {
+    extern __shared__ __align__(1024) unsigned char oz_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int emax[4][64], fmax[4][64];   // per row group: the columns' exponent maxima
+    __shared__ int ech[64], fch[64];           // the chunk's column exponents E_c, F_c'
+    unsigned char* base = oz_smem;
+    base += (1024 - (smem_u32(base) & 1023)) & 1023;
+    unsigned char* As = base;
+    unsigned char* Bs = base + (size_t)kOzS * kOzSliceA;
+    // staging: thread (c, g) takes column c of the chunk's rows [16 g, 16 g + 16)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, c = tid & 63, g = tid >> 6;
+    const uint32_t mb = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(mb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // rows 64..127 of the A slices stay zero
+    {
+        uint4* p = reinterpret_cast<uint4*>(As);
+        const int words = (int)(kOzS * kOzSliceA / 16);
+        for (int w = tid; w < words; w += kOzThreads) p[w] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_f16(kOzM, Npad);
+    // epilogue: warps w with w % 4 < 2 read tensor-memory lanes m = 32 (w % 4) + lane
+    // (the columns of X), the 16-column chunks 16 h and 16 h + 32 (h = w / 4)
+    const bool ep = (warp & 3) < 2;
+    const int m = 32 * (warp & 3) + lane, h = warp >> 2;
+    double sum[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) sum[q] = 0.0;
+    const int64_t nchunks = (n + 63) / 64;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t r0 = ch * 64 + 16 * g;
+        double xv[16], yv[16];
+        int ex = 0, ey = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const bool in = c < N && r0 + q < n;
+            xv[q] = in ? X[(r0 + q) * N + c] : 0.0;
+            yv[q] = in ? Y[(r0 + q) * N + c] : 0.0;
+            ex = max(ex, biased_exp(xv[q]));
+            ey = max(ey, biased_exp(yv[q]));
+        }
+        emax[g][c] = ex;
+        fmax[g][c] = ey;
+        __syncthreads();
+        const int E = max(max(emax[0][c], emax[1][c]), max(emax[2][c], emax[3][c]));
+        const int F = max(max(fmax[0][c], fmax[1][c]), max(fmax[2][c], fmax[3][c]));
+        if (g == 0) {
+            ech[c] = E;
+            fch[c] = F;
+        }
+        stage8(xv, E, As, kOzSliceA, c, 16 * g);
+        stage8(xv + 8, E, As, kOzSliceA, c, 16 * g + 8);
+        stage8(yv, F, Bs, kOzSliceB, c, 16 * g);
+        stage8(yv + 8, F, Bs, kOzSliceB, c, 16 * g + 8);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            for (int d = 0; d < kOzS; ++d)
+                for (int sa = 0; sa <= d; ++sa)
+                    for (int ks = 0; ks < kOzK / 16; ++ks) {
+                        const uint32_t off = (uint32_t)ks * 256;
+                        mma_f16(tmem + (uint32_t)(d * Npad), smem_desc(a0 + sa * kOzSliceA + off, 128, 1024),
+                                smem_desc(b0 + (d - sa) * kOzSliceB + off, 128, 1024), idesc,
+                                (sa | ks) ? 1u : 0u);
+                    }
+            mma_commit(mb);
+        }
+        ok = mbar_wait(mb, phase);
+        phase ^= 1u;
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ep) {
+            const int Em = ech[m];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int c0 = 16 * h + 32 * half;
+                if (c0 >= Npad) break;
+                long long acc[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] = 0;
+                for (int d = 0; d < kOzS; ++d) {
+                    uint32_t v[16];
+                    const uint32_t addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(d * Npad + c0);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                        "%14,%15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(addr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const long long w = 1LL << (7 * (kOzS - 1 - d));
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc[q] += (long long)__float2int_rn(__uint_as_float(v[q])) * w;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int Fj = fch[c0 + q];
+                    if (Em && Fj) sum[16 * half + q] = fma((double)acc[q], pow2(Em + Fj - 2100), sum[16 * half + q]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    if (!ok) {
+        atomicExch(&g_tc_error, 1);
+        mbar_wait(mb, phase ^ 1u);
+    }
+    if (ep && m < N)
+#pragma unroll
+        for (int half = 0; half < 2; ++half)
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int j = 16 * h + 32 * half + q;
+                if (j < N) part[((int64_t)blockIdx.x * N + m) * N + j] = sum[16 * half + q];
+            }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// G[a][b] = G[b][a] = sum over CTAs (in order) of part[cta][a][b], a <= b
+__global__ void k_tc_gram_finish(int nb, int N, const double* part, double* G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * N) return;
+    const int a = t / N, b = t % N;
+    if (a > b) return;
+    double s = 0.0;
+    for (int k = 0; k < nb; ++k) s += part[((int64_t)k * N + a) * N + b];
+    G[a * N + b] = s;
+    G[b * N + a] = s;
+}
+
+bool gram_tc_supported(int N) { return N >= 1 && N <= 64; }
+
+int tc_sm_count() {
+    static const int sms = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            v = 0;
+        cudaGetLastError();
+        return v > 0 ? v : 1;
+    }();
+    return sms;
+}
+
+void launch_gram_sym_tc(int64_t n, int N, const double* X, const double* Y, double* partial, double* G,
+                        cudaStream_t s) {
+    if (!gram_tc_supported(N)) fail(NAS_E_INVALID_ARG, "tensor-core Gram: N out of range");
+    const int Npad = (N + 15) / 16 * 16;
+    const int need = kOzS * Npad;
+    const uint32_t ncols = need <= 32 ? 32u : need <= 64 ? 64u : need <= 128 ? 128u : need <= 256 ? 256u : 512u;
+    const size_t smem = 1024 + (size_t)kOzS * (kOzSliceA + kOzSliceB);
+    const int64_t nchunks = (n + 63) / 64;
+    if (nchunks == 0) {
+        NAS_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * N * N, s));
+        return;
+    }
+    const int grid = (int)(nchunks < tc_sm_count() ? nchunks : tc_sm_count());
+    NAS_CUDA(cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_gram<<<grid, kOzThreads, smem, s>>>(n, N, Npad, ncols, X, Y, partial);
+    NAS_CHECK_LAUNCH();
+    k_tc_gram_finish<<<grid_for((int64_t)N * N, 256), 256, 0, s>>>(grid, N, partial, G);
     NAS_CHECK_LAUNCH();
 }
 

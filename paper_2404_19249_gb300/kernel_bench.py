@@ -4,6 +4,7 @@ timing and for profiler captures of one kernel at a time.
   python -m paper_2404_19249_gb300.kernel_bench spmm --grid 128 --N 64 --fp32 --layout rows<4,2>
   python -m paper_2404_19249_gb300.kernel_bench precond --nH 3375 --k 80 --tc 1
   python -m paper_2404_19249_gb300.kernel_bench recon --rows 7880599 --N 64 --tc 1
+  python -m paper_2404_19249_gb300.kernel_bench gram --rows 7880599 --N 64 --tc 1
 
 spmm: Y = A X for the 27-point stencil matrix of a grid^3 lattice (the
 coupling pattern of trilinear elements, rows in lattice order; values
@@ -12,7 +13,9 @@ with T a dense SPD FP32 [nH][nH] and R FP64 [nH][k], on the SIMT (tc 0) or
 tensor-core (tc 1) kernel of the small eigensolver's preconditioner.  recon:
 Psi = I u_H + U^ alpha for `rows` fine rows (random coarse columns among nH
 = 3375, U^ [rows][N], alpha [N][N]) on the FP64 SIMT (tc 0) or tensor-core
-(tc 1) kernel of Algorithm 3's reconstruction.  Prints
+(tc 1) kernel of Algorithm 3's reconstruction.  gram: the symmetric Gram
+X^T Y of two random [rows][N] blocks on the FP64 SIMT (tc 0) or tensor-core
+(tc 1) kernel.  Prints
 one JSON line with the mean time per launch (CUDA events, after warm-up) and
 the algorithmic bytes or flops per launch.
 """
@@ -62,7 +65,7 @@ def time_launches(torch, fn, reps, warm=2):
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("kernel", choices=["spmm", "precond", "recon"])
+    p.add_argument("kernel", choices=["spmm", "precond", "recon", "gram"])
     p.add_argument("--rows", type=int, default=7880599)
     p.add_argument("--grid", type=int, default=128)
     p.add_argument("--N", type=int, default=64)
@@ -95,6 +98,19 @@ def main(argv=None):
         out = {"kernel": "spmm", "layout": a.layout, "precision": "f32" if a.fp32 else "f64", "rows": n,
                "nnz": nnz, "N": a.N, "ms_per_launch": ms, "algorithmic_bytes": nbytes,
                "gbs": nbytes / (ms * 1e-3) / 1e9, "tflops": 2.0 * nnz * a.N / (ms * 1e-3) / 1e12}
+    elif a.kernel == "gram":
+        n, N = a.rows, a.N
+        g = torch.Generator(device=dev)
+        g.manual_seed(5)
+        X = torch.randn((n, N), dtype=torch.float64, device=dev, generator=g)
+        Y = torch.randn((n, N), dtype=torch.float64, device=dev, generator=g)
+        G = torch.empty((N, N), dtype=torch.float64, device=dev)
+        ms = time_launches(torch, lambda: nas.nas_gram_sym_f64(a.tc, n, N, X.data_ptr(), Y.data_ptr(), G.data_ptr(),
+                                                               st), a.reps)
+        flops = 1.0 * n * N * (N + 1)
+        out = {"kernel": "gram", "tensor_cores": bool(a.tc), "rows": n, "N": N, "ms_per_call": ms,
+               "fp64_equivalent_flops": flops, "tflops_fp64_equivalent": flops / (ms * 1e-3) / 1e12,
+               "algorithmic_bytes": 16.0 * n * N, "gbs": 16.0 * n * N / (ms * 1e-3) / 1e9}
     elif a.kernel == "recon":
         n, N, nH = a.rows, a.N, a.nH
         g = torch.Generator(device=dev)

@@ -43,7 +43,7 @@ class nas_options(C.Structure):
         ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
         ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int), ("poisson_fused", C.c_int),
         ("smearing", C.c_double), ("inner_adapt", C.c_double), ("bvp_two_level", C.c_int), ("bvp_adapt", C.c_double),
-        ("anderson_restart", C.c_double), ("poisson_f32", C.c_int), ("recon_tc", C.c_int),
+        ("anderson_restart", C.c_double), ("poisson_f32", C.c_int), ("dense_tc", C.c_int),
     ]
 
 
@@ -97,6 +97,7 @@ def _load():
         "nas_spmm_f64": (C.c_int, [I64, VP, VP, VP, C.c_int, VP, VP, VP]),
         "nas_dense_precond_f32": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP]),
         "nas_reconstruct_f64": (C.c_int, [C.c_int, I64, VP, VP, C.c_int, VP, I64, C.c_int, VP, VP, VP]),
+        "nas_gram_sym_f64": (C.c_int, [C.c_int, I64, C.c_int, VP, VP, VP, VP]),
         "nas_spmm_layouts": (C.c_int, []),
         "nas_spmm_layout_name": (C.c_char_p, [C.c_int]),
         "nas_spmm_tuning": (C.c_int, [C.c_char_p, C.c_size_t]),
@@ -118,7 +119,7 @@ EXPORTS = [
     "nas_set_system", "nas_set_options", "nas_init", "nas_step", "nas_solve", "nas_get", "nas_set_state",
     "nas_apply", "nas_batch_run", "nas_spmm_f64", "nas_coldot_f64", "nas_coldot_f64_noalloc",
     "nas_spmm_layouts", "nas_spmm_layout_name", "nas_spmm_tuning", "nas_spmm_f64_layout", "nas_spmm_f32_layout",
-    "nas_dense_precond_f32", "nas_reconstruct_f64",
+    "nas_dense_precond_f32", "nas_reconstruct_f64", "nas_gram_sym_f64",
 ]
 
 
@@ -263,6 +264,14 @@ def nas_reconstruct_f64(tc, n, icol, ival, N, U, nH, Na, Uhat, Psi, stream=0):
                                 C.c_void_p(Uhat), C.c_void_p(Psi), C.c_void_p(stream or None))
     if r != NAS_OK:
         raise NasError(r, "nas_reconstruct_f64")
+    return r
+
+
+def nas_gram_sym_f64(tc, n, N, X, Y, G, stream=0):
+    """G = X^T Y (known symmetric; exactly symmetric result) for device pointers; tc=1 on the tensor cores."""
+    r = lib.nas_gram_sym_f64(int(tc), n, N, C.c_void_p(X), C.c_void_p(Y), C.c_void_p(G), C.c_void_p(stream or None))
+    if r != NAS_OK:
+        raise NasError(r, "nas_gram_sym_f64")
     return r
 
 

@@ -169,6 +169,15 @@ typedef struct nas_options {
                               error-free integer slices (FP64-level accuracy;
                               see nas_reconstruct_f64) when N <= 64; 0: FP64
                               SIMT kernels                                     */
+    int    density_pairs;  /* 1: rho = sum f psi^2 at the quadrature points from the
+                              density matrix on the fine sparsity pattern's
+                              pairs (each pair once, then each element's pairs;
+                              needs N <= 128, about nnz + 55 n_el extra words of
+                              device memory); 0: element by element.  Measured
+                              on the 32-nucleus workload: 53.4 ms against 51.1
+                              ms - 2.3x fewer FP64 operations, but each pattern
+                              pair gathers a whole orbital row (59 GB through
+                              L2 against 31 GB), so 0 is the default          */
 } nas_options;
 
 /* Fill *opt with the defaults: mu = -1 (paper's 8 M sum Z^2), tol_bvp = 1e-12,
@@ -179,7 +188,8 @@ typedef struct nas_options {
  * poisson_two_level = 1, precision = 0, eig_device = 1, eig_precond = 1,
  * eig_adapt = 1e-3, poisson_sell = 1, poisson_adaptive = 0, poisson_fused = 0,
  * smearing = 0, inner_adapt = 0, bvp_two_level = 0, bvp_adapt = 0,
- * anderson_restart = 0, poisson_f32 = 0, dense_tc = 1. */
+ * anderson_restart = 0, poisson_f32 = 0, dense_tc = 1,
+ * density_pairs = 0. */
 void nas_default_options(nas_options* opt);
 
 /* ------------------------------------------------------------------ report */

@@ -94,6 +94,7 @@ void nas_default_options(nas_options* o) {
     o->anderson_restart = 0.0;
     o->poisson_f32 = 0;
     o->dense_tc = 1;
+    o->density_pairs = 0;
 }
 
 const char* nas_version(void) { return "nas 0.1 (sm_103a, FP64)"; }
@@ -211,7 +212,8 @@ int nas_set_options(nas_ctx* c, const nas_options* o) {
             o->poisson_sell < 0 || o->poisson_sell > 1 || o->poisson_fused < 0 || o->poisson_fused > 1 ||
             !(o->smearing >= 0.0) || !(o->inner_adapt >= 0.0) || o->bvp_two_level < 0 || o->bvp_two_level > 1 ||
             !(o->bvp_adapt >= 0.0) || !(o->anderson_restart >= 0.0) ||
-            o->poisson_f32 < 0 || o->poisson_f32 > 1 || o->dense_tc < 0 || o->dense_tc > 1)
+            o->poisson_f32 < 0 || o->poisson_f32 > 1 || o->dense_tc < 0 || o->dense_tc > 1 ||
+            o->density_pairs < 0 || o->density_pairs > 1)
             nas::fail(NAS_E_INVALID_ARG, "options out of range");
         bool rebuild = (o->mu != c->opt.mu) || (o->omega != c->opt.omega) ||
                        (o->poisson_two_level != c->opt.poisson_two_level) || (o->eig_precond != c->opt.eig_precond);

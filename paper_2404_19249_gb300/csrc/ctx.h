@@ -135,6 +135,12 @@ struct nas_ctx {
     double bvp_tol_now = 0.0;           // tolerance of the last step's linear solves
     bool have_VH = false;
     bool anl_valid = false;             // d_ANL/d_eps/d_vxc match d_rho_in and d_VH
+    // density from pattern pairs: element pair -> CSR slot map (built once per
+    // mesh), the pattern's pair density, an error flag
+    nas::DBuf<int32_t> d_pair_slot;
+    nas::DBuf<double> d_pairD;
+    nas::DBuf<int> d_pair_err;
+    bool pair_ready = false;
     int step_count = 0;
     int last_cg = 0, last_poisson = 0, last_inner = 0, last_inner_conv = 0;
     double last_drho = 0.0, last_inner_res = 0.0;

@@ -753,6 +753,29 @@ static void gram_sym(nas_ctx* c, int64_t n, int N, const double* X, const double
         launch_gram_sym(n, N, X, Y, c->d_partial.p, G, c->stream);
 }
 
+// rho = sum_i f_i psi_i^2 at the quadrature points (Algorithm 3's density
+// update): from the pattern's pair density with density_pairs when N <= 128
+// (the element pair -> CSR slot map is built on the first call per mesh),
+// else element by element
+static void density(nas_ctx* c, const double* Psi, int N, double* rho, cudaStream_t s) {
+    const Mesh m = fmesh(c);
+    if (c->opt.density_pairs && N >= 1 && N <= 128) {
+        if (!c->pair_ready) {
+            c->d_pair_slot.ensure(density_pair_count(m));
+            c->d_pairD.ensure(c->F.nnz());
+            c->d_pair_err.ensure(1);
+            if (!launch_pair_slots(m, c->d_dof_of_node.p, c->d_rowptr.p, c->d_col.p, c->d_pair_slot.p,
+                                   c->d_pair_err.p, s))
+                fail(NAS_E_MESH, "pair density: an element pair is missing from the sparsity pattern");
+            c->pair_ready = true;
+        }
+        launch_density_pairs(m, c->F.n, c->d_rowptr.p, c->d_col.p, Psi, N, c->d_occ.p, c->d_pair_slot.p,
+                             c->d_pairD.p, rho, s);
+    } else {
+        launch_density(m, c->d_dof_of_node.p, Psi, N, c->d_occ.p, rho, s);
+    }
+}
+
 static int hartree(nas_ctx* c, const double* rho, double* VH, bool* conv) {
     Phase t(c, NAS_PH_POISSON);
     cudaStream_t s = c->stream;
@@ -1237,7 +1260,7 @@ static void inner_scf(nas_ctx* c, bool reuse_first) {
             }
             {
                 Phase pd(c, NAS_PH_DENSK);
-                launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, c->N, c->d_occ.p, c->d_rho_out.p, s);
+                density(c, c->d_Psi.p, c->N, c->d_rho_out.p, s);
             }
         }
         res = weighted_norm_diff(c, c->d_rho_out.p, c->d_rho_in.p);
@@ -1409,6 +1432,7 @@ void ctx_setup(nas_ctx* c) {
     c->setup_done = false;
     c->initialized = false;
     c->bvp_coarse_ready = c->bvp_coarse_failed = false;
+    c->pair_ready = false;
     if (c->pcg1_exec) {
         cudaGraphExecDestroy(c->pcg1_exec);
         c->pcg1_exec = nullptr;
@@ -1661,7 +1685,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
         std::vector<double> zero_col(4 * n, 0.0);
         // reconstruct with the coarse part ignored (weights multiply zero rows)
         reconstruct(c, n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
-        launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, N, c->d_occ.p, c->d_rho_in.p, s);
+        density(c, c->d_Psi.p, N, c->d_rho_in.p, s);
         bool pc = true;
         if (c->opt.hartree) hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
         assemble_nl(c);
@@ -1682,7 +1706,7 @@ void ctx_init(nas_ctx* c, const double* psi0) {
         for (int i = 0; i < N * N; ++i) Ufull[c->nH * N + i] = Y[i];
         NAS_CUDA(cudaMemcpyAsync(c->d_U.p, Ufull.data(), sizeof(double) * Ufull.size(), cudaMemcpyHostToDevice, s));
         reconstruct(c, n, c->d_Icol.p, c->d_Ival.p, N, c->d_U.p, c->nH, N, c->d_Uhat.p, c->d_Psi.p, s);
-        launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, N, c->d_occ.p, c->d_rho_out.p, s);
+        density(c, c->d_Psi.p, N, c->d_rho_out.p, s);
         c->last_inner = 0;
         (void)zero_col;
     }
@@ -1825,7 +1849,7 @@ void ctx_set_state(nas_ctx* c, const double* lam, const double* psi, const doubl
     update_occupations(c);
     copy_in(c, c->d_Psi.p, psi, c->F.n * c->N, on_device);
     copy_in(c, c->d_rho_in.p, rho, c->nqt, on_device);
-    launch_density(fmesh(c), c->d_dof_of_node.p, c->d_Psi.p, c->N, c->d_occ.p, c->d_rho_out.p, s);
+    density(c, c->d_Psi.p, c->N, c->d_rho_out.p, s);
     if (c->opt.hartree) {
         bool pc;
         hartree(c, c->d_rho_in.p, c->d_VH.p, &pc);
@@ -1962,7 +1986,7 @@ void ctx_apply(nas_ctx* c, int op, const void* in, int64_t cnt, void* out, int o
         case NAS_OP_DENSITY: {
             fin(a, n * N);
             b.alloc(c->nqt);
-            launch_density(fmesh(c), c->d_dof_of_node.p, a.p, (int)N, c->d_occ.p, b.p, s);
+            density(c, a.p, (int)N, b.p, s);
             fout(b.p, c->nqt);
             break;
         }

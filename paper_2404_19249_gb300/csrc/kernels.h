@@ -67,6 +67,15 @@ void launch_nl_coef(const Mesh& m, const double* VH_nodal, const double* rho, in
 // rho[e][q] = sum_c occ[c] psi_c(x_q)^2, psi from dof values Psi[n][N]
 void launch_density(const Mesh& m, const int32_t* dof_of_node, const double* Psi, int N,
                     const double* occ, double* rho, cudaStream_t s);
+// the same density from pattern pairs: D on the fine pattern's upper entries
+// (b >= a) once, then each element's quadrature points from its pairs' slots.
+// slot [ne][10 | 55] is built once per mesh by launch_pair_slots (false if an
+// interior pair is missing from the pattern); D holds nnz doubles; N <= 128
+int64_t density_pair_count(const Mesh& m);
+bool launch_pair_slots(const Mesh& m, const int32_t* dof_of_node, const int32_t* rowptr, const int32_t* col,
+                       int32_t* slot, int* err, cudaStream_t s);
+void launch_density_pairs(const Mesh& m, int64_t n, const int32_t* rowptr, const int32_t* col, const double* Psi,
+                          int N, const double* occ, const int32_t* slot, double* D, double* rho, cudaStream_t s);
 // element load vectors Lv[e][a] = sum_q Wq f_q phi_a
 void launch_local_load(const Mesh& m, const double* Wq, const double* f, double* Lv, cudaStream_t s);
 // out[s] = scale * sum_{k in [ptr[s],ptr[s+1])} src[idx[k]]

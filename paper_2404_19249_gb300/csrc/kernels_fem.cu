@@ -373,6 +373,116 @@ __global__ void __launch_bounds__(128) k_density(Mesh m, const int32_t* dof_of_n
     }
 }
 
+// ---------------------------------------------------------------- density from pattern pairs
+// The same rho(q) as k_density, with the element density matrices assembled
+// from one density matrix on the sparsity pattern of the fine space:
+// D_p = sum_c f_c Psi_a,c Psi_b,c for every pattern entry p = (a, b), b >= a
+// (both interior; Psi vanishes on the boundary), computed once although the
+// pair (a, b) belongs to every element around it - about 115M pairs on the
+// 32-nucleus mesh against 6M x 55 element pairs.  Then rho(q) of an element
+// is sum_p (2 - delta_ab) phi_a(q) phi_b(q) D_slot(e, p), in k_density's order.
+
+// slot[e][p]: the CSR position of the element's local pair p = (a <= b) as
+// (min(d_a, d_b), max(d_a, d_b)), or -1 when a node is on the boundary; an
+// interior pair missing from the pattern (never expected) sets *err
+template <int ORDER>
+__global__ void k_pair_slots(Mesh m, const int32_t* dof_of_node, const int32_t* rowptr, const int32_t* col,
+                             int32_t* slot, int* err) {
+    constexpr int NL = El<ORDER>::NLOC, NP = El<ORDER>::NP;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.ne) return;
+    int d[NL];
+    for (int a = 0; a < NL; ++a) d[a] = dof_of_node[m.elem[e * NL + a]];
+    int p = 0;
+    for (int a = 0; a < NL; ++a)
+        for (int b = a; b < NL; ++b, ++p) {
+            int s = -1;
+            if (d[a] >= 0 && d[b] >= 0) {
+                const int lo = min(d[a], d[b]), hi = max(d[a], d[b]);
+                int L = rowptr[lo], R = rowptr[lo + 1] - 1;
+                while (L <= R) {
+                    const int M = (L + R) >> 1, cm = col[M];
+                    if (cm == hi) {
+                        s = M;
+                        break;
+                    }
+                    if (cm < hi)
+                        L = M + 1;
+                    else
+                        R = M - 1;
+                }
+                if (s < 0) atomicExch(err, 1);
+            }
+            slot[e * NP + p] = s;
+        }
+}
+
+// D[p] for the entries p = (a, b >= a) of row a: a warp per row, four groups of
+// 8 lanes take the row's upper entries in turn; lane k of a group sums the
+// orbitals c = k, k + 8, ... (fixed order), then the group adds its 8 lane sums
+// by three xor shuffles (fixed order)
+__global__ void __launch_bounds__(256) k_pattern_density(int64_t n, const int32_t* rowptr, const int32_t* col,
+                                                     const double* Psi, int N, const double* occ, double* D) {
+    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, g = lane >> 3, k = lane & 7;
+    if (a >= n) return;
+    double u[16];   // f_c Psi_a,c for c = k + 8 j (N <= 128)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int c = k + 8 * j;
+        u[j] = c < N ? occ[c] * Psi[a * N + c] : 0.0;
+    }
+    const int p0 = rowptr[a], p1 = rowptr[a + 1];
+    // first upper entry (columns are sorted)
+    int lo = p0, hi = p1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (col[mid] < a)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    for (int pb = lo; pb < p1; pb += 4) {
+        const int p = pb + g;
+        double s = 0.0;
+        if (p < p1) {
+            const double* pb_row = Psi + (int64_t)col[p] * N;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = k + 8 * j;
+                if (c < N) s = fma(u[j], pb_row[c], s);
+            }
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        if (k == 0 && p < p1) D[p] = s;
+    }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(128) k_density_pairs(Mesh m, const int32_t* slot, const double* D, double* rho) {
+    constexpr int NL = El<ORDER>::NLOC, NQ = El<ORDER>::NQ, NP = El<ORDER>::NP;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.ne) return;
+    double Dl[NP];
+#pragma unroll
+    for (int a = 0, p = 0; a < NL; ++a)
+#pragma unroll
+        for (int b = a; b < NL; ++b, ++p) {
+            const int s = slot[e * NP + p];
+            const double v = s >= 0 ? D[s] : 0.0;
+            Dl[p] = b != a ? 2.0 * v : v;   // off-diagonal pairs appear twice in the square
+        }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double r = 0.0;
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) r += T_pp<ORDER>(q, pp) * Dl[pp];
+        rho[e * NQ + q] = r;
+    }
+}
+
 template <int ORDER>
 __global__ void k_local_load(Mesh m, const double* Wq, const double* f, double* Lv) {
     constexpr int NL = El<ORDER>::NLOC, NQ = El<ORDER>::NQ;
@@ -624,6 +734,25 @@ void launch_lda(int64_t cnt, const double* rho, double* eps, double* vxc, cudaSt
 void launch_density(const Mesh& m, const int32_t* dof_of_node, const double* Psi, int N,
                     const double* occ, double* rho, cudaStream_t s) {
     NAS_DISPATCH(m, k_density, m, dof_of_node, Psi, N, occ, rho);
+}
+int64_t density_pair_count(const Mesh& m) { return m.ne * (m.nloc == 4 ? 10 : 55); }
+bool launch_pair_slots(const Mesh& m, const int32_t* dof_of_node, const int32_t* rowptr, const int32_t* col,
+                       int32_t* slot, int* err, cudaStream_t s) {
+    NAS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    NAS_DISPATCH(m, k_pair_slots, m, dof_of_node, rowptr, col, slot, err);
+    int h = 0;
+    NAS_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NAS_CUDA(cudaStreamSynchronize(s));
+    return h == 0;
+}
+void launch_density_pairs(const Mesh& m, int64_t n, const int32_t* rowptr, const int32_t* col, const double* Psi,
+                          int N, const double* occ, const int32_t* slot, double* D, double* rho, cudaStream_t s) {
+    if (N < 1 || N > 128) fail(NAS_E_INVALID_ARG, "pair density: N out of range");
+    if (n > 0) {
+        k_pattern_density<<<grid_for(n * 32, 256), 256, 0, s>>>(n, rowptr, col, Psi, N, occ, D);
+        NAS_CHECK_LAUNCH();
+    }
+    NAS_DISPATCH(m, k_density_pairs, m, slot, D, rho);
 }
 void launch_local_load(const Mesh& m, const double* Wq, const double* f, double* Lv, cudaStream_t s) {
     NAS_DISPATCH(m, k_local_load, m, Wq, f, Lv);

@@ -43,7 +43,7 @@ class nas_options(C.Structure):
         ("precision", C.c_int), ("eig_device", C.c_int), ("eig_precond", C.c_int), ("eig_adapt", C.c_double),
         ("poisson_sell", C.c_int), ("poisson_adaptive", C.c_int), ("poisson_fused", C.c_int),
         ("smearing", C.c_double), ("inner_adapt", C.c_double), ("bvp_two_level", C.c_int), ("bvp_adapt", C.c_double),
-        ("anderson_restart", C.c_double), ("poisson_f32", C.c_int), ("dense_tc", C.c_int),
+        ("anderson_restart", C.c_double), ("poisson_f32", C.c_int), ("dense_tc", C.c_int), ("density_pairs", C.c_int),
     ]
 
 

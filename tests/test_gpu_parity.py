@@ -116,11 +116,20 @@ def test_assembly_with_coefficient(pair, nasmod):
     assert abs(A - B).max() <= TOL_MAT * abs(B).max()
 
 
-def test_density_kernel(pair, nasmod):
+@pytest.mark.parametrize("pairs", [1, 0])
+def test_density_kernel(pair, nasmod, pairs):
+    """Both density kernels: element by element (the default) and from the
+    sparsity pattern's pair density (density_pairs = 1)."""
     _, inst, P, s = pair
     rng = np.random.default_rng(4)
     Psi = rng.normal(size=(P.fine.n, P.N))
-    rho = s.apply(nasmod.NAS_OP_DENSITY, Psi, P.fine.Wq.shape)
+    s.opt.density_pairs = pairs
+    nasmod.nas_set_options(s.h, s.opt)
+    try:
+        rho = s.apply(nasmod.NAS_OP_DENSITY, Psi, P.fine.Wq.shape)
+    finally:
+        s.opt.density_pairs = 0
+        nasmod.nas_set_options(s.h, s.opt)
     ref = P.density(Psi)
     assert _relmax(rho, ref) < TOL_MAT
 

@@ -218,6 +218,27 @@ def test_lockstep_steps(pair, nasmod):
         assert abs(rep.drho - st.info["drho"]) < 1e-8 * max(st.info["drho"], 1e-8)
 
 
+def test_lockstep_fp64_simt_contractions(nasmod):
+    """The lockstep comparison with the FP64 SIMT reconstruction and Gram
+    kernels (dense_tc = 0; every other solver test runs the tensor-core
+    ones) on the P2 benzene case: initial SCF and two steps at 1e-10."""
+    inst = _tight(make_instance("paper_molecule", molecule="c6h6", cells=8, coarse_cells=4))
+    P = Problem(inst)
+    st = P.initial_state()
+    s = nasmod.Solver(inst, dense_tc=0)
+    s.init()
+    try:
+        assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG
+        for step in range(2):
+            r, rep = s.step()
+            assert r == 0
+            st = P.step(st)
+            assert _relmax(s.get(nasmod.NAS_Q_EIGVALS), st.lam) < TOL_EIG
+            assert abs(rep.energy - P.energy(st)) < TOL_EIG * abs(P.energy(st))
+    finally:
+        s.close()
+
+
 INEXACT = {
     "exact": {},
     "poisson_adaptive": dict(poisson_adaptive=1),

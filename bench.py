@@ -886,7 +886,9 @@ def main():
         "per_step": {"n_inner": [r.n_inner for r in reps], "cg_iters": [r.cg_iters for r in reps],
                      "poisson_iters": [r.poisson_iters for r in reps], "eig_iters": [r.eig_iters for r in reps],
                      "drho": [r.drho for r in reps], "energy": [r.energy for r in reps],
-                     "inner_tol": [r.inner_tol for r in reps], "bvp_tol": [r.bvp_tol for r in reps]},
+                     "inner_tol": [r.inner_tol for r in reps], "bvp_tol": [r.bvp_tol for r in reps],
+                     "eig_rr_calls": [r.eig_rr_calls for r in reps],
+                     "eig_rr_fallbacks": [r.eig_rr_fallbacks for r in reps]},
         "gpu_launches": int(sum(r.kernel_launches for r in reps)), "e2e": e2e, "clocks": clk,
         "spmm_autotuner": tuner,
         "cpu_baseline": cpu, "setup_s": setup_s, "energy_ha": float(last.energy),

@@ -262,6 +262,10 @@ typedef struct nas_report {
                                  block PCG): nnz*(4+4) + 4*(n+1) + 2*n*N*4            */
     double spmm32_flops;      /* 2*nnz*N per FP32 SpMM launch                        */
     double bvp_tol;           /* tolerance of the last step's N linear solves        */
+    int eig_rr_calls;         /* Rayleigh-Ritz steps of the device LOBPCG in the step */
+    int eig_rr_fallbacks;     /* of those, the ones whose basis Gram matrix was too
+                                 ill-conditioned for its Cholesky factor (two-pass
+                                 eigen-decomposition path)                          */
 } nas_report;
 
 /* ------------------------------------------------------------------ context */

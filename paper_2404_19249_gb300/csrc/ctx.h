@@ -165,6 +165,7 @@ struct nas_ctx {
     double eig_tol_hint = 1.0;          // last inner-SCF residual (LOBPCG tolerance)
     double poisson_tol_now = 0.0;       // > 0: tolerance of the next Poisson solve
     int last_lobpcg_iters = 0;
+    int last_rr_calls = 0, last_rr_fallbacks = 0;   // device LOBPCG Rayleigh-Ritz steps of the step
 
     // ---- timing
     double phase_ms[NAS_MAX_PHASES] = {0};

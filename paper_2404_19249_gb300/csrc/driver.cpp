@@ -1084,6 +1084,7 @@ static void device_eig(nas_ctx* c, int m) {
     const bool warm = c->uwarm_dev_m == m;
     c->lob.rr_ms = 0.0;
     c->lob.wait_ms = 0.0;
+    c->lob.rr_calls = c->lob.rr_fallbacks = 0;
     const int nguard = std::max(4, c->N / 4);
     // coarse-block preconditioner: the inverse coarse stiffness (K_H = I^T K I
     // is twice the kinetic part of the coarse block of F_A), in FP32
@@ -1106,6 +1107,8 @@ static void device_eig(nas_ctx* c, int m) {
         fail(NAS_E_CUDA, "tensor-core preconditioner: an mbarrier wait exceeded its limit");
     if (it < 0) fail(NAS_E_EIGEN, "small eigenproblem: LOBPCG did not converge");
     c->last_lobpcg_iters += it;
+    c->last_rr_calls += c->lob.rr_calls;
+    c->last_rr_fallbacks += c->lob.rr_fallbacks;
     c->phase_ms[NAS_PH_EIG_RR] += c->lob.rr_ms;
     c->phase_calls[NAS_PH_EIG_RR] += 1;
     c->phase_ms[NAS_PH_EIG_WAIT] += c->lob.wait_ms;
@@ -1733,6 +1736,7 @@ int ctx_step(nas_ctx* c, nas_report* rep) {
     c->pcg1_fused_ms = 0.0;
     c->pcg1_fused_iters = 0;
     c->last_lobpcg_iters = 0;
+    c->last_rr_calls = c->last_rr_fallbacks = 0;
     int status = NAS_OK;
     if (!c->anl_valid) {
         if (c->opt.hartree) {
@@ -1828,6 +1832,8 @@ void ctx_fill_report(nas_ctx* c, nas_report* rep) {
     rep->spmm32_flops = c->spmm32_flops;
     rep->inner_tol = c->inner_tol_now;
     rep->bvp_tol = c->bvp_tol_now;
+    rep->eig_rr_calls = c->last_rr_calls;
+    rep->eig_rr_fallbacks = c->last_rr_fallbacks;
 }
 
 // ------------------------------------------------------------------ state in/out

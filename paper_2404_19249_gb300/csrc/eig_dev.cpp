@@ -96,7 +96,10 @@ int DevLobpcg::solve(const ArrowDev& A, const ArrowDev& B, const int32_t* diag_s
     // host Rayleigh-Ritz from the fetched Grams (fallback and large ns)
     auto rr_host = [&](int ns, std::vector<double>& th_out) {
         auto t0 = std::chrono::steady_clock::now();
-        int r = rayleigh_ritz_grams(ns, hG, hH, k, hY, th_out);
+        bool fb = false;
+        int r = rayleigh_ritz_grams(ns, hG, hH, k, hY, th_out, &fb);
+        ++rr_calls;
+        if (fb) ++rr_fallbacks;
         rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (r == 0) {
             // from the pinned area: it is rewritten only after the next synchronisation

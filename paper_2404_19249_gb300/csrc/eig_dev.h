@@ -25,6 +25,8 @@ struct DevLobpcg {
     int k_cap = 0;
     bool tc = false;      // the dense preconditioner product on the tensor cores
     double rr_ms = 0.0;   // host time in Rayleigh-Ritz (accumulated)
+    int rr_calls = 0;     // Rayleigh-Ritz steps, and those that took the two-pass path
+    int rr_fallbacks = 0;
     double wait_ms = 0.0; // host time waiting for the device in synchronisations
     // pinned staging area for the per-iteration transfers (Grams, norms,
     // Ritz coefficients, active columns), so that they are truly asynchronous

@@ -781,7 +781,8 @@ static int rayleigh_ritz(int64_t m, int ns, const double* S, const double* AS, c
 }
 
 int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, int k, std::vector<double>& Y,
-                        std::vector<double>& theta) {
+                        std::vector<double>& theta, bool* fallback) {
+    if (fallback) *fallback = false;
     for (int a = 0; a < ns; ++a)
         for (int b = 0; b < a; ++b) {
             double g = 0.5 * (G[a * ns + b] + G[b * ns + a]);
@@ -810,6 +811,10 @@ int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, 
             }
         }
     }
+    if (fallback) *fallback = true;
+    // the O(ns^3) products below split their output rows over the OpenMP
+    // threads; every entry keeps its summation order
+    const bool par = ns >= kParMin;
     std::vector<double> gw(ns), GV((size_t)ns * ns);
     sym_eig_all(ns, G.data(), gw.data(), GV.data());
     double gmax = gw[ns - 1];
@@ -827,12 +832,14 @@ int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, 
     // second pass: Q <- Q V2 D2^-1/2 with Q^T G Q = V2 D2 V2^T (restores B-orthonormality)
     {
         std::vector<double> GQ((size_t)ns * r), G2((size_t)r * r), w2(r), V2((size_t)r * r);
+#pragma omp parallel for schedule(static) if (par)
         for (int a = 0; a < ns; ++a)
             for (int j = 0; j < r; ++j) {
                 double sacc = 0.0;
                 for (int b = 0; b < ns; ++b) sacc += G[a * ns + b] * Q[b * r + j];
                 GQ[a * r + j] = sacc;
             }
+#pragma omp parallel for schedule(static) if (par)
         for (int i = 0; i < r; ++i)
             for (int j = 0; j < r; ++j) {
                 double sacc = 0.0;
@@ -843,6 +850,7 @@ int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, 
             for (int j = 0; j < i; ++j) G2[i * r + j] = G2[j * r + i] = 0.5 * (G2[i * r + j] + G2[j * r + i]);
         sym_eig_all(r, G2.data(), w2.data(), V2.data());
         std::vector<double> Q2((size_t)ns * r);
+#pragma omp parallel for schedule(static) if (par)
         for (int a = 0; a < ns; ++a)
             for (int j = 0; j < r; ++j) {
                 double sacc = 0.0;
@@ -853,12 +861,14 @@ int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, 
     }
     // Hr = Q^T H Q
     std::vector<double> HQ((size_t)ns * r), Hr((size_t)r * r);
+#pragma omp parallel for schedule(static) if (par)
     for (int a = 0; a < ns; ++a)
         for (int j = 0; j < r; ++j) {
             double s = 0.0;
             for (int b = 0; b < ns; ++b) s += H[a * ns + b] * Q[b * r + j];
             HQ[a * r + j] = s;
         }
+#pragma omp parallel for schedule(static) if (par)
     for (int i = 0; i < r; ++i)
         for (int j = 0; j < r; ++j) {
             double s = 0.0;
@@ -871,6 +881,7 @@ int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, 
     sym_eig_all(r, Hr.data(), hw.data(), HV.data());
     theta.assign(hw.begin(), hw.begin() + k);
     Y.assign((size_t)ns * k, 0.0);
+#pragma omp parallel for schedule(static) if (par)
     for (int a = 0; a < ns; ++a)
         for (int j = 0; j < k; ++j) {
             double s = 0.0;

@@ -60,12 +60,15 @@ int lobpcg_arrow(const ArrowMat& A, const ArrowMat& B, int nev, int nguard, doub
                  double tol, int maxit);
 
 // Rayleigh-Ritz step of LOBPCG from the Gram matrices of a basis S [m][ns]:
-// G = S^T B S and H = S^T A S (row-major [ns][ns]; symmetrised in place).  The
-// basis is B-orthonormalised by two passes of G's eigen-decomposition, dropping
-// directions whose Gram eigenvalue is below 1e-9 of the largest; then the
-// lowest k Ritz pairs: theta[k] and coefficients Y [ns][k] (S Y is
-// B-orthonormal).  Returns 0, or -1 if fewer than k directions remain.
+// G = S^T B S and H = S^T A S (row-major [ns][ns]; symmetrised in place).
+// When G's Cholesky factor has every squared pivot above 1e-8 of the largest
+// diagonal entry, the pencil (H, G) is solved through that factor; otherwise
+// (*fallback = true when given) the basis is B-orthonormalised by two passes
+// of G's eigen-decomposition, dropping directions whose Gram eigenvalue is
+// below 1e-9 of the largest.  Then the lowest k Ritz pairs: theta[k] and
+// coefficients Y [ns][k] (S Y is B-orthonormal).  Returns 0, or -1 if fewer
+// than k directions remain.
 int rayleigh_ritz_grams(int ns, std::vector<double>& G, std::vector<double>& H, int k, std::vector<double>& Y,
-                        std::vector<double>& theta);
+                        std::vector<double>& theta, bool* fallback = nullptr);
 
 }  // namespace nas

@@ -58,6 +58,7 @@ class nas_report(C.Structure):
         ("eig_iters", C.c_int), ("poisson_spmv_ms", C.c_double), ("poisson_spmv_launches", C.c_longlong),
         ("poisson_fused_ms", C.c_double), ("poisson_fused_iters", C.c_longlong),
         ("e_ts", C.c_double), ("inner_tol", C.c_double), ("spmm32_bytes", C.c_double), ("spmm32_flops", C.c_double), ("bvp_tol", C.c_double),
+        ("eig_rr_calls", C.c_int), ("eig_rr_fallbacks", C.c_int),
     ]
 
     def as_dict(self):

@@ -65,61 +65,53 @@ static bool cholesky(int m, std::vector<double>& L) {
 }
 
 // C = L^{-1} A L^{-T} (A symmetric, full storage built from its lower triangle)
-// by forward elimination applied to whole rows (Z <- L^-1 Z for all columns
-// at once: each update is a contiguous row operation), first to A, then to
-// the transpose of the result.
-static void reduce_standard(int m, const std::vector<double>& L, const double* A, std::vector<double>& C) {
-    // the columns of Z are independent right-hand sides: each thread
-    // eliminates its own block of kCb columns over all rows, reading the
-    // multipliers of step k from row k of L^T (contiguous)
-    const int kCb = 32;
-    std::vector<double> Lt;
-    if (m >= kParMin) {
-        Lt.assign((size_t)m * m, 0.0);
-        for (int i = 0; i < m; ++i)
-            for (int k = 0; k <= i; ++k) Lt[(size_t)k * m + i] = L[(size_t)i * m + k];
+// by two forward eliminations Z <- L^{-1} Z on all m columns at once, first
+// of A, then of the transpose of the result.  Each elimination is
+// left-looking over blocks of 8 columns: row i of the block is
+// (B_i - sum_{k<i} L_ik Z_k) / L_ii with the 8 partial sums in registers and
+// k ascending, so each L_ik is loaded once per 8 updates and each Z_k block
+// once per row; the column blocks are independent and split over the OpenMP
+// threads.
+static void solve_lower_rows(int m, const std::vector<double>& L, std::vector<double>& Z) {
+    const int kCb = 8;
+    const int nblk = (m + kCb - 1) / kCb;
+#pragma omp parallel for schedule(static) if (m >= kParMin)
+    for (int b = 0; b < nblk; ++b) {
+        const int j0 = b * kCb, w = std::min(kCb, m - j0);
+        for (int i = 0; i < m; ++i) {
+            const double* Li = &L[(size_t)i * m];
+            double acc[kCb];
+            double* zi = &Z[(size_t)i * m + j0];
+            for (int q = 0; q < kCb; ++q) acc[q] = q < w ? zi[q] : 0.0;
+            if (w == kCb) {
+                for (int k = 0; k < i; ++k) {
+                    const double l = Li[k];
+                    const double* zk = &Z[(size_t)k * m + j0];
+#pragma omp simd
+                    for (int q = 0; q < kCb; ++q) acc[q] -= l * zk[q];
+                }
+            } else {
+                for (int k = 0; k < i; ++k) {
+                    const double l = Li[k];
+                    const double* zk = &Z[(size_t)k * m + j0];
+                    for (int q = 0; q < w; ++q) acc[q] -= l * zk[q];
+                }
+            }
+            const double d = Li[i];
+            for (int q = 0; q < w; ++q) zi[q] = acc[q] / d;
+        }
     }
-    auto solve_rows = [&](std::vector<double>& Z) {
-        if (m < kParMin) {
-            for (int k = 0; k < m; ++k) {
-                double* zk = &Z[(size_t)k * m];
-                const double d = L[(size_t)k * m + k];
-                for (int j = 0; j < m; ++j) zk[j] /= d;
-                for (int i = k + 1; i < m; ++i) {
-                    const double l = L[(size_t)i * m + k];
-                    if (l == 0.0) continue;
-                    double* zi = &Z[(size_t)i * m];
-                    for (int j = 0; j < m; ++j) zi[j] -= l * zk[j];
-                }
-            }
-            return;
-        }
-        const int nblk = (m + kCb - 1) / kCb;
-#pragma omp parallel for schedule(static)
-        for (int b = 0; b < nblk; ++b) {
-            const int j0 = b * kCb, j1 = std::min(m, j0 + kCb);
-            for (int k = 0; k < m; ++k) {
-                double* zk = &Z[(size_t)k * m];
-                const double* lk = &Lt[(size_t)k * m];
-                const double dinv = 1.0 / lk[k];
-                for (int j = j0; j < j1; ++j) zk[j] *= dinv;
-                for (int i = k + 1; i < m; ++i) {
-                    const double l = lk[i];
-                    if (l == 0.0) continue;
-                    double* zi = &Z[(size_t)i * m];
-                    for (int j = j0; j < j1; ++j) zi[j] -= l * zk[j];
-                }
-            }
-        }
-    };
+}
+
+static void reduce_standard(int m, const std::vector<double>& L, const double* A, std::vector<double>& C) {
     std::vector<double> Y((size_t)m * m);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j <= i; ++j) Y[(size_t)i * m + j] = Y[(size_t)j * m + i] = A[(size_t)i * m + j];
-    solve_rows(Y);                       // Y = L^-1 A
+    solve_lower_rows(m, L, Y);           // Y = L^-1 A
     C.resize((size_t)m * m);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) C[(size_t)i * m + j] = Y[(size_t)j * m + i];
-    solve_rows(C);                       // C = L^-1 (L^-1 A)^T = L^-1 A L^-T
+    solve_lower_rows(m, L, C);           // C = L^-1 (L^-1 A)^T = L^-1 A L^-T
     // symmetrise
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < i; ++j) {

@@ -159,6 +159,15 @@ def test_kernel_rooflines_and_dominant(bench):
     assert rec["bound"] == "alu" and abs(rec["algorithmic_flops_per_launch"] - 2.0 * 1000 * 64 * 68) < 1e-6
     assert abs(rec["est_ms_per_step"] - 10.0) < 1e-12
     assert bench.dominant(roofs) is rec
+    # tensor-core reconstruction: the roofline counts only the FP64 work the
+    # kernel keeps (I u_H and the final scaled FMA, 10 n N), and reports the
+    # whole product's FP64-equivalent rate beside it
+    tc = bench.kernel_rooflines([Rep(), Rep()], sz, 2, phases, 6000.0, "measured", nz_occ=64,
+                                dense_tc=True)["k_reconstruct"]
+    assert "tensor cores" in tc["kernel"]
+    assert abs(tc["algorithmic_flops_per_launch"] - 10.0 * 1000 * 64) < 1e-6
+    assert abs(tc["fp64_equivalent_tflops"] - 2.0 * 1000 * 64 * 68 / 5e-3 / 1e12) < 1e-12   # 5 ms per launch
+    assert abs(tc["algorithmic_gbs"] - (16.0 * 1000 * 64 + 48.0 * 1000) / 5e-3 / 1e9) < 1e-9
 
 
 def test_cpu_extrapolation_terms(bench):
